@@ -1,0 +1,231 @@
+/*
+ * cphifi.h — C ABI of the GB300 solver for the unaligned infinite-dimensional
+ * (kernel-mode) CP-HIFI subproblem.
+ *
+ * The operation: Brust & Kolda, "Fast and Accurate CP-HIFI Tensor
+ * Decompositions Exploiting Kronecker Structure", §4.  For one kernel mode
+ * with kernel matrix K (n x n, symmetric PSD), the other modes' factor
+ * matrices A_m (n_m x r), and q observations (i_l, i_1^l, .., i_d^l, t_l),
+ * the library solves the rho-regularised normal equations of §4.1
+ * (Eq. unaligned-infinite-1)
+ *
+ *     [F'F + lambda (I_r (x) K) + rho I_rn] vec(W) = vec(K B)
+ *
+ * with F(l,:) = Zhat(l,:) (x) K(i_l,:) (Eqs. zhat, khat, F) and B the sparse
+ * MTTKRP (row i of B = sum over observations with i_l = i of t_l Zhat(l,:)),
+ * by preconditioned conjugate gradients with the matrix-free product of
+ * §4.4.1 (Eqs. vl, yhat1) and the Kronecker-eigen preconditioner of §4.4.2
+ * (Eqs. precon, fx).
+ *
+ * Conventions shared by every call:
+ *  - Matrices are column-major (Fortran order).  vec() stacks columns, so an
+ *    n x r matrix X is the vector x[i + n*j] = X(i,j).
+ *  - Indices are 0-based int32.
+ *  - `mem` arguments say where the pointers of that call live:
+ *    CPHIFI_MEM_HOST (pageable or pinned host memory) or CPHIFI_MEM_DEVICE
+ *    (device memory of the context's GPU).  Device pointers must be 8-byte
+ *    aligned.
+ *  - The caller owns every buffer it passes; the library copies what it needs
+ *    before the call returns.  Handles are released by the matching destroy.
+ *  - Every call is synchronous with respect to the host unless stated
+ *    otherwise: when it returns, outputs are written.
+ *  - Calls return a cphifi_status; the human-readable reason of the last
+ *    failure of a context is cphifi_last_error(ctx).  No C++ exception
+ *    crosses this boundary.  A context is not thread-safe: use one context per
+ *    host thread.
+ */
+#ifndef CPHIFI_H
+#define CPHIFI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum cphifi_status {
+  CPHIFI_OK = 0,
+  CPHIFI_E_INVALID_ARG = 1,   /* shape, index range, non-finite value, rho <= 0 */
+  CPHIFI_E_OOM = 2,           /* device allocation failed */
+  CPHIFI_E_ADMISSION = 3,     /* the footprint exceeds the context's HBM budget */
+  CPHIFI_E_NOT_CONVERGED = 4, /* max_iter reached; W and stats are still written */
+  CPHIFI_E_BREAKDOWN = 5,     /* p'Ap <= 0 or a non-finite CG scalar */
+  CPHIFI_E_DEVICE = 6,        /* a CUDA call failed */
+  CPHIFI_E_TIMEOUT = 7,       /* cphifi_wait ran out of time */
+  CPHIFI_E_UNSUPPORTED = 8    /* a valid request this build does not implement */
+} cphifi_status;
+
+enum { CPHIFI_MEM_HOST = 0, CPHIFI_MEM_DEVICE = 1 };
+
+/* Arithmetic of the PCG operator (§4.4.1 product).  CG vectors, scalars,
+ * reductions, the right-hand side and every true-residual evaluation are FP64
+ * in all modes.
+ *  FP64       : every step in FP64.
+ *  MIXED_FP32 : operator in FP32 (FP32 products, FP32 gather-dot/scatter)
+ *               with FP64 true-residual restarts every k_replace iterations.
+ *  MIXED_TF32 : as MIXED_FP32 with the two n x n products on the tensor
+ *               cores in TF32 (FP32 accumulate).
+ *  MIXED_BF16 : as MIXED_TF32 with BF16 operands.                           */
+typedef enum cphifi_precision {
+  CPHIFI_FP64 = 0,
+  CPHIFI_MIXED_FP32 = 1,
+  CPHIFI_MIXED_TF32 = 2,
+  CPHIFI_MIXED_BF16 = 3
+} cphifi_precision;
+
+/* Problem-creation flags. */
+#define CPHIFI_OBS_SORTED 0x1u  /* kidx is non-decreasing: skip the device sort */
+#define CPHIFI_NEED_FP64 0x2u   /* build the FP64 operator data (always built)  */
+#define CPHIFI_NEED_LOWP 0x4u   /* also build the FP32 operator data (mixed)    */
+
+typedef struct cphifi_params {
+  double lambda;      /* RKHS regularisation, >= 0 (§2)                       */
+  double rho;         /* extra ridge making the system definite, > 0 (§4.1)   */
+  double tol;         /* stop when ||b - A w|| / ||b|| <= tol                 */
+  int32_t max_iter;   /* bound on PCG iterations over all restarts            */
+  int32_t precision;  /* cphifi_precision                                      */
+  int32_t k_replace;  /* mixed: FP64 true residual + restart every k (>= 1)   */
+  int32_t check_every;/* FP64: iterations between host convergence polls (>=1)*/
+  int32_t profile;    /* 1: time every n x n product and gather-dot/scatter  */
+  int32_t reserved;
+} cphifi_params;
+
+typedef struct cphifi_stats {
+  int32_t status;            /* cphifi_status of the solve                    */
+  int32_t iterations;        /* PCG iterations (operator applications)        */
+  int32_t true_residuals;    /* FP64 true-residual evaluations                */
+  int32_t restarts;          /* refinement restarts (mixed)                   */
+  double rel_residual;       /* final ||b - A w||/||b|| (FP64, true residual) */
+  double rel_residual_recurrence;
+  double setup_ms;           /* problem creation (copies, sort, Zhat, eig V)  */
+  double solve_ms;           /* the PCG solve incl. RHS and the final W       */
+  /* profile = 1 only: summed CUDA-event durations on the launch stream */
+  double gds_ms;             /* gather-dot/scatter launches, operator arith.  */
+  int32_t gds_launches;
+  int32_t gemm_launches;     /* n x n products, operator arithmetic           */
+  double gemm_ms;
+  double gds64_ms;           /* FP64 launches used by true residuals (mixed)  */
+  int32_t gds64_launches;
+  int32_t gemm64_launches;
+  double gemm64_ms;
+  int64_t kernel_launches;   /* every kernel this solve launched              */
+} cphifi_stats;
+
+typedef struct cphifi_ctx cphifi_ctx;
+typedef struct cphifi_kernel cphifi_kernel;
+typedef struct cphifi_problem cphifi_problem;
+
+/* ---- context --------------------------------------------------------------
+ * cphifi_ctx_create: bind to CUDA device `device`, create the library's
+ * stream, and cap the device memory this context may hold at
+ * hbm_budget_bytes (0 = no cap).  Writes the handle to *out. */
+int cphifi_ctx_create(cphifi_ctx** out, int device, size_t hbm_budget_bytes);
+int cphifi_ctx_destroy(cphifi_ctx* ctx);
+/* Order the library's work after, and the caller's later work after the
+ * library's, on `stream` (a cudaStream_t; NULL = the legacy default stream).
+ * Each call records an event on `stream`, waits on it, and records its own
+ * completion back onto `stream`. */
+int cphifi_ctx_set_stream(cphifi_ctx* ctx, void* stream);
+/* Bytes of device memory the context holds now. */
+size_t cphifi_ctx_bytes_in_use(const cphifi_ctx* ctx);
+const char* cphifi_last_error(const cphifi_ctx* ctx);
+const char* cphifi_status_string(int status);
+
+/* ---- kernel matrix (one-time per K; §3.2 Eq. eigK, reused across the
+ * alternating optimisation) -------------------------------------------------
+ * n      : kernel-mode size.
+ * K      : n x n symmetric PSD kernel matrix, column-major; may be NULL when
+ *          UK and DK are given (the solver works in K's eigenbasis).
+ * UK, DK : K = UK diag(DK) UK' with UK orthogonal (n x n, column-major,
+ *          column j = eigenvector j) and DK the n eigenvalues.  Computing them
+ *          (e.g. LAPACK dsyevd) is the caller's one-time setup; passing NULL
+ *          returns CPHIFI_E_UNSUPPORTED.  Tiny negative eigenvalues are
+ *          clamped to 0 inside the preconditioner only.
+ * The library keeps FP64 and FP32 copies of UK on the device. */
+int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
+                         const double* UK, const double* DK, int mem,
+                         cphifi_kernel** out);
+int cphifi_kernel_destroy(cphifi_kernel* kern);
+
+/* ---- one subproblem (§4: everything that depends on the observations) ---
+ * d_other     : number of other (finite) modes, >= 1.
+ * other_sizes : n_m for m = 1..d_other (host array).
+ * factors     : host array of d_other pointers; factor m is n_m x r,
+ *               column-major, in memory kind `mem`.
+ * r           : rank, 1 <= r <= 64.
+ * q           : number of observations, 0 <= q < 2^31.
+ * kidx        : q kernel-mode indices in [0, n).
+ * oidx        : q x d_other other-mode indices, row-major (observation l's
+ *               indices are oidx[l*d_other .. l*d_other + d_other - 1]),
+ *               index m in [0, n_m).
+ * vals        : q observed values t_l.
+ * flags       : CPHIFI_OBS_SORTED and/or CPHIFI_NEED_LOWP.
+ * Builds on the device: the stable sort by kernel index, Zhat (Eq. zhat) in
+ * the sorted order, the Gram V = Hadamard of A_m'A_m (§3), eig(V)
+ * (Eq. eigV), the density gamma = q/(nM) and the preconditioner diagonal D
+ * (§4.4.2).  Invalid indices or non-finite inputs give CPHIFI_E_INVALID_ARG;
+ * a footprint over the context budget gives CPHIFI_E_ADMISSION. */
+int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
+                          int32_t d_other, const int64_t* other_sizes,
+                          const double* const* factors, int32_t r, int64_t q,
+                          const int32_t* kidx, const int32_t* oidx,
+                          const double* vals, uint32_t flags, int mem,
+                          cphifi_problem** out);
+int cphifi_problem_destroy(cphifi_problem* prob);
+/* Device bytes the problem holds. */
+size_t cphifi_problem_bytes(const cphifi_problem* prob);
+
+/* PCG solve of Eq. unaligned-infinite-1 (§4.4).  W0 (n x r, may be NULL =
+ * zero start) and W_out (n x r) are column-major in memory kind `mem`.
+ * Returns CPHIFI_OK when the FP64 true relative residual is <= tol,
+ * CPHIFI_E_NOT_CONVERGED at max_iter (W_out and stats still written), or
+ * CPHIFI_E_BREAKDOWN. `stats` may be NULL. */
+int cphifi_problem_solve(cphifi_problem* prob, const cphifi_params* params,
+                         const double* W0, double* W_out, int mem,
+                         cphifi_stats* stats);
+
+/* One-shot: problem_create + problem_solve + problem_destroy.  flags as in
+ * problem_create; params->precision selects the operator data built. */
+int cphifi_solve(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
+                 const int64_t* other_sizes, const double* const* factors,
+                 int32_t r, int64_t q, const int32_t* kidx,
+                 const int32_t* oidx, const double* vals, uint32_t flags,
+                 const cphifi_params* params, const double* W0, double* W_out,
+                 int mem, cphifi_stats* stats);
+
+/* ---- the steps of the path, one call each (for checking each step) ------
+ * All n x r arrays are column-major in memory kind `mem`. */
+
+/* B = T Z (sparse MTTKRP, §4) and b = vec(K B) (right-hand side of
+ * Eq. unaligned-infinite-1), both n x r, FP64.  Either output may be NULL. */
+int cphifi_problem_rhs(cphifi_problem* prob, double* B_out, double* b_out,
+                       int mem);
+/* Y = (F'F + lambda (I (x) K) + rho I) X (§4.4.1) in the operator arithmetic
+ * `precision` (FP64 or one of the mixed modes); X, Y n x r FP64. */
+int cphifi_problem_matvec(cphifi_problem* prob, int precision, double lambda,
+                          double rho, const double* X, double* Y, int mem);
+/* Y1 = Yhat1 of Eqs. vl and yhat1 for a given Xhat (n x r):
+ * xbar_l = Xhat(i_l,:).Zhat(l,:), Yhat1(i,:) = sum_{i_l = i} xbar_l Zhat(l,:),
+ * in FP64 or (precision != FP64) FP32 arithmetic. */
+int cphifi_problem_gds(cphifi_problem* prob, int precision, const double* Xhat,
+                       double* Y1, int mem);
+/* Y = M^{-1} X for the preconditioner of Eq. precon, applied as Eq. fx. */
+int cphifi_problem_precond(cphifi_problem* prob, double lambda, double rho,
+                           const double* X, double* Y, int mem);
+/* V = Z'Z (r x r), its eigenvalues DV (r) and eigenvectors UV (r x r,
+ * column-major) as computed on the device (Eq. eigV); any may be NULL.
+ * Host memory only. */
+int cphifi_problem_gram(cphifi_problem* prob, double* V, double* DV,
+                        double* UV);
+/* The sorted observation order: perm[s] = original index of the s-th
+ * observation after the stable sort by kernel index, and row_ptr (n+1) with
+ * observations of kernel index i at sorted positions [row_ptr[i],
+ * row_ptr[i+1]).  Host memory only; either may be NULL. */
+int cphifi_problem_order(cphifi_problem* prob, int32_t* perm,
+                         int64_t* row_ptr);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPHIFI_H */

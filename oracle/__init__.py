@@ -1,0 +1,7 @@
+"""FP64 CPU oracle for the unaligned kernel-mode CP-HIFI subproblem.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the library imports this package; only
+the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg
+may call it.  It shares no code with the CUDA path.
+"""
+from .cphifi_oracle import *  # noqa: F401,F403
