@@ -1,0 +1,333 @@
+"""Benchmark: kernel-mode PCG obs*iter/s and solves/s on one GB300.
+
+Workload (default): the mixed-precision kernel-mode solve with n = 8,000
+Gaussian-RBF points on [0, 1] (bandwidth 0.1), finite modes 400 x 500,
+q = 5e7 observations (uniform without replacement, sorted by kernel index),
+planted smooth rank-40 model + 1% noise, r = 40, lambda = 1e-4, rho = 1e-6,
+tolerance 1e-6 on the FP64 true relative residual.  Synthetic data (seeded).
+
+A step is one subproblem through every step of the path: problem creation
+from device-resident inputs (validation, Zhat, row pointer, pieces, Gram,
+eig(V), MTTKRP) followed by the PCG solve (right-hand side, iterations, FP64
+true-residual restarts, W = U_K Wbar).  eig(K) is the one-time per-kernel
+setup and stays outside the timed region.  Zhat (8 GB in FP32) is far larger
+than the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "kernel-mode PCG obs*iter/s & solves/s, mixed vs FP64 at 1e-6 rel err; p50/p99"
+UNIT = "obs*iter/s"
+WORKLOAD = "c3_mixed_n8000_q5e7_r40"
+TOL = 1e-6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", default="mixed_fp32")
+    ap.add_argument("--q", type=int, default=0, help="override q (smaller runs)")
+    ap.add_argument("--n", type=int, default=0, help="override n (smaller runs)")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_problem(args, seed):
+    import synth
+    over = {}
+    if args.q:
+        over["q"] = args.q
+    if args.n:
+        over["n"] = args.n
+    return synth.workload(args.workload, seed=seed, **over)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_setup(p, sample_q: int):
+    """Oracle operators on the first `sample_q` sorted observations (setup,
+    untimed: Zhat, Gram, eig(K) and eig(V), right-hand side)."""
+    import oracle as O
+    q = min(sample_q, p.q)
+    kidx, oidx, vals = p.kidx[:q], p.oidx[:q], p.vals[:q]
+    Zh = O.zhat(p.factors, oidx)
+    V = O.gram(p.factors)
+    g = O.density(p.n, p.other_sizes, q)
+    UK, UV, D = O.precond_setup(p.K, V, g, p.lam, p.rho)
+    b = p.K @ O.mttkrp(p.n, kidx, vals, Zh)
+    A = lambda X: O.matvec(p.K, kidx, Zh, p.lam, p.rho, X)
+    Minv = lambda R: O.precond_apply(UK, UV, D, R)
+    return A, Minv, b, q
+
+
+def cpu_oracle_time(setup, iters: int = 1):
+    """Seconds for `iters` oracle PCG iterations (operator + preconditioner)."""
+    import oracle as O
+    A, Minv, b, q = setup
+    t0 = time.perf_counter()
+    O.pcg(A, b, Minv, tol=0.0, maxit=iters)
+    return time.perf_counter() - t0, q, iters
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    p = make_problem(args, seed=0)
+    sample_q = int(os.environ.get("CPHIFI_CPU_SAMPLE_Q", "2000000"))
+    setup = cpu_oracle_setup(p, sample_q)
+    for _ in range(max(0, min(args.warmup, 1))):
+        cpu_oracle_time(setup)
+    secs, obs = 0.0, 0
+    for _ in range(args.steps):
+        s, q, it = cpu_oracle_time(setup)
+        secs += s
+        obs += q * it
+    v = obs / secs
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic planted low rank (seeded)",
+            "config": {"workload": args.workload, "n": p.n, "other_sizes": p.other_sizes,
+                       "q": p.q, "r": p.r, "lambda": p.lam, "rho": p.rho},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"one FP64 oracle PCG iteration (NumPy) per step on the "
+                                       f"first {min(sample_q, p.q)} sorted observations, full n"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2603_25691_gb300 as pkg
+
+    # ---- inputs (each rank: its own independent subproblem; replicas only)
+    p = make_problem(args, seed=rank)
+    dK, UK = np.linalg.eigh(p.K)
+    n, r, q = p.n, p.r, p.q
+    dev = torch.device("cuda", local)
+    kidx_d = torch.from_numpy(p.kidx).to(dev)
+    oidx_d = torch.from_numpy(np.ascontiguousarray(p.oidx).ravel()).to(dev)
+    vals_d = torch.from_numpy(p.vals).to(dev)
+    fac_d = [torch.from_numpy(np.asfortranarray(F).ravel(order="F")).to(dev) for F in p.factors]
+    W_d = torch.empty(n * r, dtype=torch.float64, device=dev)
+
+    ctx = pkg.Context(local)
+    stream = torch.cuda.current_stream()
+    ctx.set_stream(stream)
+    kern = ctx.kernel_create(n, UK, dK)
+
+    def step(precision, profile=False, device=True):
+        lowp = precision != "fp64"
+        if device:
+            prob = pkg.Problem(ctx, kern, fac_d, kidx_d, oidx_d, vals_d, r, sorted_obs=True,
+                               lowp=lowp)
+            W, st = prob.solve(p.lam, p.rho, TOL, max_iter=500, precision=precision,
+                               profile=profile, out=W_d, raise_on_error=False)
+            prob.close()
+        return st
+
+    # ---- warm-up
+    for _ in range(args.warmup):
+        st = step(args.precision)
+    # ---- timed region (device-resident inputs)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    stats = []
+    with ClockSampler(local) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            stats.append(step(args.precision, profile=True))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    iters = sum(s["iterations"] for s in stats)
+    value = q * iters * world / (elapsed_ms / 1e3)
+    solves_per_s = args.steps * world / (elapsed_ms / 1e3)
+    gds_ms = sum(s["gds_ms"] for s in stats)
+    gds_bytes_per_launch = q * r * 4 + (n + 1) * 8 + q * 0  # Zhat stream (FP32) + row data
+    gds_exec = iters
+    achieved = gds_bytes_per_launch * gds_exec / (gds_ms / 1e3) / 1e9 if gds_ms > 0 else None
+    peak, peak_kind = peaks()
+    iter_phase_ms = sum(s["gds_ms"] + s["gemm_ms"] for s in stats)
+
+    # ---- FP64 path on the same workload (the plain FP64 GPU solve)
+    fp64 = None
+    if not args.no_fp64:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s64 = step("fp64", profile=True)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        fp64 = {"solves_per_s": 1.0 / t64, "obs_iter_per_s": q * s64["iterations"] / t64,
+                "iterations": s64["iterations"], "rel_residual": s64["rel_residual"],
+                "status": s64["status"]}
+
+    # ---- end to end through the public API with host buffers (pinned)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    kh, oh, vh = pin(p.kidx), pin(p.oidx.ravel()), pin(p.vals)
+    fh = [pin(np.asfortranarray(F).ravel(order="F")).reshape(F.shape[1], F.shape[0]).T
+          for F in p.factors]
+    Wh = pin(np.zeros((r, n))).T
+    e2e_steps = max(1, min(3, args.steps))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(e2e_steps):
+        Wo, st = pkg.solve(ctx, kern, fh, kh, oh, vh, r, p.lam, p.rho, TOL, 500,
+                           precision=args.precision, sorted_obs=True, out=Wh)
+        e2e_iters += st["iterations"]
+    torch.cuda.synchronize()
+    te2e = time.perf_counter() - t0
+    h2d = q * 4 + q * 4 * p.oidx.shape[1] + q * 8 + sum(F.size * 8 for F in p.factors)
+    e2e = {"value": q * e2e_iters / te2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(n * r * 8), "solves_per_s": e2e_steps / te2e}
+
+    # ---- CPU baseline: the oracle on a bounded sample, rank 0 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        sample_q = int(os.environ.get("CPHIFI_CPU_SAMPLE_Q", "2000000"))
+        secs, sq, it = cpu_oracle_time(cpu_oracle_setup(p, sample_q), iters=2)
+        cpu = {"value": sq * it / secs, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one FP64 oracle PCG iteration (NumPy, BLAS threads = host cores) on "
+                         f"the first {sq} sorted observations of this workload, full n = {n}"}
+
+    launches = sum(s["kernel_launches"] + s["setup_launches"] for s in stats)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 operator, f64 CG/residuals" if args.precision != "fp64" else "f64",
+            "data": "synthetic planted low rank (seeded), inputs larger than L2 (no flush)",
+            "config": {"workload": args.workload, "n": n, "other_sizes": p.other_sizes, "q": q,
+                       "r": r, "lambda": p.lam, "rho": p.rho, "tol": TOL,
+                       "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2"},
+            "solves_per_s": solves_per_s,
+            "iterations_per_solve": iters / args.steps,
+            "rel_residual": [s["rel_residual"] for s in stats],
+            "iter_phase_obs_iter_per_s": q * iters / (iter_phase_ms / 1e3) if iter_phase_ms else None,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "kernel": "gds_kernel<float> (gather-dot/scatter, Eqs. vl/yhat1)",
+                         "peak_source": f"{peak_kind} hbm_gbs",
+                         "bytes_per_launch": gds_bytes_per_launch,
+                         "avg_launch_ms": gds_ms / max(1, gds_exec)},
+            "fp64_path": fp64,
+            "mixed_vs_fp64_solves": (solves_per_s / fp64["solves_per_s"]) if fp64 else None,
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary(),
+            "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    kern.close()
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -110,6 +110,7 @@ typedef struct cphifi_stats {
   int32_t gemm64_launches;
   double gemm64_ms;
   int64_t kernel_launches;   /* every kernel this solve launched              */
+  int64_t setup_launches;    /* kernels launched by the problem's creation    */
 } cphifi_stats;
 
 typedef struct cphifi_ctx cphifi_ctx;

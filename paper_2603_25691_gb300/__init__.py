@@ -1,0 +1,392 @@
+"""GB300 (sm_103a) solver for the unaligned kernel-mode CP-HIFI subproblem.
+
+Python binding of ``libcphifi.so``: argument marshalling only.  Every step of
+the solve runs in the library's CUDA kernels; there is no CPU fallback and
+importing the functions below raises when the shared library is missing.
+
+Host buffers are NumPy arrays; device buffers are CUDA ``torch.Tensor`` s.
+n x r matrices are column-major (the paper's vec order) on both sides: pass
+NumPy arrays of shape (n, r) (they are converted to Fortran order) or
+device tensors holding the column-major data (``to_colmajor`` builds one).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcphifi.so")
+
+OK = 0
+E_INVALID_ARG = 1
+E_OOM = 2
+E_ADMISSION = 3
+E_NOT_CONVERGED = 4
+E_BREAKDOWN = 5
+E_DEVICE = 6
+E_TIMEOUT = 7
+E_UNSUPPORTED = 8
+
+MEM_HOST = 0
+MEM_DEVICE = 1
+
+FP64 = 0
+MIXED_FP32 = 1
+MIXED_TF32 = 2
+MIXED_BF16 = 3
+
+OBS_SORTED = 0x1
+NEED_LOWP = 0x4
+
+PRECISIONS = {"fp64": FP64, "mixed_fp32": MIXED_FP32, "mixed_tf32": MIXED_TF32,
+              "mixed_bf16": MIXED_BF16}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("rho", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("k_replace", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("true_residuals", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double), ("rel_residual_recurrence", ctypes.c_double),
+                ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("gds_ms", ctypes.c_double), ("gds_launches", ctypes.c_int32),
+                ("gemm_launches", ctypes.c_int32), ("gemm_ms", ctypes.c_double),
+                ("gds64_ms", ctypes.c_double), ("gds64_launches", ctypes.c_int32),
+                ("gemm64_launches", ctypes.c_int32), ("gemm64_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64), ("setup_launches", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class CphifiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cphifi status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_PP = ctypes.POINTER(ctypes.c_void_p)
+_SIG = {
+    "cphifi_ctx_create": (ctypes.c_int, [_PP, ctypes.c_int, ctypes.c_size_t]),
+    "cphifi_ctx_destroy": (ctypes.c_int, [_P]),
+    "cphifi_ctx_set_stream": (ctypes.c_int, [_P, _P]),
+    "cphifi_ctx_bytes_in_use": (ctypes.c_size_t, [_P]),
+    "cphifi_last_error": (ctypes.c_char_p, [_P]),
+    "cphifi_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "cphifi_kernel_create": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, ctypes.c_int, _PP]),
+    "cphifi_kernel_destroy": (ctypes.c_int, [_P]),
+    "cphifi_problem_create": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32,
+                                             ctypes.c_int64, _P, _P, _P, ctypes.c_uint32,
+                                             ctypes.c_int, _PP]),
+    "cphifi_problem_destroy": (ctypes.c_int, [_P]),
+    "cphifi_problem_bytes": (ctypes.c_size_t, [_P]),
+    "cphifi_problem_solve": (ctypes.c_int, [_P, ctypes.POINTER(Params), _P, _P, ctypes.c_int,
+                                            ctypes.POINTER(Stats)]),
+    "cphifi_solve": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32,
+                                    ctypes.c_int64, _P, _P, _P, ctypes.c_uint32,
+                                    ctypes.POINTER(Params), _P, _P, ctypes.c_int,
+                                    ctypes.POINTER(Stats)]),
+    "cphifi_problem_rhs": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "cphifi_problem_matvec": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                             _P, _P, ctypes.c_int]),
+    "cphifi_problem_gds": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int]),
+    "cphifi_problem_precond": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, _P,
+                                              ctypes.c_int]),
+    "cphifi_problem_gram": (ctypes.c_int, [_P, _P, _P, _P]),
+    "cphifi_problem_order": (ctypes.c_int, [_P, _P, _P]),
+}
+
+
+def exported_symbols() -> list:
+    """Names of the C entry points this binding expects (all of include/cphifi.h)."""
+    return list(_SIG)
+
+
+def lib():
+    """Load libcphifi.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIG.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().cphifi_status_string(code).decode()
+
+
+# --------------------------------------------------------------- buffers ---
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+class _Buf:
+    """Keeps a host array or device tensor alive and yields (pointer, kind)."""
+
+    def __init__(self, x, dtype, shape_check=None, colmajor=False):
+        if _is_torch(x):
+            import torch
+            want = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+            if not x.is_cuda:
+                x = x.numpy()
+            else:
+                if x.dtype != want:
+                    raise TypeError(f"device buffer must be {want}, got {x.dtype}")
+                if not x.is_contiguous():
+                    raise ValueError("device buffers must be contiguous")
+                self.obj, self.ptr, self.mem = x, x.data_ptr(), MEM_DEVICE
+                self.numel = x.numel()
+                return
+        a = np.asarray(x, dtype=dtype)
+        a = np.asfortranarray(a) if colmajor else np.ascontiguousarray(a)
+        self.obj, self.ptr, self.mem = a, a.ctypes.data, MEM_HOST
+        self.numel = a.size
+
+
+def to_colmajor(X):
+    """(n, r) torch tensor -> contiguous tensor holding its column-major data."""
+    return X.t().contiguous()
+
+
+def _check(ctx_ptr, rc: int, what: str):
+    if rc != OK:
+        msg = lib().cphifi_last_error(ctx_ptr).decode() if ctx_ptr else status_string(rc)
+        raise CphifiError(rc, f"{what}: {msg}")
+
+
+# ---------------------------------------------------------------- handles ---
+class Context:
+    """cphifi_ctx_create / cphifi_ctx_destroy."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        h = ctypes.c_void_p()
+        rc = lib().cphifi_ctx_create(ctypes.byref(h), device, hbm_budget_bytes)
+        _check(None, rc, "ctx_create")
+        self.h = h
+
+    def set_stream(self, stream) -> None:
+        """cphifi_ctx_set_stream: order calls on a torch.cuda.Stream or raw handle."""
+        handle = getattr(stream, "cuda_stream", stream)
+        _check(self.h, lib().cphifi_ctx_set_stream(self.h, ctypes.c_void_p(handle)),
+               "ctx_set_stream")
+
+    def bytes_in_use(self) -> int:
+        return lib().cphifi_ctx_bytes_in_use(self.h)
+
+    def last_error(self) -> str:
+        return lib().cphifi_last_error(self.h).decode()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cphifi_ctx_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def kernel_create(self, n: int, UK, DK, K=None) -> "Kernel":
+        return Kernel(self, n, UK, DK, K)
+
+
+class Kernel:
+    """cphifi_kernel_create: the kernel matrix's eigendecomposition (Eq. eigK)."""
+
+    def __init__(self, ctx: Context, n: int, UK, DK, K=None):
+        self.ctx = ctx
+        self.n = int(n)
+        u = _Buf(UK, np.float64, colmajor=True)
+        d = _Buf(DK, np.float64)
+        if u.mem != d.mem:
+            raise ValueError("UK and DK must live in the same memory kind")
+        if u.numel != self.n * self.n or d.numel != self.n:
+            raise ValueError("UK must be n x n and DK length n")
+        h = ctypes.c_void_p()
+        rc = lib().cphifi_kernel_create(ctx.h, self.n, None, u.ptr, d.ptr, u.mem, ctypes.byref(h))
+        _check(ctx.h, rc, "kernel_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cphifi_kernel_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+
+def _factor_bufs(factors, r):
+    bufs = [_Buf(F, np.float64, colmajor=True) for F in factors]
+    sizes = []
+    for F, b in zip(factors, bufs):
+        sizes.append(int(F.shape[0]) if b.mem == MEM_HOST else b.numel // r)
+    return bufs, sizes
+
+
+def _obs_bufs(kidx, oidx, vals):
+    k = _Buf(kidx, np.int32)
+    o = _Buf(oidx, np.int32)
+    v = _Buf(vals, np.float64)
+    if not (k.mem == o.mem == v.mem):
+        raise ValueError("observation lists must live in the same memory kind")
+    return k, o, v
+
+
+class Problem:
+    """cphifi_problem_create: one subproblem (sort, Zhat, Gram, eig(V), B)."""
+
+    def __init__(self, ctx: Context, kernel: Kernel, factors, kidx, oidx, vals, r: int,
+                 sorted_obs: bool = False, lowp: bool = False):
+        self.ctx, self.kernel, self.r = ctx, kernel, int(r)
+        self.n = kernel.n
+        fb, sizes = _factor_bufs(factors, self.r)
+        k, o, v = _obs_bufs(kidx, oidx, vals)
+        if any(b.mem != k.mem for b in fb):
+            raise ValueError("factors and observations must live in the same memory kind")
+        self.q = k.numel
+        self.d_other = len(factors)
+        self.sizes = sizes
+        sizes_arr = (ctypes.c_int64 * len(sizes))(*sizes)
+        fptrs = (ctypes.c_void_p * len(fb))(*[b.ptr for b in fb])
+        flags = (OBS_SORTED if sorted_obs else 0) | (NEED_LOWP if lowp else 0)
+        h = ctypes.c_void_p()
+        rc = lib().cphifi_problem_create(ctx.h, kernel.h, len(fb), sizes_arr, fptrs, self.r,
+                                         self.q, k.ptr, o.ptr, v.ptr, flags, k.mem,
+                                         ctypes.byref(h))
+        _check(ctx.h, rc, "problem_create")
+        self.h = h
+        self.mem = k.mem
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cphifi_problem_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def bytes(self) -> int:
+        return lib().cphifi_problem_bytes(self.h)
+
+    # ---- outputs: host numpy (n, r) or a device tensor (flat, column-major)
+    def _out(self, like_device: bool):
+        if like_device:
+            import torch
+            return torch.empty(self.n * self.r, dtype=torch.float64, device="cuda")
+        return np.empty((self.n, self.r), dtype=np.float64, order="F")
+
+    def solve(self, lam: float, rho: float, tol: float, max_iter: int = 1000,
+              precision: str | int = "fp64", k_replace: int = 10, check_every: int = 8,
+              profile: bool = False, W0=None, out=None, raise_on_error: bool = True):
+        """cphifi_problem_solve.  Returns (W, stats dict)."""
+        prm = make_params(lam, rho, tol, max_iter, precision, k_replace, check_every, profile)
+        st = Stats()
+        W = out if out is not None else self._out(False)
+        wb = _Buf(W, np.float64, colmajor=True) if not _is_torch(W) else _Buf(W, np.float64)
+        w0 = _Buf(W0, np.float64, colmajor=True) if W0 is not None else None
+        rc = lib().cphifi_problem_solve(self.h, ctypes.byref(prm), w0.ptr if w0 else None,
+                                        wb.ptr, wb.mem, ctypes.byref(st))
+        if rc not in (OK, E_NOT_CONVERGED) or (raise_on_error and rc != OK):
+            _check(self.ctx.h, rc, "problem_solve")
+        return (wb.obj if wb.mem == MEM_DEVICE else wb.obj), st.as_dict()
+
+    def rhs(self):
+        """cphifi_problem_rhs: (B, b) as (n, r) host arrays."""
+        B = self._out(False)
+        b = self._out(False)
+        _check(self.ctx.h, lib().cphifi_problem_rhs(self.h, B.ctypes.data, b.ctypes.data, MEM_HOST),
+               "problem_rhs")
+        return B, b
+
+    def matvec(self, X, lam: float, rho: float, precision: str | int = "fp64"):
+        """cphifi_problem_matvec: Y = A X in the given operator arithmetic."""
+        x = _Buf(X, np.float64, colmajor=True)
+        Y = self._out(False)
+        _check(self.ctx.h, lib().cphifi_problem_matvec(self.h, _prec(precision), lam, rho, x.ptr,
+                                                       Y.ctypes.data, MEM_HOST), "problem_matvec")
+        return Y
+
+    def gds(self, Xhat, precision: str | int = "fp64"):
+        """cphifi_problem_gds: Yhat1 for a given Xhat (Eqs. vl and yhat1)."""
+        x = _Buf(Xhat, np.float64, colmajor=True)
+        Y = self._out(False)
+        _check(self.ctx.h, lib().cphifi_problem_gds(self.h, _prec(precision), x.ptr, Y.ctypes.data,
+                                                    MEM_HOST), "problem_gds")
+        return Y
+
+    def precond(self, X, lam: float, rho: float):
+        """cphifi_problem_precond: M^{-1} X (Eq. fx)."""
+        x = _Buf(X, np.float64, colmajor=True)
+        Y = self._out(False)
+        _check(self.ctx.h, lib().cphifi_problem_precond(self.h, lam, rho, x.ptr, Y.ctypes.data,
+                                                        MEM_HOST), "problem_precond")
+        return Y
+
+    def gram(self):
+        """cphifi_problem_gram: (V, DV, UV) computed on the device."""
+        r = self.r
+        V = np.empty((r, r), order="F")
+        DV = np.empty(r)
+        UV = np.empty((r, r), order="F")
+        _check(self.ctx.h, lib().cphifi_problem_gram(self.h, V.ctypes.data, DV.ctypes.data,
+                                                     UV.ctypes.data), "problem_gram")
+        return V, DV, UV
+
+    def order(self):
+        """cphifi_problem_order: (perm, row_ptr) of the stable sort by kernel index."""
+        perm = np.empty(self.q, dtype=np.int32)
+        rp = np.empty(self.n + 1, dtype=np.int64)
+        _check(self.ctx.h, lib().cphifi_problem_order(self.h, perm.ctypes.data, rp.ctypes.data),
+               "problem_order")
+        return perm, rp
+
+
+def _prec(p) -> int:
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def make_params(lam, rho, tol, max_iter=1000, precision="fp64", k_replace=10, check_every=8,
+                profile=False) -> Params:
+    return Params(float(lam), float(rho), float(tol), int(max_iter), _prec(precision),
+                  int(k_replace), int(check_every), 1 if profile else 0, 0)
+
+
+def solve(ctx: Context, kernel: Kernel, factors, kidx, oidx, vals, r: int, lam: float, rho: float,
+          tol: float, max_iter: int = 1000, precision="fp64", sorted_obs=False, k_replace=10,
+          check_every=8, profile=False, W0=None, out=None):
+    """cphifi_solve: one-shot create + solve + destroy.  Returns (W, stats)."""
+    fb, sizes = _factor_bufs(factors, r)
+    k, o, v = _obs_bufs(kidx, oidx, vals)
+    prm = make_params(lam, rho, tol, max_iter, precision, k_replace, check_every, profile)
+    st = Stats()
+    n = kernel.n
+    if out is None:
+        out = np.empty((n, r), order="F") if k.mem == MEM_HOST else None
+        if out is None:
+            import torch
+            out = torch.empty(n * r, dtype=torch.float64, device="cuda")
+    wb = _Buf(out, np.float64, colmajor=not _is_torch(out))
+    w0 = _Buf(W0, np.float64, colmajor=True) if W0 is not None else None
+    sizes_arr = (ctypes.c_int64 * len(sizes))(*sizes)
+    fptrs = (ctypes.c_void_p * len(fb))(*[b.ptr for b in fb])
+    flags = OBS_SORTED if sorted_obs else 0
+    rc = lib().cphifi_solve(ctx.h, kernel.h, len(fb), sizes_arr, fptrs, int(r), k.numel, k.ptr,
+                            o.ptr, v.ptr, flags, ctypes.byref(prm), w0.ptr if w0 else None,
+                            wb.ptr, k.mem, ctypes.byref(st))
+    if rc not in (OK, E_NOT_CONVERGED):
+        _check(ctx.h, rc, "solve")
+    return wb.obj, st.as_dict()

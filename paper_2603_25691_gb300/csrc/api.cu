@@ -1,0 +1,1023 @@
+// C ABI and host orchestration of one unaligned kernel-mode PCG solve
+// (Brust & Kolda, §4.4).  Declarations and argument conventions:
+// include/cphifi.h.
+//
+// The solve runs in the eigenbasis of K: with K = U_K D_K U_K' (Eq. eigK) and
+// X = U_K Xbar, the system of Eq. unaligned-infinite-1 becomes
+//   Abar xbar = D_K U_K' Yhat1(U_K D_K Xbar) + (lambda D_K + rho) Xbar = bbar,
+//   bbar = D_K U_K' B,
+// where Yhat1(Xhat) is the gather-dot/scatter of Eqs. vl and yhat1.  The
+// preconditioner of Eqs. precon/fx becomes the row-local r x r map
+// ((Xbar U_V) .* D) U_V'.  Each iteration therefore reads the n x n matrix
+// U_K twice (instead of K twice and U_K twice) and the operator built from a
+// rounded U_K stays symmetric positive definite because U_K appears on both
+// sides.  W = U_K Wbar at the end.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "cphifi.h"
+#include "launch.h"
+
+using namespace cphifi;
+
+struct cphifi_ctx {
+  int device = 0;
+  int num_sms = 1;
+  cudaStream_t stream = nullptr;
+  cudaStream_t user_stream = nullptr;
+  bool has_user_stream = false;
+  size_t budget = 0;
+  size_t in_use = 0;
+  std::string last_error;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  DevScalars* h_scalars = nullptr;  // pinned
+  std::vector<cudaEvent_t> ev_pool;
+};
+
+struct cphifi_kernel {
+  cphifi_ctx* ctx = nullptr;
+  int n = 0;
+  double* UK64 = nullptr;  // n x n column-major
+  float* UK32 = nullptr;
+  double* dK = nullptr;    // n
+  size_t bytes = 0;
+};
+
+struct cphifi_problem {
+  cphifi_ctx* ctx = nullptr;
+  const cphifi_kernel* kern = nullptr;
+  int n = 0, r = 0, d_other = 0;
+  int64_t q = 0;
+  double gamma = 0.0;
+  std::vector<int64_t> sizes;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  // observation data (sorted by kernel index)
+  int32_t* perm = nullptr;
+  int64_t* row_ptr = nullptr;
+  double* z64 = nullptr;
+  float* z32 = nullptr;
+  int64_t zld = 0;
+  int32_t *pseg = nullptr, *pbeg = nullptr, *pend = nullptr, *seg_first = nullptr,
+          *seg_count = nullptr;
+  unsigned* seg_ticket = nullptr;
+  int npieces = 0;
+  void* gds_partial = nullptr;  // npieces x 64 doubles
+  // factors and their Gram
+  std::vector<double*> factors;
+  double** factors_dev = nullptr;
+  int64_t* sizes_dev = nullptr;
+  double *V = nullptr, *dV = nullptr, *UV = nullptr;
+  float* UV32 = nullptr;
+  int* info = nullptr;
+  double* Bm = nullptr;  // sparse MTTKRP B (n x r, original basis)
+  // solve workspace (n x r each)
+  double *x = nullptr, *res = nullptr, *z = nullptr, *p = nullptr, *y = nullptr,
+         *bbar = nullptr, *xh64 = nullptr, *y164 = nullptr, *tmp64 = nullptr,
+         *tmp64b = nullptr, *D64 = nullptr;
+  float *pop32 = nullptr, *xh32 = nullptr, *y132 = nullptr, *D32 = nullptr;
+  void* cpart = nullptr;  // nsplit x n x r doubles
+  int nsplit = 1;
+  RedScratch red{};
+  DevScalars* s = nullptr;    // the solve's scalars
+  DevScalars* s2 = nullptr;   // scalars of the step-by-step calls
+  int* err = nullptr;
+  int64_t create_launches = 0;
+};
+
+// ------------------------------------------------------------ helpers -----
+namespace {
+
+int fail(cphifi_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return code;
+}
+
+#define CK(...)                                                                          \
+  do {                                                                                   \
+    cudaError_t e_ = (__VA_ARGS__);                                                      \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(ctx, CPHIFI_E_DEVICE, std::string(#__VA_ARGS__ " failed: ") +         \
+                                            cudaGetErrorString(e_));                     \
+  } while (0)
+
+struct Enter {
+  // Orders the call after the caller's stream and makes the context's device
+  // current for the duration of the call.
+  cphifi_ctx* ctx;
+  int prev = -1;
+  explicit Enter(cphifi_ctx* c) : ctx(c) {
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    if (ctx->has_user_stream) {
+      cudaEventRecord(ctx->ev_in, ctx->user_stream);
+      cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0);
+    }
+  }
+  ~Enter() {
+    if (ctx->has_user_stream) {
+      cudaEventRecord(ctx->ev_out, ctx->stream);
+      cudaStreamWaitEvent(ctx->user_stream, ctx->ev_out, 0);
+    }
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+cudaError_t dalloc(cphifi_problem* P, T** out, size_t count) {
+  *out = nullptr;
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  if (e != cudaSuccess) return e;
+  P->allocs.push_back(p);
+  P->bytes += count * sizeof(T);
+  P->ctx->in_use += count * sizeof(T);
+  *out = (T*)p;
+  return cudaSuccess;
+}
+
+void free_problem(cphifi_problem* P) {
+  for (void* a : P->allocs) cudaFree(a);
+  P->ctx->in_use -= std::min(P->ctx->in_use, P->bytes);
+  P->allocs.clear();
+  P->bytes = 0;
+}
+
+// Kernel count of a launcher call as written in problem_create (the scan
+// launches three kernels, each radix pass three plus the scan's three).
+bool is_launch(const char* call) {
+  return strncmp(call, "launch_", 7) == 0 || strncmp(call, "radix_sort_pairs", 16) == 0 ||
+         strncmp(call, "exclusive_scan_i32", 18) == 0;
+}
+int64_t launch_weight(const char* call) {
+  if (strncmp(call, "exclusive_scan_i32", 18) == 0) return 3;
+  if (strncmp(call, "radix_sort_pairs", 16) == 0) return 10;
+  return 1;
+}
+
+int bits_for(int n) {
+  int b = 1;
+  while (b < 31 && (1LL << b) < n) ++b;
+  return b;
+}
+
+// Copies `bytes` from a caller buffer (host or device) into device memory.
+cudaError_t upload(void* dst, const void* src, size_t bytes, int mem, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, bytes,
+                         mem == CPHIFI_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                  : cudaMemcpyHostToDevice,
+                         st);
+}
+
+cudaError_t download(void* dst, const void* src, size_t bytes, int mem, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, bytes,
+                         mem == CPHIFI_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                  : cudaMemcpyDeviceToHost,
+                         st);
+}
+
+// Launch timing: pairs of events around selected launches.
+struct Timer {
+  cphifi_ctx* ctx;
+  bool on;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gds, gemm, gds64, gemm64;
+  size_t used = 0;
+  Timer(cphifi_ctx* c, bool enabled) : ctx(c), on(enabled) {}
+  cudaEvent_t ev() {
+    if (used == ctx->ev_pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      ctx->ev_pool.push_back(e);
+    }
+    return ctx->ev_pool[used++];
+  }
+  cudaEvent_t begin() {
+    if (!on) return nullptr;
+    cudaEvent_t e = ev();
+    cudaEventRecord(e, ctx->stream);
+    return e;
+  }
+  void end(cudaEvent_t b, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v) {
+    if (!on) return;
+    cudaEvent_t e = ev();
+    cudaEventRecord(e, ctx->stream);
+    v.push_back({b, e});
+  }
+  static double total(const std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v) {
+    double t = 0;
+    for (auto& pr : v) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, pr.first, pr.second);
+      t += ms;
+    }
+    return t;
+  }
+};
+
+}  // namespace
+
+// ----------------------------------------------------------- context ------
+extern "C" const char* cphifi_status_string(int status) {
+  switch (status) {
+    case CPHIFI_OK: return "ok";
+    case CPHIFI_E_INVALID_ARG: return "invalid argument";
+    case CPHIFI_E_OOM: return "device allocation failed";
+    case CPHIFI_E_ADMISSION: return "footprint exceeds the HBM budget";
+    case CPHIFI_E_NOT_CONVERGED: return "not converged within max_iter";
+    case CPHIFI_E_BREAKDOWN: return "PCG breakdown (p'Ap <= 0 or non-finite scalar)";
+    case CPHIFI_E_DEVICE: return "CUDA error";
+    case CPHIFI_E_TIMEOUT: return "timed out";
+    case CPHIFI_E_UNSUPPORTED: return "unsupported in this build";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int cphifi_ctx_create(cphifi_ctx** out, int device, size_t hbm_budget_bytes) {
+  if (!out) return CPHIFI_E_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+    return CPHIFI_E_INVALID_ARG;
+  cphifi_ctx* ctx = new cphifi_ctx();
+  ctx->device = device;
+  ctx->budget = hbm_budget_bytes;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(device);
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  bool ok = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) == cudaSuccess &&
+            cudaMallocHost(&ctx->h_scalars, sizeof(DevScalars)) == cudaSuccess;
+  cudaSetDevice(prev);
+  if (!ok) {
+    delete ctx;
+    return CPHIFI_E_DEVICE;
+  }
+  *out = ctx;
+  return CPHIFI_OK;
+}
+
+extern "C" int cphifi_ctx_destroy(cphifi_ctx* ctx) {
+  if (!ctx) return CPHIFI_E_INVALID_ARG;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+  if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+  if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  cudaSetDevice(prev);
+  delete ctx;
+  return CPHIFI_OK;
+}
+
+extern "C" int cphifi_ctx_set_stream(cphifi_ctx* ctx, void* stream) {
+  if (!ctx) return CPHIFI_E_INVALID_ARG;
+  ctx->user_stream = (cudaStream_t)stream;
+  ctx->has_user_stream = true;
+  return CPHIFI_OK;
+}
+
+extern "C" size_t cphifi_ctx_bytes_in_use(const cphifi_ctx* ctx) { return ctx ? ctx->in_use : 0; }
+
+extern "C" const char* cphifi_last_error(const cphifi_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : "null context";
+}
+
+// ------------------------------------------------------------ kernel ------
+extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
+                                    const double* UK, const double* DK, int mem,
+                                    cphifi_kernel** out) {
+  (void)K;
+  if (!ctx || !out) return CPHIFI_E_INVALID_ARG;
+  *out = nullptr;
+  if (n < 1 || n > (1 << 20)) return fail(ctx, CPHIFI_E_INVALID_ARG, "n out of range");
+  if (!UK || !DK)
+    return fail(ctx, CPHIFI_E_UNSUPPORTED,
+                "the eigendecomposition of K must be passed (UK, DK)");
+  if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
+  const size_t nn = (size_t)n * n;
+  const size_t bytes = nn * (sizeof(double) + sizeof(float)) + n * sizeof(double);
+  if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+    return fail(ctx, CPHIFI_E_ADMISSION, "kernel matrix exceeds the HBM budget");
+  Enter guard(ctx);
+  cphifi_kernel* kern = new cphifi_kernel();
+  kern->ctx = ctx;
+  kern->n = (int)n;
+  int* err = nullptr;
+  auto cleanup = [&](int code, const std::string& m) {
+    if (kern->UK64) cudaFree(kern->UK64);
+    if (kern->UK32) cudaFree(kern->UK32);
+    if (kern->dK) cudaFree(kern->dK);
+    if (err) cudaFree(err);
+    delete kern;
+    return fail(ctx, code, m);
+  };
+  if (cudaMalloc(&kern->UK64, nn * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&kern->UK32, nn * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&kern->dK, n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&err, sizeof(int)) != cudaSuccess)
+    return cleanup(CPHIFI_E_OOM, "cudaMalloc failed for the kernel matrix");
+  cudaStream_t st = ctx->stream;
+  int herr = 0;
+  if (upload(kern->UK64, UK, nn * sizeof(double), mem, st) != cudaSuccess ||
+      upload(kern->dK, DK, n * sizeof(double), mem, st) != cudaSuccess ||
+      cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess ||
+      launch_validate_dense(kern->UK64, (int64_t)nn, err, st) != cudaSuccess ||
+      launch_validate_dense(kern->dK, n, err, st) != cudaSuccess ||
+      launch_convert<double, float>(kern->UK64, kern->UK32, (int64_t)nn, st) != cudaSuccess ||
+      cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return cleanup(CPHIFI_E_DEVICE, "uploading the kernel eigendecomposition failed");
+  if (herr) return cleanup(CPHIFI_E_INVALID_ARG, "non-finite entry in UK or DK");
+  cudaFree(err);
+  kern->bytes = bytes;
+  ctx->in_use += bytes;
+  *out = kern;
+  return CPHIFI_OK;
+}
+
+extern "C" int cphifi_kernel_destroy(cphifi_kernel* kern) {
+  if (!kern) return CPHIFI_E_INVALID_ARG;
+  cphifi_ctx* ctx = kern->ctx;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(kern->UK64);
+  cudaFree(kern->UK32);
+  cudaFree(kern->dK);
+  ctx->in_use -= std::min(ctx->in_use, kern->bytes);
+  cudaSetDevice(prev);
+  delete kern;
+  return CPHIFI_OK;
+}
+
+// ----------------------------------------------------------- problem ------
+static size_t problem_footprint(int64_t n, int64_t q, int r, int d_other,
+                                const std::vector<int64_t>& sizes, bool lowp, int nsplit,
+                                int64_t npieces_max) {
+  size_t b = 0;
+  const size_t nr = (size_t)n * r;
+  b += (size_t)q * r * sizeof(double);                 // Zhat FP64
+  if (lowp) b += (size_t)q * r * sizeof(float);        // Zhat FP32
+  b += (size_t)q * sizeof(int32_t);                    // perm
+  b += (n + 1) * sizeof(int64_t) + 4 * n * sizeof(int32_t) + (n + 1) * sizeof(int32_t);
+  b += (size_t)npieces_max * (3 * sizeof(int32_t) + 64 * sizeof(double));
+  for (int m = 0; m < d_other; ++m) b += (size_t)sizes[m] * r * sizeof(double);
+  b += 12 * nr * sizeof(double) + 4 * nr * sizeof(float);
+  b += (size_t)nsplit * nr * sizeof(double);
+  b += (size_t)kRedMaxBlocks * kRedSlots * sizeof(double);
+  return b;
+}
+
+extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
+                                     const int64_t* other_sizes, const double* const* factors,
+                                     int32_t r, int64_t q, const int32_t* kidx,
+                                     const int32_t* oidx, const double* vals, uint32_t flags,
+                                     int mem, cphifi_problem** out) {
+  if (!ctx || !out) return CPHIFI_E_INVALID_ARG;
+  *out = nullptr;
+  if (!kern || kern->ctx != ctx) return fail(ctx, CPHIFI_E_INVALID_ARG, "kernel of another context");
+  if (d_other < 1 || d_other > 16) return fail(ctx, CPHIFI_E_INVALID_ARG, "d_other must be in [1, 16]");
+  if (r < 1 || r > kMaxRank) return fail(ctx, CPHIFI_E_INVALID_ARG, "r must be in [1, 64]");
+  if (q < 0 || q >= (int64_t(1) << 31)) return fail(ctx, CPHIFI_E_INVALID_ARG, "q must be in [0, 2^31)");
+  if (!other_sizes || !factors) return fail(ctx, CPHIFI_E_INVALID_ARG, "null sizes or factors");
+  if (q > 0 && (!kidx || !oidx || !vals)) return fail(ctx, CPHIFI_E_INVALID_ARG, "null observation list");
+  if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
+  std::vector<int64_t> sizes(other_sizes, other_sizes + d_other);
+  double M = 1.0;
+  for (int m = 0; m < d_other; ++m) {
+    if (sizes[m] < 1 || sizes[m] > (int64_t(1) << 31) - 1 || !factors[m])
+      return fail(ctx, CPHIFI_E_INVALID_ARG, "bad other-mode size or null factor");
+    M *= (double)sizes[m];
+  }
+  const int n = kern->n;
+  const int piece_len = 512;
+  const int64_t npieces_max = q / piece_len + n + 1;
+  const int nsplit = gemm_pick_split(n, ctx->num_sms);
+  const bool lowp = (flags & CPHIFI_NEED_LOWP) != 0;
+  const size_t need = problem_footprint(n, q, r, d_other, sizes, lowp, nsplit, npieces_max);
+  const size_t tmp_need = (size_t)q * (sizeof(int32_t) * (1 + d_other) + sizeof(double) * 2 +
+                                       sizeof(uint32_t)) + radix_sort_tmp_bytes(q);
+  if (ctx->budget && ctx->in_use + need + tmp_need > ctx->budget)
+    return fail(ctx, CPHIFI_E_ADMISSION, "problem footprint exceeds the HBM budget");
+  Enter guard(ctx);
+  auto t0 = std::chrono::steady_clock::now();
+  cphifi_problem* P = new cphifi_problem();
+  P->ctx = ctx;
+  P->kern = kern;
+  P->n = n;
+  P->r = r;
+  P->d_other = d_other;
+  P->q = q;
+  P->sizes = sizes;
+  P->gamma = (double)q / ((double)n * M);
+  P->nsplit = nsplit;
+  P->zld = q;
+  cudaStream_t st = ctx->stream;
+  std::vector<void*> temps;
+  auto tmp_alloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 1) != cudaSuccess) return nullptr;
+    temps.push_back(p);
+    return p;
+  };
+  auto bail = [&](int code, const std::string& m) {
+    cudaStreamSynchronize(st);
+    for (void* t : temps) cudaFree(t);
+    free_problem(P);
+    delete P;
+    return fail(ctx, code, m);
+  };
+#define PCK(...)                                                                            \
+  do {                                                                                      \
+    if (is_launch(#__VA_ARGS__)) P->create_launches += launch_weight(#__VA_ARGS__);         \
+    cudaError_t e_ = (__VA_ARGS__);                                                         \
+    if (e_ != cudaSuccess)                                                                  \
+      return bail(e_ == cudaErrorMemoryAllocation ? CPHIFI_E_OOM : CPHIFI_E_DEVICE,        \
+                  std::string(#__VA_ARGS__ " failed: ") + cudaGetErrorString(e_));         \
+  } while (0)
+
+  // ---- persistent arrays
+  const size_t nr = (size_t)n * r;
+  PCK(dalloc(P, &P->perm, q));
+  PCK(dalloc(P, &P->row_ptr, n + 1));
+  PCK(dalloc(P, &P->z64, (size_t)q * r));
+  if (lowp) PCK(dalloc(P, &P->z32, (size_t)q * r));
+  PCK(dalloc(P, &P->seg_first, n + 1));
+  PCK(dalloc(P, &P->seg_count, n));
+  PCK(dalloc(P, &P->seg_ticket, n));
+  PCK(dalloc(P, &P->factors_dev, d_other));
+  PCK(dalloc(P, &P->sizes_dev, d_other));
+  P->factors.resize(d_other);
+  for (int m = 0; m < d_other; ++m) PCK(dalloc(P, &P->factors[m], (size_t)sizes[m] * r));
+  PCK(dalloc(P, &P->V, r * r));
+  PCK(dalloc(P, &P->dV, r));
+  PCK(dalloc(P, &P->UV, r * r));
+  PCK(dalloc(P, &P->UV32, r * r));
+  PCK(dalloc(P, &P->info, 4));
+  PCK(dalloc(P, &P->err, 4));
+  PCK(dalloc(P, &P->Bm, nr));
+  for (double** v : {&P->x, &P->res, &P->z, &P->p, &P->y, &P->bbar, &P->xh64, &P->y164,
+                     &P->tmp64, &P->tmp64b, &P->D64})
+    PCK(dalloc(P, v, nr));
+  for (float** v : {&P->pop32, &P->xh32, &P->y132, &P->D32}) PCK(dalloc(P, v, nr));
+  PCK(dalloc(P, (double**)&P->cpart, (size_t)nsplit * nr));
+  PCK(dalloc(P, &P->red.partials, (size_t)kRedMaxBlocks * kRedSlots));
+  PCK(dalloc(P, &P->red.ticket, 4));
+  PCK(dalloc(P, &P->s, 1));
+  PCK(dalloc(P, &P->s2, 1));
+  PCK(cudaMemsetAsync(P->red.ticket, 0, 4 * sizeof(unsigned), st));
+  PCK(cudaMemsetAsync(P->seg_ticket, 0, n * sizeof(unsigned), st));
+  PCK(cudaMemsetAsync(P->err, 0, sizeof(int), st));
+  PCK(cudaMemsetAsync(P->info, 0, sizeof(int), st));
+
+  // ---- factors
+  PCK(cudaMemcpyAsync(P->factors_dev, P->factors.data(), d_other * sizeof(double*),
+                      cudaMemcpyHostToDevice, st));
+  PCK(cudaMemcpyAsync(P->sizes_dev, sizes.data(), d_other * sizeof(int64_t),
+                      cudaMemcpyHostToDevice, st));
+  for (int m = 0; m < d_other; ++m) {
+    PCK(upload(P->factors[m], factors[m], (size_t)sizes[m] * r * sizeof(double), mem, st));
+    PCK(launch_validate_dense(P->factors[m], sizes[m] * r, P->err, st));
+  }
+
+  // ---- observations: copy, validate, sort by kernel index
+  uint32_t* keys = (uint32_t*)tmp_alloc((size_t)q * sizeof(uint32_t));
+  int32_t* oidx_d = nullptr;
+  const double* vals_d = nullptr;
+  const int32_t* kidx_d = nullptr;
+  if (!keys) return bail(CPHIFI_E_OOM, "temporary allocation failed");
+  if (mem == CPHIFI_MEM_DEVICE) {
+    oidx_d = (int32_t*)oidx;
+    vals_d = vals;
+    kidx_d = kidx;
+  } else {
+    oidx_d = (int32_t*)tmp_alloc((size_t)q * d_other * sizeof(int32_t));
+    double* v = (double*)tmp_alloc((size_t)q * sizeof(double));
+    int32_t* k = (int32_t*)tmp_alloc((size_t)q * sizeof(int32_t));
+    if (!oidx_d || !v || !k) return bail(CPHIFI_E_OOM, "temporary allocation failed");
+    PCK(upload(oidx_d, oidx, (size_t)q * d_other * sizeof(int32_t), mem, st));
+    PCK(upload(v, vals, (size_t)q * sizeof(double), mem, st));
+    PCK(upload(k, kidx, (size_t)q * sizeof(int32_t), mem, st));
+    vals_d = v;
+    kidx_d = k;
+  }
+  double* vals_sorted = (double*)tmp_alloc((size_t)q * sizeof(double));
+  if (!vals_sorted) return bail(CPHIFI_E_OOM, "temporary allocation failed");
+  PCK(launch_validate_obs(kidx_d, oidx_d, vals_d, q, n, d_other, P->sizes_dev, P->err, st));
+  PCK(cudaMemcpyAsync(keys, kidx_d, (size_t)q * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+  PCK(launch_iota(P->perm, q, st));
+  int herr = 0;
+  PCK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PCK(cudaStreamSynchronize(st));
+  if (herr & 1) return bail(CPHIFI_E_INVALID_ARG, "observation index out of range");
+  if (herr & 2) return bail(CPHIFI_E_INVALID_ARG, "non-finite observation value or factor entry");
+  if (!(flags & CPHIFI_OBS_SORTED) && q > 1) {
+    void* rtmp = tmp_alloc(radix_sort_tmp_bytes(q));
+    if (!rtmp) return bail(CPHIFI_E_OOM, "temporary allocation failed");
+    PCK(radix_sort_pairs(keys, P->perm, q, bits_for(n), rtmp, st));
+  }
+  else if (q > 1) PCK(launch_check_sorted(keys, q, P->err, st));
+  PCK(launch_row_ptr(keys, q, n, P->row_ptr, st));
+  PCK(launch_zhat((flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm, oidx_d, d_other,
+                  P->factors_dev, P->sizes_dev, r, q, P->z64, P->z32, P->zld, vals_d,
+                  vals_sorted, P->err, st));
+
+  // ---- pieces
+  {
+    void* stmp = tmp_alloc(exclusive_scan_tmp_bytes(n));
+    if (!stmp) return bail(CPHIFI_E_OOM, "temporary allocation failed");
+    PCK(launch_piece_counts(P->row_ptr, n, piece_len, P->seg_count, st));
+    PCK(exclusive_scan_i32(P->seg_count, P->seg_first, n, stmp, exclusive_scan_tmp_bytes(n), st));
+    int np = 0;
+    PCK(cudaMemcpyAsync(&np, P->seg_first + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PCK(cudaStreamSynchronize(st));
+    P->npieces = np;
+    PCK(dalloc(P, &P->pseg, np));
+    PCK(dalloc(P, &P->pbeg, np));
+    PCK(dalloc(P, &P->pend, np));
+    PCK(dalloc(P, (double**)&P->gds_partial, (size_t)np * 64));
+    PCK(launch_piece_fill(P->row_ptr, n, P->seg_first, P->seg_count, P->pseg, P->pbeg, P->pend, st));
+  }
+
+  // ---- Gram, eig(V), right-hand side MTTKRP
+  PCK(launch_gram(P->factors_dev, P->sizes_dev, d_other, r, P->V, st));
+  PCK(launch_jacobi_eig(P->V, r, P->dV, P->UV, 60, P->info, st));
+  PCK(launch_convert<double, float>(P->UV, P->UV32, (int64_t)r * r, st));
+  PieceList pl{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket, P->npieces};
+  PCK(launch_gds<double>(pl, P->z64, P->zld, r, nullptr, n, vals_sorted, (double*)P->gds_partial,
+                         P->Bm, n, nullptr, ctx->num_sms, st));
+  PCK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PCK(cudaStreamSynchronize(st));
+  if (herr & 4) return bail(CPHIFI_E_INVALID_ARG, "CPHIFI_OBS_SORTED set but kidx is not sorted");
+  if (herr) return bail(CPHIFI_E_INVALID_ARG, "invalid observation data");
+  for (void* t : temps) cudaFree(t);
+  temps.clear();
+  PCK(cudaStreamSynchronize(st));
+  (void)t0;
+  *out = P;
+  return CPHIFI_OK;
+#undef PCK
+}
+
+extern "C" int cphifi_problem_destroy(cphifi_problem* P) {
+  if (!P) return CPHIFI_E_INVALID_ARG;
+  cphifi_ctx* ctx = P->ctx;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  free_problem(P);
+  cudaSetDevice(prev);
+  delete P;
+  return CPHIFI_OK;
+}
+
+extern "C" size_t cphifi_problem_bytes(const cphifi_problem* P) { return P ? P->bytes : 0; }
+
+// ------------------------------------------------------------- solve ------
+namespace {
+
+struct Launcher {
+  cphifi_problem* P;
+  cudaStream_t st;
+  Timer* tm;
+  int64_t launches = 0;
+
+  PieceList pieces() const {
+    return PieceList{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket,
+                     P->npieces};
+  }
+  int64_t split_stride() const { return (int64_t)P->n * P->r; }
+
+  // out = U_K diag(scale) Bx  (a_trans: U_K itself), FP64, into out (n x r)
+  // cat: 0 untimed, 1 operator arithmetic of the PCG iteration, 2 FP64
+  // true-residual arithmetic of the mixed solve.
+  cudaError_t gemm64(bool a_trans, const double* scale, const double* B, double* out_part,
+                     const DevScalars* skip, int cat) {
+    cudaEvent_t b = cat && tm ? tm->begin() : nullptr;
+    cudaError_t e = launch_gemm_skinny<double, double>(P->kern->UK64, P->n, a_trans, scale, B, P->n,
+                                                       out_part, P->n, split_stride(), P->n, P->r,
+                                                       P->nsplit, skip, st);
+    if (cat && tm) tm->end(b, cat == 1 ? tm->gemm : tm->gemm64);
+    ++launches;
+    return e;
+  }
+  cudaError_t gemm32(bool a_trans, const double* scale, const float* B, float* out_part,
+                     const DevScalars* skip) {
+    cudaEvent_t b = tm ? tm->begin() : nullptr;
+    cudaError_t e = launch_gemm_skinny<float, float>(P->kern->UK32, P->n, a_trans, scale, B, P->n,
+                                                     out_part, P->n, split_stride(), P->n, P->r,
+                                                     P->nsplit, skip, st);
+    if (tm) tm->end(b, tm->gemm);
+    ++launches;
+    return e;
+  }
+  template <typename TC, typename TO>
+  cudaError_t combine(int mode, const TC* C, const double* V, const double* Bv, TO* out,
+                      DevScalars* s, const DevScalars* skip) {
+    ++launches;
+    return launch_combine<TC, TO>(mode, C, split_stride(), P->nsplit, P->n, P->r, P->kern->dK, V,
+                                  Bv, out, s, P->red, skip, st);
+  }
+  template <typename T>
+  cudaError_t gds(const T* Z, const T* Xh, T* Y, const DevScalars* skip, int cat) {
+    cudaEvent_t b = (cat && tm) ? tm->begin() : nullptr;
+    cudaError_t e = launch_gds<T>(pieces(), Z, P->zld, P->r, Xh, P->n, nullptr, (T*)P->gds_partial,
+                                  Y, P->n, skip, P->ctx->num_sms, st);
+    if (cat && tm) tm->end(b, cat == 1 ? tm->gds : tm->gds64);
+    ++launches;
+    return e;
+  }
+
+  // FP64 operator in the eigenbasis: out = Abar xin (mode CM_APPLY) or the
+  // true residual res = bbar - Abar xin (mode CM_RESID).
+  cudaError_t op64(int mode, const double* xin, double* out, DevScalars* s,
+                   const DevScalars* skip, int cat) {
+    double* Cp = (double*)P->cpart;
+    cudaError_t e;
+    if ((e = gemm64(true, P->kern->dK, xin, Cp, skip, cat)) != cudaSuccess) return e;
+    if ((e = combine<double, double>(CM_STORE, Cp, nullptr, nullptr, P->xh64, s, skip)) != cudaSuccess) return e;
+    if ((e = gds<double>(P->z64, P->xh64, P->y164, skip, cat)) != cudaSuccess) return e;
+    if ((e = gemm64(false, nullptr, P->y164, Cp, skip, cat)) != cudaSuccess) return e;
+    return combine<double, double>(mode, Cp, xin, P->bbar, out, s, skip);
+  }
+  // FP32 operator (mixed): pop32 holds the FP32 copy of xin.
+  cudaError_t op32(const double* xin, double* out, DevScalars* s, const DevScalars* skip) {
+    float* Cp = (float*)P->cpart;
+    cudaError_t e;
+    if ((e = gemm32(true, P->kern->dK, P->pop32, Cp, skip)) != cudaSuccess) return e;
+    if ((e = combine<float, float>(CM_STORE, Cp, nullptr, nullptr, P->xh32, s, skip)) != cudaSuccess) return e;
+    if ((e = gds<float>(P->z32, P->xh32, P->y132, skip, 1)) != cudaSuccess) return e;
+    if ((e = gemm32(false, nullptr, P->y132, Cp, skip)) != cudaSuccess) return e;
+    return combine<float, double>(CM_APPLY, Cp, xin, nullptr, out, s, skip);
+  }
+
+  // One PCG iteration (operator, update + preconditioner, direction).
+  cudaError_t iteration(bool mixed) {
+    DevScalars* s = P->s;
+    cudaError_t e;
+    if (mixed) {
+      if ((e = op32(P->p, P->y, s, s)) != cudaSuccess) return e;
+      ++launches;
+      if ((e = launch_update_precond<float>(UP_ITER, P->n, P->r, P->x, P->res, P->p, P->y, P->z,
+                                            P->UV32, P->D32, s, P->red, st)) != cudaSuccess)
+        return e;
+      ++launches;
+      return launch_pupdate<float>(P->n, P->r, P->z, P->p, P->pop32, s, st);
+    }
+    if ((e = op64(CM_APPLY, P->p, P->y, s, s, 1)) != cudaSuccess) return e;
+    ++launches;
+    if ((e = launch_update_precond<double>(UP_ITER, P->n, P->r, P->x, P->res, P->p, P->y, P->z,
+                                           P->UV, P->D64, s, P->red, st)) != cudaSuccess)
+      return e;
+    ++launches;
+    return launch_pupdate<double>(P->n, P->r, P->z, P->p, nullptr, s, st);
+  }
+
+  // FP64 true residual of x, then a restart from it (p = z).
+  cudaError_t true_residual_restart(bool mixed) {
+    DevScalars* s = P->s;
+    cudaError_t e;
+    if ((e = op64(CM_RESID, P->x, P->res, s, nullptr, mixed ? 2 : 1)) != cudaSuccess) return e;
+    return restart(mixed);
+  }
+  cudaError_t restart(bool mixed) {
+    DevScalars* s = P->s;
+    cudaError_t e;
+    launches += 2;
+    if (mixed) {
+      if ((e = launch_update_precond<float>(UP_RESTART, P->n, P->r, P->x, P->res, P->p, P->y,
+                                            P->z, P->UV32, P->D32, s, P->red, st)) != cudaSuccess)
+        return e;
+      return launch_pupdate<float>(P->n, P->r, P->z, P->p, P->pop32, s, st);
+    }
+    if ((e = launch_update_precond<double>(UP_RESTART, P->n, P->r, P->x, P->res, P->p, P->y, P->z,
+                                           P->UV, P->D64, s, P->red, st)) != cudaSuccess)
+      return e;
+    return launch_pupdate<double>(P->n, P->r, P->z, P->p, nullptr, s, st);
+  }
+};
+
+int check_params(cphifi_ctx* ctx, const cphifi_params* prm) {
+  if (!prm) return fail(ctx, CPHIFI_E_INVALID_ARG, "null params");
+  if (!(prm->lambda >= 0.0) || !std::isfinite(prm->lambda))
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "lambda must be finite and >= 0");
+  if (!(prm->rho > 0.0) || !std::isfinite(prm->rho))
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "rho must be finite and > 0");
+  if (!(prm->tol > 0.0) || !std::isfinite(prm->tol))
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "tol must be finite and > 0");
+  if (prm->max_iter < 0) return fail(ctx, CPHIFI_E_INVALID_ARG, "max_iter must be >= 0");
+  if (prm->precision < CPHIFI_FP64 || prm->precision > CPHIFI_MIXED_BF16)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
+  if (prm->precision == CPHIFI_MIXED_TF32 || prm->precision == CPHIFI_MIXED_BF16)
+    return fail(ctx, CPHIFI_E_UNSUPPORTED, "tensor-core operator not built");
+  return CPHIFI_OK;
+}
+
+int ensure_lowp(cphifi_problem* P) {
+  cphifi_ctx* ctx = P->ctx;
+  if (P->z32) return CPHIFI_OK;
+  const size_t bytes = (size_t)P->q * P->r * sizeof(float);
+  if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+    return fail(ctx, CPHIFI_E_ADMISSION, "FP32 operator data exceeds the HBM budget");
+  CK(dalloc(P, &P->z32, (size_t)P->q * P->r));
+  CK(launch_convert<double, float>(P->z64, P->z32, P->q * (int64_t)P->r, ctx->stream));
+  return CPHIFI_OK;
+}
+
+}  // namespace
+
+extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm, const double* W0,
+                                    double* W_out, int mem, cphifi_stats* stats) {
+  if (!P) return CPHIFI_E_INVALID_ARG;
+  cphifi_ctx* ctx = P->ctx;
+  int rc = check_params(ctx, prm);
+  if (rc != CPHIFI_OK) return rc;
+  if (!W_out) return fail(ctx, CPHIFI_E_INVALID_ARG, "null W_out");
+  if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
+  Enter guard(ctx);
+  const bool mixed = prm->precision != CPHIFI_FP64;
+  if (mixed && (rc = ensure_lowp(P)) != CPHIFI_OK) return rc;
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = ctx->stream;
+  const int n = P->n, r = P->r;
+  const size_t nr = (size_t)n * r;
+  Timer tm(ctx, prm->profile != 0);
+  Launcher L{P, st, &tm};
+
+  DevScalars h{};
+  h.tol2 = prm->tol * prm->tol;
+  h.lam = prm->lambda;
+  h.rho = prm->rho;
+  h.max_iter = prm->max_iter;
+  h.mode = mixed ? 1 : 0;
+  CK(cudaMemcpyAsync(P->s, &h, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
+  CK(launch_build_D(P->kern->dK, P->dV, n, r, P->gamma, prm->lambda, prm->rho, P->D64, P->D32, st));
+  // right-hand side in the eigenbasis: bbar = D_K U_K' B, and ||bbar||^2
+  CK(L.gemm64(false, nullptr, P->Bm, (double*)P->cpart, nullptr, 0));
+  CK(L.combine<double, double>(CM_DK_NORM, (double*)P->cpart, nullptr, nullptr, P->bbar, P->s, nullptr));
+  // start: x = U_K' W0 (or 0) and its true residual
+  if (W0) {
+    CK(upload(P->tmp64, W0, nr * sizeof(double), mem, st));
+    CK(L.gemm64(false, nullptr, P->tmp64, (double*)P->cpart, nullptr, 0));
+    CK(L.combine<double, double>(CM_STORE, (double*)P->cpart, nullptr, nullptr, P->x, P->s, nullptr));
+    CK(L.op64(CM_RESID, P->x, P->res, P->s, nullptr, 0));
+  } else {
+    CK(cudaMemsetAsync(P->x, 0, nr * sizeof(double), st));
+    CK(cudaMemcpyAsync(P->res, P->bbar, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  CK(L.restart(mixed));
+  DevScalars* hs = ctx->h_scalars;
+  CK(cudaMemcpyAsync(hs, P->s, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+
+  int status = CPHIFI_OK;
+  bool converged = false;
+  if (hs->bb == 0.0) {
+    converged = true;  // b = 0: W = 0 solves the system exactly
+    CK(cudaMemsetAsync(P->x, 0, nr * sizeof(double), st));
+  } else if (W0 && hs->done) {
+    converged = true;  // the warm start already meets the tolerance
+  } else {
+    const int cycle = mixed ? std::max(1, prm->k_replace) : std::max(1, prm->check_every);
+    // Every pass either adds iterations or ends the loop; the bound is a
+    // second guarantee that the host loop terminates.
+    for (int64_t pass = 0; pass <= (int64_t)prm->max_iter + 2; ++pass) {
+      const int left = prm->max_iter - hs->iter;
+      if (left <= 0) break;
+      const int m = std::min(cycle, left);
+      for (int k = 0; k < m; ++k) CK(L.iteration(mixed));
+      if (mixed) CK(L.true_residual_restart(true));
+      CK(cudaMemcpyAsync(hs, P->s, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (hs->status) break;
+      if (mixed) {
+        if (hs->done) { converged = true; break; }
+        continue;
+      }
+      if (hs->done) {
+        // FP64: the recurrence met tol; confirm with the true residual and
+        // restart from it if it does not (one refinement step).
+        CK(L.true_residual_restart(false));
+        CK(cudaMemcpyAsync(hs, P->s, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (hs->status) break;
+        if (hs->done) { converged = true; break; }
+      }
+    }
+    if (!converged && !hs->status) {
+      // final true residual of the returned iterate
+      CK(L.op64(CM_RESID, P->x, P->res, P->s, nullptr, 0));
+      CK(cudaMemcpyAsync(hs, P->s, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (hs->done) converged = true;
+    }
+    if (hs->status) status = hs->status;
+    else if (!converged) status = CPHIFI_E_NOT_CONVERGED;
+  }
+  // W = U_K Wbar
+  CK(L.gemm64(true, nullptr, P->x, (double*)P->cpart, nullptr, 0));
+  double* Wdev = (mem == CPHIFI_MEM_DEVICE) ? W_out : P->tmp64;
+  CK(L.combine<double, double>(CM_STORE, (double*)P->cpart, nullptr, nullptr, Wdev, P->s, nullptr));
+  if (mem != CPHIFI_MEM_DEVICE) CK(download(W_out, Wdev, nr * sizeof(double), mem, st));
+  CK(cudaStreamSynchronize(st));
+  auto t1 = std::chrono::steady_clock::now();
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->status = status;
+    stats->iterations = hs->iter;
+    stats->true_residuals = hs->true_evals;
+    stats->restarts = hs->restarts;
+    const double bn = std::sqrt(hs->bb);
+    stats->rel_residual = hs->bb > 0 ? std::sqrt(hs->true_rr) / bn : 0.0;
+    if (hs->true_evals == 0) stats->rel_residual = hs->bb > 0 ? std::sqrt(hs->rr) / bn : 0.0;
+    stats->rel_residual_recurrence = hs->bb > 0 ? std::sqrt(hs->rr) / bn : 0.0;
+    stats->solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    stats->kernel_launches = L.launches;
+    stats->setup_launches = P->create_launches;
+    if (tm.on) {
+      stats->gds_ms = Timer::total(tm.gds);
+      stats->gds_launches = (int)tm.gds.size();
+      stats->gemm_ms = Timer::total(tm.gemm);
+      stats->gemm_launches = (int)tm.gemm.size();
+      stats->gds64_ms = Timer::total(tm.gds64);
+      stats->gds64_launches = (int)tm.gds64.size();
+      stats->gemm64_ms = Timer::total(tm.gemm64);
+      stats->gemm64_launches = (int)tm.gemm64.size();
+    }
+  }
+  if (status != CPHIFI_OK)
+    ctx->last_error = std::string("solve: ") + cphifi_status_string(status);
+  return status;
+}
+
+extern "C" int cphifi_solve(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
+                            const int64_t* other_sizes, const double* const* factors, int32_t r,
+                            int64_t q, const int32_t* kidx, const int32_t* oidx,
+                            const double* vals, uint32_t flags, const cphifi_params* params,
+                            const double* W0, double* W_out, int mem, cphifi_stats* stats) {
+  if (!ctx) return CPHIFI_E_INVALID_ARG;
+  int rc = check_params(ctx, params);
+  if (rc != CPHIFI_OK) return rc;
+  if (params->precision != CPHIFI_FP64) flags |= CPHIFI_NEED_LOWP;
+  auto t0 = std::chrono::steady_clock::now();
+  cphifi_problem* P = nullptr;
+  rc = cphifi_problem_create(ctx, kern, d_other, other_sizes, factors, r, q, kidx, oidx, vals,
+                             flags, mem, &P);
+  if (rc != CPHIFI_OK) return rc;
+  auto t1 = std::chrono::steady_clock::now();
+  rc = cphifi_problem_solve(P, params, W0, W_out, mem, stats);
+  if (stats) stats->setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  std::string keep = ctx->last_error;
+  cphifi_problem_destroy(P);
+  ctx->last_error = keep;
+  return rc;
+}
+
+// ------------------------------------------------- step-by-step calls -----
+extern "C" int cphifi_problem_rhs(cphifi_problem* P, double* B_out, double* b_out, int mem) {
+  if (!P) return CPHIFI_E_INVALID_ARG;
+  cphifi_ctx* ctx = P->ctx;
+  Enter guard(ctx);
+  cudaStream_t st = ctx->stream;
+  const size_t nr = (size_t)P->n * P->r;
+  Launcher L{P, st, nullptr};
+  if (B_out) CK(download(B_out, P->Bm, nr * sizeof(double), mem, st));
+  if (b_out) {
+    // b = vec(K B) = U_K D_K U_K' B
+    CK(L.gemm64(false, nullptr, P->Bm, (double*)P->cpart, nullptr, 0));
+    CK(L.combine<double, double>(CM_DK, (double*)P->cpart, nullptr, nullptr, P->tmp64b, P->s2, nullptr));
+    CK(L.gemm64(true, nullptr, P->tmp64b, (double*)P->cpart, nullptr, 0));
+    CK(L.combine<double, double>(CM_STORE, (double*)P->cpart, nullptr, nullptr, P->tmp64, P->s2, nullptr));
+    CK(download(b_out, P->tmp64, nr * sizeof(double), mem, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return CPHIFI_OK;
+}
+
+extern "C" int cphifi_problem_matvec(cphifi_problem* P, int precision, double lambda, double rho,
+                                     const double* X, double* Y, int mem) {
+  if (!P || !X || !Y) return CPHIFI_E_INVALID_ARG;
+  cphifi_ctx* ctx = P->ctx;
+  if (precision != CPHIFI_FP64 && precision != CPHIFI_MIXED_FP32)
+    return fail(ctx, precision >= 0 && precision <= CPHIFI_MIXED_BF16 ? CPHIFI_E_UNSUPPORTED
+                                                                        : CPHIFI_E_INVALID_ARG,
+                "matvec precision");
+  Enter guard(ctx);
+  int rc;
+  if (precision != CPHIFI_FP64 && (rc = ensure_lowp(P)) != CPHIFI_OK) return rc;
+  cudaStream_t st = ctx->stream;
+  const size_t nr = (size_t)P->n * P->r;
+  Launcher L{P, st, nullptr};
+  DevScalars h{};
+  h.lam = lambda;
+  h.rho = rho;
+  h.rz = 1.0;
+  CK(cudaMemcpyAsync(P->s2, &h, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
+  CK(upload(P->tmp64, X, nr * sizeof(double), mem, st));
+  // xbar = U_K' X
+  CK(L.gemm64(false, nullptr, P->tmp64, (double*)P->cpart, nullptr, 0));
+  CK(L.combine<double, double>(CM_STORE, (double*)P->cpart, nullptr, nullptr, P->tmp64b, P->s2, nullptr));
+  if (precision == CPHIFI_FP64) {
+    CK(L.op64(CM_APPLY, P->tmp64b, P->y, P->s2, nullptr, 0));
+  } else {
+    CK(launch_convert<double, float>(P->tmp64b, P->pop32, (int64_t)nr, st));
+    CK(L.op32(P->tmp64b, P->y, P->s2, nullptr));
+  }
+  // Y = U_K ybar
+  CK(L.gemm64(true, nullptr, P->y, (double*)P->cpart, nullptr, 0));
+  CK(L.combine<double, double>(CM_STORE, (double*)P->cpart, nullptr, nullptr, P->tmp64, P->s2, nullptr));
+  CK(download(Y, P->tmp64, nr * sizeof(double), mem, st));
+  CK(cudaStreamSynchronize(st));
+  return CPHIFI_OK;
+}
+
+extern "C" int cphifi_problem_gds(cphifi_problem* P, int precision, const double* Xhat, double* Y1,
+                                  int mem) {
+  if (!P || !Xhat || !Y1) return CPHIFI_E_INVALID_ARG;
+  cphifi_ctx* ctx = P->ctx;
+  if (precision < CPHIFI_FP64 || precision > CPHIFI_MIXED_BF16)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
+  Enter guard(ctx);
+  int rc;
+  if (precision != CPHIFI_FP64 && (rc = ensure_lowp(P)) != CPHIFI_OK) return rc;
+  cudaStream_t st = ctx->stream;
+  const size_t nr = (size_t)P->n * P->r;
+  Launcher L{P, st, nullptr};
+  CK(upload(P->xh64, Xhat, nr * sizeof(double), mem, st));
+  if (precision == CPHIFI_FP64) {
+    CK(L.gds<double>(P->z64, P->xh64, P->y164, nullptr, 0));
+  } else {
+    CK(launch_convert<double, float>(P->xh64, P->xh32, (int64_t)nr, st));
+    CK(L.gds<float>(P->z32, P->xh32, P->y132, nullptr, 0));
+    CK(launch_convert<float, double>(P->y132, P->y164, (int64_t)nr, st));
+  }
+  CK(download(Y1, P->y164, nr * sizeof(double), mem, st));
+  CK(cudaStreamSynchronize(st));
+  return CPHIFI_OK;
+}
+
+extern "C" int cphifi_problem_precond(cphifi_problem* P, double lambda, double rho, const double* X,
+                                      double* Y, int mem) {
+  if (!P || !X || !Y) return CPHIFI_E_INVALID_ARG;
+  cphifi_ctx* ctx = P->ctx;
+  if (!(rho > 0.0) || !(lambda >= 0.0)) return fail(ctx, CPHIFI_E_INVALID_ARG, "lambda/rho");
+  Enter guard(ctx);
+  cudaStream_t st = ctx->stream;
+  const size_t nr = (size_t)P->n * P->r;
+  Launcher L{P, st, nullptr};
+  CK(launch_build_D(P->kern->dK, P->dV, P->n, P->r, P->gamma, lambda, rho, P->D64, P->D32, st));
+  CK(upload(P->tmp64, X, nr * sizeof(double), mem, st));
+  CK(L.gemm64(false, nullptr, P->tmp64, (double*)P->cpart, nullptr, 0));
+  CK(L.combine<double, double>(CM_STORE, (double*)P->cpart, nullptr, nullptr, P->tmp64b, P->s2, nullptr));
+  CK(launch_precond_only(P->n, P->r, P->tmp64b, P->tmp64, P->UV, P->D64, st));
+  CK(L.gemm64(true, nullptr, P->tmp64, (double*)P->cpart, nullptr, 0));
+  CK(L.combine<double, double>(CM_STORE, (double*)P->cpart, nullptr, nullptr, P->tmp64b, P->s2, nullptr));
+  CK(download(Y, P->tmp64b, nr * sizeof(double), mem, st));
+  CK(cudaStreamSynchronize(st));
+  return CPHIFI_OK;
+}
+
+extern "C" int cphifi_problem_gram(cphifi_problem* P, double* V, double* DV, double* UV) {
+  if (!P) return CPHIFI_E_INVALID_ARG;
+  cphifi_ctx* ctx = P->ctx;
+  Enter guard(ctx);
+  cudaStream_t st = ctx->stream;
+  const size_t rr = (size_t)P->r * P->r;
+  if (V) CK(cudaMemcpyAsync(V, P->V, rr * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (DV) CK(cudaMemcpyAsync(DV, P->dV, P->r * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (UV) CK(cudaMemcpyAsync(UV, P->UV, rr * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return CPHIFI_OK;
+}
+
+extern "C" int cphifi_problem_order(cphifi_problem* P, int32_t* perm, int64_t* row_ptr) {
+  if (!P) return CPHIFI_E_INVALID_ARG;
+  cphifi_ctx* ctx = P->ctx;
+  Enter guard(ctx);
+  cudaStream_t st = ctx->stream;
+  if (perm) CK(cudaMemcpyAsync(perm, P->perm, P->q * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  if (row_ptr)
+    CK(cudaMemcpyAsync(row_ptr, P->row_ptr, (P->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return CPHIFI_OK;
+}

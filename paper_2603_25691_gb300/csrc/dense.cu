@@ -1,0 +1,137 @@
+// Skinny dense products with the kernel eigenbasis (§4.4.1 "K X" and
+// "K Yhat1", §4.4.2 "U_K' X", "U_K S"): C = op(A) diag(s) B where A is the
+// n x n eigenvector matrix U_K, B is n x r (r <= 64) and s an optional
+// per-row scale of B (the eigenvalues D_K).  op(A)(i,k) is read as
+// A[k*lda + i] when a_trans is true (A column-major, i.e. U_K itself) and as
+// A[i*lda + k] otherwise (U_K').  The k-range is split so that the grid
+// covers every SM; partial products are combined (and the elementwise tail
+// of the operator applied) by the combine kernel in cg.cu.
+//
+// SIMT FP64/FP32 version: 256 threads, a 128 x r tile of C per block,
+// 32-wide (FP32) or 16-wide (FP64) k slabs staged through shared memory.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "launch.h"
+
+namespace cphifi {
+
+template <typename TA, typename TC, bool ATRANS, bool SCALEB>
+__global__ void __launch_bounds__(256)
+gemm_skinny_kernel(const TA* __restrict__ A, int64_t lda, const double* __restrict__ sk,
+                   const TC* __restrict__ B, int64_t ldb, TC* __restrict__ C, int64_t ldc,
+                   int64_t split_stride, int n, int ncols, int kchunk, const DevScalars* skip) {
+  if (dev_skip(skip)) return;
+  // 16-wide k slabs in FP64 keep the static shared memory under 48 KB.
+  constexpr int BM = 128, BK = sizeof(TC) == 8 ? 16 : 32, TM = BM / 32, TNMAX = 8;
+  __shared__ TC As[BK][BM + 1];
+  __shared__ TC Bs[BK][64];
+  const int tid = threadIdx.x;
+  const int ty = tid & 31;       // row group: rows ty, ty+32, ty+64, ty+96
+  const int tx = tid >> 5;       // column group
+  const int tn = (ncols + 7) / 8;  // columns per thread (<= 8)
+  const int i0 = blockIdx.x * BM;
+  const int kbeg = blockIdx.y * kchunk;
+  const int kend = min(n, kbeg + kchunk);
+  TC acc[TM][TNMAX];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TNMAX; ++b) acc[a][b] = TC(0);
+
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    if (ATRANS) {
+      for (int idx = tid; idx < BM * BK; idx += 256) {
+        const int ii = idx % BM, kk = idx / BM;
+        const int i = i0 + ii, k = k0 + kk;
+        As[kk][ii] = (i < n && k < kend) ? TC(A[(int64_t)k * lda + i]) : TC(0);
+      }
+    } else {
+      for (int idx = tid; idx < BM * BK; idx += 256) {
+        const int kk = idx % BK, ii = idx / BK;
+        const int i = i0 + ii, k = k0 + kk;
+        As[kk][ii] = (i < n && k < kend) ? TC(A[(int64_t)i * lda + k]) : TC(0);
+      }
+    }
+    for (int idx = tid; idx < BK * 64; idx += 256) {
+      const int kk = idx % BK, j = idx / BK;
+      const int k = k0 + kk;
+      TC v = TC(0);
+      if (k < kend && j < ncols) {
+        v = B[(int64_t)j * ldb + k];
+        if (SCALEB) v = TC(double(v) * sk[k]);
+      }
+      Bs[kk][j] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < BK; ++kk) {
+      TC a[TM], b[TNMAX];
+#pragma unroll
+      for (int m = 0; m < TM; ++m) a[m] = As[kk][ty + 32 * m];
+#pragma unroll
+      for (int c = 0; c < TNMAX; ++c) b[c] = c < tn ? Bs[kk][tx * tn + c] : TC(0);
+#pragma unroll
+      for (int m = 0; m < TM; ++m)
+#pragma unroll
+        for (int c = 0; c < TNMAX; ++c) acc[m][c] = fma(a[m], b[c], acc[m][c]);
+    }
+    __syncthreads();
+  }
+  TC* Cs = C + (int64_t)blockIdx.y * split_stride;
+#pragma unroll
+  for (int m = 0; m < TM; ++m) {
+    const int i = i0 + ty + 32 * m;
+    if (i >= n) continue;
+#pragma unroll
+    for (int c = 0; c < TNMAX; ++c) {
+      const int j = tx * tn + c;
+      if (c < tn && j < ncols) Cs[(int64_t)j * ldc + i] = acc[m][c];
+    }
+  }
+}
+
+int gemm_pick_split(int n, int num_sms) {
+  const int mt = (n + 127) / 128;
+  int s = (2 * num_sms + mt - 1) / mt;
+  const int kslabs = (n + 31) / 32;
+  if (s > kslabs) s = kslabs;
+  if (s > 32) s = 32;
+  if (s < 1) s = 1;
+  return s;
+}
+
+template <typename TA, typename TC>
+cudaError_t launch_gemm_skinny(const TA* A, int64_t lda, bool a_trans, const double* scale_k,
+                               const TC* B, int64_t ldb, TC* C, int64_t ldc,
+                               int64_t split_stride, int n, int ncols, int nsplit,
+                               const DevScalars* skip, cudaStream_t st) {
+  if (n == 0 || ncols == 0) return cudaSuccess;
+  if (ncols > 64) return cudaErrorInvalidValue;
+  int kchunk = (n + nsplit - 1) / nsplit;
+  kchunk = (kchunk + 31) / 32 * 32;
+  const dim3 grid((n + 127) / 128, nsplit);
+  if (a_trans) {
+    if (scale_k)
+      gemm_skinny_kernel<TA, TC, true, true><<<grid, 256, 0, st>>>(A, lda, scale_k, B, ldb, C, ldc, split_stride, n, ncols, kchunk, skip);
+    else
+      gemm_skinny_kernel<TA, TC, true, false><<<grid, 256, 0, st>>>(A, lda, scale_k, B, ldb, C, ldc, split_stride, n, ncols, kchunk, skip);
+  } else {
+    if (scale_k)
+      gemm_skinny_kernel<TA, TC, false, true><<<grid, 256, 0, st>>>(A, lda, scale_k, B, ldb, C, ldc, split_stride, n, ncols, kchunk, skip);
+    else
+      gemm_skinny_kernel<TA, TC, false, false><<<grid, 256, 0, st>>>(A, lda, scale_k, B, ldb, C, ldc, split_stride, n, ncols, kchunk, skip);
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_gemm_skinny<double, double>(const double*, int64_t, bool, const double*,
+                                                        const double*, int64_t, double*, int64_t,
+                                                        int64_t, int, int, int, const DevScalars*,
+                                                        cudaStream_t);
+template cudaError_t launch_gemm_skinny<float, float>(const float*, int64_t, bool, const double*,
+                                                      const float*, int64_t, float*, int64_t,
+                                                      int64_t, int, int, int, const DevScalars*,
+                                                      cudaStream_t);
+
+}  // namespace cphifi

@@ -1,0 +1,122 @@
+// Host-side launchers of the solver's kernels (one declaration per kernel
+// family; definitions live beside the kernels).  All take a stream and
+// return the cudaError_t of the launch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace cphifi {
+
+// ---------------------------------------------------------------- obs.cu ---
+// Range / finiteness checks of the observation lists; sets *err (int) to a
+// non-zero code on a bad index (1) or a non-finite value (2).
+cudaError_t launch_validate_obs(const int32_t* kidx, const int32_t* oidx,
+                                const double* vals, int64_t q, int n,
+                                int d_other, const int64_t* other_sizes_dev,
+                                int* err, cudaStream_t st);
+cudaError_t launch_validate_dense(const double* a, int64_t count, int* err,
+                                  cudaStream_t st);
+// Stable LSD radix sort of (key, value) pairs by key < 2^key_bits.
+// tmp must hold radix_sort_tmp_bytes(q) bytes.  On return keys/vals hold the
+// sorted sequence.
+size_t radix_sort_tmp_bytes(int64_t q);
+cudaError_t radix_sort_pairs(uint32_t* keys, int32_t* vals, int64_t q,
+                             int key_bits, void* tmp, cudaStream_t st);
+cudaError_t launch_iota(int32_t* v, int64_t q, cudaStream_t st);
+// Sets bit 4 of *err when keys are not non-decreasing.
+cudaError_t launch_check_sorted(const uint32_t* keys, int64_t q, int* err, cudaStream_t st);
+cudaError_t launch_row_ptr(const uint32_t* sorted_keys, int64_t q, int n,
+                           int64_t* row_ptr, cudaStream_t st);
+// Pieces: every kernel index owns >= 1 piece of <= piece_len observations.
+cudaError_t launch_piece_counts(const int64_t* row_ptr, int n, int piece_len,
+                                int32_t* seg_count, cudaStream_t st);
+cudaError_t launch_piece_fill(const int64_t* row_ptr, int n,
+                              const int32_t* seg_first, const int32_t* seg_count,
+                              int32_t* pseg, int32_t* pbeg, int32_t* pend,
+                              cudaStream_t st);
+// Exclusive scan of int32 counts into int32 offsets (out has n+1 entries).
+cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n,
+                               void* tmp, size_t tmp_bytes, cudaStream_t st);
+size_t exclusive_scan_tmp_bytes(int64_t n);
+// Zhat (Eq. zhat) in sorted order, column-major q x r, FP64 and optional FP32.
+cudaError_t launch_zhat(const int32_t* perm, const int32_t* oidx, int d_other,
+                        const double* const* factors_dev, const int64_t* sizes_dev,
+                        int r, int64_t q, double* z64, float* z32, int64_t zld,
+                        const double* vals, double* vals_sorted, int* err,
+                        cudaStream_t st);
+// Gather-dot/scatter (Eqs. vl and yhat1).  with_dot = false computes the
+// sparse MTTKRP B(i,:) = sum t_l Zhat(l,:) with t taken from `tvals`.
+struct PieceList {
+  const int32_t* seg;
+  const int32_t* beg;
+  const int32_t* end;
+  const int32_t* seg_first;
+  const int32_t* seg_count;
+  unsigned* seg_ticket;
+  int npieces;
+};
+template <typename T>
+cudaError_t launch_gds(const PieceList& pl, const T* Z, int64_t zld, int r,
+                       const T* Xh, int64_t xld, const T* tvals, T* partial,
+                       T* Y, int64_t yld, const DevScalars* skip,
+                       int num_sms, cudaStream_t st);
+
+// -------------------------------------------------------------- dense.cu ---
+// Skinny product C = op(A) diag(s) B for A n x n (op = identity when a_trans
+// is true, transpose otherwise, see dense.cu), B n x ncols column-major; the
+// k-range is split over `nsplit` blocks of columns of A and the partial
+// products land in C + split * split_stride.
+template <typename TA, typename TC>
+cudaError_t launch_gemm_skinny(const TA* A, int64_t lda, bool a_trans,
+                               const double* scale_k, const TC* B, int64_t ldb,
+                               TC* C, int64_t ldc, int64_t split_stride,
+                               int n, int ncols, int nsplit,
+                               const DevScalars* skip, cudaStream_t st);
+int gemm_pick_split(int n, int num_sms);
+
+// ----------------------------------------------------------------- cg.cu ---
+cudaError_t launch_gram(const double* const* factors_dev, const int64_t* sizes_host,
+                        int d_other, int r, double* V, cudaStream_t st);
+cudaError_t launch_jacobi_eig(const double* V, int r, double* dV, double* UV,
+                              int max_sweeps, int* info, cudaStream_t st);
+cudaError_t launch_build_D(const double* dK, const double* dV, int n, int r,
+                           double gamma, double lam, double rho, double* D64,
+                           float* D32, cudaStream_t st);
+
+enum CombineMode {
+  CM_STORE = 0,  // out = sum_s C_s
+  CM_DK = 1,     // out = dK .* sum_s C_s
+  CM_APPLY = 2,  // out = dK .* sum_s C_s + (lam dK + rho) .* V; pAp -> alpha
+  CM_RESID = 3,  // out = Bv - (dK .* sum_s C_s + (lam dK + rho) .* V); ||out||^2 -> true residual
+  CM_DK_NORM = 4 // out = dK .* sum_s C_s; ||out||^2 -> bb (the right-hand side)
+};
+template <typename TC, typename TO>
+cudaError_t launch_combine(int mode, const TC* C, int64_t split_stride, int nsplit,
+                           int n, int r, const double* dK, const double* V,
+                           const double* Bv, TO* out, DevScalars* s,
+                           RedScratch red, const DevScalars* skip, cudaStream_t st);
+
+enum UpdateMode {
+  UP_ITER = 0,     // x += a p; r -= a y; z = M^-1 r; (r,z), ||r||^2 -> beta
+  UP_RESTART = 1   // z = M^-1 r; (r,z) -> rz, beta = 0
+};
+template <typename TP>
+cudaError_t launch_update_precond(int mode, int n, int r, double* x, double* rres,
+                                  const double* p, const double* y, double* z,
+                                  const TP* UV, const TP* D, DevScalars* s,
+                                  RedScratch red, cudaStream_t st);
+// p = z + beta p; and the operand of the next n x n product, in type TB.
+template <typename TB>
+cudaError_t launch_pupdate(int n, int r, const double* z, double* p, TB* pop,
+                           DevScalars* s, cudaStream_t st);
+cudaError_t launch_precond_only(int n, int r, const double* X, double* Y,
+                                const double* UV, const double* D, cudaStream_t st);
+template <typename TS, typename TD>
+cudaError_t launch_convert(const TS* src, TD* dst, int64_t count, cudaStream_t st);
+cudaError_t launch_scale_rows(const double* dK, const double* X, double* Y,
+                              int n, int r, cudaStream_t st);
+
+}  // namespace cphifi

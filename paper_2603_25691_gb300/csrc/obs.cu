@@ -1,0 +1,529 @@
+// Observation-side kernels: validation, the stable sort by kernel index, the
+// CSR row pointer, the piece list, Zhat (Eq. zhat, §4.2) and the fused
+// gather-dot/scatter of the matrix-free product (Eqs. vl and yhat1, §4.4.1).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "launch.h"
+
+namespace cphifi {
+
+// ----------------------------------------------------------- validation ---
+__global__ void validate_obs_kernel(const int32_t* __restrict__ kidx,
+                                    const int32_t* __restrict__ oidx,
+                                    const double* __restrict__ vals, int64_t q, int n,
+                                    int d_other, const int64_t* __restrict__ sizes,
+                                    int* err) {
+  int bad = 0;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < q;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k = kidx[l];
+    if (k < 0 || k >= n) bad |= 1;
+    for (int m = 0; m < d_other; ++m) {
+      const int32_t o = oidx[l * d_other + m];
+      if (o < 0 || o >= sizes[m]) bad |= 1;
+    }
+    if (!isfinite(vals[l])) bad |= 2;
+  }
+  if (bad) atomicOr(err, bad);
+}
+
+cudaError_t launch_validate_obs(const int32_t* kidx, const int32_t* oidx,
+                                const double* vals, int64_t q, int n, int d_other,
+                                const int64_t* sizes_dev, int* err, cudaStream_t st) {
+  if (q == 0) return cudaSuccess;
+  const int blocks = (int)((q + 255) / 256 < 4096 ? (q + 255) / 256 : 4096);
+  validate_obs_kernel<<<blocks, 256, 0, st>>>(kidx, oidx, vals, q, n, d_other, sizes_dev, err);
+  return cudaGetLastError();
+}
+
+__global__ void validate_dense_kernel(const double* __restrict__ a, int64_t count, int* err) {
+  int bad = 0;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < count;
+       l += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(a[l])) bad = 2;
+  if (bad) atomicOr(err, bad);
+}
+
+cudaError_t launch_validate_dense(const double* a, int64_t count, int* err, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  const int blocks = (int)((count + 255) / 256 < 2048 ? (count + 255) / 256 : 2048);
+  validate_dense_kernel<<<blocks, 256, 0, st>>>(a, count, err);
+  return cudaGetLastError();
+}
+
+__global__ void iota_kernel(int32_t* v, int64_t q) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < q;
+       l += (int64_t)gridDim.x * blockDim.x)
+    v[l] = (int32_t)l;
+}
+
+cudaError_t launch_iota(int32_t* v, int64_t q, cudaStream_t st) {
+  if (q == 0) return cudaSuccess;
+  const int blocks = (int)((q + 255) / 256 < 4096 ? (q + 255) / 256 : 4096);
+  iota_kernel<<<blocks, 256, 0, st>>>(v, q);
+  return cudaGetLastError();
+}
+
+__global__ void check_sorted_kernel(const uint32_t* __restrict__ keys, int64_t q, int* err) {
+  int bad = 0;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l + 1 < q;
+       l += (int64_t)gridDim.x * blockDim.x)
+    if (keys[l] > keys[l + 1]) bad = 4;
+  if (bad) atomicOr(err, bad);
+}
+
+cudaError_t launch_check_sorted(const uint32_t* keys, int64_t q, int* err, cudaStream_t st) {
+  if (q < 2) return cudaSuccess;
+  const int blocks = (int)((q + 255) / 256 < 4096 ? (q + 255) / 256 : 4096);
+  check_sorted_kernel<<<blocks, 256, 0, st>>>(keys, q, err);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------ exclusive scan ----
+// Three-phase scan of int32 counts: per-chunk sums, a scan of the chunk sums
+// by one block, then per-chunk scans with the chunk offset.  out[n] = total.
+constexpr int kScanChunk = 2048;  // 256 threads x 8 items
+
+__global__ void scan_chunk_sums(const int32_t* __restrict__ in, int64_t n, int64_t* sums) {
+  __shared__ double sm[32];
+  const int64_t base = blockIdx.x * (int64_t)kScanChunk;
+  double v[1] = {0.0};
+  for (int k = threadIdx.x; k < kScanChunk; k += blockDim.x) {
+    const int64_t i = base + k;
+    if (i < n) v[0] += (double)in[i];
+  }
+  block_sum<1>(v, sm);
+  if (threadIdx.x == 0) sums[blockIdx.x] = (int64_t)v[0];
+}
+
+__global__ void scan_sums_serial(int64_t* sums, int64_t nchunks) {
+  // One block: exclusive scan of the chunk sums in place, tile by tile.
+  __shared__ int64_t tile[1024];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t t0 = 0; t0 < nchunks; t0 += 1024) {
+    const int64_t i = t0 + threadIdx.x;
+    const int64_t v = i < nchunks ? sums[i] : 0;
+    tile[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const int64_t add = threadIdx.x >= o ? tile[threadIdx.x - o] : 0;
+      __syncthreads();
+      tile[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (i < nchunks) sums[i] = carry + tile[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += tile[1023];
+    __syncthreads();
+  }
+}
+
+__global__ void scan_chunks_final(const int32_t* __restrict__ in, int64_t n,
+                                  const int64_t* __restrict__ sums, int32_t* out) {
+  __shared__ int64_t ts[256];
+  const int64_t base = blockIdx.x * (int64_t)kScanChunk + threadIdx.x * 8;
+  int64_t loc[8];
+  int64_t run = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int64_t i = base + k;
+    loc[k] = run;
+    run += i < n ? in[i] : 0;
+  }
+  ts[threadIdx.x] = run;
+  __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {
+    const int64_t add = threadIdx.x >= o ? ts[threadIdx.x - o] : 0;
+    __syncthreads();
+    ts[threadIdx.x] += add;
+    __syncthreads();
+  }
+  const int64_t off = sums[blockIdx.x] + ts[threadIdx.x] - run;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int64_t i = base + k;
+    if (i < n) out[i] = (int32_t)(off + loc[k]);
+    if (i == n - 1) out[n] = (int32_t)(off + loc[k] + in[i]);
+  }
+}
+
+size_t exclusive_scan_tmp_bytes(int64_t n) {
+  return (size_t)((n + kScanChunk - 1) / kScanChunk + 1) * sizeof(int64_t);
+}
+
+cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, void* tmp,
+                               size_t tmp_bytes, cudaStream_t st) {
+  if (n == 0) return cudaMemsetAsync(out, 0, sizeof(int32_t), st);
+  const int64_t nchunks = (n + kScanChunk - 1) / kScanChunk;
+  if (tmp_bytes < exclusive_scan_tmp_bytes(n)) return cudaErrorInvalidValue;
+  int64_t* sums = (int64_t*)tmp;
+  scan_chunk_sums<<<(unsigned)nchunks, 256, 0, st>>>(in, n, sums);
+  scan_sums_serial<<<1, 1024, 0, st>>>(sums, nchunks);
+  scan_chunks_final<<<(unsigned)nchunks, 256, 0, st>>>(in, n, sums, out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------- LSD radix sort ---
+// 8-bit digits; a tile of 4096 keys per block (8 warps x 16 rounds x 32).
+// The scatter ranks each key among equal digits of its tile in input order
+// (warp match + per-warp counters + a scan over warps), so every pass is
+// stable and so is the whole sort.
+constexpr int kRsTile = 4096;
+
+__global__ void radix_hist_kernel(const uint32_t* __restrict__ keys, int64_t q, int shift,
+                                  uint32_t* hist, int ntiles) {
+  __shared__ uint32_t h[256];
+  for (int t = threadIdx.x; t < 256; t += blockDim.x) h[t] = 0;
+  __syncthreads();
+  const int64_t base = blockIdx.x * (int64_t)kRsTile;
+  for (int k = threadIdx.x; k < kRsTile; k += blockDim.x) {
+    const int64_t l = base + k;
+    if (l < q) atomicAdd(&h[(keys[l] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
+}
+
+__global__ void radix_scatter_kernel(const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin,
+                                     uint32_t* __restrict__ kout, int32_t* __restrict__ vout,
+                                     int64_t q, int shift, const int32_t* __restrict__ offs,
+                                     int ntiles) {
+  __shared__ uint32_t wcount[8][256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < 8 * 256; t += blockDim.x) (&wcount[0][0])[t] = 0;
+  __syncthreads();
+  const int64_t base = blockIdx.x * (int64_t)kRsTile + w * 512;
+  uint32_t key[16], rank[16];
+  int32_t val[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int64_t l = base + k * 32 + lane;
+    const bool valid = l < q;
+    key[k] = valid ? kin[l] : 0u;
+    val[k] = valid ? vin[l] : 0;
+    const uint32_t d = valid ? ((key[k] >> shift) & 255u) : 256u;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const unsigned lower = peers & ((1u << lane) - 1u);
+    const uint32_t before = valid ? wcount[w][d] : 0u;
+    __syncwarp();
+    if (valid && lower == 0u) wcount[w][d] = before + __popc(peers);
+    __syncwarp();
+    rank[k] = before + __popc(lower);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+    uint32_t run = 0;
+    for (int ww = 0; ww < 8; ++ww) {
+      const uint32_t c = wcount[ww][d];
+      wcount[ww][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int64_t l = base + k * 32 + lane;
+    if (l < q) {
+      const uint32_t d = (key[k] >> shift) & 255u;
+      const int64_t pos = (int64_t)offs[(int64_t)d * ntiles + blockIdx.x] + wcount[w][d] + rank[k];
+      kout[pos] = key[k];
+      vout[pos] = val[k];
+    }
+  }
+}
+
+size_t radix_sort_tmp_bytes(int64_t q) {
+  const int64_t ntiles = (q + kRsTile - 1) / kRsTile;
+  const int64_t nh = 256 * ntiles;
+  size_t b = 0;
+  b += (size_t)q * sizeof(uint32_t) + 256;        // alternate keys
+  b += (size_t)q * sizeof(int32_t) + 256;         // alternate values
+  b += (size_t)nh * sizeof(int32_t) + 256;        // histogram
+  b += (size_t)(nh + 1) * sizeof(int32_t) + 256;  // offsets
+  b += exclusive_scan_tmp_bytes(nh) + 256;
+  return b;
+}
+
+static inline char* align256(char* p) {
+  return (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
+}
+
+cudaError_t radix_sort_pairs(uint32_t* keys, int32_t* vals, int64_t q, int key_bits,
+                             void* tmp, cudaStream_t st) {
+  if (q <= 1) return cudaSuccess;
+  const int64_t ntiles = (q + kRsTile - 1) / kRsTile;
+  const int64_t nh = 256 * ntiles;
+  char* p = align256((char*)tmp);
+  uint32_t* k2 = (uint32_t*)p; p = align256(p + q * sizeof(uint32_t));
+  int32_t* v2 = (int32_t*)p; p = align256(p + q * sizeof(int32_t));
+  uint32_t* hist = (uint32_t*)p; p = align256(p + nh * sizeof(int32_t));
+  int32_t* offs = (int32_t*)p; p = align256(p + (nh + 1) * sizeof(int32_t));
+  void* scan_tmp = p;
+  const int passes = (key_bits + 7) / 8;
+  uint32_t *ka = keys, *kb = k2;
+  int32_t *va = vals, *vb = v2;
+  for (int ps = 0; ps < passes; ++ps) {
+    const int shift = 8 * ps;
+    radix_hist_kernel<<<(unsigned)ntiles, 256, 0, st>>>(ka, q, shift, hist, (int)ntiles);
+    cudaError_t e = exclusive_scan_i32((const int32_t*)hist, offs, nh, scan_tmp,
+                                       exclusive_scan_tmp_bytes(nh), st);
+    if (e != cudaSuccess) return e;
+    radix_scatter_kernel<<<(unsigned)ntiles, 256, 0, st>>>(ka, va, kb, vb, q, shift, offs, (int)ntiles);
+    uint32_t* tk = ka; ka = kb; kb = tk;
+    int32_t* tv = va; va = vb; vb = tv;
+  }
+  if (ka != keys) {
+    cudaMemcpyAsync(keys, ka, q * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(vals, va, q * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------- CSR and piece lists ----
+__global__ void row_ptr_kernel(const uint32_t* __restrict__ keys, int64_t q, int n,
+                               int64_t* row_ptr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  int64_t lo = 0, hi = q;  // first position with key >= i
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (keys[mid] < (uint32_t)i) lo = mid + 1; else hi = mid;
+  }
+  row_ptr[i] = lo;
+}
+
+cudaError_t launch_row_ptr(const uint32_t* sorted_keys, int64_t q, int n, int64_t* row_ptr,
+                           cudaStream_t st) {
+  row_ptr_kernel<<<(n + 1 + 255) / 256, 256, 0, st>>>(sorted_keys, q, n, row_ptr);
+  return cudaGetLastError();
+}
+
+__global__ void piece_counts_kernel(const int64_t* __restrict__ row_ptr, int n, int piece_len,
+                                    int32_t* seg_count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t len = row_ptr[i + 1] - row_ptr[i];
+  const int64_t c = (len + piece_len - 1) / piece_len;
+  seg_count[i] = (int32_t)(c > 0 ? c : 1);
+}
+
+cudaError_t launch_piece_counts(const int64_t* row_ptr, int n, int piece_len,
+                                int32_t* seg_count, cudaStream_t st) {
+  piece_counts_kernel<<<(n + 255) / 256, 256, 0, st>>>(row_ptr, n, piece_len, seg_count);
+  return cudaGetLastError();
+}
+
+__global__ void piece_fill_kernel(const int64_t* __restrict__ row_ptr, int n,
+                                  const int32_t* __restrict__ seg_first,
+                                  const int32_t* __restrict__ seg_count, int32_t* pseg,
+                                  int32_t* pbeg, int32_t* pend) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t b = row_ptr[i], e = row_ptr[i + 1];
+  const int c = seg_count[i];
+  const int64_t len = e - b;
+  const int64_t step = (len + c - 1) / c;  // balanced pieces of one segment
+  for (int k = 0; k < c; ++k) {
+    const int p = seg_first[i] + k;
+    int64_t pb = b + k * step, pe = pb + step;
+    if (pb > e) pb = e;
+    if (pe > e) pe = e;
+    pseg[p] = i;
+    pbeg[p] = (int32_t)pb;
+    pend[p] = (int32_t)pe;
+  }
+}
+
+cudaError_t launch_piece_fill(const int64_t* row_ptr, int n, const int32_t* seg_first,
+                              const int32_t* seg_count, int32_t* pseg, int32_t* pbeg,
+                              int32_t* pend, cudaStream_t st) {
+  piece_fill_kernel<<<(n + 255) / 256, 256, 0, st>>>(row_ptr, n, seg_first, seg_count, pseg,
+                                                     pbeg, pend);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- Zhat ------
+// Zhat(s, j) = prod_m A_m(oidx[perm[s], m], j) for the s-th observation in the
+// sorted order (Eq. zhat).  Factors are column-major n_m x r.
+__global__ void zhat_kernel(const int32_t* __restrict__ perm, const int32_t* __restrict__ oidx,
+                            int d_other, const double* const* __restrict__ factors,
+                            const int64_t* __restrict__ sizes, int r, int64_t q,
+                            double* __restrict__ z64, float* __restrict__ z32, int64_t zld,
+                            const double* __restrict__ vals, double* __restrict__ vals_sorted,
+                            int* err) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < q;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = perm ? perm[s] : s;
+    vals_sorted[s] = vals[l];
+    int32_t id[8];
+    bool ok = true;
+    for (int m = 0; m < d_other && m < 8; ++m) {
+      id[m] = oidx[l * d_other + m];
+      if (id[m] < 0 || id[m] >= sizes[m]) ok = false;
+    }
+    if (!ok) atomicOr(err, 1);
+    for (int j = 0; j < r; ++j) {
+      double v = 1.0;
+      if (ok) {
+        for (int m = 0; m < d_other; ++m) {
+          const int32_t im = m < 8 ? id[m] : oidx[l * d_other + m];
+          v *= factors[m][(int64_t)j * sizes[m] + im];
+        }
+      } else {
+        v = 0.0;
+      }
+      z64[j * zld + s] = v;
+      if (z32) z32[j * zld + s] = (float)v;
+    }
+  }
+}
+
+cudaError_t launch_zhat(const int32_t* perm, const int32_t* oidx, int d_other,
+                        const double* const* factors_dev, const int64_t* sizes_dev, int r,
+                        int64_t q, double* z64, float* z32, int64_t zld, const double* vals,
+                        double* vals_sorted, int* err, cudaStream_t st) {
+  if (q == 0) return cudaSuccess;
+  const int blocks = (int)((q + 255) / 256 < 8192 ? (q + 255) / 256 : 8192);
+  zhat_kernel<<<blocks, 256, 0, st>>>(perm, oidx, d_other, factors_dev, sizes_dev, r, q, z64,
+                                      z32, zld, vals, vals_sorted, err);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------ gather-dot / scatter ----
+// One warp per piece (a run of sorted observations that share the kernel
+// index i).  Lane t takes observations b+t, b+t+32, ...: it loads Zhat(l, :)
+// column by column (coalesced across the warp), forms
+// xbar_l = Xhat(i,:).Zhat(l,:) (Eq. vl) and accumulates xbar_l Zhat(l,:) in
+// registers (Eq. yhat1).  The warp then sums its 32 partial rows; a kernel
+// index with one piece writes Yhat1(i,:) directly, otherwise each piece stores
+// its row and the last piece to finish (per-index ticket) adds the pieces in
+// piece order.  No floating-point atomics: the result is deterministic.
+// RP is the register width (>= r); KEEPZ keeps the loaded row in registers
+// between the dot and the update, otherwise the update reloads it (L1 hit).
+template <typename T, int RP, bool WITH_DOT, bool KEEPZ>
+__global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const T* __restrict__ Z,
+                                                  int64_t zld, int r, const T* __restrict__ Xh,
+                                                  int64_t xld, const T* __restrict__ tvals,
+                                                  T* __restrict__ partial, T* __restrict__ Y,
+                                                  int64_t yld, const DevScalars* skip) {
+  if (dev_skip(skip)) return;
+  __shared__ T xs[8][RP];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int p = warp; p < pl.npieces; p += nwarps) {
+    const int seg = pl.seg[p];
+    const int b = pl.beg[p], e = pl.end[p];
+    if (WITH_DOT) {
+      __syncwarp();
+      for (int j = lane; j < RP; j += 32) xs[wib][j] = j < r ? Xh[(int64_t)j * xld + seg] : T(0);
+      __syncwarp();
+    }
+    T acc[RP];
+#pragma unroll
+    for (int j = 0; j < RP; ++j) acc[j] = T(0);
+    for (int l = b + lane; l < e; l += 32) {
+      T xb;
+      if (KEEPZ) {
+        T z[RP];
+#pragma unroll
+        for (int j = 0; j < RP; ++j) z[j] = j < r ? __ldcs(&Z[(int64_t)j * zld + l]) : T(0);
+        if (WITH_DOT) {
+          xb = T(0);
+#pragma unroll
+          for (int j = 0; j < RP; ++j) xb = fma(xs[wib][j], z[j], xb);
+        } else {
+          xb = tvals[l];
+        }
+#pragma unroll
+        for (int j = 0; j < RP; ++j) acc[j] = fma(xb, z[j], acc[j]);
+      } else {
+        if (WITH_DOT) {
+          xb = T(0);
+#pragma unroll
+          for (int j = 0; j < RP; ++j)
+            if (j < r) xb = fma(xs[wib][j], Z[(int64_t)j * zld + l], xb);
+        } else {
+          xb = tvals[l];
+        }
+#pragma unroll
+        for (int j = 0; j < RP; ++j)
+          if (j < r) acc[j] = fma(xb, __ldcs(&Z[(int64_t)j * zld + l]), acc[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < RP; ++j)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+    const int np = pl.seg_count[seg];
+    if (np == 1) {
+#pragma unroll
+      for (int j = 0; j < RP; ++j)
+        if ((j & 31) == lane && j < r) Y[(int64_t)j * yld + seg] = acc[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < RP; ++j)
+        if ((j & 31) == lane && j < r) partial[(int64_t)p * RP + j] = acc[j];
+      __threadfence();
+      __syncwarp();
+      unsigned t = 0;
+      if (lane == 0) t = atomicAdd(&pl.seg_ticket[seg], 1u);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if (t == (unsigned)(np - 1)) {
+        __threadfence();
+        const int f = pl.seg_first[seg];
+        for (int j = lane; j < r; j += 32) {
+          T s = T(0);
+          for (int k = 0; k < np; ++k) s += __ldcg(&partial[(int64_t)(f + k) * RP + j]);
+          Y[(int64_t)j * yld + seg] = s;
+        }
+        if (lane == 0) pl.seg_ticket[seg] = 0u;
+      }
+    }
+  }
+}
+
+template <typename T, int RP>
+static cudaError_t gds_dispatch_keep(const PieceList& pl, const T* Z, int64_t zld, int r,
+                                     const T* Xh, int64_t xld, const T* tvals, T* partial, T* Y,
+                                     int64_t yld, const DevScalars* skip, int blocks,
+                                     cudaStream_t st) {
+  constexpr bool keep = RP * sizeof(T) <= 256;
+  if (Xh)
+    gds_kernel<T, RP, true, keep><<<blocks, 256, 0, st>>>(pl, Z, zld, r, Xh, xld, tvals, partial,
+                                                          Y, yld, skip);
+  else
+    gds_kernel<T, RP, false, keep><<<blocks, 256, 0, st>>>(pl, Z, zld, r, Xh, xld, tvals,
+                                                           partial, Y, yld, skip);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gds(const PieceList& pl, const T* Z, int64_t zld, int r, const T* Xh,
+                       int64_t xld, const T* tvals, T* partial, T* Y, int64_t yld,
+                       const DevScalars* skip, int num_sms, cudaStream_t st) {
+  if (pl.npieces == 0) return cudaSuccess;
+  const int warps = pl.npieces;
+  int blocks = (warps + 7) / 8;
+  const int cap = num_sms * 16;
+  if (blocks > cap) blocks = cap;
+  if (r <= 8) return gds_dispatch_keep<T, 8>(pl, Z, zld, r, Xh, xld, tvals, partial, Y, yld, skip, blocks, st);
+  if (r <= 16) return gds_dispatch_keep<T, 16>(pl, Z, zld, r, Xh, xld, tvals, partial, Y, yld, skip, blocks, st);
+  if (r <= 32) return gds_dispatch_keep<T, 32>(pl, Z, zld, r, Xh, xld, tvals, partial, Y, yld, skip, blocks, st);
+  if (r <= 48) return gds_dispatch_keep<T, 48>(pl, Z, zld, r, Xh, xld, tvals, partial, Y, yld, skip, blocks, st);
+  if (r <= 64) return gds_dispatch_keep<T, 64>(pl, Z, zld, r, Xh, xld, tvals, partial, Y, yld, skip, blocks, st);
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_gds<double>(const PieceList&, const double*, int64_t, int,
+                                        const double*, int64_t, const double*, double*, double*,
+                                        int64_t, const DevScalars*, int, cudaStream_t);
+template cudaError_t launch_gds<float>(const PieceList&, const float*, int64_t, int,
+                                       const float*, int64_t, const float*, float*, float*,
+                                       int64_t, const DevScalars*, int, cudaStream_t);
+
+}  // namespace cphifi
