@@ -64,11 +64,12 @@ struct cphifi_problem {
   int64_t* row_ptr = nullptr;
   double* z64 = nullptr;
   float* z32 = nullptr;
-  int64_t zld = 0;
   int32_t *pseg = nullptr, *pbeg = nullptr, *pend = nullptr, *seg_first = nullptr,
-          *seg_count = nullptr;
+          *seg_count = nullptr, *warp_first = nullptr;
   unsigned* seg_ticket = nullptr;
   int npieces = 0;
+  int nwarps = 1;     // warps of the gather-dot/scatter, L observations each
+  int64_t obs_per_warp = 1;
   void* gds_partial = nullptr;  // npieces x 64 doubles
   // factors and their Gram
   std::vector<double*> factors;
@@ -373,8 +374,8 @@ static size_t problem_footprint(int64_t n, int64_t q, int r, int d_other,
                                 int64_t npieces_max) {
   size_t b = 0;
   const size_t nr = (size_t)n * r;
-  b += (size_t)q * r * sizeof(double);                 // Zhat FP64
-  if (lowp) b += (size_t)q * r * sizeof(float);        // Zhat FP32
+  b += (size_t)zhat_elems(q, r) * sizeof(double);     // Zhat FP64
+  if (lowp) b += (size_t)zhat_elems(q, r) * sizeof(float);  // Zhat FP32
   b += (size_t)q * sizeof(int32_t);                    // perm
   b += (n + 1) * sizeof(int64_t) + 4 * n * sizeof(int32_t) + (n + 1) * sizeof(int32_t);
   b += (size_t)npieces_max * (3 * sizeof(int32_t) + 64 * sizeof(double));
@@ -408,8 +409,12 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
     M *= (double)sizes[m];
   }
   const int n = kern->n;
-  const int piece_len = 512;
-  const int64_t npieces_max = q / piece_len + n + 1;
+  // Gather-dot/scatter decomposition: W warps (two resident 8-warp blocks per
+  // SM at most, and no fewer than 64 observations per warp), L = ceil(q / W).
+  const int64_t W64 = std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 16, (q + 63) / 64));
+  const int W = (int)W64;
+  const int64_t L = std::max<int64_t>(1, (q + W - 1) / W);
+  const int64_t npieces_max = (int64_t)n + W + 1;
   const int nsplit = gemm_pick_split(n, ctx->num_sms);
   const bool lowp = (flags & CPHIFI_NEED_LOWP) != 0;
   const size_t need = problem_footprint(n, q, r, d_other, sizes, lowp, nsplit, npieces_max);
@@ -429,7 +434,8 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   P->sizes = sizes;
   P->gamma = (double)q / ((double)n * M);
   P->nsplit = nsplit;
-  P->zld = q;
+  P->nwarps = W;
+  P->obs_per_warp = L;
   cudaStream_t st = ctx->stream;
   std::vector<void*> temps;
   auto tmp_alloc = [&](size_t bytes) -> void* {
@@ -458,8 +464,9 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   const size_t nr = (size_t)n * r;
   PCK(dalloc(P, &P->perm, q));
   PCK(dalloc(P, &P->row_ptr, n + 1));
-  PCK(dalloc(P, &P->z64, (size_t)q * r));
-  if (lowp) PCK(dalloc(P, &P->z32, (size_t)q * r));
+  PCK(dalloc(P, &P->z64, (size_t)zhat_elems(q, r)));
+  if (lowp) PCK(dalloc(P, &P->z32, (size_t)zhat_elems(q, r)));
+  PCK(dalloc(P, &P->warp_first, (size_t)W + 1));
   PCK(dalloc(P, &P->seg_first, n + 1));
   PCK(dalloc(P, &P->seg_count, n));
   PCK(dalloc(P, &P->seg_ticket, n));
@@ -537,14 +544,14 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   else if (q > 1) PCK(launch_check_sorted(keys, q, P->err, st));
   PCK(launch_row_ptr(keys, q, n, P->row_ptr, st));
   PCK(launch_zhat((flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm, oidx_d, d_other,
-                  P->factors_dev, P->sizes_dev, r, q, P->z64, P->z32, P->zld, vals_d,
+                  P->factors_dev, P->sizes_dev, r, q, P->z64, P->z32, vals_d,
                   vals_sorted, P->err, st));
 
   // ---- pieces
   {
     void* stmp = tmp_alloc(exclusive_scan_tmp_bytes(n));
     if (!stmp) return bail(CPHIFI_E_OOM, "temporary allocation failed");
-    PCK(launch_piece_counts(P->row_ptr, n, piece_len, P->seg_count, st));
+    PCK(launch_piece_counts(P->row_ptr, n, L, P->seg_count, st));
     PCK(exclusive_scan_i32(P->seg_count, P->seg_first, n, stmp, exclusive_scan_tmp_bytes(n), st));
     int np = 0;
     PCK(cudaMemcpyAsync(&np, P->seg_first + n, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -554,16 +561,18 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
     PCK(dalloc(P, &P->pbeg, np));
     PCK(dalloc(P, &P->pend, np));
     PCK(dalloc(P, (double**)&P->gds_partial, (size_t)np * 64));
-    PCK(launch_piece_fill(P->row_ptr, n, P->seg_first, P->seg_count, P->pseg, P->pbeg, P->pend, st));
+    PCK(launch_piece_fill(P->row_ptr, n, L, P->seg_first, P->seg_count, P->pseg, P->pbeg, P->pend, st));
+    PCK(launch_warp_first(P->pbeg, np, L, W, P->warp_first, st));
   }
 
   // ---- Gram, eig(V), right-hand side MTTKRP
   PCK(launch_gram(P->factors_dev, P->sizes_dev, d_other, r, P->V, st));
   PCK(launch_jacobi_eig(P->V, r, P->dV, P->UV, 60, P->info, st));
   PCK(launch_convert<double, float>(P->UV, P->UV32, (int64_t)r * r, st));
-  PieceList pl{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket, P->npieces};
-  PCK(launch_gds<double>(pl, P->z64, P->zld, r, nullptr, n, vals_sorted, (double*)P->gds_partial,
-                         P->Bm, n, nullptr, ctx->num_sms, st));
+  PieceList pl{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket,
+               P->warp_first, P->npieces, P->nwarps};
+  PCK(launch_gds<double>(pl, P->z64, r, nullptr, n, vals_sorted, (double*)P->gds_partial,
+                         P->Bm, n, nullptr, st));
   PCK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   PCK(cudaStreamSynchronize(st));
   if (herr & 4) return bail(CPHIFI_E_INVALID_ARG, "CPHIFI_OBS_SORTED set but kidx is not sorted");
@@ -603,7 +612,7 @@ struct Launcher {
 
   PieceList pieces() const {
     return PieceList{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket,
-                     P->npieces};
+                     P->warp_first, P->npieces, P->nwarps};
   }
   int64_t split_stride() const { return (int64_t)P->n * P->r; }
 
@@ -640,8 +649,8 @@ struct Launcher {
   template <typename T>
   cudaError_t gds(const T* Z, const T* Xh, T* Y, const DevScalars* skip, int cat) {
     cudaEvent_t b = (cat && tm) ? tm->begin() : nullptr;
-    cudaError_t e = launch_gds<T>(pieces(), Z, P->zld, P->r, Xh, P->n, nullptr, (T*)P->gds_partial,
-                                  Y, P->n, skip, P->ctx->num_sms, st);
+    cudaError_t e = launch_gds<T>(pieces(), Z, P->r, Xh, P->n, nullptr, (T*)P->gds_partial,
+                                  Y, P->n, skip, st);
     if (cat && tm) tm->end(b, cat == 1 ? tm->gds : tm->gds64);
     ++launches;
     return e;
@@ -735,11 +744,11 @@ int check_params(cphifi_ctx* ctx, const cphifi_params* prm) {
 int ensure_lowp(cphifi_problem* P) {
   cphifi_ctx* ctx = P->ctx;
   if (P->z32) return CPHIFI_OK;
-  const size_t bytes = (size_t)P->q * P->r * sizeof(float);
-  if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+  const size_t elems = (size_t)zhat_elems(P->q, P->r);
+  if (ctx->budget && ctx->in_use + elems * sizeof(float) > ctx->budget)
     return fail(ctx, CPHIFI_E_ADMISSION, "FP32 operator data exceeds the HBM budget");
-  CK(dalloc(P, &P->z32, (size_t)P->q * P->r));
-  CK(launch_convert<double, float>(P->z64, P->z32, P->q * (int64_t)P->r, ctx->stream));
+  CK(dalloc(P, &P->z32, elems));
+  CK(launch_convert<double, float>(P->z64, P->z32, (int64_t)elems, ctx->stream));
   return CPHIFI_OK;
 }
 

@@ -62,7 +62,7 @@ __global__ void jacobi_kernel(const double* __restrict__ Vin, int r, double* dV,
   double* Q = A + R * R;        // R x R
   double* cs = Q + R * R;       // R/2 x 2
   int* pq = (int*)(cs + R);     // R/2 x 2
-  __shared__ double red[32];
+  __shared__ double red[64];  // block_sum<2> scratch: 2 x 32
   __shared__ double off_s, nrm_s;
   for (int t = threadIdx.x; t < R * R; t += blockDim.x) {
     const int i = t % R, j = t / R;

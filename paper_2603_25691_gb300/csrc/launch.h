@@ -30,21 +30,32 @@ cudaError_t launch_iota(int32_t* v, int64_t q, cudaStream_t st);
 cudaError_t launch_check_sorted(const uint32_t* keys, int64_t q, int* err, cudaStream_t st);
 cudaError_t launch_row_ptr(const uint32_t* sorted_keys, int64_t q, int n,
                            int64_t* row_ptr, cudaStream_t st);
-// Pieces: every kernel index owns >= 1 piece of <= piece_len observations.
-cudaError_t launch_piece_counts(const int64_t* row_ptr, int n, int piece_len,
+// Pieces: the kernel-index segments cut at multiples of L (each warp of the
+// gather-dot/scatter owns L sorted observations); every index owns >= 1 piece.
+cudaError_t launch_piece_counts(const int64_t* row_ptr, int n, int64_t L,
                                 int32_t* seg_count, cudaStream_t st);
-cudaError_t launch_piece_fill(const int64_t* row_ptr, int n,
+cudaError_t launch_piece_fill(const int64_t* row_ptr, int n, int64_t L,
                               const int32_t* seg_first, const int32_t* seg_count,
                               int32_t* pseg, int32_t* pbeg, int32_t* pend,
                               cudaStream_t st);
+cudaError_t launch_warp_first(const int32_t* pbeg, int npieces, int64_t L, int W,
+                              int32_t* warp_first, cudaStream_t st);
 // Exclusive scan of int32 counts into int32 offsets (out has n+1 entries).
 cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n,
                                void* tmp, size_t tmp_bytes, cudaStream_t st);
 size_t exclusive_scan_tmp_bytes(int64_t n);
-// Zhat (Eq. zhat) in sorted order, column-major q x r, FP64 and optional FP32.
+// Zhat storage: tiles of 32 sorted observations, each a 32 x r column-major
+// block; (l, j) lives at zidx(l, j, r).  Buffers hold zhat_elems(q, r) values.
+__host__ __device__ __forceinline__ int64_t zidx(int64_t l, int j, int r) {
+  return (l >> 5) * (32 * (int64_t)r) + 32 * (int64_t)j + (l & 31);
+}
+__host__ __device__ __forceinline__ int64_t zhat_elems(int64_t q, int r) {
+  return ((q + 31) >> 5) * 32 * (int64_t)r;
+}
+// Zhat (Eq. zhat) in sorted order, FP64 and optional FP32.
 cudaError_t launch_zhat(const int32_t* perm, const int32_t* oidx, int d_other,
                         const double* const* factors_dev, const int64_t* sizes_dev,
-                        int r, int64_t q, double* z64, float* z32, int64_t zld,
+                        int r, int64_t q, double* z64, float* z32,
                         const double* vals, double* vals_sorted, int* err,
                         cudaStream_t st);
 // Gather-dot/scatter (Eqs. vl and yhat1).  with_dot = false computes the
@@ -56,13 +67,14 @@ struct PieceList {
   const int32_t* seg_first;
   const int32_t* seg_count;
   unsigned* seg_ticket;
+  const int32_t* warp_first;  // nwarps + 1
   int npieces;
+  int nwarps;
 };
 template <typename T>
-cudaError_t launch_gds(const PieceList& pl, const T* Z, int64_t zld, int r,
-                       const T* Xh, int64_t xld, const T* tvals, T* partial,
-                       T* Y, int64_t yld, const DevScalars* skip,
-                       int num_sms, cudaStream_t st);
+cudaError_t launch_gds(const PieceList& pl, const T* Z, int r, const T* Xh,
+                       int64_t xld, const T* tvals, T* partial, T* Y, int64_t yld,
+                       const DevScalars* skip, cudaStream_t st);
 
 // -------------------------------------------------------------- dense.cu ---
 // Skinny product C = op(A) diag(s) B for A n x n (op = identity when a_trans

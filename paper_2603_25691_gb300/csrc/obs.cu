@@ -301,22 +301,24 @@ cudaError_t launch_row_ptr(const uint32_t* sorted_keys, int64_t q, int n, int64_
   return cudaGetLastError();
 }
 
-__global__ void piece_counts_kernel(const int64_t* __restrict__ row_ptr, int n, int piece_len,
+// Pieces are the pieces of kernel-index segments cut at multiples of L, the
+// observation range of one warp: every warp then owns exactly L sorted
+// observations (the last one fewer) whatever the segment lengths are.
+__global__ void piece_counts_kernel(const int64_t* __restrict__ row_ptr, int n, int64_t L,
                                     int32_t* seg_count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int64_t len = row_ptr[i + 1] - row_ptr[i];
-  const int64_t c = (len + piece_len - 1) / piece_len;
-  seg_count[i] = (int32_t)(c > 0 ? c : 1);
+  const int64_t b = row_ptr[i], e = row_ptr[i + 1];
+  seg_count[i] = e > b ? (int32_t)((e - 1) / L - b / L + 1) : 1;
 }
 
-cudaError_t launch_piece_counts(const int64_t* row_ptr, int n, int piece_len,
-                                int32_t* seg_count, cudaStream_t st) {
-  piece_counts_kernel<<<(n + 255) / 256, 256, 0, st>>>(row_ptr, n, piece_len, seg_count);
+cudaError_t launch_piece_counts(const int64_t* row_ptr, int n, int64_t L, int32_t* seg_count,
+                                cudaStream_t st) {
+  piece_counts_kernel<<<(n + 255) / 256, 256, 0, st>>>(row_ptr, n, L, seg_count);
   return cudaGetLastError();
 }
 
-__global__ void piece_fill_kernel(const int64_t* __restrict__ row_ptr, int n,
+__global__ void piece_fill_kernel(const int64_t* __restrict__ row_ptr, int n, int64_t L,
                                   const int32_t* __restrict__ seg_first,
                                   const int32_t* __restrict__ seg_count, int32_t* pseg,
                                   int32_t* pbeg, int32_t* pend) {
@@ -324,34 +326,59 @@ __global__ void piece_fill_kernel(const int64_t* __restrict__ row_ptr, int n,
   if (i >= n) return;
   const int64_t b = row_ptr[i], e = row_ptr[i + 1];
   const int c = seg_count[i];
-  const int64_t len = e - b;
-  const int64_t step = (len + c - 1) / c;  // balanced pieces of one segment
+  const int64_t k0 = b / L;
   for (int k = 0; k < c; ++k) {
     const int p = seg_first[i] + k;
-    int64_t pb = b + k * step, pe = pb + step;
-    if (pb > e) pb = e;
+    int64_t pb = (k0 + k) * L, pe = pb + L;
+    if (pb < b) pb = b;
     if (pe > e) pe = e;
+    if (e == b) pb = pe = b;
     pseg[p] = i;
     pbeg[p] = (int32_t)pb;
     pend[p] = (int32_t)pe;
   }
 }
 
-cudaError_t launch_piece_fill(const int64_t* row_ptr, int n, const int32_t* seg_first,
+cudaError_t launch_piece_fill(const int64_t* row_ptr, int n, int64_t L, const int32_t* seg_first,
                               const int32_t* seg_count, int32_t* pseg, int32_t* pbeg,
                               int32_t* pend, cudaStream_t st) {
-  piece_fill_kernel<<<(n + 255) / 256, 256, 0, st>>>(row_ptr, n, seg_first, seg_count, pseg,
+  piece_fill_kernel<<<(n + 255) / 256, 256, 0, st>>>(row_ptr, n, L, seg_first, seg_count, pseg,
                                                      pbeg, pend);
+  return cudaGetLastError();
+}
+
+// warp_first[w] = first piece starting at or after w*L (w < W); warp_first[W]
+// = npieces, so warp w owns pieces [warp_first[w], warp_first[w+1]).
+__global__ void warp_first_kernel(const int32_t* __restrict__ pbeg, int npieces, int64_t L, int W,
+                                  int32_t* warp_first) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w > W) return;
+  if (w == W) { warp_first[W] = npieces; return; }
+  const int64_t v = (int64_t)w * L;
+  int lo = 0, hi = npieces;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((int64_t)pbeg[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  warp_first[w] = lo;
+}
+
+cudaError_t launch_warp_first(const int32_t* pbeg, int npieces, int64_t L, int W,
+                              int32_t* warp_first, cudaStream_t st) {
+  warp_first_kernel<<<(W + 1 + 255) / 256, 256, 0, st>>>(pbeg, npieces, L, W, warp_first);
   return cudaGetLastError();
 }
 
 // -------------------------------------------------------------- Zhat ------
 // Zhat(s, j) = prod_m A_m(oidx[perm[s], m], j) for the s-th observation in the
-// sorted order (Eq. zhat).  Factors are column-major n_m x r.
+// sorted order (Eq. zhat).  Factors are column-major n_m x r.  Zhat is stored
+// in tiles of 32 observations: tile t holds a 32 x r column-major block, so
+// element (s, j) lives at zidx(s, j, r) (see launch.h) and the 32 x r values
+// a warp reads in one round form one contiguous block.
 __global__ void zhat_kernel(const int32_t* __restrict__ perm, const int32_t* __restrict__ oidx,
                             int d_other, const double* const* __restrict__ factors,
                             const int64_t* __restrict__ sizes, int r, int64_t q,
-                            double* __restrict__ z64, float* __restrict__ z32, int64_t zld,
+                            double* __restrict__ z64, float* __restrict__ z32,
                             const double* __restrict__ vals, double* __restrict__ vals_sorted,
                             int* err) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < q;
@@ -375,155 +402,156 @@ __global__ void zhat_kernel(const int32_t* __restrict__ perm, const int32_t* __r
       } else {
         v = 0.0;
       }
-      z64[j * zld + s] = v;
-      if (z32) z32[j * zld + s] = (float)v;
+      z64[zidx(s, j, r)] = v;
+      if (z32) z32[zidx(s, j, r)] = (float)v;
     }
   }
 }
 
 cudaError_t launch_zhat(const int32_t* perm, const int32_t* oidx, int d_other,
                         const double* const* factors_dev, const int64_t* sizes_dev, int r,
-                        int64_t q, double* z64, float* z32, int64_t zld, const double* vals,
+                        int64_t q, double* z64, float* z32, const double* vals,
                         double* vals_sorted, int* err, cudaStream_t st) {
   if (q == 0) return cudaSuccess;
   const int blocks = (int)((q + 255) / 256 < 8192 ? (q + 255) / 256 : 8192);
   zhat_kernel<<<blocks, 256, 0, st>>>(perm, oidx, d_other, factors_dev, sizes_dev, r, q, z64,
-                                      z32, zld, vals, vals_sorted, err);
+                                      z32, vals, vals_sorted, err);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------ gather-dot / scatter ----
-// One warp per piece (a run of sorted observations that share the kernel
-// index i).  Lane t takes observations b+t, b+t+32, ...: it loads Zhat(l, :)
-// column by column (coalesced across the warp), forms
-// xbar_l = Xhat(i,:).Zhat(l,:) (Eq. vl) and accumulates xbar_l Zhat(l,:) in
-// registers (Eq. yhat1).  The warp then sums its 32 partial rows; a kernel
-// index with one piece writes Yhat1(i,:) directly, otherwise each piece stores
-// its row and the last piece to finish (per-index ticket) adds the pieces in
-// piece order.  No floating-point atomics: the result is deterministic.
+// Warp w owns the pieces [warp_first[w], warp_first[w+1]), i.e. the sorted
+// observations [w L, (w+1) L).  Per piece (one kernel index i), lane t takes
+// observations b+t, b+t+32, ...: it loads Zhat(l, :) (a 32-observation round of
+// the warp reads one contiguous tile), forms xbar_l = Xhat(i,:).Zhat(l,:)
+// (Eq. vl) and accumulates xbar_l Zhat(l,:) in registers (Eq. yhat1).  The
+// warp then sums its 32 partial rows; a kernel index covered by one piece is
+// written directly, otherwise each piece stores its row and the last piece to
+// finish (per-index ticket) adds the pieces in piece order.  No
+// floating-point atomics: the result is deterministic.
 // RP is the register width (>= r); KEEPZ keeps the loaded row in registers
 // between the dot and the update, otherwise the update reloads it (L1 hit).
 template <typename T, int RP, bool WITH_DOT, bool KEEPZ>
-__global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const T* __restrict__ Z,
-                                                  int64_t zld, int r, const T* __restrict__ Xh,
-                                                  int64_t xld, const T* __restrict__ tvals,
+__global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const T* __restrict__ Z, int r,
+                                                  const T* __restrict__ Xh, int64_t xld,
+                                                  const T* __restrict__ tvals,
                                                   T* __restrict__ partial, T* __restrict__ Y,
                                                   int64_t yld, const DevScalars* skip) {
   if (dev_skip(skip)) return;
   __shared__ T xs[8][RP];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int p = warp; p < pl.npieces; p += nwarps) {
-    const int seg = pl.seg[p];
-    const int b = pl.beg[p], e = pl.end[p];
-    if (WITH_DOT) {
-      __syncwarp();
-      for (int j = lane; j < RP; j += 32) xs[wib][j] = j < r ? Xh[(int64_t)j * xld + seg] : T(0);
-      __syncwarp();
-    }
-    T acc[RP];
+  for (int w = gw; w < pl.nwarps; w += nwarps) {
+    const int p_end = pl.warp_first[w + 1];
+    for (int p = pl.warp_first[w]; p < p_end; ++p) {
+      const int seg = pl.seg[p];
+      const int b = pl.beg[p], e = pl.end[p];
+      if (WITH_DOT) {
+        __syncwarp();
+        for (int j = lane; j < RP; j += 32) xs[wib][j] = j < r ? Xh[(int64_t)j * xld + seg] : T(0);
+        __syncwarp();
+      }
+      T acc[RP];
 #pragma unroll
-    for (int j = 0; j < RP; ++j) acc[j] = T(0);
-    for (int l = b + lane; l < e; l += 32) {
-      T xb;
-      if (KEEPZ) {
-        T z[RP];
+      for (int j = 0; j < RP; ++j) acc[j] = T(0);
+      for (int l = b + lane; l < e; l += 32) {
+        const T* zrow = Z + zidx(l, 0, r);
+        T xb;
+        if (KEEPZ) {
+          T z[RP];
 #pragma unroll
-        for (int j = 0; j < RP; ++j) z[j] = j < r ? __ldcs(&Z[(int64_t)j * zld + l]) : T(0);
-        if (WITH_DOT) {
-          xb = T(0);
+          for (int j = 0; j < RP; ++j) z[j] = j < r ? __ldcs(zrow + 32 * j) : T(0);
+          if (WITH_DOT) {
+            xb = T(0);
 #pragma unroll
-          for (int j = 0; j < RP; ++j) xb = fma(xs[wib][j], z[j], xb);
+            for (int j = 0; j < RP; ++j) xb = fma(xs[wib][j], z[j], xb);
+          } else {
+            xb = tvals[l];
+          }
+#pragma unroll
+          for (int j = 0; j < RP; ++j) acc[j] = fma(xb, z[j], acc[j]);
         } else {
-          xb = tvals[l];
-        }
+          if (WITH_DOT) {
+            xb = T(0);
 #pragma unroll
-        for (int j = 0; j < RP; ++j) acc[j] = fma(xb, z[j], acc[j]);
-      } else {
-        if (WITH_DOT) {
-          xb = T(0);
+            for (int j = 0; j < RP; ++j)
+              if (j < r) xb = fma(xs[wib][j], zrow[32 * j], xb);
+          } else {
+            xb = tvals[l];
+          }
 #pragma unroll
           for (int j = 0; j < RP; ++j)
-            if (j < r) xb = fma(xs[wib][j], Z[(int64_t)j * zld + l], xb);
-        } else {
-          xb = tvals[l];
+            if (j < r) acc[j] = fma(xb, __ldcs(zrow + 32 * j), acc[j]);
         }
+      }
+#pragma unroll
+      for (int j = 0; j < RP; ++j)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+      const int np = pl.seg_count[seg];
+      if (np == 1) {
 #pragma unroll
         for (int j = 0; j < RP; ++j)
-          if (j < r) acc[j] = fma(xb, __ldcs(&Z[(int64_t)j * zld + l]), acc[j]);
-      }
-    }
+          if ((j & 31) == lane && j < r) Y[(int64_t)j * yld + seg] = acc[j];
+      } else {
 #pragma unroll
-    for (int j = 0; j < RP; ++j)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
-    const int np = pl.seg_count[seg];
-    if (np == 1) {
-#pragma unroll
-      for (int j = 0; j < RP; ++j)
-        if ((j & 31) == lane && j < r) Y[(int64_t)j * yld + seg] = acc[j];
-    } else {
-#pragma unroll
-      for (int j = 0; j < RP; ++j)
-        if ((j & 31) == lane && j < r) partial[(int64_t)p * RP + j] = acc[j];
-      __threadfence();
-      __syncwarp();
-      unsigned t = 0;
-      if (lane == 0) t = atomicAdd(&pl.seg_ticket[seg], 1u);
-      t = __shfl_sync(0xffffffffu, t, 0);
-      if (t == (unsigned)(np - 1)) {
+        for (int j = 0; j < RP; ++j)
+          if ((j & 31) == lane && j < r) partial[(int64_t)p * RP + j] = acc[j];
         __threadfence();
-        const int f = pl.seg_first[seg];
-        for (int j = lane; j < r; j += 32) {
-          T s = T(0);
-          for (int k = 0; k < np; ++k) s += __ldcg(&partial[(int64_t)(f + k) * RP + j]);
-          Y[(int64_t)j * yld + seg] = s;
+        __syncwarp();
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(&pl.seg_ticket[seg], 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t == (unsigned)(np - 1)) {
+          __threadfence();
+          const int f = pl.seg_first[seg];
+          for (int j = lane; j < r; j += 32) {
+            T sacc = T(0);
+            for (int k = 0; k < np; ++k) sacc += __ldcg(&partial[(int64_t)(f + k) * RP + j]);
+            Y[(int64_t)j * yld + seg] = sacc;
+          }
+          if (lane == 0) pl.seg_ticket[seg] = 0u;
         }
-        if (lane == 0) pl.seg_ticket[seg] = 0u;
       }
     }
   }
 }
 
 template <typename T, int RP>
-static cudaError_t gds_dispatch_keep(const PieceList& pl, const T* Z, int64_t zld, int r,
-                                     const T* Xh, int64_t xld, const T* tvals, T* partial, T* Y,
-                                     int64_t yld, const DevScalars* skip, int blocks,
-                                     cudaStream_t st) {
+static cudaError_t gds_dispatch_keep(const PieceList& pl, const T* Z, int r, const T* Xh,
+                                     int64_t xld, const T* tvals, T* partial, T* Y, int64_t yld,
+                                     const DevScalars* skip, cudaStream_t st) {
   constexpr bool keep = RP * sizeof(T) <= 256;
+  const int blocks = (pl.nwarps + 7) / 8;
   if (Xh)
-    gds_kernel<T, RP, true, keep><<<blocks, 256, 0, st>>>(pl, Z, zld, r, Xh, xld, tvals, partial,
-                                                          Y, yld, skip);
+    gds_kernel<T, RP, true, keep><<<blocks, 256, 0, st>>>(pl, Z, r, Xh, xld, tvals, partial, Y,
+                                                          yld, skip);
   else
-    gds_kernel<T, RP, false, keep><<<blocks, 256, 0, st>>>(pl, Z, zld, r, Xh, xld, tvals,
-                                                           partial, Y, yld, skip);
+    gds_kernel<T, RP, false, keep><<<blocks, 256, 0, st>>>(pl, Z, r, Xh, xld, tvals, partial, Y,
+                                                           yld, skip);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_gds(const PieceList& pl, const T* Z, int64_t zld, int r, const T* Xh,
-                       int64_t xld, const T* tvals, T* partial, T* Y, int64_t yld,
-                       const DevScalars* skip, int num_sms, cudaStream_t st) {
-  if (pl.npieces == 0) return cudaSuccess;
-  const int warps = pl.npieces;
-  int blocks = (warps + 7) / 8;
-  const int cap = num_sms * 16;
-  if (blocks > cap) blocks = cap;
-  if (r <= 8) return gds_dispatch_keep<T, 8>(pl, Z, zld, r, Xh, xld, tvals, partial, Y, yld, skip, blocks, st);
-  if (r <= 16) return gds_dispatch_keep<T, 16>(pl, Z, zld, r, Xh, xld, tvals, partial, Y, yld, skip, blocks, st);
-  if (r <= 32) return gds_dispatch_keep<T, 32>(pl, Z, zld, r, Xh, xld, tvals, partial, Y, yld, skip, blocks, st);
-  if (r <= 48) return gds_dispatch_keep<T, 48>(pl, Z, zld, r, Xh, xld, tvals, partial, Y, yld, skip, blocks, st);
-  if (r <= 64) return gds_dispatch_keep<T, 64>(pl, Z, zld, r, Xh, xld, tvals, partial, Y, yld, skip, blocks, st);
+cudaError_t launch_gds(const PieceList& pl, const T* Z, int r, const T* Xh, int64_t xld,
+                       const T* tvals, T* partial, T* Y, int64_t yld, const DevScalars* skip,
+                       cudaStream_t st) {
+  if (pl.npieces == 0 || pl.nwarps == 0) return cudaSuccess;
+  if (r <= 8) return gds_dispatch_keep<T, 8>(pl, Z, r, Xh, xld, tvals, partial, Y, yld, skip, st);
+  if (r <= 16) return gds_dispatch_keep<T, 16>(pl, Z, r, Xh, xld, tvals, partial, Y, yld, skip, st);
+  if (r <= 32) return gds_dispatch_keep<T, 32>(pl, Z, r, Xh, xld, tvals, partial, Y, yld, skip, st);
+  if (r <= 48) return gds_dispatch_keep<T, 48>(pl, Z, r, Xh, xld, tvals, partial, Y, yld, skip, st);
+  if (r <= 64) return gds_dispatch_keep<T, 64>(pl, Z, r, Xh, xld, tvals, partial, Y, yld, skip, st);
   return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_gds<double>(const PieceList&, const double*, int64_t, int,
-                                        const double*, int64_t, const double*, double*, double*,
-                                        int64_t, const DevScalars*, int, cudaStream_t);
-template cudaError_t launch_gds<float>(const PieceList&, const float*, int64_t, int,
-                                       const float*, int64_t, const float*, float*, float*,
-                                       int64_t, const DevScalars*, int, cudaStream_t);
+template cudaError_t launch_gds<double>(const PieceList&, const double*, int, const double*,
+                                        int64_t, const double*, double*, double*, int64_t,
+                                        const DevScalars*, cudaStream_t);
+template cudaError_t launch_gds<float>(const PieceList&, const float*, int, const float*,
+                                       int64_t, const float*, float*, float*, int64_t,
+                                       const DevScalars*, cudaStream_t);
 
 }  // namespace cphifi
