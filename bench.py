@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="override n (smaller runs)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
@@ -184,6 +185,31 @@ def run_reference(args):
     return 0
 
 
+def run_e2e(args, pkg, ctx, kern, p):
+    """Same metric through cphifi_solve with pinned HOST buffers: the H2D copy
+    of the inputs and the D2H copy of W are inside the timed region."""
+    import torch
+    n, r, q = p.n, p.r, p.q
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    kh, oh, vh = pin(p.kidx), pin(p.oidx.ravel()), pin(p.vals)
+    fh = [pin(np.asfortranarray(F).ravel(order="F")).reshape(F.shape[1], F.shape[0]).T
+          for F in p.factors]
+    Wh = pin(np.zeros((r, n))).T
+    e2e_steps = max(1, min(3, args.steps))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(e2e_steps):
+        Wo, st = pkg.solve(ctx, kern, fh, kh, oh, vh, r, p.lam, p.rho, TOL, 500,
+                           precision=args.precision, sorted_obs=True, out=Wh)
+        e2e_iters += st["iterations"]
+    torch.cuda.synchronize()
+    te2e = time.perf_counter() - t0
+    h2d = q * 4 + q * 4 * p.oidx.shape[1] + q * 8 + sum(F.size * 8 for F in p.factors)
+    return {"value": q * e2e_iters / te2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(n * r * 8), "solves_per_s": e2e_steps / te2e}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -266,24 +292,9 @@ def main():
                 "status": s64["status"]}
 
     # ---- end to end through the public API with host buffers (pinned)
-    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-    kh, oh, vh = pin(p.kidx), pin(p.oidx.ravel()), pin(p.vals)
-    fh = [pin(np.asfortranarray(F).ravel(order="F")).reshape(F.shape[1], F.shape[0]).T
-          for F in p.factors]
-    Wh = pin(np.zeros((r, n))).T
-    e2e_steps = max(1, min(3, args.steps))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e2e_iters = 0
-    for _ in range(e2e_steps):
-        Wo, st = pkg.solve(ctx, kern, fh, kh, oh, vh, r, p.lam, p.rho, TOL, 500,
-                           precision=args.precision, sorted_obs=True, out=Wh)
-        e2e_iters += st["iterations"]
-    torch.cuda.synchronize()
-    te2e = time.perf_counter() - t0
-    h2d = q * 4 + q * 4 * p.oidx.shape[1] + q * 8 + sum(F.size * 8 for F in p.factors)
-    e2e = {"value": q * e2e_iters / te2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-           "d2h_bytes_per_step": int(n * r * 8), "solves_per_s": e2e_steps / te2e}
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, pkg, ctx, kern, p)
 
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 only
     cpu = None
@@ -293,7 +304,6 @@ def main():
         cpu = {"value": sq * it / secs, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"one FP64 oracle PCG iteration (NumPy, BLAS threads = host cores) on "
                          f"the first {sq} sorted observations of this workload, full n = {n}"}
-
     launches = sum(s["kernel_launches"] + s["setup_launches"] for s in stats)
     if rank == 0:
         line = {
