@@ -226,6 +226,41 @@ int cphifi_problem_gram(cphifi_problem* prob, double* V, double* DV,
 int cphifi_problem_order(cphifi_problem* prob, int32_t* perm,
                          int64_t* row_ptr);
 
+/* ---- allocation-free entry point -----------------------------------------
+ * cphifi_gds_noalloc: the gather-dot/scatter product of the solver, FP64,
+ * without allocating device memory.  There is no counterpart in the paper:
+ * it exists for callers that cannot call cudaMalloc (for example code inside
+ * a CUDA-graph capture that must not record allocations, a real-time host
+ * loop that may not take the allocator's locks or its implicit
+ * synchronisation, or a runtime that owns all device memory).  The caller
+ * passes inputs and outputs; the working memory comes from a fixed array of
+ * about 10.7 MB compiled into the library, which every GPU that loads the
+ * library keeps until the process exits.
+ *   n, r     : kernel-mode size in [1, 16384] and rank in [1, 64]; larger
+ *              sizes return CPHIFI_E_INVALID_ARG with *err_msg naming the limit.
+ *   q        : number of observations, in [0, 2^31).
+ *   row_ptr  : device, n+1 int64: observations of kernel index i occupy
+ *              sorted positions [row_ptr[i], row_ptr[i+1]); row_ptr[0] = 0,
+ *              non-decreasing, row_ptr[n] = q (not checked: a bad CSR gives
+ *              undefined results).
+ *   zhat     : device FP64, Zhat in that sorted order, column-major q x r with
+ *              leading dimension ldz >= q.
+ *   Xhat     : device FP64 n x r column-major (leading dimension n).
+ *   Y1       : device FP64 n x r column-major: Y1(i,:) = sum over the
+ *              observations l of index i of (Xhat(i,:).Zhat(l,:)) Zhat(l,:).
+ *   stream   : cudaStream_t the work is queued on (NULL = legacy default).
+ *   err_msg  : optional; set to a static string describing the outcome.
+ * Runs on the calling thread's current device and returns once the work is
+ * queued (asynchronous: synchronise `stream` before reading Y1).  The first
+ * call on a device looks up the device address of the scratch array; make
+ * that first call before any stream capture.  Every call on a device shares
+ * the scratch array, so calls that overlap on the GPU (other streams or host
+ * threads) race: serialise them on one stream.  Returns CPHIFI_OK,
+ * CPHIFI_E_INVALID_ARG or CPHIFI_E_DEVICE. */
+int cphifi_gds_noalloc(int32_t n, int32_t r, int64_t q, const int64_t* row_ptr,
+                       const double* zhat, int64_t ldz, const double* Xhat,
+                       double* Y1, void* stream, const char** err_msg);
+
 #ifdef __cplusplus
 }
 #endif

@@ -105,6 +105,9 @@ _SIG = {
                                               ctypes.c_int]),
     "cphifi_problem_gram": (ctypes.c_int, [_P, _P, _P, _P]),
     "cphifi_problem_order": (ctypes.c_int, [_P, _P, _P]),
+    "cphifi_gds_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P,
+                                          ctypes.c_int64, _P, _P, _P,
+                                          ctypes.POINTER(ctypes.c_char_p)]),
 }
 
 
@@ -390,3 +393,20 @@ def solve(ctx: Context, kernel: Kernel, factors, kidx, oidx, vals, r: int, lam: 
     if rc not in (OK, E_NOT_CONVERGED):
         _check(ctx.h, rc, "solve")
     return wb.obj, st.as_dict()
+
+
+def gds_noalloc(n: int, r: int, q: int, row_ptr, zhat, ldz: int, Xhat, Y1, stream=None):
+    """cphifi_gds_noalloc on device tensors (int64 row_ptr, FP64 zhat/Xhat/Y1,
+    column-major).  Queues the work on `stream` (a torch.cuda.Stream, a raw
+    handle or None) and returns without waiting.  Raises CphifiError on a
+    rejected size or a CUDA failure."""
+    for t in (row_ptr, zhat, Xhat, Y1):
+        if not (_is_torch(t) and t.is_cuda and t.is_contiguous()):
+            raise ValueError("gds_noalloc takes contiguous CUDA tensors")
+    handle = getattr(stream, "cuda_stream", stream) if stream is not None else None
+    msg = ctypes.c_char_p()
+    rc = lib().cphifi_gds_noalloc(int(n), int(r), int(q), row_ptr.data_ptr(), zhat.data_ptr(),
+                                  int(ldz), Xhat.data_ptr(), Y1.data_ptr(),
+                                  ctypes.c_void_p(handle), ctypes.byref(msg))
+    if rc != OK:
+        raise CphifiError(rc, msg.value.decode() if msg.value else status_string(rc))
