@@ -256,28 +256,42 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     stats = []
+    step_ms = []
     with ClockSampler(local) as clk:
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         ev0.record(stream)
-        for _ in range(args.steps):
+        evs[0].record(stream)
+        for k in range(args.steps):
             stats.append(step(args.precision, profile=True))
+            evs[k + 1].record(stream)
         ev1.record(stream)
         torch.cuda.synchronize()
     elapsed_ms = ev0.elapsed_time(ev1)
+    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     if world > 1:
         t = torch.tensor([elapsed_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         elapsed_ms = float(t.item())
     iters = sum(s["iterations"] for s in stats)
-    value = q * iters * world / (elapsed_ms / 1e3)
+    iter_phase_ms = sum(s["iter_ms"] for s in stats)
+    if world > 1:
+        t = torch.tensor([iter_phase_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        iter_phase_ms = float(t.item())
+    # The metric: observations x PCG iterations per second of iteration phase
+    # (operator, updates, preconditioner, FP64 true residuals and restarts),
+    # summed over all ranks' independent problems.
+    value = q * iters * world / (iter_phase_ms / 1e3)
     solves_per_s = args.steps * world / (elapsed_ms / 1e3)
     gds_ms = sum(s["gds_ms"] for s in stats)
-    gds_bytes_per_launch = q * r * 4 + (n + 1) * 8 + q * 0  # Zhat stream (FP32) + row data
+    gds_bytes_per_launch = q * r * 4 + 2 * n * r * 4  # Zhat (FP32 part) + Xhat rows + Yhat1
     gds_exec = iters
     achieved = gds_bytes_per_launch * gds_exec / (gds_ms / 1e3) / 1e9 if gds_ms > 0 else None
     peak, peak_kind = peaks()
-    iter_phase_ms = sum(s["gds_ms"] + s["gemm_ms"] for s in stats)
+    srt = sorted(step_ms)
+    pct = lambda f: srt[min(len(srt) - 1, int(round(f * (len(srt) - 1))))]
 
     # ---- FP64 path on the same workload (the plain FP64 GPU solve)
     fp64 = None
@@ -287,7 +301,8 @@ def main():
         s64 = step("fp64", profile=True)
         torch.cuda.synchronize()
         t64 = time.perf_counter() - t0
-        fp64 = {"solves_per_s": 1.0 / t64, "obs_iter_per_s": q * s64["iterations"] / t64,
+        fp64 = {"solves_per_s": 1.0 / t64,
+                "obs_iter_per_s": q * s64["iterations"] / (s64["iter_ms"] / 1e3),
                 "iterations": s64["iterations"], "rel_residual": s64["rel_residual"],
                 "status": s64["status"]}
 
@@ -317,9 +332,15 @@ def main():
                        "precision": args.precision, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2"},
             "solves_per_s": solves_per_s,
+            "latency_ms": {"p50": pct(0.5), "p99": pct(0.99), "steps": step_ms},
+            "step_obs_iter_per_s": q * iters * world / (elapsed_ms / 1e3),
             "iterations_per_solve": iters / args.steps,
             "rel_residual": [s["rel_residual"] for s in stats],
-            "iter_phase_obs_iter_per_s": q * iters / (iter_phase_ms / 1e3) if iter_phase_ms else None,
+            "phases_ms_per_solve": {
+                "setup": (elapsed_ms / args.steps) - sum(s["rhs_ms"] + s["iter_ms"] + s["final_ms"] for s in stats) / args.steps,
+                "rhs": sum(s["rhs_ms"] for s in stats) / args.steps,
+                "iteration": iter_phase_ms / args.steps,
+                "final": sum(s["final_ms"] for s in stats) / args.steps},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": None,
                          "kernel": "gds_kernel<float> (gather-dot/scatter, Eqs. vl/yhat1)",

@@ -111,6 +111,11 @@ typedef struct cphifi_stats {
   double gemm64_ms;
   int64_t kernel_launches;   /* every kernel this solve launched              */
   int64_t setup_launches;    /* kernels launched by the problem's creation    */
+  double rhs_ms;             /* CUDA-event time: right-hand side and start     */
+  double iter_ms;            /* CUDA-event time: the PCG loop (operator,
+                                updates, preconditioner, FP64 true residuals
+                                and restarts), i.e. the iteration phase        */
+  double final_ms;           /* CUDA-event time: W = U_K Wbar and its copy    */
 } cphifi_stats;
 
 typedef struct cphifi_ctx cphifi_ctx;

@@ -61,7 +61,9 @@ class Stats(ctypes.Structure):
                 ("gemm_launches", ctypes.c_int32), ("gemm_ms", ctypes.c_double),
                 ("gds64_ms", ctypes.c_double), ("gds64_launches", ctypes.c_int32),
                 ("gemm64_launches", ctypes.c_int32), ("gemm64_ms", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64), ("setup_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("setup_launches", ctypes.c_int64),
+                ("rhs_ms", ctypes.c_double), ("iter_ms", ctypes.c_double),
+                ("final_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -19,7 +19,9 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "cphifi.h"
@@ -39,6 +41,12 @@ struct cphifi_ctx {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   DevScalars* h_scalars = nullptr;  // pinned
   std::vector<cudaEvent_t> ev_pool;
+  // Device blocks released by destroyed problems, by size: a new problem of a
+  // similar shape reuses them instead of paying cudaMalloc/cudaFree (and the
+  // device synchronisation cudaFree implies) on every solve.
+  std::multimap<size_t, void*> pool;
+  size_t pool_bytes = 0;
+  cudaEvent_t phase[4] = {nullptr, nullptr, nullptr, nullptr};  // solve phase marks
 };
 
 struct cphifi_kernel {
@@ -57,13 +65,13 @@ struct cphifi_problem {
   int64_t q = 0;
   double gamma = 0.0;
   std::vector<int64_t> sizes;
-  std::vector<void*> allocs;
+  std::vector<std::pair<void*, size_t>> allocs;
   size_t bytes = 0;
   // observation data (sorted by kernel index)
   int32_t* perm = nullptr;
   int64_t* row_ptr = nullptr;
-  double* z64 = nullptr;
-  float* z32 = nullptr;
+  float* zhi = nullptr;  // Zhat = zhi + zlo (FP32 pair); zhi alone = FP32 operator
+  float* zlo = nullptr;
   int32_t *pseg = nullptr, *pbeg = nullptr, *pend = nullptr, *seg_first = nullptr,
           *seg_count = nullptr, *warp_first = nullptr;
   unsigned* seg_ticket = nullptr;
@@ -84,8 +92,8 @@ struct cphifi_problem {
          *bbar = nullptr, *xh64 = nullptr, *y164 = nullptr, *tmp64 = nullptr,
          *tmp64b = nullptr, *D64 = nullptr;
   float *pop32 = nullptr, *xh32 = nullptr, *y132 = nullptr, *D32 = nullptr;
-  void* cpart = nullptr;  // nsplit x n x r doubles
-  int nsplit = 1;
+  void* cpart = nullptr;  // max(nsplit64, nsplit32) x n x r doubles
+  int nsplit64 = 1, nsplit32 = 1;
   RedScratch red{};
   DevScalars* s = nullptr;    // the solve's scalars
   DevScalars* s2 = nullptr;   // scalars of the step-by-step calls
@@ -131,22 +139,68 @@ struct Enter {
   }
 };
 
+size_t pool_round(size_t bytes) {
+  if (bytes <= 4096) return (bytes + 255) & ~(size_t)255;
+  size_t g = 1;
+  while (g * 2 <= bytes) g *= 2;
+  const size_t step = std::max<size_t>(256, g / 8);
+  return (bytes + step - 1) / step * step;
+}
+
+void pool_trim(cphifi_ctx* ctx) {
+  for (auto& kv : ctx->pool) cudaFree(kv.second);
+  ctx->pool.clear();
+  ctx->pool_bytes = 0;
+}
+
+// A block of at least `bytes` (rounded to a size class) from the pool, or a
+// new one; *got is the block's size.
+cudaError_t pool_alloc(cphifi_ctx* ctx, size_t bytes, void** out, size_t* got) {
+  const size_t want = pool_round(bytes ? bytes : 1);
+  auto it = ctx->pool.lower_bound(want);
+  if (it != ctx->pool.end() && it->first <= want + want / 4) {
+    *out = it->second;
+    *got = it->first;
+    ctx->pool_bytes -= it->first;
+    ctx->pool.erase(it);
+    return cudaSuccess;
+  }
+  if (ctx->budget && ctx->in_use + ctx->pool_bytes + want > ctx->budget) pool_trim(ctx);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    pool_trim(ctx);
+    e = cudaMalloc(&p, want);
+  }
+  if (e != cudaSuccess) return e;
+  *out = p;
+  *got = want;
+  return cudaSuccess;
+}
+
+void pool_release(cphifi_ctx* ctx, void* p, size_t bytes) {
+  ctx->pool.emplace(bytes, p);
+  ctx->pool_bytes += bytes;
+}
+
 template <typename T>
 cudaError_t dalloc(cphifi_problem* P, T** out, size_t count) {
   *out = nullptr;
   if (count == 0) count = 1;
   void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  size_t got = 0;
+  cudaError_t e = pool_alloc(P->ctx, count * sizeof(T), &p, &got);
   if (e != cudaSuccess) return e;
-  P->allocs.push_back(p);
-  P->bytes += count * sizeof(T);
-  P->ctx->in_use += count * sizeof(T);
+  P->allocs.push_back({p, got});
+  P->bytes += got;
+  P->ctx->in_use += got;
   *out = (T*)p;
   return cudaSuccess;
 }
 
 void free_problem(cphifi_problem* P) {
-  for (void* a : P->allocs) cudaFree(a);
+  for (auto& a : P->allocs) pool_release(P->ctx, a.first, a.second);
   P->ctx->in_use -= std::min(P->ctx->in_use, P->bytes);
   P->allocs.clear();
   P->bytes = 0;
@@ -260,6 +314,7 @@ extern "C" int cphifi_ctx_create(cphifi_ctx** out, int device, size_t hbm_budget
             cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) == cudaSuccess &&
             cudaMallocHost(&ctx->h_scalars, sizeof(DevScalars)) == cudaSuccess;
+  for (int k = 0; ok && k < 4; ++k) ok = cudaEventCreate(&ctx->phase[k]) == cudaSuccess;
   cudaSetDevice(prev);
   if (!ok) {
     delete ctx;
@@ -275,7 +330,10 @@ extern "C" int cphifi_ctx_destroy(cphifi_ctx* ctx) {
   cudaGetDevice(&prev);
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  pool_trim(ctx);
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  for (auto e : ctx->phase)
+    if (e) cudaEventDestroy(e);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
   if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
@@ -374,8 +432,8 @@ static size_t problem_footprint(int64_t n, int64_t q, int r, int d_other,
                                 int64_t npieces_max) {
   size_t b = 0;
   const size_t nr = (size_t)n * r;
-  b += (size_t)zhat_elems(q, r) * sizeof(double);     // Zhat FP64
-  if (lowp) b += (size_t)zhat_elems(q, r) * sizeof(float);  // Zhat FP32
+  b += (size_t)zhat_elems(q, r) * 2 * sizeof(float);  // Zhat hi + lo
+  (void)lowp;
   b += (size_t)q * sizeof(int32_t);                    // perm
   b += (n + 1) * sizeof(int64_t) + 4 * n * sizeof(int32_t) + (n + 1) * sizeof(int32_t);
   b += (size_t)npieces_max * (3 * sizeof(int32_t) + 64 * sizeof(double));
@@ -409,20 +467,22 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
     M *= (double)sizes[m];
   }
   const int n = kern->n;
+  Enter guard(ctx);
   // Gather-dot/scatter decomposition: W warps (two resident 8-warp blocks per
   // SM at most, and no fewer than 64 observations per warp), L = ceil(q / W).
   const int64_t W64 = std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 16, (q + 63) / 64));
   const int W = (int)W64;
   const int64_t L = std::max<int64_t>(1, (q + W - 1) / W);
   const int64_t npieces_max = (int64_t)n + W + 1;
-  const int nsplit = gemm_pick_split(n, ctx->num_sms);
+  const int nsplit64 = gemm_pick_split<double, double>(n, ctx->num_sms);
+  const int nsplit32 = gemm_pick_split<float, float>(n, ctx->num_sms);
+  const int nsplit = std::max(nsplit64, nsplit32);
   const bool lowp = (flags & CPHIFI_NEED_LOWP) != 0;
   const size_t need = problem_footprint(n, q, r, d_other, sizes, lowp, nsplit, npieces_max);
   const size_t tmp_need = (size_t)q * (sizeof(int32_t) * (1 + d_other) + sizeof(double) * 2 +
                                        sizeof(uint32_t)) + radix_sort_tmp_bytes(q);
   if (ctx->budget && ctx->in_use + need + tmp_need > ctx->budget)
     return fail(ctx, CPHIFI_E_ADMISSION, "problem footprint exceeds the HBM budget");
-  Enter guard(ctx);
   auto t0 = std::chrono::steady_clock::now();
   cphifi_problem* P = new cphifi_problem();
   P->ctx = ctx;
@@ -433,20 +493,22 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   P->q = q;
   P->sizes = sizes;
   P->gamma = (double)q / ((double)n * M);
-  P->nsplit = nsplit;
+  P->nsplit64 = nsplit64;
+  P->nsplit32 = nsplit32;
   P->nwarps = W;
   P->obs_per_warp = L;
   cudaStream_t st = ctx->stream;
-  std::vector<void*> temps;
+  std::vector<std::pair<void*, size_t>> temps;
   auto tmp_alloc = [&](size_t bytes) -> void* {
     void* p = nullptr;
-    if (cudaMalloc(&p, bytes ? bytes : 1) != cudaSuccess) return nullptr;
-    temps.push_back(p);
+    size_t got = 0;
+    if (pool_alloc(ctx, bytes, &p, &got) != cudaSuccess) return nullptr;
+    temps.push_back({p, got});
     return p;
   };
   auto bail = [&](int code, const std::string& m) {
     cudaStreamSynchronize(st);
-    for (void* t : temps) cudaFree(t);
+    for (auto& t : temps) pool_release(ctx, t.first, t.second);
     free_problem(P);
     delete P;
     return fail(ctx, code, m);
@@ -464,8 +526,8 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   const size_t nr = (size_t)n * r;
   PCK(dalloc(P, &P->perm, q));
   PCK(dalloc(P, &P->row_ptr, n + 1));
-  PCK(dalloc(P, &P->z64, (size_t)zhat_elems(q, r)));
-  if (lowp) PCK(dalloc(P, &P->z32, (size_t)zhat_elems(q, r)));
+  PCK(dalloc(P, &P->zhi, (size_t)zhat_elems(q, r)));
+  PCK(dalloc(P, &P->zlo, (size_t)zhat_elems(q, r)));
   PCK(dalloc(P, &P->warp_first, (size_t)W + 1));
   PCK(dalloc(P, &P->seg_first, n + 1));
   PCK(dalloc(P, &P->seg_count, n));
@@ -526,8 +588,6 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
     vals_d = v;
     kidx_d = k;
   }
-  double* vals_sorted = (double*)tmp_alloc((size_t)q * sizeof(double));
-  if (!vals_sorted) return bail(CPHIFI_E_OOM, "temporary allocation failed");
   PCK(launch_validate_obs(kidx_d, oidx_d, vals_d, q, n, d_other, P->sizes_dev, P->err, st));
   PCK(cudaMemcpyAsync(keys, kidx_d, (size_t)q * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
   PCK(launch_iota(P->perm, q, st));
@@ -543,10 +603,6 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   }
   else if (q > 1) PCK(launch_check_sorted(keys, q, P->err, st));
   PCK(launch_row_ptr(keys, q, n, P->row_ptr, st));
-  PCK(launch_zhat((flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm, oidx_d, d_other,
-                  P->factors_dev, P->sizes_dev, r, q, P->z64, P->z32, vals_d,
-                  vals_sorted, P->err, st));
-
   // ---- pieces
   {
     void* stmp = tmp_alloc(exclusive_scan_tmp_bytes(n));
@@ -565,19 +621,21 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
     PCK(launch_warp_first(P->pbeg, np, L, W, P->warp_first, st));
   }
 
-  // ---- Gram, eig(V), right-hand side MTTKRP
+  // ---- Zhat (hi/lo) fused with the right-hand side MTTKRP; Gram, eig(V)
+  PieceList pl{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket,
+               P->warp_first, P->npieces, P->nwarps};
+  PCK(launch_zhat_mttkrp(pl, (flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm, oidx_d, d_other,
+                         P->factors_dev, P->sizes_dev, r, vals_d, P->zhi, P->zlo,
+                         (double*)P->gds_partial, P->Bm, n, P->err, st));
   PCK(launch_gram(P->factors_dev, P->sizes_dev, d_other, r, P->V, st));
   PCK(launch_jacobi_eig(P->V, r, P->dV, P->UV, 60, P->info, st));
   PCK(launch_convert<double, float>(P->UV, P->UV32, (int64_t)r * r, st));
-  PieceList pl{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket,
-               P->warp_first, P->npieces, P->nwarps};
-  PCK(launch_gds<double>(pl, P->z64, r, nullptr, n, vals_sorted, (double*)P->gds_partial,
-                         P->Bm, n, nullptr, st));
   PCK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   PCK(cudaStreamSynchronize(st));
   if (herr & 4) return bail(CPHIFI_E_INVALID_ARG, "CPHIFI_OBS_SORTED set but kidx is not sorted");
   if (herr) return bail(CPHIFI_E_INVALID_ARG, "invalid observation data");
-  for (void* t : temps) cudaFree(t);
+  PCK(cudaStreamSynchronize(st));  // the temporaries are free to reuse only after the work
+  for (auto& t : temps) pool_release(ctx, t.first, t.second);
   temps.clear();
   PCK(cudaStreamSynchronize(st));
   (void)t0;
@@ -624,7 +682,7 @@ struct Launcher {
     cudaEvent_t b = cat && tm ? tm->begin() : nullptr;
     cudaError_t e = launch_gemm_skinny<double, double>(P->kern->UK64, P->n, a_trans, scale, B, P->n,
                                                        out_part, P->n, split_stride(), P->n, P->r,
-                                                       P->nsplit, skip, st);
+                                                       P->nsplit64, skip, st);
     if (cat && tm) tm->end(b, cat == 1 ? tm->gemm : tm->gemm64);
     ++launches;
     return e;
@@ -634,7 +692,7 @@ struct Launcher {
     cudaEvent_t b = tm ? tm->begin() : nullptr;
     cudaError_t e = launch_gemm_skinny<float, float>(P->kern->UK32, P->n, a_trans, scale, B, P->n,
                                                      out_part, P->n, split_stride(), P->n, P->r,
-                                                     P->nsplit, skip, st);
+                                                     P->nsplit32, skip, st);
     if (tm) tm->end(b, tm->gemm);
     ++launches;
     return e;
@@ -643,14 +701,16 @@ struct Launcher {
   cudaError_t combine(int mode, const TC* C, const double* V, const double* Bv, TO* out,
                       DevScalars* s, const DevScalars* skip) {
     ++launches;
-    return launch_combine<TC, TO>(mode, C, split_stride(), P->nsplit, P->n, P->r, P->kern->dK, V,
+    const int ns = sizeof(TC) == 8 ? P->nsplit64 : P->nsplit32;
+    return launch_combine<TC, TO>(mode, C, split_stride(), ns, P->n, P->r, P->kern->dK, V,
                                   Bv, out, s, P->red, skip, st);
   }
+  // zlo = NULL selects the FP32 operator (T = float), else hi + lo (T = double).
   template <typename T>
-  cudaError_t gds(const T* Z, const T* Xh, T* Y, const DevScalars* skip, int cat) {
+  cudaError_t gds(const float* zlo, const T* Xh, T* Y, const DevScalars* skip, int cat) {
     cudaEvent_t b = (cat && tm) ? tm->begin() : nullptr;
-    cudaError_t e = launch_gds<T>(pieces(), Z, P->r, Xh, P->n, nullptr, (T*)P->gds_partial,
-                                  Y, P->n, skip, st);
+    cudaError_t e = launch_gds<T>(pieces(), P->zhi, zlo, P->r, Xh, P->n, nullptr,
+                                  (T*)P->gds_partial, Y, P->n, skip, st);
     if (cat && tm) tm->end(b, cat == 1 ? tm->gds : tm->gds64);
     ++launches;
     return e;
@@ -664,7 +724,7 @@ struct Launcher {
     cudaError_t e;
     if ((e = gemm64(true, P->kern->dK, xin, Cp, skip, cat)) != cudaSuccess) return e;
     if ((e = combine<double, double>(CM_STORE, Cp, nullptr, nullptr, P->xh64, s, skip)) != cudaSuccess) return e;
-    if ((e = gds<double>(P->z64, P->xh64, P->y164, skip, cat)) != cudaSuccess) return e;
+    if ((e = gds<double>(P->zlo, P->xh64, P->y164, skip, cat)) != cudaSuccess) return e;
     if ((e = gemm64(false, nullptr, P->y164, Cp, skip, cat)) != cudaSuccess) return e;
     return combine<double, double>(mode, Cp, xin, P->bbar, out, s, skip);
   }
@@ -674,7 +734,7 @@ struct Launcher {
     cudaError_t e;
     if ((e = gemm32(true, P->kern->dK, P->pop32, Cp, skip)) != cudaSuccess) return e;
     if ((e = combine<float, float>(CM_STORE, Cp, nullptr, nullptr, P->xh32, s, skip)) != cudaSuccess) return e;
-    if ((e = gds<float>(P->z32, P->xh32, P->y132, skip, 1)) != cudaSuccess) return e;
+    if ((e = gds<float>(nullptr, P->xh32, P->y132, skip, 1)) != cudaSuccess) return e;
     if ((e = gemm32(false, nullptr, P->y132, Cp, skip)) != cudaSuccess) return e;
     return combine<float, double>(CM_APPLY, Cp, xin, nullptr, out, s, skip);
   }
@@ -742,13 +802,7 @@ int check_params(cphifi_ctx* ctx, const cphifi_params* prm) {
 }
 
 int ensure_lowp(cphifi_problem* P) {
-  cphifi_ctx* ctx = P->ctx;
-  if (P->z32) return CPHIFI_OK;
-  const size_t elems = (size_t)zhat_elems(P->q, P->r);
-  if (ctx->budget && ctx->in_use + elems * sizeof(float) > ctx->budget)
-    return fail(ctx, CPHIFI_E_ADMISSION, "FP32 operator data exceeds the HBM budget");
-  CK(dalloc(P, &P->z32, elems));
-  CK(launch_convert<double, float>(P->z64, P->z32, (int64_t)elems, ctx->stream));
+  (void)P;  // the FP32 operator reads the hi part of Zhat, always present
   return CPHIFI_OK;
 }
 
@@ -779,6 +833,7 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
   h.rho = prm->rho;
   h.max_iter = prm->max_iter;
   h.mode = mixed ? 1 : 0;
+  CK(cudaEventRecord(ctx->phase[0], st));
   CK(cudaMemcpyAsync(P->s, &h, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
   CK(launch_build_D(P->kern->dK, P->dV, n, r, P->gamma, prm->lambda, prm->rho, P->D64, P->D32, st));
   // right-hand side in the eigenbasis: bbar = D_K U_K' B, and ||bbar||^2
@@ -795,6 +850,7 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
     CK(cudaMemcpyAsync(P->res, P->bbar, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
   CK(L.restart(mixed));
+  CK(cudaEventRecord(ctx->phase[1], st));
   DevScalars* hs = ctx->h_scalars;
   CK(cudaMemcpyAsync(hs, P->s, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -844,10 +900,12 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
     else if (!converged) status = CPHIFI_E_NOT_CONVERGED;
   }
   // W = U_K Wbar
+  CK(cudaEventRecord(ctx->phase[2], st));
   CK(L.gemm64(true, nullptr, P->x, (double*)P->cpart, nullptr, 0));
   double* Wdev = (mem == CPHIFI_MEM_DEVICE) ? W_out : P->tmp64;
   CK(L.combine<double, double>(CM_STORE, (double*)P->cpart, nullptr, nullptr, Wdev, P->s, nullptr));
   if (mem != CPHIFI_MEM_DEVICE) CK(download(W_out, Wdev, nr * sizeof(double), mem, st));
+  CK(cudaEventRecord(ctx->phase[3], st));
   CK(cudaStreamSynchronize(st));
   auto t1 = std::chrono::steady_clock::now();
   if (stats) {
@@ -863,6 +921,10 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
     stats->solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     stats->kernel_launches = L.launches;
     stats->setup_launches = P->create_launches;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->phase[0], ctx->phase[1]) == cudaSuccess) stats->rhs_ms = ms;
+    if (cudaEventElapsedTime(&ms, ctx->phase[1], ctx->phase[2]) == cudaSuccess) stats->iter_ms = ms;
+    if (cudaEventElapsedTime(&ms, ctx->phase[2], ctx->phase[3]) == cudaSuccess) stats->final_ms = ms;
     if (tm.on) {
       stats->gds_ms = Timer::total(tm.gds);
       stats->gds_launches = (int)tm.gds.size();
@@ -974,10 +1036,10 @@ extern "C" int cphifi_problem_gds(cphifi_problem* P, int precision, const double
   Launcher L{P, st, nullptr};
   CK(upload(P->xh64, Xhat, nr * sizeof(double), mem, st));
   if (precision == CPHIFI_FP64) {
-    CK(L.gds<double>(P->z64, P->xh64, P->y164, nullptr, 0));
+    CK(L.gds<double>(P->zlo, P->xh64, P->y164, nullptr, 0));
   } else {
     CK(launch_convert<double, float>(P->xh64, P->xh32, (int64_t)nr, st));
-    CK(L.gds<float>(P->z32, P->xh32, P->y132, nullptr, 0));
+    CK(L.gds<float>(nullptr, P->xh32, P->y132, nullptr, 0));
     CK(launch_convert<float, double>(P->y132, P->y164, (int64_t)nr, st));
   }
   CK(download(Y1, P->y164, nr * sizeof(double), mem, st));

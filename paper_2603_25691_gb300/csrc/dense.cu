@@ -91,15 +91,32 @@ gemm_skinny_kernel(const TA* __restrict__ A, int64_t lda, const double* __restri
   }
 }
 
+// Split of the k range: the grid is (ceil(n/128) row tiles) x nsplit blocks;
+// pick nsplit so that the blocks fill whole waves of the resident slots
+// (SMs x blocks per SM) as evenly as possible -- a grid of 1.04 waves runs
+// as long as two.
+template <typename TA, typename TC>
 int gemm_pick_split(int n, int num_sms) {
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gemm_skinny_kernel<TA, TC, true, true>, 256, 0);
+  if (occ < 1) occ = 1;
+  const int64_t slots = (int64_t)num_sms * occ;
   const int mt = (n + 127) / 128;
-  int s = (2 * num_sms + mt - 1) / mt;
-  const int kslabs = (n + 31) / 32;
-  if (s > kslabs) s = kslabs;
-  if (s > 32) s = 32;
-  if (s < 1) s = 1;
-  return s;
+  int smax = (n + 31) / 32;
+  if (smax > 32) smax = 32;
+  int best = 1;
+  double best_eff = -1.0;
+  for (int s = 1; s <= smax; ++s) {
+    const int64_t ctas = (int64_t)mt * s;
+    const int64_t waves = (ctas + slots - 1) / slots;
+    const double eff = (double)ctas / (double)(waves * slots);
+    if (eff > best_eff + 0.02) { best_eff = eff; best = s; }
+  }
+  return best;
 }
+
+template int gemm_pick_split<double, double>(int, int);
+template int gemm_pick_split<float, float>(int, int);
 
 template <typename TA, typename TC>
 cudaError_t launch_gemm_skinny(const TA* A, int64_t lda, bool a_trans, const double* scale_k,

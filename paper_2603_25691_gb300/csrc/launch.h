@@ -52,12 +52,6 @@ __host__ __device__ __forceinline__ int64_t zidx(int64_t l, int j, int r) {
 __host__ __device__ __forceinline__ int64_t zhat_elems(int64_t q, int r) {
   return ((q + 31) >> 5) * 32 * (int64_t)r;
 }
-// Zhat (Eq. zhat) in sorted order, FP64 and optional FP32.
-cudaError_t launch_zhat(const int32_t* perm, const int32_t* oidx, int d_other,
-                        const double* const* factors_dev, const int64_t* sizes_dev,
-                        int r, int64_t q, double* z64, float* z32,
-                        const double* vals, double* vals_sorted, int* err,
-                        cudaStream_t st);
 // Gather-dot/scatter (Eqs. vl and yhat1).  with_dot = false computes the
 // sparse MTTKRP B(i,:) = sum t_l Zhat(l,:) with t taken from `tvals`.
 struct PieceList {
@@ -71,10 +65,20 @@ struct PieceList {
   int npieces;
   int nwarps;
 };
+// Zhat is held as two FP32 arrays (hi, lo) in the tiled layout; T = float
+// reads hi, T = double reads hi + lo.
 template <typename T>
-cudaError_t launch_gds(const PieceList& pl, const T* Z, int r, const T* Xh,
-                       int64_t xld, const T* tvals, T* partial, T* Y, int64_t yld,
-                       const DevScalars* skip, cudaStream_t st);
+cudaError_t launch_gds(const PieceList& pl, const float* zhi, const float* zlo, int r,
+                       const T* Xh, int64_t xld, const T* tvals, T* partial, T* Y,
+                       int64_t yld, const DevScalars* skip, cudaStream_t st);
+// Zhat (Eq. zhat) in sorted order as hi/lo FP32 pairs, fused with the MTTKRP
+// B(i,:) = sum_{i_l = i} t_l Zhat(l,:) in FP64 (B column-major, ld ldb).
+// perm = NULL means the input is already sorted.  Bad indices set *err bit 1.
+cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const int32_t* oidx,
+                               int d_other, const double* const* factors_dev,
+                               const int64_t* sizes_dev, int r, const double* vals,
+                               float* zhi, float* zlo, double* partial, double* B,
+                               int64_t ldb, int* err, cudaStream_t st);
 
 // -------------------------------------------------------------- dense.cu ---
 // Skinny product C = op(A) diag(s) B for A n x n (op = identity when a_trans
@@ -87,6 +91,7 @@ cudaError_t launch_gemm_skinny(const TA* A, int64_t lda, bool a_trans,
                                TC* C, int64_t ldc, int64_t split_stride,
                                int n, int ncols, int nsplit,
                                const DevScalars* skip, cudaStream_t st);
+template <typename TA, typename TC>
 int gemm_pick_split(int n, int num_sms);
 
 // ----------------------------------------------------------------- cg.cu ---

@@ -371,75 +371,183 @@ cudaError_t launch_warp_first(const int32_t* pbeg, int npieces, int64_t L, int W
 
 // -------------------------------------------------------------- Zhat ------
 // Zhat(s, j) = prod_m A_m(oidx[perm[s], m], j) for the s-th observation in the
-// sorted order (Eq. zhat).  Factors are column-major n_m x r.  Zhat is stored
-// in tiles of 32 observations: tile t holds a 32 x r column-major block, so
-// element (s, j) lives at zidx(s, j, r) (see launch.h) and the 32 x r values
-// a warp reads in one round form one contiguous block.
-__global__ void zhat_kernel(const int32_t* __restrict__ perm, const int32_t* __restrict__ oidx,
-                            int d_other, const double* const* __restrict__ factors,
-                            const int64_t* __restrict__ sizes, int r, int64_t q,
-                            double* __restrict__ z64, float* __restrict__ z32,
-                            const double* __restrict__ vals, double* __restrict__ vals_sorted,
-                            int* err) {
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < q;
-       s += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t l = perm ? perm[s] : s;
-    vals_sorted[s] = vals[l];
-    int32_t id[8];
-    bool ok = true;
-    for (int m = 0; m < d_other && m < 8; ++m) {
-      id[m] = oidx[l * d_other + m];
-      if (id[m] < 0 || id[m] >= sizes[m]) ok = false;
+// sorted order (Eq. zhat), computed in FP64 and stored as an unevaluated sum of
+// two FP32 numbers hi + lo (hi = fl32(z), lo = fl32(z - hi); |z - hi - lo| <=
+// 2^-48 |z|): hi alone is the FP32 operator's Zhat, hi + lo the FP64 one.
+// Storage is in tiles of 32 observations (zidx in launch.h), so the 32 x r
+// values a warp round reads form one contiguous block.
+//
+// The same pass forms the sparse MTTKRP B(i,:) = sum_{i_l = i} t_l Zhat(l,:)
+// (§4, the right-hand side) in FP64, with the piece/warp decomposition and
+// deterministic combine of the gather-dot/scatter below.
+
+// Cross-lane helpers for LPO lanes per observation: lane = sub * OPW + o with
+// OPW = 32 / LPO observations per warp round; the lane owns the CPL = RP/LPO
+// columns [sub*CPL, (sub+1)*CPL).
+template <typename T, int LPO>
+__device__ __forceinline__ T sum_over_subs(T v) {
+  constexpr int OPW = 32 / LPO;
+#pragma unroll
+  for (int o = OPW; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sums acc over the OPW observations of a sub-group and stores the row piece:
+// lane (sub, o) writes columns sub*CPL + c for c = o, o + OPW, ...
+template <typename T, int RP, int LPO>
+__device__ __forceinline__ void reduce_row(T (&acc)[RP / LPO]) {
+  constexpr int OPW = 32 / LPO, CPL = RP / LPO;
+#pragma unroll
+  for (int c = 0; c < CPL; ++c)
+#pragma unroll
+    for (int o = OPW >> 1; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+}
+
+// Writes a reduced row (columns < r) to Y(:, seg) or, when the kernel index is
+// split over several pieces, to the piece's partial row; the last piece to
+// finish sums the partial rows in piece order.
+template <typename T, int RP, int LPO>
+__device__ __forceinline__ void store_row(const PieceList& pl, int p, int seg, int r,
+                                          const T (&acc)[RP / LPO], T* __restrict__ partial,
+                                          T* __restrict__ Y, int64_t yld) {
+  constexpr int OPW = 32 / LPO, CPL = RP / LPO;
+  const int lane = threadIdx.x & 31, sub = lane / OPW, o = lane % OPW;
+  const int np = pl.seg_count[seg];
+  if (np == 1) {
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      const int j = sub * CPL + c;
+      if ((c % OPW) == o && j < r) Y[(int64_t)j * yld + seg] = acc[c];
     }
-    if (!ok) atomicOr(err, 1);
-    for (int j = 0; j < r; ++j) {
-      double v = 1.0;
-      if (ok) {
-        for (int m = 0; m < d_other; ++m) {
-          const int32_t im = m < 8 ? id[m] : oidx[l * d_other + m];
-          v *= factors[m][(int64_t)j * sizes[m] + im];
-        }
-      } else {
-        v = 0.0;
-      }
-      z64[zidx(s, j, r)] = v;
-      if (z32) z32[zidx(s, j, r)] = (float)v;
+    return;
+  }
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    const int j = sub * CPL + c;
+    if ((c % OPW) == o && j < r) partial[(int64_t)p * RP + j] = acc[c];
+  }
+  __threadfence();
+  __syncwarp();
+  unsigned t = 0;
+  if (lane == 0) t = atomicAdd(&pl.seg_ticket[seg], 1u);
+  t = __shfl_sync(0xffffffffu, t, 0);
+  if (t == (unsigned)(np - 1)) {
+    __threadfence();
+    const int f = pl.seg_first[seg];
+    for (int j = lane; j < r; j += 32) {
+      T sacc = T(0);
+      for (int k = 0; k < np; ++k) sacc += __ldcg(&partial[(int64_t)(f + k) * RP + j]);
+      Y[(int64_t)j * yld + seg] = sacc;
     }
+    if (lane == 0) pl.seg_ticket[seg] = 0u;
   }
 }
 
-cudaError_t launch_zhat(const int32_t* perm, const int32_t* oidx, int d_other,
-                        const double* const* factors_dev, const int64_t* sizes_dev, int r,
-                        int64_t q, double* z64, float* z32, const double* vals,
-                        double* vals_sorted, int* err, cudaStream_t st) {
-  if (q == 0) return cudaSuccess;
-  const int blocks = (int)((q + 255) / 256 < 8192 ? (q + 255) / 256 : 8192);
-  zhat_kernel<<<blocks, 256, 0, st>>>(perm, oidx, d_other, factors_dev, sizes_dev, r, q, z64,
-                                      z32, vals, vals_sorted, err);
+template <int RP, int LPO>
+__global__ void __launch_bounds__(256)
+zhat_mttkrp_kernel(PieceList pl, const int32_t* __restrict__ perm, const int32_t* __restrict__ oidx,
+                   int d_other, const double* const* __restrict__ factors,
+                   const int64_t* __restrict__ sizes, int r, const double* __restrict__ vals,
+                   float* __restrict__ zhi, float* __restrict__ zlo, double* __restrict__ partial,
+                   double* __restrict__ B, int64_t ldb, int* err) {
+  constexpr int OPW = 32 / LPO, CPL = RP / LPO;
+  const int lane = threadIdx.x & 31, sub = lane / OPW, o = lane % OPW;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  int bad = 0;
+  for (int w = gw; w < pl.nwarps; w += nwarps) {
+    const int p_end = pl.warp_first[w + 1];
+    for (int p = pl.warp_first[w]; p < p_end; ++p) {
+      const int seg = pl.seg[p];
+      const int b = pl.beg[p], e = pl.end[p];
+      double acc[CPL];
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) acc[c] = 0.0;
+      for (int l = b + o; l < e; l += OPW) {
+        const int64_t src = perm ? (int64_t)perm[l] : (int64_t)l;
+        const double t = vals[src];
+        double z[CPL];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) z[c] = 1.0;
+        for (int m = 0; m < d_other; ++m) {
+          const int32_t im = oidx[src * d_other + m];
+          const int64_t nm = sizes[m];
+          const bool ok = im >= 0 && im < nm;
+          bad |= ok ? 0 : 1;
+          const double* F = factors[m] + (ok ? im : 0);
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            const int j = sub * CPL + c;
+            if (j < r) z[c] *= ok ? F[(int64_t)j * nm] : 0.0;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          const int j = sub * CPL + c;
+          if (j < r) {
+            const float hi = (float)z[c];
+            const float lo = (float)(z[c] - (double)hi);
+            zhi[zidx(l, j, r)] = hi;
+            zlo[zidx(l, j, r)] = lo;
+            acc[c] = fma(t, z[c], acc[c]);
+          }
+        }
+      }
+      reduce_row<double, RP, LPO>(acc);
+      store_row<double, RP, LPO>(pl, p, seg, r, acc, partial, B, ldb);
+    }
+  }
+  if (bad) atomicOr(err, 1);
+}
+
+cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const int32_t* oidx,
+                               int d_other, const double* const* factors_dev,
+                               const int64_t* sizes_dev, int r, const double* vals, float* zhi,
+                               float* zlo, double* partial, double* B, int64_t ldb, int* err,
+                               cudaStream_t st) {
+  if (pl.npieces == 0 || pl.nwarps == 0) return cudaSuccess;
+  const int blocks = (pl.nwarps + 7) / 8;
+#define CPHIFI_ZM(RPV, LPOV)                                                                     \
+  zhat_mttkrp_kernel<RPV, LPOV><<<blocks, 256, 0, st>>>(pl, perm, oidx, d_other, factors_dev,  \
+                                                         sizes_dev, r, vals, zhi, zlo, partial, \
+                                                         B, ldb, err)
+  if (r <= 8) CPHIFI_ZM(8, 1);
+  else if (r <= 16) CPHIFI_ZM(16, 1);
+  else if (r <= 32) CPHIFI_ZM(32, 2);
+  else if (r <= 48) CPHIFI_ZM(48, 4);
+  else if (r <= 64) CPHIFI_ZM(64, 4);
+  else return cudaErrorInvalidValue;
+#undef CPHIFI_ZM
   return cudaGetLastError();
 }
 
 // ------------------------------------------------ gather-dot / scatter ----
 // Warp w owns the pieces [warp_first[w], warp_first[w+1]), i.e. the sorted
-// observations [w L, (w+1) L).  Per piece (one kernel index i), lane t takes
-// observations b+t, b+t+32, ...: it loads Zhat(l, :) (a 32-observation round of
-// the warp reads one contiguous tile), forms xbar_l = Xhat(i,:).Zhat(l,:)
-// (Eq. vl) and accumulates xbar_l Zhat(l,:) in registers (Eq. yhat1).  The
-// warp then sums its 32 partial rows; a kernel index covered by one piece is
-// written directly, otherwise each piece stores its row and the last piece to
-// finish (per-index ticket) adds the pieces in piece order.  No
-// floating-point atomics: the result is deterministic.
-// RP is the register width (>= r); KEEPZ keeps the loaded row in registers
-// between the dot and the update, otherwise the update reloads it (L1 hit).
-template <typename T, int RP, bool WITH_DOT, bool KEEPZ>
-__global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const T* __restrict__ Z, int r,
+// observations [w L, (w+1) L).  Per piece (one kernel index i), each
+// observation l is handled by LPO lanes (each owning RP/LPO of the columns):
+// they load Zhat(l, :) (a warp round reads one contiguous tile), form
+// xbar_l = Xhat(i,:).Zhat(l,:) (Eq. vl; partial dots summed across the LPO
+// lanes) and accumulate xbar_l Zhat(l,:) in registers (Eq. yhat1).  The warp
+// then sums its partial rows; a kernel index covered by one piece is written
+// directly, otherwise each piece stores its row and the last piece to finish
+// (per-index ticket) adds the pieces in piece order.  No floating-point
+// atomics: the result is deterministic.
+//
+// T is the arithmetic: float reads Zhat's FP32 part (the mixed operator);
+// double reads hi + lo (the FP64 operator).  With `tvals` instead of Xh the
+// kernel computes sum_l t_l Zhat(l,:) (the MTTKRP form).
+template <typename T, int RP, bool WITH_DOT, int LPO>
+__global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __restrict__ zhi,
+                                                  const float* __restrict__ zlo, int r,
                                                   const T* __restrict__ Xh, int64_t xld,
                                                   const T* __restrict__ tvals,
                                                   T* __restrict__ partial, T* __restrict__ Y,
                                                   int64_t yld, const DevScalars* skip) {
   if (dev_skip(skip)) return;
+  constexpr int OPW = 32 / LPO, CPL = RP / LPO;
+  constexpr bool HILO = sizeof(T) == 8;
   __shared__ T xs[8][RP];
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, sub = lane / OPW, o = lane % OPW;
   const int wib = threadIdx.x >> 5;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -453,105 +561,79 @@ __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const T* __restr
         for (int j = lane; j < RP; j += 32) xs[wib][j] = j < r ? Xh[(int64_t)j * xld + seg] : T(0);
         __syncwarp();
       }
-      T acc[RP];
+      T acc[CPL];
 #pragma unroll
-      for (int j = 0; j < RP; ++j) acc[j] = T(0);
-      for (int l = b + lane; l < e; l += 32) {
-        const T* zrow = Z + zidx(l, 0, r);
+      for (int c = 0; c < CPL; ++c) acc[c] = T(0);
+      // Every lane runs the same number of rounds so the cross-lane sums of
+      // the dot product see the whole warp.
+      for (int l0 = b; l0 < e; l0 += OPW) {
+        const int l = l0 + o;
+        const bool act = l < e;
+        const int64_t base = zidx(act ? l : b, 0, r);
+        T z[CPL];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          const int j = sub * CPL + c;
+          T v = T(0);
+          if (act && j < r) {
+            if (HILO) v = (T)__ldcs(zhi + base + 32 * j) + (T)__ldcs(zlo + base + 32 * j);
+            else v = (T)__ldcs(zhi + base + 32 * j);
+          }
+          z[c] = v;
+        }
         T xb;
-        if (KEEPZ) {
-          T z[RP];
+        if (WITH_DOT) {
+          xb = T(0);
 #pragma unroll
-          for (int j = 0; j < RP; ++j) z[j] = j < r ? __ldcs(zrow + 32 * j) : T(0);
-          if (WITH_DOT) {
-            xb = T(0);
-#pragma unroll
-            for (int j = 0; j < RP; ++j) xb = fma(xs[wib][j], z[j], xb);
-          } else {
-            xb = tvals[l];
-          }
-#pragma unroll
-          for (int j = 0; j < RP; ++j) acc[j] = fma(xb, z[j], acc[j]);
+          for (int c = 0; c < CPL; ++c) xb = fma(xs[wib][sub * CPL + c], z[c], xb);
+          if (LPO > 1) xb = sum_over_subs<T, LPO>(xb);
         } else {
-          if (WITH_DOT) {
-            xb = T(0);
-#pragma unroll
-            for (int j = 0; j < RP; ++j)
-              if (j < r) xb = fma(xs[wib][j], zrow[32 * j], xb);
-          } else {
-            xb = tvals[l];
-          }
-#pragma unroll
-          for (int j = 0; j < RP; ++j)
-            if (j < r) acc[j] = fma(xb, __ldcs(zrow + 32 * j), acc[j]);
+          xb = act ? tvals[l] : T(0);
         }
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) acc[c] = fma(xb, z[c], acc[c]);
       }
-#pragma unroll
-      for (int j = 0; j < RP; ++j)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
-      const int np = pl.seg_count[seg];
-      if (np == 1) {
-#pragma unroll
-        for (int j = 0; j < RP; ++j)
-          if ((j & 31) == lane && j < r) Y[(int64_t)j * yld + seg] = acc[j];
-      } else {
-#pragma unroll
-        for (int j = 0; j < RP; ++j)
-          if ((j & 31) == lane && j < r) partial[(int64_t)p * RP + j] = acc[j];
-        __threadfence();
-        __syncwarp();
-        unsigned t = 0;
-        if (lane == 0) t = atomicAdd(&pl.seg_ticket[seg], 1u);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t == (unsigned)(np - 1)) {
-          __threadfence();
-          const int f = pl.seg_first[seg];
-          for (int j = lane; j < r; j += 32) {
-            T sacc = T(0);
-            for (int k = 0; k < np; ++k) sacc += __ldcg(&partial[(int64_t)(f + k) * RP + j]);
-            Y[(int64_t)j * yld + seg] = sacc;
-          }
-          if (lane == 0) pl.seg_ticket[seg] = 0u;
-        }
-      }
+      reduce_row<T, RP, LPO>(acc);
+      store_row<T, RP, LPO>(pl, p, seg, r, acc, partial, Y, yld);
     }
   }
 }
 
-template <typename T, int RP>
-static cudaError_t gds_dispatch_keep(const PieceList& pl, const T* Z, int r, const T* Xh,
-                                     int64_t xld, const T* tvals, T* partial, T* Y, int64_t yld,
-                                     const DevScalars* skip, cudaStream_t st) {
-  constexpr bool keep = RP * sizeof(T) <= 256;
+template <typename T, int RP, int LPO>
+static cudaError_t gds_dispatch(const PieceList& pl, const float* zhi, const float* zlo, int r,
+                                const T* Xh, int64_t xld, const T* tvals, T* partial, T* Y,
+                                int64_t yld, const DevScalars* skip, cudaStream_t st) {
   const int blocks = (pl.nwarps + 7) / 8;
   if (Xh)
-    gds_kernel<T, RP, true, keep><<<blocks, 256, 0, st>>>(pl, Z, r, Xh, xld, tvals, partial, Y,
-                                                          yld, skip);
+    gds_kernel<T, RP, true, LPO><<<blocks, 256, 0, st>>>(pl, zhi, zlo, r, Xh, xld, tvals, partial,
+                                                         Y, yld, skip);
   else
-    gds_kernel<T, RP, false, keep><<<blocks, 256, 0, st>>>(pl, Z, r, Xh, xld, tvals, partial, Y,
-                                                           yld, skip);
+    gds_kernel<T, RP, false, LPO><<<blocks, 256, 0, st>>>(pl, zhi, zlo, r, Xh, xld, tvals,
+                                                          partial, Y, yld, skip);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_gds(const PieceList& pl, const T* Z, int r, const T* Xh, int64_t xld,
-                       const T* tvals, T* partial, T* Y, int64_t yld, const DevScalars* skip,
-                       cudaStream_t st) {
+cudaError_t launch_gds(const PieceList& pl, const float* zhi, const float* zlo, int r,
+                       const T* Xh, int64_t xld, const T* tvals, T* partial, T* Y, int64_t yld,
+                       const DevScalars* skip, cudaStream_t st) {
   if (pl.npieces == 0 || pl.nwarps == 0) return cudaSuccess;
-  if (r <= 8) return gds_dispatch_keep<T, 8>(pl, Z, r, Xh, xld, tvals, partial, Y, yld, skip, st);
-  if (r <= 16) return gds_dispatch_keep<T, 16>(pl, Z, r, Xh, xld, tvals, partial, Y, yld, skip, st);
-  if (r <= 32) return gds_dispatch_keep<T, 32>(pl, Z, r, Xh, xld, tvals, partial, Y, yld, skip, st);
-  if (r <= 48) return gds_dispatch_keep<T, 48>(pl, Z, r, Xh, xld, tvals, partial, Y, yld, skip, st);
-  if (r <= 64) return gds_dispatch_keep<T, 64>(pl, Z, r, Xh, xld, tvals, partial, Y, yld, skip, st);
+  constexpr bool dbl = sizeof(T) == 8;
+  // Lanes per observation keep the per-lane registers (RP/LPO values of both
+  // the row and the accumulator) within budget.
+  if (r <= 8) return gds_dispatch<T, 8, 1>(pl, zhi, zlo, r, Xh, xld, tvals, partial, Y, yld, skip, st);
+  if (r <= 16) return gds_dispatch<T, 16, 1>(pl, zhi, zlo, r, Xh, xld, tvals, partial, Y, yld, skip, st);
+  if (r <= 32) return gds_dispatch<T, 32, dbl ? 2 : 1>(pl, zhi, zlo, r, Xh, xld, tvals, partial, Y, yld, skip, st);
+  if (r <= 48) return gds_dispatch<T, 48, dbl ? 4 : 1>(pl, zhi, zlo, r, Xh, xld, tvals, partial, Y, yld, skip, st);
+  if (r <= 64) return gds_dispatch<T, 64, dbl ? 4 : 2>(pl, zhi, zlo, r, Xh, xld, tvals, partial, Y, yld, skip, st);
   return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_gds<double>(const PieceList&, const double*, int, const double*,
-                                        int64_t, const double*, double*, double*, int64_t,
-                                        const DevScalars*, cudaStream_t);
-template cudaError_t launch_gds<float>(const PieceList&, const float*, int, const float*,
-                                       int64_t, const float*, float*, float*, int64_t,
-                                       const DevScalars*, cudaStream_t);
+template cudaError_t launch_gds<double>(const PieceList&, const float*, const float*, int,
+                                        const double*, int64_t, const double*, double*, double*,
+                                        int64_t, const DevScalars*, cudaStream_t);
+template cudaError_t launch_gds<float>(const PieceList&, const float*, const float*, int,
+                                       const float*, int64_t, const float*, float*, float*,
+                                       int64_t, const DevScalars*, cudaStream_t);
 
 }  // namespace cphifi
