@@ -58,26 +58,35 @@ typedef enum cphifi_status {
 
 enum { CPHIFI_MEM_HOST = 0, CPHIFI_MEM_DEVICE = 1 };
 
-/* Arithmetic of the PCG operator (§4.4.1 product).  CG vectors, scalars,
- * reductions, the right-hand side and every true-residual evaluation are FP64
- * in all modes.
- *  FP64       : every step in FP64.
- *  MIXED_FP32 : operator in FP32 (FP32 products, FP32 gather-dot/scatter)
- *               with FP64 true-residual restarts every k_replace iterations.
- *  MIXED_TF32 : as MIXED_FP32 with the two n x n products on the tensor
- *               cores in TF32 (FP32 accumulate).
- *  MIXED_BF16 : as MIXED_TF32 with BF16 operands.                           */
+/* Arithmetic of the PCG operator (§4.4.1 product).  CG vectors, scalars and
+ * reductions are FP64 in all modes.
+ *  FP64          : every step in FP64 (FP64 FMA units).
+ *  MIXED_FP32    : operator in FP32 (FP32 products, FP32 gather-dot/scatter);
+ *                  every k_replace iterations an FP64-accurate true residual
+ *                  restarts PCG, and only it decides convergence.
+ *  MIXED_TF32    : as MIXED_FP32 with the two n x n products on the tensor
+ *                  cores in TF32 (FP32 accumulate).
+ *  MIXED_BF16    : as MIXED_TF32 with BF16 operands.
+ *  FP64_EMULATED : every step FP64-accurate in double-float arithmetic (pairs
+ *                  of FP32 numbers, 48-bit significand, error-free TwoSum /
+ *                  TwoProd transforms) on the FP32 units.
+ * In every mode but FP64, the FP64-accurate steps (right-hand side, true
+ * residuals, W = U_K Wbar) use the double-float arithmetic: on GB300 its FP32
+ * units are ~60x faster than its FP64 units.                                */
 typedef enum cphifi_precision {
   CPHIFI_FP64 = 0,
   CPHIFI_MIXED_FP32 = 1,
   CPHIFI_MIXED_TF32 = 2,
-  CPHIFI_MIXED_BF16 = 3
+  CPHIFI_MIXED_BF16 = 3,
+  CPHIFI_FP64_EMULATED = 4
 } cphifi_precision;
 
 /* Problem-creation flags. */
 #define CPHIFI_OBS_SORTED 0x1u  /* kidx is non-decreasing: skip the device sort */
-#define CPHIFI_NEED_FP64 0x2u   /* build the FP64 operator data (always built)  */
-#define CPHIFI_NEED_LOWP 0x4u   /* also build the FP32 operator data (mixed)    */
+#define CPHIFI_NEED_FP64 0x2u   /* build the FP64 operator data (FP64 mode)      */
+#define CPHIFI_NEED_LOWP 0x4u   /* build the hi/lo FP32 operator data (other
+                                   modes); neither flag: both are built; a mode
+                                   whose data is missing builds it on first use */
 
 typedef struct cphifi_params {
   double lambda;      /* RKHS regularisation, >= 0 (§2)                       */

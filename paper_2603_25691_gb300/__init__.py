@@ -37,12 +37,14 @@ FP64 = 0
 MIXED_FP32 = 1
 MIXED_TF32 = 2
 MIXED_BF16 = 3
+FP64_EMULATED = 4
 
 OBS_SORTED = 0x1
 NEED_LOWP = 0x4
 
 PRECISIONS = {"fp64": FP64, "mixed_fp32": MIXED_FP32, "mixed_tf32": MIXED_TF32,
-              "mixed_bf16": MIXED_BF16}
+              "mixed_bf16": MIXED_BF16, "fp64_emulated": FP64_EMULATED}
+NEED_FP64 = 0x2
 
 
 class Params(ctypes.Structure):
@@ -256,7 +258,9 @@ class Problem:
     """cphifi_problem_create: one subproblem (sort, Zhat, Gram, eig(V), B)."""
 
     def __init__(self, ctx: Context, kernel: Kernel, factors, kidx, oidx, vals, r: int,
-                 sorted_obs: bool = False, lowp: bool = False):
+                 sorted_obs: bool = False, lowp: bool | None = None):
+        # lowp: True = build only the hi/lo data of the mixed/emulated modes,
+        # False = only the FP64 data, None = both.
         self.ctx, self.kernel, self.r = ctx, kernel, int(r)
         self.n = kernel.n
         fb, sizes = _factor_bufs(factors, self.r)
@@ -268,7 +272,11 @@ class Problem:
         self.sizes = sizes
         sizes_arr = (ctypes.c_int64 * len(sizes))(*sizes)
         fptrs = (ctypes.c_void_p * len(fb))(*[b.ptr for b in fb])
-        flags = (OBS_SORTED if sorted_obs else 0) | (NEED_LOWP if lowp else 0)
+        flags = (OBS_SORTED if sorted_obs else 0)
+        if lowp is True:
+            flags |= NEED_LOWP
+        elif lowp is False:
+            flags |= NEED_FP64
         h = ctypes.c_void_p()
         rc = lib().cphifi_problem_create(ctx.h, kernel.h, len(fb), sizes_arr, fptrs, self.r,
                                          self.q, k.ptr, o.ptr, v.ptr, flags, k.mem,

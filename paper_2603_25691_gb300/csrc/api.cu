@@ -53,7 +53,8 @@ struct cphifi_kernel {
   cphifi_ctx* ctx = nullptr;
   int n = 0;
   double* UK64 = nullptr;  // n x n column-major
-  float* UK32 = nullptr;
+  float* UK32 = nullptr;   // fl32(U_K): the FP32 operator's U_K and the hi part
+  float* UKlo = nullptr;   // fl32(U_K - UK32): U_K = UK32 + UKlo to 2^-48 (double-float)
   double* dK = nullptr;    // n
   size_t bytes = 0;
 };
@@ -70,7 +71,8 @@ struct cphifi_problem {
   // observation data (sorted by kernel index)
   int32_t* perm = nullptr;
   int64_t* row_ptr = nullptr;
-  float* zhi = nullptr;  // Zhat = zhi + zlo (FP32 pair); zhi alone = FP32 operator
+  double* z64 = nullptr;  // Zhat in FP64 (the FP64 operator)
+  float* zhi = nullptr;   // Zhat = zhi + zlo (FP32 pair, mixed modes); zhi = FP32 operator
   float* zlo = nullptr;
   int32_t *pseg = nullptr, *pbeg = nullptr, *pend = nullptr, *seg_first = nullptr,
           *seg_count = nullptr, *warp_first = nullptr;
@@ -81,7 +83,10 @@ struct cphifi_problem {
   void* gds_partial = nullptr;  // npieces x 64 doubles
   // factors and their Gram
   std::vector<double*> factors;
+  std::vector<float*> fhi, flo;  // factors as double-float pairs
   double** factors_dev = nullptr;
+  float** fhi_dev = nullptr;
+  float** flo_dev = nullptr;
   int64_t* sizes_dev = nullptr;
   double *V = nullptr, *dV = nullptr, *UV = nullptr;
   float* UV32 = nullptr;
@@ -92,8 +97,9 @@ struct cphifi_problem {
          *bbar = nullptr, *xh64 = nullptr, *y164 = nullptr, *tmp64 = nullptr,
          *tmp64b = nullptr, *D64 = nullptr;
   float *pop32 = nullptr, *xh32 = nullptr, *y132 = nullptr, *D32 = nullptr;
-  void* cpart = nullptr;  // max(nsplit64, nsplit32) x n x r doubles
-  int nsplit64 = 1, nsplit32 = 1;
+  float *Bhi = nullptr, *Blo = nullptr;  // double-float product operand
+  void* cpart = nullptr;  // max(nsplit64, nsplit32, nsplitdf) x n x r doubles
+  int nsplit64 = 1, nsplit32 = 1, nsplitdf = 1;
   RedScratch red{};
   DevScalars* s = nullptr;    // the solve's scalars
   DevScalars* s2 = nullptr;   // scalars of the step-by-step calls
@@ -370,7 +376,7 @@ extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
   if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
   const size_t nn = (size_t)n * n;
-  const size_t bytes = nn * (sizeof(double) + sizeof(float)) + n * sizeof(double);
+  const size_t bytes = nn * (sizeof(double) + 2 * sizeof(float)) + n * sizeof(double);
   if (ctx->budget && ctx->in_use + bytes > ctx->budget)
     return fail(ctx, CPHIFI_E_ADMISSION, "kernel matrix exceeds the HBM budget");
   Enter guard(ctx);
@@ -381,6 +387,7 @@ extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
   auto cleanup = [&](int code, const std::string& m) {
     if (kern->UK64) cudaFree(kern->UK64);
     if (kern->UK32) cudaFree(kern->UK32);
+    if (kern->UKlo) cudaFree(kern->UKlo);
     if (kern->dK) cudaFree(kern->dK);
     if (err) cudaFree(err);
     delete kern;
@@ -388,6 +395,7 @@ extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
   };
   if (cudaMalloc(&kern->UK64, nn * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&kern->UK32, nn * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&kern->UKlo, nn * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&kern->dK, n * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&err, sizeof(int)) != cudaSuccess)
     return cleanup(CPHIFI_E_OOM, "cudaMalloc failed for the kernel matrix");
@@ -398,7 +406,8 @@ extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
       cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess ||
       launch_validate_dense(kern->UK64, (int64_t)nn, err, st) != cudaSuccess ||
       launch_validate_dense(kern->dK, n, err, st) != cudaSuccess ||
-      launch_convert<double, float>(kern->UK64, kern->UK32, (int64_t)nn, st) != cudaSuccess ||
+      launch_split_df(kern->UK64, nullptr, (int64_t)nn, (int64_t)nn, kern->UK32, kern->UKlo, st) !=
+          cudaSuccess ||
       cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return cleanup(CPHIFI_E_DEVICE, "uploading the kernel eigendecomposition failed");
@@ -419,6 +428,7 @@ extern "C" int cphifi_kernel_destroy(cphifi_kernel* kern) {
   cudaStreamSynchronize(ctx->stream);
   cudaFree(kern->UK64);
   cudaFree(kern->UK32);
+  cudaFree(kern->UKlo);
   cudaFree(kern->dK);
   ctx->in_use -= std::min(ctx->in_use, kern->bytes);
   cudaSetDevice(prev);
@@ -476,9 +486,14 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   const int64_t npieces_max = (int64_t)n + W + 1;
   const int nsplit64 = gemm_pick_split<double, double>(n, ctx->num_sms);
   const int nsplit32 = gemm_pick_split<float, float>(n, ctx->num_sms);
-  const int nsplit = std::max(nsplit64, nsplit32);
-  const bool lowp = (flags & CPHIFI_NEED_LOWP) != 0;
-  const size_t need = problem_footprint(n, q, r, d_other, sizes, lowp, nsplit, npieces_max);
+  const int nsplitdf = gemm_df_pick_split(n, ctx->num_sms);
+  const int nsplit = std::max(std::max(nsplit64, nsplit32), nsplitdf);
+  // Operator data: FP64 Zhat for the FP64 operator, hi/lo FP32 pairs for the
+  // mixed modes; neither flag set means both.
+  const bool need64 = (flags & CPHIFI_NEED_FP64) || !(flags & CPHIFI_NEED_LOWP);
+  const bool lowp = (flags & CPHIFI_NEED_LOWP) || !(flags & CPHIFI_NEED_FP64);
+  const size_t need = problem_footprint(n, q, r, d_other, sizes, lowp, nsplit, npieces_max) +
+                      (need64 ? (size_t)zhat_elems(q, r) * sizeof(double) : 0);
   const size_t tmp_need = (size_t)q * (sizeof(int32_t) * (1 + d_other) + sizeof(double) * 2 +
                                        sizeof(uint32_t)) + radix_sort_tmp_bytes(q);
   if (ctx->budget && ctx->in_use + need + tmp_need > ctx->budget)
@@ -495,6 +510,7 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   P->gamma = (double)q / ((double)n * M);
   P->nsplit64 = nsplit64;
   P->nsplit32 = nsplit32;
+  P->nsplitdf = nsplitdf;
   P->nwarps = W;
   P->obs_per_warp = L;
   cudaStream_t st = ctx->stream;
@@ -526,16 +542,27 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   const size_t nr = (size_t)n * r;
   PCK(dalloc(P, &P->perm, q));
   PCK(dalloc(P, &P->row_ptr, n + 1));
-  PCK(dalloc(P, &P->zhi, (size_t)zhat_elems(q, r)));
-  PCK(dalloc(P, &P->zlo, (size_t)zhat_elems(q, r)));
+  if (lowp) {
+    PCK(dalloc(P, &P->zhi, (size_t)zhat_elems(q, r)));
+    PCK(dalloc(P, &P->zlo, (size_t)zhat_elems(q, r)));
+  }
+  if (need64) PCK(dalloc(P, &P->z64, (size_t)zhat_elems(q, r)));
   PCK(dalloc(P, &P->warp_first, (size_t)W + 1));
   PCK(dalloc(P, &P->seg_first, n + 1));
   PCK(dalloc(P, &P->seg_count, n));
   PCK(dalloc(P, &P->seg_ticket, n));
   PCK(dalloc(P, &P->factors_dev, d_other));
+  PCK(dalloc(P, &P->fhi_dev, d_other));
+  PCK(dalloc(P, &P->flo_dev, d_other));
   PCK(dalloc(P, &P->sizes_dev, d_other));
   P->factors.resize(d_other);
-  for (int m = 0; m < d_other; ++m) PCK(dalloc(P, &P->factors[m], (size_t)sizes[m] * r));
+  P->fhi.resize(d_other);
+  P->flo.resize(d_other);
+  for (int m = 0; m < d_other; ++m) {
+    PCK(dalloc(P, &P->factors[m], (size_t)sizes[m] * r));
+    PCK(dalloc(P, &P->fhi[m], (size_t)sizes[m] * r));
+    PCK(dalloc(P, &P->flo[m], (size_t)sizes[m] * r));
+  }
   PCK(dalloc(P, &P->V, r * r));
   PCK(dalloc(P, &P->dV, r));
   PCK(dalloc(P, &P->UV, r * r));
@@ -546,7 +573,7 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   for (double** v : {&P->x, &P->res, &P->z, &P->p, &P->y, &P->bbar, &P->xh64, &P->y164,
                      &P->tmp64, &P->tmp64b, &P->D64})
     PCK(dalloc(P, v, nr));
-  for (float** v : {&P->pop32, &P->xh32, &P->y132, &P->D32}) PCK(dalloc(P, v, nr));
+  for (float** v : {&P->pop32, &P->xh32, &P->y132, &P->D32, &P->Bhi, &P->Blo}) PCK(dalloc(P, v, nr));
   PCK(dalloc(P, (double**)&P->cpart, (size_t)nsplit * nr));
   PCK(dalloc(P, &P->red.partials, (size_t)kRedMaxBlocks * kRedSlots));
   PCK(dalloc(P, &P->red.ticket, 4));
@@ -560,11 +587,16 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   // ---- factors
   PCK(cudaMemcpyAsync(P->factors_dev, P->factors.data(), d_other * sizeof(double*),
                       cudaMemcpyHostToDevice, st));
+  PCK(cudaMemcpyAsync(P->fhi_dev, P->fhi.data(), d_other * sizeof(float*),
+                      cudaMemcpyHostToDevice, st));
+  PCK(cudaMemcpyAsync(P->flo_dev, P->flo.data(), d_other * sizeof(float*),
+                      cudaMemcpyHostToDevice, st));
   PCK(cudaMemcpyAsync(P->sizes_dev, sizes.data(), d_other * sizeof(int64_t),
                       cudaMemcpyHostToDevice, st));
   for (int m = 0; m < d_other; ++m) {
     PCK(upload(P->factors[m], factors[m], (size_t)sizes[m] * r * sizeof(double), mem, st));
     PCK(launch_validate_dense(P->factors[m], sizes[m] * r, P->err, st));
+    PCK(launch_split_df(P->factors[m], nullptr, sizes[m] * r, sizes[m] * r, P->fhi[m], P->flo[m], st));
   }
 
   // ---- observations: copy, validate, sort by kernel index
@@ -625,8 +657,8 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   PieceList pl{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket,
                P->warp_first, P->npieces, P->nwarps};
   PCK(launch_zhat_mttkrp(pl, (flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm, oidx_d, d_other,
-                         P->factors_dev, P->sizes_dev, r, vals_d, P->zhi, P->zlo,
-                         (double*)P->gds_partial, P->Bm, n, P->err, st));
+                         P->fhi_dev, P->flo_dev, P->sizes_dev, r, vals_d, P->zhi, P->zlo,
+                         P->z64, (double*)P->gds_partial, P->Bm, n, P->err, st));
   PCK(launch_gram(P->factors_dev, P->sizes_dev, d_other, r, P->V, st));
   PCK(launch_jacobi_eig(P->V, r, P->dV, P->UV, 60, P->info, st));
   PCK(launch_convert<double, float>(P->UV, P->UV32, (int64_t)r * r, st));
@@ -697,20 +729,50 @@ struct Launcher {
     ++launches;
     return e;
   }
+  // Double-float product (FP64-accurate on FP32 units): out_part gets the
+  // partial products of op(U_K) diag(scale) B over nsplitdf splits.
+  cudaError_t gemm_df(bool a_trans, const double* scale, const double* B, double* out_part,
+                      const DevScalars* skip, int cat) {
+    cudaError_t e = launch_split_df(B, scale, P->n, (int64_t)P->n * P->r, P->Bhi, P->Blo, st);
+    ++launches;
+    if (e != cudaSuccess) return e;
+    cudaEvent_t b = cat && tm ? tm->begin() : nullptr;
+    e = launch_gemm_df(P->kern->UK32, P->kern->UKlo, P->n, a_trans, P->Bhi, P->Blo, P->n,
+                       out_part, P->n, split_stride(), P->n, P->r, P->nsplitdf, skip, st);
+    if (cat && tm) tm->end(b, cat == 1 ? tm->gemm : tm->gemm64);
+    ++launches;
+    return e;
+  }
+  // ns: number of split partials in C (0 = the FP64/FP32 product default).
   template <typename TC, typename TO>
   cudaError_t combine(int mode, const TC* C, const double* V, const double* Bv, TO* out,
-                      DevScalars* s, const DevScalars* skip) {
+                      DevScalars* s, const DevScalars* skip, int ns = 0) {
     ++launches;
-    const int ns = sizeof(TC) == 8 ? P->nsplit64 : P->nsplit32;
+    if (ns == 0) ns = sizeof(TC) == 8 ? P->nsplit64 : P->nsplit32;
     return launch_combine<TC, TO>(mode, C, split_stride(), ns, P->n, P->r, P->kern->dK, V,
                                   Bv, out, s, P->red, skip, st);
   }
-  // zlo = NULL selects the FP32 operator (T = float), else hi + lo (T = double).
-  template <typename T>
-  cudaError_t gds(const float* zlo, const T* Xh, T* Y, const DevScalars* skip, int cat) {
+  // Gather-dot/scatter in the three arithmetics (cat as for the products).
+  cudaError_t gds32(const float* Xh, float* Y, const DevScalars* skip, int cat) {
     cudaEvent_t b = (cat && tm) ? tm->begin() : nullptr;
-    cudaError_t e = launch_gds<T>(pieces(), P->zhi, zlo, P->r, Xh, P->n, nullptr,
-                                  (T*)P->gds_partial, Y, P->n, skip, st);
+    cudaError_t e = launch_gds_f32(pieces(), P->zhi, P->r, Xh, P->n, (float*)P->gds_partial, Y,
+                                   P->n, skip, st);
+    if (cat && tm) tm->end(b, cat == 1 ? tm->gds : tm->gds64);
+    ++launches;
+    return e;
+  }
+  cudaError_t gds64(const double* Xh, double* Y, const DevScalars* skip, int cat) {
+    cudaEvent_t b = (cat && tm) ? tm->begin() : nullptr;
+    cudaError_t e = launch_gds_f64(pieces(), P->z64, P->r, Xh, P->n, (double*)P->gds_partial, Y,
+                                   P->n, skip, st);
+    if (cat && tm) tm->end(b, cat == 1 ? tm->gds : tm->gds64);
+    ++launches;
+    return e;
+  }
+  cudaError_t gdsdf(const double* Xh, double* Y, const DevScalars* skip, int cat) {
+    cudaEvent_t b = (cat && tm) ? tm->begin() : nullptr;
+    cudaError_t e = launch_gds_df(pieces(), P->zhi, P->zlo, P->r, Xh, P->n,
+                                  (double*)P->gds_partial, Y, P->n, skip, st);
     if (cat && tm) tm->end(b, cat == 1 ? tm->gds : tm->gds64);
     ++launches;
     return e;
@@ -724,9 +786,21 @@ struct Launcher {
     cudaError_t e;
     if ((e = gemm64(true, P->kern->dK, xin, Cp, skip, cat)) != cudaSuccess) return e;
     if ((e = combine<double, double>(CM_STORE, Cp, nullptr, nullptr, P->xh64, s, skip)) != cudaSuccess) return e;
-    if ((e = gds<double>(P->zlo, P->xh64, P->y164, skip, cat)) != cudaSuccess) return e;
+    if ((e = gds64(P->xh64, P->y164, skip, cat)) != cudaSuccess) return e;
     if ((e = gemm64(false, nullptr, P->y164, Cp, skip, cat)) != cudaSuccess) return e;
     return combine<double, double>(mode, Cp, xin, P->bbar, out, s, skip);
+  }
+  // The same operator in double-float arithmetic (FP64-accurate, FP32 units).
+  cudaError_t opdf(int mode, const double* xin, double* out, DevScalars* s,
+                   const DevScalars* skip, int cat) {
+    double* Cp = (double*)P->cpart;
+    const int ns = P->nsplitdf;
+    cudaError_t e;
+    if ((e = gemm_df(true, P->kern->dK, xin, Cp, skip, cat)) != cudaSuccess) return e;
+    if ((e = combine<double, double>(CM_STORE, Cp, nullptr, nullptr, P->xh64, s, skip, ns)) != cudaSuccess) return e;
+    if ((e = gdsdf(P->xh64, P->y164, skip, cat)) != cudaSuccess) return e;
+    if ((e = gemm_df(false, nullptr, P->y164, Cp, skip, cat)) != cudaSuccess) return e;
+    return combine<double, double>(mode, Cp, xin, P->bbar, out, s, skip, ns);
   }
   // FP32 operator (mixed): pop32 holds the FP32 copy of xin.
   cudaError_t op32(const double* xin, double* out, DevScalars* s, const DevScalars* skip) {
@@ -734,45 +808,69 @@ struct Launcher {
     cudaError_t e;
     if ((e = gemm32(true, P->kern->dK, P->pop32, Cp, skip)) != cudaSuccess) return e;
     if ((e = combine<float, float>(CM_STORE, Cp, nullptr, nullptr, P->xh32, s, skip)) != cudaSuccess) return e;
-    if ((e = gds<float>(nullptr, P->xh32, P->y132, skip, 1)) != cudaSuccess) return e;
+    if ((e = gds32(P->xh32, P->y132, skip, 1)) != cudaSuccess) return e;
     if ((e = gemm32(false, nullptr, P->y132, Cp, skip)) != cudaSuccess) return e;
     return combine<float, double>(CM_APPLY, Cp, xin, nullptr, out, s, skip);
   }
+  // FP64-accurate operator of the given arithmetic (mode: CM_APPLY / CM_RESID).
+  cudaError_t opwide(bool emulated, int mode, const double* xin, double* out, DevScalars* s,
+                     const DevScalars* skip, int cat) {
+    return emulated ? opdf(mode, xin, out, s, skip, cat) : op64(mode, xin, out, s, skip, cat);
+  }
+  // out = D_K U_K' B (emulated: double-float product) with ||out||^2 -> bb
+  // when norm is set; the right-hand side and the start transform.
+  cudaError_t utb(bool emulated, int mode, const double* B, double* out, DevScalars* s) {
+    double* Cp = (double*)P->cpart;
+    cudaError_t e = emulated ? gemm_df(false, nullptr, B, Cp, nullptr, 0)
+                             : gemm64(false, nullptr, B, Cp, nullptr, 0);
+    if (e != cudaSuccess) return e;
+    return combine<double, double>(mode, Cp, nullptr, nullptr, out, s, nullptr,
+                                   emulated ? P->nsplitdf : P->nsplit64);
+  }
+  // out = U_K x (emulated: double-float product).
+  cudaError_t ux(bool emulated, const double* x, double* out, DevScalars* s) {
+    double* Cp = (double*)P->cpart;
+    cudaError_t e = emulated ? gemm_df(true, nullptr, x, Cp, nullptr, 0)
+                             : gemm64(true, nullptr, x, Cp, nullptr, 0);
+    if (e != cudaSuccess) return e;
+    return combine<double, double>(CM_STORE, Cp, nullptr, nullptr, out, s, nullptr,
+                                   emulated ? P->nsplitdf : P->nsplit64);
+  }
 
   // One PCG iteration (operator, update + preconditioner, direction).
-  cudaError_t iteration(bool mixed) {
-    DevScalars* s = P->s;
-    cudaError_t e;
-    if (mixed) {
-      if ((e = op32(P->p, P->y, s, s)) != cudaSuccess) return e;
-      ++launches;
-      if ((e = launch_update_precond<float>(UP_ITER, P->n, P->r, P->x, P->res, P->p, P->y, P->z,
-                                            P->UV32, P->D32, s, P->red, st)) != cudaSuccess)
-        return e;
-      ++launches;
-      return launch_pupdate<float>(P->n, P->r, P->z, P->p, P->pop32, s, st);
-    }
-    if ((e = op64(CM_APPLY, P->p, P->y, s, s, 1)) != cudaSuccess) return e;
-    ++launches;
-    if ((e = launch_update_precond<double>(UP_ITER, P->n, P->r, P->x, P->res, P->p, P->y, P->z,
-                                           P->UV, P->D64, s, P->red, st)) != cudaSuccess)
-      return e;
-    ++launches;
-    return launch_pupdate<double>(P->n, P->r, P->z, P->p, nullptr, s, st);
-  }
-
-  // FP64 true residual of x, then a restart from it (p = z).
-  cudaError_t true_residual_restart(bool mixed) {
-    DevScalars* s = P->s;
-    cudaError_t e;
-    if ((e = op64(CM_RESID, P->x, P->res, s, nullptr, mixed ? 2 : 1)) != cudaSuccess) return e;
-    return restart(mixed);
-  }
-  cudaError_t restart(bool mixed) {
+  // lowop: FP32 operator and FP32 preconditioner (mixed modes); otherwise
+  // the FP64-accurate operator (emul: double-float, else FP64).
+  cudaError_t iteration(bool lowop, bool emul) {
     DevScalars* s = P->s;
     cudaError_t e;
     launches += 2;
-    if (mixed) {
+    if (lowop) {
+      if ((e = op32(P->p, P->y, s, s)) != cudaSuccess) return e;
+      if ((e = launch_update_precond<float>(UP_ITER, P->n, P->r, P->x, P->res, P->p, P->y, P->z,
+                                            P->UV32, P->D32, s, P->red, st)) != cudaSuccess)
+        return e;
+      return launch_pupdate<float>(P->n, P->r, P->z, P->p, P->pop32, s, st);
+    }
+    if ((e = opwide(emul, CM_APPLY, P->p, P->y, s, s, 1)) != cudaSuccess) return e;
+    if ((e = launch_update_precond<double>(UP_ITER, P->n, P->r, P->x, P->res, P->p, P->y, P->z,
+                                           P->UV, P->D64, s, P->red, st)) != cudaSuccess)
+      return e;
+    return launch_pupdate<double>(P->n, P->r, P->z, P->p, nullptr, s, st);
+  }
+
+  // FP64-accurate true residual of x, then a restart from it (p = z).
+  cudaError_t true_residual_restart(bool lowop, bool emul) {
+    DevScalars* s = P->s;
+    cudaError_t e;
+    if ((e = opwide(emul, CM_RESID, P->x, P->res, s, nullptr, lowop ? 2 : 1)) != cudaSuccess)
+      return e;
+    return restart(lowop);
+  }
+  cudaError_t restart(bool lowop) {
+    DevScalars* s = P->s;
+    cudaError_t e;
+    launches += 2;
+    if (lowop) {
       if ((e = launch_update_precond<float>(UP_RESTART, P->n, P->r, P->x, P->res, P->p, P->y,
                                             P->z, P->UV32, P->D32, s, P->red, st)) != cudaSuccess)
         return e;
@@ -794,15 +892,36 @@ int check_params(cphifi_ctx* ctx, const cphifi_params* prm) {
   if (!(prm->tol > 0.0) || !std::isfinite(prm->tol))
     return fail(ctx, CPHIFI_E_INVALID_ARG, "tol must be finite and > 0");
   if (prm->max_iter < 0) return fail(ctx, CPHIFI_E_INVALID_ARG, "max_iter must be >= 0");
-  if (prm->precision < CPHIFI_FP64 || prm->precision > CPHIFI_MIXED_BF16)
+  if (prm->precision < CPHIFI_FP64 || prm->precision > CPHIFI_FP64_EMULATED)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
   if (prm->precision == CPHIFI_MIXED_TF32 || prm->precision == CPHIFI_MIXED_BF16)
     return fail(ctx, CPHIFI_E_UNSUPPORTED, "tensor-core operator not built");
   return CPHIFI_OK;
 }
 
+// The mixed and double-float arithmetics read Zhat as hi/lo FP32 pairs; the
+// FP64 operator reads FP64.  A problem built for one gets the other on first
+// use (one elementwise pass).
 int ensure_lowp(cphifi_problem* P) {
-  (void)P;  // the FP32 operator reads the hi part of Zhat, always present
+  cphifi_ctx* ctx = P->ctx;
+  if (P->zhi) return CPHIFI_OK;
+  const size_t elems = (size_t)zhat_elems(P->q, P->r);
+  if (ctx->budget && ctx->in_use + 2 * elems * sizeof(float) > ctx->budget)
+    return fail(ctx, CPHIFI_E_ADMISSION, "hi/lo operator data exceeds the HBM budget");
+  CK(dalloc(P, &P->zhi, elems));
+  CK(dalloc(P, &P->zlo, elems));
+  CK(launch_split_df(P->z64, nullptr, (int64_t)elems, (int64_t)elems, P->zhi, P->zlo, ctx->stream));
+  return CPHIFI_OK;
+}
+
+int ensure_fp64(cphifi_problem* P) {
+  cphifi_ctx* ctx = P->ctx;
+  if (P->z64) return CPHIFI_OK;
+  const size_t elems = (size_t)zhat_elems(P->q, P->r);
+  if (ctx->budget && ctx->in_use + elems * sizeof(double) > ctx->budget)
+    return fail(ctx, CPHIFI_E_ADMISSION, "FP64 operator data exceeds the HBM budget");
+  CK(dalloc(P, &P->z64, elems));
+  CK(launch_join_df(P->zhi, P->zlo, (int64_t)elems, P->z64, ctx->stream));
   return CPHIFI_OK;
 }
 
@@ -818,8 +937,12 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
   if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
   Enter guard(ctx);
-  const bool mixed = prm->precision != CPHIFI_FP64;
-  if (mixed && (rc = ensure_lowp(P)) != CPHIFI_OK) return rc;
+  // mixed: FP32 operator inside PCG, stop only on the FP64-accurate true
+  // residual (restart every k_replace); emul: the FP64-accurate steps run in
+  // double-float arithmetic (every mode but FP64).
+  const bool mixed = prm->precision == CPHIFI_MIXED_FP32;
+  const bool emul = prm->precision != CPHIFI_FP64;
+  if ((rc = emul ? ensure_lowp(P) : ensure_fp64(P)) != CPHIFI_OK) return rc;
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = ctx->stream;
   const int n = P->n, r = P->r;
@@ -837,14 +960,12 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
   CK(cudaMemcpyAsync(P->s, &h, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
   CK(launch_build_D(P->kern->dK, P->dV, n, r, P->gamma, prm->lambda, prm->rho, P->D64, P->D32, st));
   // right-hand side in the eigenbasis: bbar = D_K U_K' B, and ||bbar||^2
-  CK(L.gemm64(false, nullptr, P->Bm, (double*)P->cpart, nullptr, 0));
-  CK(L.combine<double, double>(CM_DK_NORM, (double*)P->cpart, nullptr, nullptr, P->bbar, P->s, nullptr));
+  CK(L.utb(emul, CM_DK_NORM, P->Bm, P->bbar, P->s));
   // start: x = U_K' W0 (or 0) and its true residual
   if (W0) {
     CK(upload(P->tmp64, W0, nr * sizeof(double), mem, st));
-    CK(L.gemm64(false, nullptr, P->tmp64, (double*)P->cpart, nullptr, 0));
-    CK(L.combine<double, double>(CM_STORE, (double*)P->cpart, nullptr, nullptr, P->x, P->s, nullptr));
-    CK(L.op64(CM_RESID, P->x, P->res, P->s, nullptr, 0));
+    CK(L.utb(emul, CM_STORE, P->tmp64, P->x, P->s));
+    CK(L.opwide(emul, CM_RESID, P->x, P->res, P->s, nullptr, 0));
   } else {
     CK(cudaMemsetAsync(P->x, 0, nr * sizeof(double), st));
     CK(cudaMemcpyAsync(P->res, P->bbar, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -870,8 +991,8 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
       const int left = prm->max_iter - hs->iter;
       if (left <= 0) break;
       const int m = std::min(cycle, left);
-      for (int k = 0; k < m; ++k) CK(L.iteration(mixed));
-      if (mixed) CK(L.true_residual_restart(true));
+      for (int k = 0; k < m; ++k) CK(L.iteration(mixed, emul));
+      if (mixed) CK(L.true_residual_restart(true, emul));
       CK(cudaMemcpyAsync(hs, P->s, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       if (hs->status) break;
@@ -880,9 +1001,9 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
         continue;
       }
       if (hs->done) {
-        // FP64: the recurrence met tol; confirm with the true residual and
-        // restart from it if it does not (one refinement step).
-        CK(L.true_residual_restart(false));
+        // FP64-accurate operator: the recurrence met tol; confirm with the
+        // true residual and restart from it if it does not (refinement).
+        CK(L.true_residual_restart(false, emul));
         CK(cudaMemcpyAsync(hs, P->s, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if (hs->status) break;
@@ -891,7 +1012,7 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
     }
     if (!converged && !hs->status) {
       // final true residual of the returned iterate
-      CK(L.op64(CM_RESID, P->x, P->res, P->s, nullptr, 0));
+      CK(L.opwide(emul, CM_RESID, P->x, P->res, P->s, nullptr, 0));
       CK(cudaMemcpyAsync(hs, P->s, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       if (hs->done) converged = true;
@@ -901,9 +1022,8 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
   }
   // W = U_K Wbar
   CK(cudaEventRecord(ctx->phase[2], st));
-  CK(L.gemm64(true, nullptr, P->x, (double*)P->cpart, nullptr, 0));
   double* Wdev = (mem == CPHIFI_MEM_DEVICE) ? W_out : P->tmp64;
-  CK(L.combine<double, double>(CM_STORE, (double*)P->cpart, nullptr, nullptr, Wdev, P->s, nullptr));
+  CK(L.ux(emul, P->x, Wdev, P->s));
   if (mem != CPHIFI_MEM_DEVICE) CK(download(W_out, Wdev, nr * sizeof(double), mem, st));
   CK(cudaEventRecord(ctx->phase[3], st));
   CK(cudaStreamSynchronize(st));
@@ -949,7 +1069,7 @@ extern "C" int cphifi_solve(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t 
   if (!ctx) return CPHIFI_E_INVALID_ARG;
   int rc = check_params(ctx, params);
   if (rc != CPHIFI_OK) return rc;
-  if (params->precision != CPHIFI_FP64) flags |= CPHIFI_NEED_LOWP;
+  flags |= params->precision == CPHIFI_FP64 ? CPHIFI_NEED_FP64 : CPHIFI_NEED_LOWP;
   auto t0 = std::chrono::steady_clock::now();
   cphifi_problem* P = nullptr;
   rc = cphifi_problem_create(ctx, kern, d_other, other_sizes, factors, r, q, kidx, oidx, vals,
@@ -989,13 +1109,13 @@ extern "C" int cphifi_problem_matvec(cphifi_problem* P, int precision, double la
                                      const double* X, double* Y, int mem) {
   if (!P || !X || !Y) return CPHIFI_E_INVALID_ARG;
   cphifi_ctx* ctx = P->ctx;
-  if (precision != CPHIFI_FP64 && precision != CPHIFI_MIXED_FP32)
-    return fail(ctx, precision >= 0 && precision <= CPHIFI_MIXED_BF16 ? CPHIFI_E_UNSUPPORTED
-                                                                        : CPHIFI_E_INVALID_ARG,
-                "matvec precision");
+  if (precision == CPHIFI_MIXED_TF32 || precision == CPHIFI_MIXED_BF16)
+    return fail(ctx, CPHIFI_E_UNSUPPORTED, "tensor-core operator not built");
+  if (precision < CPHIFI_FP64 || precision > CPHIFI_FP64_EMULATED)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
   Enter guard(ctx);
   int rc;
-  if (precision != CPHIFI_FP64 && (rc = ensure_lowp(P)) != CPHIFI_OK) return rc;
+  if ((rc = precision == CPHIFI_FP64 ? ensure_fp64(P) : ensure_lowp(P)) != CPHIFI_OK) return rc;
   cudaStream_t st = ctx->stream;
   const size_t nr = (size_t)P->n * P->r;
   Launcher L{P, st, nullptr};
@@ -1005,16 +1125,15 @@ extern "C" int cphifi_problem_matvec(cphifi_problem* P, int precision, double la
   h.rz = 1.0;
   CK(cudaMemcpyAsync(P->s2, &h, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
   CK(upload(P->tmp64, X, nr * sizeof(double), mem, st));
-  // xbar = U_K' X
+  // xbar = U_K' X, then the operator in the eigenbasis, then Y = U_K ybar
   CK(L.gemm64(false, nullptr, P->tmp64, (double*)P->cpart, nullptr, 0));
   CK(L.combine<double, double>(CM_STORE, (double*)P->cpart, nullptr, nullptr, P->tmp64b, P->s2, nullptr));
-  if (precision == CPHIFI_FP64) {
-    CK(L.op64(CM_APPLY, P->tmp64b, P->y, P->s2, nullptr, 0));
-  } else {
+  if (precision == CPHIFI_MIXED_FP32) {
     CK(launch_convert<double, float>(P->tmp64b, P->pop32, (int64_t)nr, st));
     CK(L.op32(P->tmp64b, P->y, P->s2, nullptr));
+  } else {
+    CK(L.opwide(precision == CPHIFI_FP64_EMULATED, CM_APPLY, P->tmp64b, P->y, P->s2, nullptr, 0));
   }
-  // Y = U_K ybar
   CK(L.gemm64(true, nullptr, P->y, (double*)P->cpart, nullptr, 0));
   CK(L.combine<double, double>(CM_STORE, (double*)P->cpart, nullptr, nullptr, P->tmp64, P->s2, nullptr));
   CK(download(Y, P->tmp64, nr * sizeof(double), mem, st));
@@ -1026,20 +1145,22 @@ extern "C" int cphifi_problem_gds(cphifi_problem* P, int precision, const double
                                   int mem) {
   if (!P || !Xhat || !Y1) return CPHIFI_E_INVALID_ARG;
   cphifi_ctx* ctx = P->ctx;
-  if (precision < CPHIFI_FP64 || precision > CPHIFI_MIXED_BF16)
+  if (precision < CPHIFI_FP64 || precision > CPHIFI_FP64_EMULATED)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
   Enter guard(ctx);
   int rc;
-  if (precision != CPHIFI_FP64 && (rc = ensure_lowp(P)) != CPHIFI_OK) return rc;
+  if ((rc = precision == CPHIFI_FP64 ? ensure_fp64(P) : ensure_lowp(P)) != CPHIFI_OK) return rc;
   cudaStream_t st = ctx->stream;
   const size_t nr = (size_t)P->n * P->r;
   Launcher L{P, st, nullptr};
   CK(upload(P->xh64, Xhat, nr * sizeof(double), mem, st));
   if (precision == CPHIFI_FP64) {
-    CK(L.gds<double>(P->zlo, P->xh64, P->y164, nullptr, 0));
+    CK(L.gds64(P->xh64, P->y164, nullptr, 0));
+  } else if (precision == CPHIFI_FP64_EMULATED) {
+    CK(L.gdsdf(P->xh64, P->y164, nullptr, 0));
   } else {
     CK(launch_convert<double, float>(P->xh64, P->xh32, (int64_t)nr, st));
-    CK(L.gds<float>(nullptr, P->xh32, P->y132, nullptr, 0));
+    CK(L.gds32(P->xh32, P->y132, nullptr, 0));
     CK(launch_convert<float, double>(P->y132, P->y164, (int64_t)nr, st));
   }
   CK(download(Y1, P->y164, nr * sizeof(double), mem, st));

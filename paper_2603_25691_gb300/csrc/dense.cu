@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df.cuh"
 #include "launch.h"
 
 namespace cphifi {
@@ -139,6 +140,165 @@ cudaError_t launch_gemm_skinny(const TA* A, int64_t lda, bool a_trans, const dou
     else
       gemm_skinny_kernel<TA, TC, false, false><<<grid, 256, 0, st>>>(A, lda, scale_k, B, ldb, C, ldc, split_stride, n, ncols, kchunk, skip);
   }
+  return cudaGetLastError();
+}
+
+// Double-float version (FP64-accurate products of the mixed solve: the
+// right-hand side, the true residual, W = U_K Wbar).  A and B arrive as hi/lo
+// FP32 pairs (A = U_K split once per kernel, B split per call with the
+// optional row scale folded in); every multiply-add is an exact TwoProd and a
+// TwoSum-compensated accumulation (df.cuh), the partial products are written
+// as FP64.  FP32 units only: GB300 runs them ~60x faster than FP64 FMA.
+template <bool ATRANS>
+__global__ void __launch_bounds__(256)
+gemm_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo, int64_t lda,
+               const float* __restrict__ Bhi, const float* __restrict__ Blo, int64_t ldb,
+               double* __restrict__ C, int64_t ldc, int64_t split_stride, int n, int ncols,
+               int kchunk, const DevScalars* skip) {
+  if (dev_skip(skip)) return;
+  constexpr int BM = 128, BK = 16, TM = BM / 32, TNMAX = 8;
+  __shared__ float Ash[BK][BM + 1], Asl[BK][BM + 1];
+  __shared__ float Bsh[BK][64], Bsl[BK][64];
+  const int tid = threadIdx.x;
+  const int ty = tid & 31, tx = tid >> 5;
+  const int tn = (ncols + 7) / 8;
+  const int i0 = blockIdx.x * BM;
+  const int kbeg = blockIdx.y * kchunk;
+  const int kend = min(n, kbeg + kchunk);
+  df acc[TM][TNMAX];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TNMAX; ++b) acc[a][b] = df{0.f, 0.f};
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    for (int idx = tid; idx < BM * BK; idx += 256) {
+      int ii, kk;
+      if (ATRANS) { ii = idx % BM; kk = idx / BM; } else { kk = idx % BK; ii = idx / BK; }
+      const int i = i0 + ii, k = k0 + kk;
+      float h = 0.f, l = 0.f;
+      if (i < n && k < kend) {
+        const int64_t off = ATRANS ? (int64_t)k * lda + i : (int64_t)i * lda + k;
+        h = Ahi[off];
+        l = Alo[off];
+      }
+      Ash[kk][ii] = h;
+      Asl[kk][ii] = l;
+    }
+    for (int idx = tid; idx < BK * 64; idx += 256) {
+      const int kk = idx % BK, j = idx / BK;
+      const int k = k0 + kk;
+      float h = 0.f, l = 0.f;
+      if (k < kend && j < ncols) {
+        h = Bhi[(int64_t)j * ldb + k];
+        l = Blo[(int64_t)j * ldb + k];
+      }
+      Bsh[kk][j] = h;
+      Bsl[kk][j] = l;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < BK; ++kk) {
+      df a[TM], b[TNMAX];
+#pragma unroll
+      for (int m = 0; m < TM; ++m) a[m] = df{Ash[kk][ty + 32 * m], Asl[kk][ty + 32 * m]};
+#pragma unroll
+      for (int c = 0; c < TNMAX; ++c)
+        b[c] = c < tn ? df{Bsh[kk][tx * tn + c], Bsl[kk][tx * tn + c]} : df{0.f, 0.f};
+#pragma unroll
+      for (int m = 0; m < TM; ++m)
+#pragma unroll
+        for (int c = 0; c < TNMAX; ++c)
+          if (c < tn) df_acc_prod(acc[m][c], a[m], b[c]);
+    }
+    __syncthreads();
+  }
+  double* Cs = C + (int64_t)blockIdx.y * split_stride;
+#pragma unroll
+  for (int m = 0; m < TM; ++m) {
+    const int i = i0 + ty + 32 * m;
+    if (i >= n) continue;
+#pragma unroll
+    for (int c = 0; c < TNMAX; ++c) {
+      const int j = tx * tn + c;
+      if (c < tn && j < ncols) Cs[(int64_t)j * ldc + i] = df_to_double(df_norm(acc[m][c]));
+    }
+  }
+}
+
+int gemm_df_pick_split(int n, int num_sms) {
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gemm_df_kernel<true>, 256, 0);
+  if (occ < 1) occ = 1;
+  const int64_t slots = (int64_t)num_sms * occ;
+  const int mt = (n + 127) / 128;
+  int smax = (n + 15) / 16;
+  if (smax > 32) smax = 32;
+  int best = 1;
+  double best_eff = -1.0;
+  for (int s = 1; s <= smax; ++s) {
+    const int64_t ctas = (int64_t)mt * s;
+    const int64_t waves = (ctas + slots - 1) / slots;
+    const double eff = (double)ctas / (double)(waves * slots);
+    if (eff > best_eff + 0.02) { best_eff = eff; best = s; }
+  }
+  return best;
+}
+
+cudaError_t launch_gemm_df(const float* Ahi, const float* Alo, int64_t lda, bool a_trans,
+                           const float* Bhi, const float* Blo, int64_t ldb, double* C, int64_t ldc,
+                           int64_t split_stride, int n, int ncols, int nsplit,
+                           const DevScalars* skip, cudaStream_t st) {
+  if (n == 0 || ncols == 0) return cudaSuccess;
+  if (ncols > 64) return cudaErrorInvalidValue;
+  int kchunk = (n + nsplit - 1) / nsplit;
+  kchunk = (kchunk + 15) / 16 * 16;
+  const dim3 grid((n + 127) / 128, nsplit);
+  if (a_trans)
+    gemm_df_kernel<true><<<grid, 256, 0, st>>>(Ahi, Alo, lda, Bhi, Blo, ldb, C, ldc, split_stride,
+                                               n, ncols, kchunk, skip);
+  else
+    gemm_df_kernel<false><<<grid, 256, 0, st>>>(Ahi, Alo, lda, Bhi, Blo, ldb, C, ldc,
+                                                split_stride, n, ncols, kchunk, skip);
+  return cudaGetLastError();
+}
+
+// hi + lo = scale[i] * X(i, j) (scale may be NULL), the double-float operand
+// of gemm_df_kernel.
+__global__ void split_df_kernel(const double* __restrict__ X, const double* __restrict__ scale,
+                                int64_t rows, int64_t total, float* __restrict__ hi,
+                                float* __restrict__ lo) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const double v = scale ? scale[t % rows] * X[t] : X[t];
+    const df d = df_from_double(v);
+    hi[t] = d.hi;
+    lo[t] = d.lo;
+  }
+}
+
+cudaError_t launch_split_df(const double* X, const double* scale, int64_t rows, int64_t total,
+                            float* hi, float* lo, cudaStream_t st) {
+  if (total == 0) return cudaSuccess;
+  int64_t b = (total + 255) / 256;
+  if (b > 4096) b = 4096;
+  split_df_kernel<<<(int)b, 256, 0, st>>>(X, scale, rows, total, hi, lo);
+  return cudaGetLastError();
+}
+
+// out = hi + lo in FP64.
+__global__ void join_df_kernel(const float* __restrict__ hi, const float* __restrict__ lo,
+                               int64_t total, double* __restrict__ out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = (double)hi[t] + (double)lo[t];
+}
+
+cudaError_t launch_join_df(const float* hi, const float* lo, int64_t total, double* out,
+                           cudaStream_t st) {
+  if (total == 0) return cudaSuccess;
+  int64_t b = (total + 255) / 256;
+  if (b > 4096) b = 4096;
+  join_df_kernel<<<(int)b, 256, 0, st>>>(hi, lo, total, out);
   return cudaGetLastError();
 }
 

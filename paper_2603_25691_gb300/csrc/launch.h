@@ -65,19 +65,27 @@ struct PieceList {
   int npieces;
   int nwarps;
 };
-// Zhat is held as two FP32 arrays (hi, lo) in the tiled layout; T = float
-// reads hi, T = double reads hi + lo.
-template <typename T>
-cudaError_t launch_gds(const PieceList& pl, const float* zhi, const float* zlo, int r,
-                       const T* Xh, int64_t xld, const T* tvals, T* partial, T* Y,
-                       int64_t yld, const DevScalars* skip, cudaStream_t st);
-// Zhat (Eq. zhat) in sorted order as hi/lo FP32 pairs, fused with the MTTKRP
-// B(i,:) = sum_{i_l = i} t_l Zhat(l,:) in FP64 (B column-major, ld ldb).
-// perm = NULL means the input is already sorted.  Bad indices set *err bit 1.
+// Gather-dot/scatter in three arithmetics (all in the tiled Zhat layout):
+// FP32 reading Zhat's hi part (mixed operator), FP64 reading z64 (FP64
+// operator), double-float reading hi + lo (FP64-accurate true residuals).
+cudaError_t launch_gds_f32(const PieceList& pl, const float* zhi, int r, const float* Xh,
+                           int64_t xld, float* partial, float* Y, int64_t yld,
+                           const DevScalars* skip, cudaStream_t st);
+cudaError_t launch_gds_f64(const PieceList& pl, const double* z64, int r, const double* Xh,
+                           int64_t xld, double* partial, double* Y, int64_t yld,
+                           const DevScalars* skip, cudaStream_t st);
+cudaError_t launch_gds_df(const PieceList& pl, const float* zhi, const float* zlo, int r,
+                          const double* Xh, int64_t xld, double* partial, double* Y,
+                          int64_t yld, const DevScalars* skip, cudaStream_t st);
+// Zhat (Eq. zhat) in sorted order, computed in double-float from the factors'
+// hi/lo parts, written as hi/lo FP32 pairs and/or FP64 (either may be NULL),
+// fused with the MTTKRP B(i,:) = sum_{i_l = i} t_l Zhat(l,:) (B column-major,
+// ld ldb, FP64 result).  perm = NULL: input already sorted.  Bad indices set
+// *err bit 1.
 cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const int32_t* oidx,
-                               int d_other, const double* const* factors_dev,
+                               int d_other, const float* const* fhi, const float* const* flo,
                                const int64_t* sizes_dev, int r, const double* vals,
-                               float* zhi, float* zlo, double* partial, double* B,
+                               float* zhi, float* zlo, double* z64, double* partial, double* B,
                                int64_t ldb, int* err, cudaStream_t st);
 
 // -------------------------------------------------------------- dense.cu ---
@@ -93,6 +101,19 @@ cudaError_t launch_gemm_skinny(const TA* A, int64_t lda, bool a_trans,
                                const DevScalars* skip, cudaStream_t st);
 template <typename TA, typename TC>
 int gemm_pick_split(int n, int num_sms);
+// Double-float product C = op(A) B with A = Ahi + Alo and B = Bhi + Blo
+// (hi/lo FP32 pairs), FP64 partial products per split.
+cudaError_t launch_gemm_df(const float* Ahi, const float* Alo, int64_t lda, bool a_trans,
+                           const float* Bhi, const float* Blo, int64_t ldb, double* C,
+                           int64_t ldc, int64_t split_stride, int n, int ncols, int nsplit,
+                           const DevScalars* skip, cudaStream_t st);
+int gemm_df_pick_split(int n, int num_sms);
+// out[t] = hi[t] + lo[t] in FP64.
+cudaError_t launch_join_df(const float* hi, const float* lo, int64_t total, double* out,
+                           cudaStream_t st);
+// hi + lo = scale[t % rows] * X[t] (scale may be NULL), t < total.
+cudaError_t launch_split_df(const double* X, const double* scale, int64_t rows, int64_t total,
+                            float* hi, float* lo, cudaStream_t st);
 
 // ----------------------------------------------------------------- cg.cu ---
 cudaError_t launch_gram(const double* const* factors_dev, const int64_t* sizes_host,

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df.cuh"
 #include "launch.h"
 
 namespace cphifi {
@@ -446,10 +447,11 @@ __device__ __forceinline__ void store_row(const PieceList& pl, int p, int seg, i
 template <int RP, int LPO>
 __global__ void __launch_bounds__(256)
 zhat_mttkrp_kernel(PieceList pl, const int32_t* __restrict__ perm, const int32_t* __restrict__ oidx,
-                   int d_other, const double* const* __restrict__ factors,
-                   const int64_t* __restrict__ sizes, int r, const double* __restrict__ vals,
-                   float* __restrict__ zhi, float* __restrict__ zlo, double* __restrict__ partial,
-                   double* __restrict__ B, int64_t ldb, int* err) {
+                   int d_other, const float* const* __restrict__ fhi,
+                   const float* const* __restrict__ flo, const int64_t* __restrict__ sizes, int r,
+                   const double* __restrict__ vals, float* __restrict__ zhi,
+                   float* __restrict__ zlo, double* __restrict__ z64,
+                   double* __restrict__ partial, double* __restrict__ B, int64_t ldb, int* err) {
   constexpr int OPW = 32 / LPO, CPL = RP / LPO;
   const int lane = threadIdx.x & 31, sub = lane / OPW, o = lane % OPW;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -460,57 +462,59 @@ zhat_mttkrp_kernel(PieceList pl, const int32_t* __restrict__ perm, const int32_t
     for (int p = pl.warp_first[w]; p < p_end; ++p) {
       const int seg = pl.seg[p];
       const int b = pl.beg[p], e = pl.end[p];
-      double acc[CPL];
+      df acc[CPL];
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) acc[c] = 0.0;
+      for (int c = 0; c < CPL; ++c) acc[c] = df{0.f, 0.f};
       for (int l = b + o; l < e; l += OPW) {
         const int64_t src = perm ? (int64_t)perm[l] : (int64_t)l;
-        const double t = vals[src];
-        double z[CPL];
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) z[c] = 1.0;
+        const df t = df_from_double(vals[src]);
+        df z[CPL];
         for (int m = 0; m < d_other; ++m) {
           const int32_t im = oidx[src * d_other + m];
           const int64_t nm = sizes[m];
           const bool ok = im >= 0 && im < nm;
           bad |= ok ? 0 : 1;
-          const double* F = factors[m] + (ok ? im : 0);
+          const int64_t off = ok ? im : 0;
 #pragma unroll
           for (int c = 0; c < CPL; ++c) {
             const int j = sub * CPL + c;
-            if (j < r) z[c] *= ok ? F[(int64_t)j * nm] : 0.0;
+            df f{0.f, 0.f};
+            if (ok && j < r) f = df{fhi[m][(int64_t)j * nm + off], flo[m][(int64_t)j * nm + off]};
+            z[c] = m == 0 ? f : df_mul(z[c], f);
           }
         }
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
           const int j = sub * CPL + c;
           if (j < r) {
-            const float hi = (float)z[c];
-            const float lo = (float)(z[c] - (double)hi);
-            zhi[zidx(l, j, r)] = hi;
-            zlo[zidx(l, j, r)] = lo;
-            acc[c] = fma(t, z[c], acc[c]);
+            const int64_t zi = zidx(l, j, r);
+            if (zhi) { zhi[zi] = z[c].hi; zlo[zi] = z[c].lo; }
+            if (z64) z64[zi] = df_to_double(z[c]);
+            df_acc_prod(acc[c], t, z[c]);
           }
         }
       }
-      reduce_row<double, RP, LPO>(acc);
-      store_row<double, RP, LPO>(pl, p, seg, r, acc, partial, B, ldb);
+      double accd[CPL];
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) accd[c] = df_to_double(df_norm(acc[c]));
+      reduce_row<double, RP, LPO>(accd);
+      store_row<double, RP, LPO>(pl, p, seg, r, accd, partial, B, ldb);
     }
   }
   if (bad) atomicOr(err, 1);
 }
 
 cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const int32_t* oidx,
-                               int d_other, const double* const* factors_dev,
+                               int d_other, const float* const* fhi, const float* const* flo,
                                const int64_t* sizes_dev, int r, const double* vals, float* zhi,
-                               float* zlo, double* partial, double* B, int64_t ldb, int* err,
-                               cudaStream_t st) {
+                               float* zlo, double* z64, double* partial, double* B, int64_t ldb,
+                               int* err, cudaStream_t st) {
   if (pl.npieces == 0 || pl.nwarps == 0) return cudaSuccess;
   const int blocks = (pl.nwarps + 7) / 8;
-#define CPHIFI_ZM(RPV, LPOV)                                                                     \
-  zhat_mttkrp_kernel<RPV, LPOV><<<blocks, 256, 0, st>>>(pl, perm, oidx, d_other, factors_dev,  \
-                                                         sizes_dev, r, vals, zhi, zlo, partial, \
-                                                         B, ldb, err)
+#define CPHIFI_ZM(RPV, LPOV)                                                                  \
+  zhat_mttkrp_kernel<RPV, LPOV><<<blocks, 256, 0, st>>>(pl, perm, oidx, d_other, fhi, flo,   \
+                                                         sizes_dev, r, vals, zhi, zlo, z64,  \
+                                                         partial, B, ldb, err)
   if (r <= 8) CPHIFI_ZM(8, 1);
   else if (r <= 16) CPHIFI_ZM(16, 1);
   else if (r <= 32) CPHIFI_ZM(32, 2);
@@ -533,20 +537,46 @@ cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const i
 // (per-index ticket) adds the pieces in piece order.  No floating-point
 // atomics: the result is deterministic.
 //
-// T is the arithmetic: float reads Zhat's FP32 part (the mixed operator);
-// double reads hi + lo (the FP64 operator).  With `tvals` instead of Xh the
-// kernel computes sum_l t_l Zhat(l,:) (the MTTKRP form).
-template <typename T, int RP, bool WITH_DOT, int LPO>
+// Arithmetic modes:
+//   GDS_F32 : FP32 throughout, Zhat = hi        (the mixed-precision operator)
+//   GDS_F64 : FP64 throughout, Zhat = z64        (the FP64 operator)
+//   GDS_DF  : double-float (df.cuh), Zhat = hi + lo, Xhat and Yhat1 FP64
+//             (FP64-accurate true residuals of the mixed solve)
+enum { GDS_F32 = 0, GDS_F64 = 1, GDS_DF = 2 };
+
+template <int MODE>
+struct GdsTypes;
+template <>
+struct GdsTypes<GDS_F32> { using IO = float; using Acc = float; };
+template <>
+struct GdsTypes<GDS_F64> { using IO = double; using Acc = double; };
+template <>
+struct GdsTypes<GDS_DF> { using IO = double; using Acc = df; };
+
+__device__ __forceinline__ void acc_fma(float& a, float x, float y) { a = fmaf(x, y, a); }
+__device__ __forceinline__ void acc_fma(double& a, double x, double y) { a = fma(x, y, a); }
+__device__ __forceinline__ void acc_fma(df& a, df x, df y) { df_acc_prod(a, x, y); }
+__device__ __forceinline__ float acc_zero(float) { return 0.f; }
+__device__ __forceinline__ double acc_zero(double) { return 0.0; }
+__device__ __forceinline__ df acc_zero(df) { return df{0.f, 0.f}; }
+__device__ __forceinline__ float acc_out(float a) { return a; }
+__device__ __forceinline__ double acc_out(double a) { return a; }
+__device__ __forceinline__ double acc_out(df a) { return df_to_double(df_norm(a)); }
+
+template <int MODE, int RP, int LPO>
 __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __restrict__ zhi,
-                                                  const float* __restrict__ zlo, int r,
-                                                  const T* __restrict__ Xh, int64_t xld,
-                                                  const T* __restrict__ tvals,
-                                                  T* __restrict__ partial, T* __restrict__ Y,
+                                                  const float* __restrict__ zlo,
+                                                  const double* __restrict__ z64, int r,
+                                                  const typename GdsTypes<MODE>::IO* __restrict__ Xh,
+                                                  int64_t xld,
+                                                  typename GdsTypes<MODE>::IO* __restrict__ partial,
+                                                  typename GdsTypes<MODE>::IO* __restrict__ Y,
                                                   int64_t yld, const DevScalars* skip) {
+  using IO = typename GdsTypes<MODE>::IO;
+  using Acc = typename GdsTypes<MODE>::Acc;
   if (dev_skip(skip)) return;
   constexpr int OPW = 32 / LPO, CPL = RP / LPO;
-  constexpr bool HILO = sizeof(T) == 8;
-  __shared__ T xs[8][RP];
+  __shared__ Acc xs[8][RP];
   const int lane = threadIdx.x & 31, sub = lane / OPW, o = lane % OPW;
   const int wib = threadIdx.x >> 5;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -556,84 +586,105 @@ __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __r
     for (int p = pl.warp_first[w]; p < p_end; ++p) {
       const int seg = pl.seg[p];
       const int b = pl.beg[p], e = pl.end[p];
-      if (WITH_DOT) {
-        __syncwarp();
-        for (int j = lane; j < RP; j += 32) xs[wib][j] = j < r ? Xh[(int64_t)j * xld + seg] : T(0);
-        __syncwarp();
+      __syncwarp();
+      for (int j = lane; j < RP; j += 32) {
+        const IO v = j < r ? Xh[(int64_t)j * xld + seg] : IO(0);
+        if constexpr (MODE == GDS_DF) xs[wib][j] = df_from_double(v);
+        else xs[wib][j] = v;
       }
-      T acc[CPL];
+      __syncwarp();
+      Acc acc[CPL];
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) acc[c] = T(0);
+      for (int c = 0; c < CPL; ++c) acc[c] = acc_zero(Acc());
       // Every lane runs the same number of rounds so the cross-lane sums of
       // the dot product see the whole warp.
       for (int l0 = b; l0 < e; l0 += OPW) {
         const int l = l0 + o;
         const bool act = l < e;
         const int64_t base = zidx(act ? l : b, 0, r);
-        T z[CPL];
+        Acc z[CPL];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
           const int j = sub * CPL + c;
-          T v = T(0);
-          if (act && j < r) {
-            if (HILO) v = (T)__ldcs(zhi + base + 32 * j) + (T)__ldcs(zlo + base + 32 * j);
-            else v = (T)__ldcs(zhi + base + 32 * j);
+          const bool ld = act && j < r;
+          if constexpr (MODE == GDS_F32) z[c] = ld ? __ldcs(zhi + base + 32 * j) : 0.f;
+          else if constexpr (MODE == GDS_F64) z[c] = ld ? __ldcs(z64 + base + 32 * j) : 0.0;
+          else z[c] = ld ? df{__ldcs(zhi + base + 32 * j), __ldcs(zlo + base + 32 * j)}
+                         : df{0.f, 0.f};
+        }
+        Acc dot = acc_zero(Acc());
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) acc_fma(dot, xs[wib][sub * CPL + c], z[c]);
+        Acc xb;
+        if constexpr (MODE == GDS_DF) {
+          df d = df_norm(dot);
+          // sum the partial dots of the LPO lanes of this observation
+#pragma unroll
+          for (int s = OPW; s < 32; s <<= 1) {
+            const df other{__shfl_xor_sync(0xffffffffu, d.hi, s),
+                           __shfl_xor_sync(0xffffffffu, d.lo, s)};
+            d = df_add(d, other);
           }
-          z[c] = v;
-        }
-        T xb;
-        if (WITH_DOT) {
-          xb = T(0);
-#pragma unroll
-          for (int c = 0; c < CPL; ++c) xb = fma(xs[wib][sub * CPL + c], z[c], xb);
-          if (LPO > 1) xb = sum_over_subs<T, LPO>(xb);
+          xb = d;
         } else {
-          xb = act ? tvals[l] : T(0);
+          xb = LPO > 1 ? sum_over_subs<Acc, LPO>(dot) : dot;
         }
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) acc[c] = fma(xb, z[c], acc[c]);
+        for (int c = 0; c < CPL; ++c) acc_fma(acc[c], xb, z[c]);
       }
-      reduce_row<T, RP, LPO>(acc);
-      store_row<T, RP, LPO>(pl, p, seg, r, acc, partial, Y, yld);
+      IO accd[CPL];
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) accd[c] = (IO)acc_out(acc[c]);
+      reduce_row<IO, RP, LPO>(accd);
+      store_row<IO, RP, LPO>(pl, p, seg, r, accd, partial, Y, yld);
     }
   }
 }
 
-template <typename T, int RP, int LPO>
-static cudaError_t gds_dispatch(const PieceList& pl, const float* zhi, const float* zlo, int r,
-                                const T* Xh, int64_t xld, const T* tvals, T* partial, T* Y,
-                                int64_t yld, const DevScalars* skip, cudaStream_t st) {
+template <int MODE, int RP, int LPO>
+static cudaError_t gds_dispatch(const PieceList& pl, const float* zhi, const float* zlo,
+                                const double* z64, int r, const typename GdsTypes<MODE>::IO* Xh,
+                                int64_t xld, typename GdsTypes<MODE>::IO* partial,
+                                typename GdsTypes<MODE>::IO* Y, int64_t yld,
+                                const DevScalars* skip, cudaStream_t st) {
   const int blocks = (pl.nwarps + 7) / 8;
-  if (Xh)
-    gds_kernel<T, RP, true, LPO><<<blocks, 256, 0, st>>>(pl, zhi, zlo, r, Xh, xld, tvals, partial,
-                                                         Y, yld, skip);
-  else
-    gds_kernel<T, RP, false, LPO><<<blocks, 256, 0, st>>>(pl, zhi, zlo, r, Xh, xld, tvals,
-                                                          partial, Y, yld, skip);
+  gds_kernel<MODE, RP, LPO><<<blocks, 256, 0, st>>>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y,
+                                                    yld, skip);
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_gds(const PieceList& pl, const float* zhi, const float* zlo, int r,
-                       const T* Xh, int64_t xld, const T* tvals, T* partial, T* Y, int64_t yld,
-                       const DevScalars* skip, cudaStream_t st) {
+// Lanes per observation keep the per-lane registers (RP/LPO values of the
+// row and of the accumulator) within budget.
+template <int MODE>
+static cudaError_t gds_by_rank(const PieceList& pl, const float* zhi, const float* zlo,
+                               const double* z64, int r, const typename GdsTypes<MODE>::IO* Xh,
+                               int64_t xld, typename GdsTypes<MODE>::IO* partial,
+                               typename GdsTypes<MODE>::IO* Y, int64_t yld,
+                               const DevScalars* skip, cudaStream_t st) {
   if (pl.npieces == 0 || pl.nwarps == 0) return cudaSuccess;
-  constexpr bool dbl = sizeof(T) == 8;
-  // Lanes per observation keep the per-lane registers (RP/LPO values of both
-  // the row and the accumulator) within budget.
-  if (r <= 8) return gds_dispatch<T, 8, 1>(pl, zhi, zlo, r, Xh, xld, tvals, partial, Y, yld, skip, st);
-  if (r <= 16) return gds_dispatch<T, 16, 1>(pl, zhi, zlo, r, Xh, xld, tvals, partial, Y, yld, skip, st);
-  if (r <= 32) return gds_dispatch<T, 32, dbl ? 2 : 1>(pl, zhi, zlo, r, Xh, xld, tvals, partial, Y, yld, skip, st);
-  if (r <= 48) return gds_dispatch<T, 48, dbl ? 4 : 1>(pl, zhi, zlo, r, Xh, xld, tvals, partial, Y, yld, skip, st);
-  if (r <= 64) return gds_dispatch<T, 64, dbl ? 4 : 2>(pl, zhi, zlo, r, Xh, xld, tvals, partial, Y, yld, skip, st);
+  constexpr bool wide = MODE != GDS_F32;
+  if (r <= 8) return gds_dispatch<MODE, 8, 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st);
+  if (r <= 16) return gds_dispatch<MODE, 16, 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st);
+  if (r <= 32) return gds_dispatch<MODE, 32, wide ? 2 : 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st);
+  if (r <= 48) return gds_dispatch<MODE, 48, wide ? 4 : 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st);
+  if (r <= 64) return gds_dispatch<MODE, 64, wide ? 4 : 2>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st);
   return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_gds<double>(const PieceList&, const float*, const float*, int,
-                                        const double*, int64_t, const double*, double*, double*,
-                                        int64_t, const DevScalars*, cudaStream_t);
-template cudaError_t launch_gds<float>(const PieceList&, const float*, const float*, int,
-                                       const float*, int64_t, const float*, float*, float*,
-                                       int64_t, const DevScalars*, cudaStream_t);
+cudaError_t launch_gds_f32(const PieceList& pl, const float* zhi, int r, const float* Xh,
+                           int64_t xld, float* partial, float* Y, int64_t yld,
+                           const DevScalars* skip, cudaStream_t st) {
+  return gds_by_rank<GDS_F32>(pl, zhi, nullptr, nullptr, r, Xh, xld, partial, Y, yld, skip, st);
+}
+cudaError_t launch_gds_f64(const PieceList& pl, const double* z64, int r, const double* Xh,
+                           int64_t xld, double* partial, double* Y, int64_t yld,
+                           const DevScalars* skip, cudaStream_t st) {
+  return gds_by_rank<GDS_F64>(pl, nullptr, nullptr, z64, r, Xh, xld, partial, Y, yld, skip, st);
+}
+cudaError_t launch_gds_df(const PieceList& pl, const float* zhi, const float* zlo, int r,
+                          const double* Xh, int64_t xld, double* partial, double* Y, int64_t yld,
+                          const DevScalars* skip, cudaStream_t st) {
+  return gds_by_rank<GDS_DF>(pl, zhi, zlo, nullptr, r, Xh, xld, partial, Y, yld, skip, st);
+}
 
 }  // namespace cphifi

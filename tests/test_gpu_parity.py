@@ -43,7 +43,7 @@ def rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / (nb if nb > 0 else 1.0)
 
 
-def make(ctx, pkg, p, sorted_obs=None, lowp=True):
+def make(ctx, pkg, p, sorted_obs=None, lowp=None):
     dK, UK = np.linalg.eigh(p.K)
     kern = ctx.kernel_create(p.n, UK, dK)
     if sorted_obs is None:
@@ -107,6 +107,7 @@ def test_gather_dot_scatter(case):
     Xh = np.random.default_rng(11).standard_normal((p.n, p.r))
     ref = O.scatter_rows(p.n, p.kidx, O.gather_dot(Xh, p.kidx, Zh), Zh)
     assert rel(prob.gds(Xh, "fp64"), ref) <= 1e-12
+    assert rel(prob.gds(Xh, "fp64_emulated"), ref) <= 1e-12
     assert rel(prob.gds(Xh, "mixed_fp32"), ref) <= 2e-5
 
 
@@ -117,6 +118,7 @@ def test_matvec(case):
     for lam, rho in ((1e-4, 1e-6), (0.3, 0.05)):
         ref = O.matvec(p.K, p.kidx, Zh, lam, rho, X)
         assert rel(prob.matvec(X, lam, rho, "fp64"), ref) <= 1e-11
+        assert rel(prob.matvec(X, lam, rho, "fp64_emulated"), ref) <= 1e-11
         assert rel(prob.matvec(X, lam, rho, "mixed_fp32"), ref) <= 2e-5
 
 
@@ -138,12 +140,13 @@ def _gate(p, W, tol, Wd=None):
     return res, fit, rel(W, Wd)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed_fp32", 1e-6),
-                                           ("mixed_fp32", 1e-8)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp64_emulated", 1e-10),
+                                           ("mixed_fp32", 1e-6), ("mixed_fp32", 1e-8),
+                                           ("mixed_fp32", 1e-10)])
 def test_solve_c1_workload(ctx, pkg, precision, tol):
     """n=100, 20x30, q=6000, r=5, lambda=1e-4, rho=1e-6 (planted, 1% noise)."""
     p = synth.workload("c1_fp64_n100_q6e3_r5", seed=0)
-    kern, prob = make(ctx, pkg, p)
+    kern, prob = make(ctx, pkg, p, lowp=(precision != "fp64"))
     W, st = prob.solve(p.lam, p.rho, tol, max_iter=2000, precision=precision)
     res, fit, werr = _gate(p, W, tol)
     assert st["status"] == 0, st
@@ -164,6 +167,8 @@ def test_solve_well_conditioned_W_itself(ctx, pkg, seed):
     assert rel(W, Wd) <= 1e-10, st
     W2, st2 = prob.solve(p.lam, p.rho, 1e-10, max_iter=500, precision="mixed_fp32")
     assert rel(W2, Wd) <= 1e-8, st2
+    W3, st3 = prob.solve(p.lam, p.rho, 1e-13, max_iter=500, precision="fp64_emulated")
+    assert rel(W3, Wd) <= 1e-10, st3
     prob.close()
     kern.close()
 
@@ -198,7 +203,7 @@ def test_unsorted_equals_sorted(ctx, pkg):
 def test_deterministic(ctx, pkg):
     p = synth.planted_problem(9, 70, (15, 16), 8000, 12, bandwidth=0.1, lam=1e-4, rho=1e-6)
     kern, prob = make(ctx, pkg, p)
-    for prec in ("fp64", "mixed_fp32"):
+    for prec in ("fp64", "mixed_fp32", "fp64_emulated"):
         W1, s1 = prob.solve(p.lam, p.rho, 1e-9, 500, precision=prec)
         W2, s2 = prob.solve(p.lam, p.rho, 1e-9, 500, precision=prec)
         np.testing.assert_array_equal(W1, W2)
