@@ -47,6 +47,10 @@ struct cphifi_ctx {
   std::multimap<size_t, void*> pool;
   size_t pool_bytes = 0;
   cudaEvent_t phase[4] = {nullptr, nullptr, nullptr, nullptr};  // solve phase marks
+  // Side stream for small serial work (Gram, eig(V)) that overlaps the
+  // bandwidth-bound Zhat pass on the main stream.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 struct cphifi_kernel {
@@ -321,6 +325,9 @@ extern "C" int cphifi_ctx_create(cphifi_ctx** out, int device, size_t hbm_budget
             cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) == cudaSuccess &&
             cudaMallocHost(&ctx->h_scalars, sizeof(DevScalars)) == cudaSuccess;
   for (int k = 0; ok && k < 4; ++k) ok = cudaEventCreate(&ctx->phase[k]) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) == cudaSuccess;
   cudaSetDevice(prev);
   if (!ok) {
     delete ctx;
@@ -340,6 +347,12 @@ extern "C" int cphifi_ctx_destroy(cphifi_ctx* ctx) {
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   for (auto e : ctx->phase)
     if (e) cudaEventDestroy(e);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side) {
+    cudaStreamSynchronize(ctx->side);
+    cudaStreamDestroy(ctx->side);
+  }
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
   if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
@@ -523,6 +536,7 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
     return p;
   };
   auto bail = [&](int code, const std::string& m) {
+    cudaStreamSynchronize(ctx->side);
     cudaStreamSynchronize(st);
     for (auto& t : temps) pool_release(ctx, t.first, t.second);
     free_problem(P);
@@ -596,8 +610,17 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   for (int m = 0; m < d_other; ++m) {
     PCK(upload(P->factors[m], factors[m], (size_t)sizes[m] * r * sizeof(double), mem, st));
     PCK(launch_validate_dense(P->factors[m], sizes[m] * r, P->err, st));
-    PCK(launch_split_df(P->factors[m], nullptr, sizes[m] * r, sizes[m] * r, P->fhi[m], P->flo[m], st));
+    PCK(launch_split_rows_df(P->factors[m], sizes[m], r, P->fhi[m], P->flo[m], st));
   }
+
+  // ---- Gram V (§3) and eig(V) (Eq. eigV) on the side stream: they need only
+  // the factors and overlap the observation passes below.
+  PCK(cudaEventRecord(ctx->ev_fork, st));
+  PCK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  PCK(launch_gram(P->factors_dev, P->sizes_dev, d_other, r, P->V, ctx->side));
+  PCK(launch_jacobi_eig(P->V, r, P->dV, P->UV, 60, P->info, ctx->side));
+  PCK(launch_convert<double, float>(P->UV, P->UV32, (int64_t)r * r, ctx->side));
+  PCK(cudaEventRecord(ctx->ev_join, ctx->side));
 
   // ---- observations: copy, validate, sort by kernel index
   uint32_t* keys = (uint32_t*)tmp_alloc((size_t)q * sizeof(uint32_t));
@@ -659,9 +682,7 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   PCK(launch_zhat_mttkrp(pl, (flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm, oidx_d, d_other,
                          P->fhi_dev, P->flo_dev, P->sizes_dev, r, vals_d, P->zhi, P->zlo,
                          P->z64, (double*)P->gds_partial, P->Bm, n, P->err, st));
-  PCK(launch_gram(P->factors_dev, P->sizes_dev, d_other, r, P->V, st));
-  PCK(launch_jacobi_eig(P->V, r, P->dV, P->UV, 60, P->info, st));
-  PCK(launch_convert<double, float>(P->UV, P->UV32, (int64_t)r * r, st));
+  PCK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
   PCK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   PCK(cudaStreamSynchronize(st));
   if (herr & 4) return bail(CPHIFI_E_INVALID_ARG, "CPHIFI_OBS_SORTED set but kidx is not sorted");

@@ -149,14 +149,16 @@ cudaError_t launch_gemm_skinny(const TA* A, int64_t lda, bool a_trans, const dou
 // optional row scale folded in); every multiply-add is an exact TwoProd and a
 // TwoSum-compensated accumulation (df.cuh), the partial products are written
 // as FP64.  FP32 units only: GB300 runs them ~60x faster than FP64 FMA.
-template <bool ATRANS>
+// TNMAX = columns per thread (ncols <= 8 TNMAX), a compile-time bound that
+// keeps the accumulator tile in registers without padding to 64 columns.
+template <bool ATRANS, int TNMAX>
 __global__ void __launch_bounds__(256)
 gemm_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo, int64_t lda,
                const float* __restrict__ Bhi, const float* __restrict__ Blo, int64_t ldb,
                double* __restrict__ C, int64_t ldc, int64_t split_stride, int n, int ncols,
                int kchunk, const DevScalars* skip) {
   if (dev_skip(skip)) return;
-  constexpr int BM = 128, BK = 16, TM = BM / 32, TNMAX = 8;
+  constexpr int BM = 128, BK = 16, TM = BM / 32;
   __shared__ float Ash[BK][BM + 1], Asl[BK][BM + 1];
   __shared__ float Bsh[BK][64], Bsl[BK][64];
   const int tid = threadIdx.x;
@@ -227,7 +229,7 @@ gemm_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo, int
 
 int gemm_df_pick_split(int n, int num_sms) {
   int occ = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gemm_df_kernel<true>, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gemm_df_kernel<true, 5>, 256, 0);
   if (occ < 1) occ = 1;
   const int64_t slots = (int64_t)num_sms * occ;
   const int mt = (n + 127) / 128;
@@ -253,12 +255,24 @@ cudaError_t launch_gemm_df(const float* Ahi, const float* Alo, int64_t lda, bool
   int kchunk = (n + nsplit - 1) / nsplit;
   kchunk = (kchunk + 15) / 16 * 16;
   const dim3 grid((n + 127) / 128, nsplit);
-  if (a_trans)
-    gemm_df_kernel<true><<<grid, 256, 0, st>>>(Ahi, Alo, lda, Bhi, Blo, ldb, C, ldc, split_stride,
-                                               n, ncols, kchunk, skip);
-  else
-    gemm_df_kernel<false><<<grid, 256, 0, st>>>(Ahi, Alo, lda, Bhi, Blo, ldb, C, ldc,
-                                                split_stride, n, ncols, kchunk, skip);
+  const int tn = (ncols + 7) / 8;
+#define CPHIFI_GDF(TNV)                                                                        \
+  do {                                                                                         \
+    if (a_trans)                                                                               \
+      gemm_df_kernel<true, TNV><<<grid, 256, 0, st>>>(Ahi, Alo, lda, Bhi, Blo, ldb, C, ldc,    \
+                                                      split_stride, n, ncols, kchunk, skip);   \
+    else                                                                                       \
+      gemm_df_kernel<false, TNV><<<grid, 256, 0, st>>>(Ahi, Alo, lda, Bhi, Blo, ldb, C, ldc,   \
+                                                       split_stride, n, ncols, kchunk, skip);  \
+  } while (0)
+  if (tn <= 1) CPHIFI_GDF(1);
+  else if (tn <= 2) CPHIFI_GDF(2);
+  else if (tn <= 3) CPHIFI_GDF(3);
+  else if (tn <= 4) CPHIFI_GDF(4);
+  else if (tn <= 5) CPHIFI_GDF(5);
+  else if (tn <= 6) CPHIFI_GDF(6);
+  else CPHIFI_GDF(8);
+#undef CPHIFI_GDF
   return cudaGetLastError();
 }
 
@@ -282,6 +296,29 @@ cudaError_t launch_split_df(const double* X, const double* scale, int64_t rows, 
   int64_t b = (total + 255) / 256;
   if (b > 4096) b = 4096;
   split_df_kernel<<<(int)b, 256, 0, st>>>(X, scale, rows, total, hi, lo);
+  return cudaGetLastError();
+}
+
+__global__ void split_rows_df_kernel(const double* __restrict__ X, int64_t rows, int cols,
+                                     float* __restrict__ hi, float* __restrict__ lo) {
+  const int64_t total = rows * cols;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / cols;
+    const int j = (int)(t % cols);
+    const df d = df_from_double(X[i + rows * j]);
+    hi[t] = d.hi;
+    lo[t] = d.lo;
+  }
+}
+
+cudaError_t launch_split_rows_df(const double* X, int64_t rows, int cols, float* hi, float* lo,
+                                 cudaStream_t st) {
+  const int64_t total = rows * cols;
+  if (total == 0) return cudaSuccess;
+  int64_t b = (total + 255) / 256;
+  if (b > 4096) b = 4096;
+  split_rows_df_kernel<<<(int)b, 256, 0, st>>>(X, rows, cols, hi, lo);
   return cudaGetLastError();
 }
 

@@ -78,7 +78,7 @@ cudaError_t launch_gds_df(const PieceList& pl, const float* zhi, const float* zl
                           const double* Xh, int64_t xld, double* partial, double* Y,
                           int64_t yld, const DevScalars* skip, cudaStream_t st);
 // Zhat (Eq. zhat) in sorted order, computed in double-float from the factors'
-// hi/lo parts, written as hi/lo FP32 pairs and/or FP64 (either may be NULL),
+// hi/lo parts (row-major n_m x r, see launch_split_rows_df), written as hi/lo FP32 pairs and/or FP64 (either may be NULL),
 // fused with the MTTKRP B(i,:) = sum_{i_l = i} t_l Zhat(l,:) (B column-major,
 // ld ldb, FP64 result).  perm = NULL: input already sorted.  Bad indices set
 // *err bit 1.
@@ -108,6 +108,10 @@ cudaError_t launch_gemm_df(const float* Ahi, const float* Alo, int64_t lda, bool
                            int64_t ldc, int64_t split_stride, int n, int ncols, int nsplit,
                            const DevScalars* skip, cudaStream_t st);
 int gemm_df_pick_split(int n, int num_sms);
+// Row-major hi/lo split of a column-major rows x cols matrix X:
+// hi[i*cols + j] + lo[i*cols + j] = X[i + rows*j].
+cudaError_t launch_split_rows_df(const double* X, int64_t rows, int cols, float* hi, float* lo,
+                                 cudaStream_t st);
 // out[t] = hi[t] + lo[t] in FP64.
 cudaError_t launch_join_df(const float* hi, const float* lo, int64_t total, double* out,
                            cudaStream_t st);

@@ -475,11 +475,15 @@ zhat_mttkrp_kernel(PieceList pl, const int32_t* __restrict__ perm, const int32_t
           const bool ok = im >= 0 && im < nm;
           bad |= ok ? 0 : 1;
           const int64_t off = ok ? im : 0;
+          // factors' hi/lo parts are row-major: the lane's columns of row
+          // im are contiguous (one or two cache lines per row)
+          const float* rh = fhi[m] + off * r + sub * CPL;
+          const float* rl = flo[m] + off * r + sub * CPL;
 #pragma unroll
           for (int c = 0; c < CPL; ++c) {
             const int j = sub * CPL + c;
             df f{0.f, 0.f};
-            if (ok && j < r) f = df{fhi[m][(int64_t)j * nm + off], flo[m][(int64_t)j * nm + off]};
+            if (ok && j < r) f = df{rh[c], rl[c]};
             z[c] = m == 0 ? f : df_mul(z[c], f);
           }
         }

@@ -273,7 +273,8 @@ def test_invalid_inputs_are_rejected(ctx, pkg):
 def test_admission_by_budget(pkg):
     p = synth.planted_problem(12, 40, (10, 10), 2000, 4)
     dK, UK = np.linalg.eigh(p.K)
-    c = pkg.Context(0, hbm_budget_bytes=40 * 40 * 12 + 40 * 8 + 4096)
+    # room for the kernel handle (U_K in FP64 + hi/lo FP32, D_K) but not the problem
+    c = pkg.Context(0, hbm_budget_bytes=40 * 40 * 16 + 40 * 8 + 4096)
     kern = c.kernel_create(p.n, UK, dK)
     with pytest.raises(pkg.CphifiError) as e:
         pkg.Problem(c, kern, p.factors, p.kidx, p.oidx, p.vals, p.r)
