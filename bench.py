@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--precision", default="mixed_fp32")
+    ap.add_argument("--precision", default="mixed_tf32")
     ap.add_argument("--q", type=int, default=0, help="override q (smaller runs)")
     ap.add_argument("--n", type=int, default=0, help="override n (smaller runs)")
     ap.add_argument("--no-fp64", action="store_true")
@@ -325,7 +325,11 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 operator, f64 CG/residuals" if args.precision != "fp64" else "f64",
+            "dtype": {"mixed_tf32": "tf32 products + f32 gather, f64 CG, df64 residuals",
+                      "mixed_bf16": "bf16 products + f32 gather, f64 CG, df64 residuals",
+                      "mixed_fp32": "f32 operator, f64 CG, df64 residuals",
+                      "fp64_emulated": "df64 (fp32-pair) operator, f64 CG",
+                      "fp64": "f64"}[args.precision],
             "data": "synthetic planted low rank (seeded), inputs larger than L2 (no flush)",
             "config": {"workload": args.workload, "n": n, "other_sizes": p.other_sizes, "q": q,
                        "r": r, "lambda": p.lam, "rho": p.rho, "tol": TOL,

@@ -59,6 +59,13 @@ struct cphifi_kernel {
   double* UK64 = nullptr;  // n x n column-major
   float* UK32 = nullptr;   // fl32(U_K): the FP32 operator's U_K and the hi part
   float* UKlo = nullptr;   // fl32(U_K - UK32): U_K = UK32 + UKlo to 2^-48 (double-float)
+  // Tensor-core operand copies (leading dimension ldt = n rounded up to 8):
+  // A1 = row-major U_K (A of U_K X), A2 = row-major U_K' (A of U_K' X).
+  bool tc = false;
+  int64_t ldt = 0;
+  float *A1f = nullptr, *A2f = nullptr;
+  __nv_bfloat16 *A1b = nullptr, *A2b = nullptr;
+  CUtensorMap mA1f, mA2f, mA1b, mA2b;
   double* dK = nullptr;    // n
   size_t bytes = 0;
 };
@@ -102,8 +109,16 @@ struct cphifi_problem {
          *tmp64b = nullptr, *D64 = nullptr;
   float *pop32 = nullptr, *xh32 = nullptr, *y132 = nullptr, *D32 = nullptr;
   float *Bhi = nullptr, *Blo = nullptr;  // double-float product operand
+  // Low-precision product operands pop (D_K P̄) and y1 (Ŷ1) use leading
+  // dimension ldt (= the kernel's tensor-core ldt, else n); BF16 copies and
+  // TMA maps for the tensor-core modes.
+  int64_t ldt = 0;
+  __nv_bfloat16 *pop16 = nullptr, *y116 = nullptr;
+  CUtensorMap mBpf, mBpb, mByf, mByb;
+  int nsplittc = 1;
+  int* tc_err = nullptr;
   void* cpart = nullptr;  // max(nsplit64, nsplit32, nsplitdf) x n x r doubles
-  int nsplit64 = 1, nsplit32 = 1, nsplitdf = 1;
+  int nsplit64 = 1, nsplit32 = 1, nsplitdf = 1;  // splits of the k range per product kind
   RedScratch red{};
   DevScalars* s = nullptr;    // the solve's scalars
   DevScalars* s2 = nullptr;   // scalars of the step-by-step calls
@@ -402,6 +417,8 @@ extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
     if (kern->UK32) cudaFree(kern->UK32);
     if (kern->UKlo) cudaFree(kern->UKlo);
     if (kern->dK) cudaFree(kern->dK);
+    for (void* a : {(void*)kern->A1f, (void*)kern->A2f, (void*)kern->A1b, (void*)kern->A2b})
+      if (a) cudaFree(a);
     if (err) cudaFree(err);
     delete kern;
     return fail(ctx, code, m);
@@ -425,8 +442,35 @@ extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
       cudaStreamSynchronize(st) != cudaSuccess)
     return cleanup(CPHIFI_E_DEVICE, "uploading the kernel eigendecomposition failed");
   if (herr) return cleanup(CPHIFI_E_INVALID_ARG, "non-finite entry in UK or DK");
+  size_t tc_bytes = 0;
+  if (tc_available((int)n)) {
+    const int64_t ldt = (n + 7) / 8 * 8;
+    const size_t cnt = (size_t)n * ldt;
+    tc_bytes = cnt * (2 * sizeof(float) + 2 * sizeof(__nv_bfloat16));
+    if (ctx->budget && ctx->in_use + bytes + tc_bytes > ctx->budget) {
+      tc_bytes = 0;  // no room: the tensor-core modes stay unavailable
+    } else if (cudaMalloc(&kern->A1f, cnt * sizeof(float)) == cudaSuccess &&
+               cudaMalloc(&kern->A2f, cnt * sizeof(float)) == cudaSuccess &&
+               cudaMalloc(&kern->A1b, cnt * sizeof(__nv_bfloat16)) == cudaSuccess &&
+               cudaMalloc(&kern->A2b, cnt * sizeof(__nv_bfloat16)) == cudaSuccess &&
+               launch_uk_copy<float>(kern->UK64, (int)n, ldt, true, kern->A1f, st) == cudaSuccess &&
+               launch_uk_copy<float>(kern->UK64, (int)n, ldt, false, kern->A2f, st) == cudaSuccess &&
+               launch_uk_copy<__nv_bfloat16>(kern->UK64, (int)n, ldt, true, kern->A1b, st) == cudaSuccess &&
+               launch_uk_copy<__nv_bfloat16>(kern->UK64, (int)n, ldt, false, kern->A2b, st) == cudaSuccess &&
+               tc_make_map(&kern->mA1f, kern->A1f, false, n, n, ldt * 4, 128) == cudaSuccess &&
+               tc_make_map(&kern->mA2f, kern->A2f, false, n, n, ldt * 4, 128) == cudaSuccess &&
+               tc_make_map(&kern->mA1b, kern->A1b, true, n, n, ldt * 2, 128) == cudaSuccess &&
+               tc_make_map(&kern->mA2b, kern->A2b, true, n, n, ldt * 2, 128) == cudaSuccess &&
+               cudaStreamSynchronize(st) == cudaSuccess) {
+      kern->tc = true;
+      kern->ldt = ldt;
+    } else {
+      cudaGetLastError();
+      return cleanup(CPHIFI_E_DEVICE, "building the tensor-core copies of U_K failed");
+    }
+  }
   cudaFree(err);
-  kern->bytes = bytes;
+  kern->bytes = bytes + (kern->tc ? tc_bytes : 0);
   ctx->in_use += bytes;
   *out = kern;
   return CPHIFI_OK;
@@ -443,6 +487,8 @@ extern "C" int cphifi_kernel_destroy(cphifi_kernel* kern) {
   cudaFree(kern->UK32);
   cudaFree(kern->UKlo);
   cudaFree(kern->dK);
+  for (void* a : {(void*)kern->A1f, (void*)kern->A2f, (void*)kern->A1b, (void*)kern->A2b})
+    if (a) cudaFree(a);
   ctx->in_use -= std::min(ctx->in_use, kern->bytes);
   cudaSetDevice(prev);
   delete kern;
@@ -500,7 +546,8 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   const int nsplit64 = gemm_pick_split<double, double>(n, ctx->num_sms);
   const int nsplit32 = gemm_pick_split<float, float>(n, ctx->num_sms);
   const int nsplitdf = gemm_df_pick_split(n, ctx->num_sms);
-  const int nsplit = std::max(std::max(nsplit64, nsplit32), nsplitdf);
+  const int nsplittc = kern->tc ? tc_pick_split(n, ctx->num_sms) : 1;
+  const int nsplit = std::max(std::max(nsplit64, nsplit32), std::max(nsplitdf, nsplittc));
   // Operator data: FP64 Zhat for the FP64 operator, hi/lo FP32 pairs for the
   // mixed modes; neither flag set means both.
   const bool need64 = (flags & CPHIFI_NEED_FP64) || !(flags & CPHIFI_NEED_LOWP);
@@ -524,6 +571,8 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   P->nsplit64 = nsplit64;
   P->nsplit32 = nsplit32;
   P->nsplitdf = nsplitdf;
+  P->nsplittc = nsplittc;
+  P->ldt = kern->tc ? kern->ldt : n;
   P->nwarps = W;
   P->obs_per_warp = L;
   cudaStream_t st = ctx->stream;
@@ -587,7 +636,22 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   for (double** v : {&P->x, &P->res, &P->z, &P->p, &P->y, &P->bbar, &P->xh64, &P->y164,
                      &P->tmp64, &P->tmp64b, &P->D64})
     PCK(dalloc(P, v, nr));
-  for (float** v : {&P->pop32, &P->xh32, &P->y132, &P->D32, &P->Bhi, &P->Blo}) PCK(dalloc(P, v, nr));
+  for (float** v : {&P->xh32, &P->D32, &P->Bhi, &P->Blo}) PCK(dalloc(P, v, nr));
+  PCK(dalloc(P, &P->pop32, (size_t)P->ldt * r));
+  PCK(dalloc(P, &P->y132, (size_t)P->ldt * r));
+  PCK(cudaMemsetAsync(P->pop32, 0, (size_t)P->ldt * r * sizeof(float), st));
+  PCK(cudaMemsetAsync(P->y132, 0, (size_t)P->ldt * r * sizeof(float), st));
+  if (kern->tc) {
+    PCK(dalloc(P, &P->pop16, (size_t)P->ldt * r));
+    PCK(dalloc(P, &P->y116, (size_t)P->ldt * r));
+    PCK(dalloc(P, &P->tc_err, 1));
+    PCK(cudaMemsetAsync(P->tc_err, 0, sizeof(int), st));
+    const uint32_t np = (uint32_t)tc_pad_cols(r);
+    PCK(tc_make_map(&P->mBpf, P->pop32, false, n, r, P->ldt * 4, np));
+    PCK(tc_make_map(&P->mByf, P->y132, false, n, r, P->ldt * 4, np));
+    PCK(tc_make_map(&P->mBpb, P->pop16, true, n, r, P->ldt * 2, np));
+    PCK(tc_make_map(&P->mByb, P->y116, true, n, r, P->ldt * 2, np));
+  }
   PCK(dalloc(P, (double**)&P->cpart, (size_t)nsplit * nr));
   PCK(dalloc(P, &P->red.partials, (size_t)kRedMaxBlocks * kRedSlots));
   PCK(dalloc(P, &P->red.ticket, 4));
@@ -715,6 +779,10 @@ extern "C" size_t cphifi_problem_bytes(const cphifi_problem* P) { return P ? P->
 // ------------------------------------------------------------- solve ------
 namespace {
 
+bool is_lowp(int prec) {
+  return prec == CPHIFI_MIXED_FP32 || prec == CPHIFI_MIXED_TF32 || prec == CPHIFI_MIXED_BF16;
+}
+
 struct Launcher {
   cphifi_problem* P;
   cudaStream_t st;
@@ -740,12 +808,25 @@ struct Launcher {
     ++launches;
     return e;
   }
-  cudaError_t gemm32(bool a_trans, const double* scale, const float* B, float* out_part,
-                     const DevScalars* skip) {
+  // FP32 SIMT product; B has leading dimension ldb.
+  cudaError_t gemm32(bool a_trans, const double* scale, const float* B, int64_t ldb,
+                     float* out_part, const DevScalars* skip) {
     cudaEvent_t b = tm ? tm->begin() : nullptr;
-    cudaError_t e = launch_gemm_skinny<float, float>(P->kern->UK32, P->n, a_trans, scale, B, P->n,
+    cudaError_t e = launch_gemm_skinny<float, float>(P->kern->UK32, P->n, a_trans, scale, B, ldb,
                                                      out_part, P->n, split_stride(), P->n, P->r,
                                                      P->nsplit32, skip, st);
+    if (tm) tm->end(b, tm->gemm);
+    ++launches;
+    return e;
+  }
+  // Tensor-core product (tcgen05): g1 = U_K pop, else U_K' y1; TF32 or BF16.
+  cudaError_t gemm_tc(bool g1, bool bf16, float* out_part, const DevScalars* skip) {
+    const cphifi_kernel* K = P->kern;
+    const CUtensorMap& ma = g1 ? (bf16 ? K->mA1b : K->mA1f) : (bf16 ? K->mA2b : K->mA2f);
+    const CUtensorMap& mb = g1 ? (bf16 ? P->mBpb : P->mBpf) : (bf16 ? P->mByb : P->mByf);
+    cudaEvent_t b = tm ? tm->begin() : nullptr;
+    cudaError_t e = launch_tc_gemm(bf16, ma, mb, out_part, P->n, split_stride(), P->n, P->r,
+                                   P->nsplittc, skip, P->tc_err, st);
     if (tm) tm->end(b, tm->gemm);
     ++launches;
     return e;
@@ -774,10 +855,11 @@ struct Launcher {
                                   Bv, out, s, P->red, skip, st);
   }
   // Gather-dot/scatter in the three arithmetics (cat as for the products).
-  cudaError_t gds32(const float* Xh, float* Y, const DevScalars* skip, int cat) {
+  cudaError_t gds32(const float* Xh, float* Y, const DevScalars* skip, int cat,
+                    int64_t yld = 0) {
     cudaEvent_t b = (cat && tm) ? tm->begin() : nullptr;
     cudaError_t e = launch_gds_f32(pieces(), P->zhi, P->r, Xh, P->n, (float*)P->gds_partial, Y,
-                                   P->n, skip, st);
+                                   yld ? yld : P->n, skip, st);
     if (cat && tm) tm->end(b, cat == 1 ? tm->gds : tm->gds64);
     ++launches;
     return e;
@@ -823,15 +905,31 @@ struct Launcher {
     if ((e = gemm_df(false, nullptr, P->y164, Cp, skip, cat)) != cudaSuccess) return e;
     return combine<double, double>(mode, Cp, xin, P->bbar, out, s, skip, ns);
   }
-  // FP32 operator (mixed): pop32 holds the FP32 copy of xin.
-  cudaError_t op32(const double* xin, double* out, DevScalars* s, const DevScalars* skip) {
+  // Low-precision operator (mixed modes): pop32 (and pop16 for BF16) hold
+  // D_K xin in the operand type; FP32 SIMT products, or tcgen05 TF32/BF16.
+  cudaError_t op_lowp(int prec, const double* xin, double* out, DevScalars* s,
+                      const DevScalars* skip) {
+    const bool tc = prec == CPHIFI_MIXED_TF32 || prec == CPHIFI_MIXED_BF16;
+    const bool bf = prec == CPHIFI_MIXED_BF16;
     float* Cp = (float*)P->cpart;
+    const int ns = tc ? P->nsplittc : P->nsplit32;
     cudaError_t e;
-    if ((e = gemm32(true, P->kern->dK, P->pop32, Cp, skip)) != cudaSuccess) return e;
-    if ((e = combine<float, float>(CM_STORE, Cp, nullptr, nullptr, P->xh32, s, skip)) != cudaSuccess) return e;
-    if ((e = gds32(P->xh32, P->y132, skip, 1)) != cudaSuccess) return e;
-    if ((e = gemm32(false, nullptr, P->y132, Cp, skip)) != cudaSuccess) return e;
-    return combine<float, double>(CM_APPLY, Cp, xin, nullptr, out, s, skip);
+    e = tc ? gemm_tc(true, bf, Cp, skip) : gemm32(true, nullptr, P->pop32, P->ldt, Cp, skip);
+    if (e != cudaSuccess) return e;
+    if ((e = combine<float, float>(CM_STORE, Cp, nullptr, nullptr, P->xh32, s, skip, ns)) != cudaSuccess) return e;
+    // Yhat1 with leading dimension ldt (the product operand), dense for the
+    // BF16 conversion that feeds the BF16 product
+    const int64_t yld = bf ? P->n : P->ldt;
+    if ((e = gds32(P->xh32, P->y132, skip, 1, yld)) != cudaSuccess) return e;
+    if (bf) {
+      ++launches;
+      if ((e = launch_scale_to<float, __nv_bfloat16>(P->y132, nullptr, P->n, (int64_t)P->n * P->r,
+                                                     P->y116, P->ldt, st)) != cudaSuccess)
+        return e;
+    }
+    e = tc ? gemm_tc(false, bf, Cp, skip) : gemm32(false, nullptr, P->y132, P->ldt, Cp, skip);
+    if (e != cudaSuccess) return e;
+    return combine<float, double>(CM_APPLY, Cp, xin, nullptr, out, s, skip, ns);
   }
   // FP64-accurate operator of the given arithmetic (mode: CM_APPLY / CM_RESID).
   cudaError_t opwide(bool emulated, int mode, const double* xin, double* out, DevScalars* s,
@@ -858,49 +956,61 @@ struct Launcher {
                                    emulated ? P->nsplitdf : P->nsplit64);
   }
 
-  // One PCG iteration (operator, update + preconditioner, direction).
-  // lowop: FP32 operator and FP32 preconditioner (mixed modes); otherwise
-  // the FP64-accurate operator (emul: double-float, else FP64).
-  cudaError_t iteration(bool lowop, bool emul) {
+  // The operand of the next low-precision product: pop = D_K p (+ BF16 copy).
+  cudaError_t pupdate_lowp(int prec) {
+    ++launches;
+    return launch_pupdate<float>(P->n, P->r, P->z, P->p, P->pop32, P->kern->dK, P->ldt,
+                                 prec == CPHIFI_MIXED_BF16 ? P->pop16 : nullptr, P->s, st);
+  }
+
+  // One PCG iteration (operator, update + preconditioner, direction).  The
+  // mixed modes use the low-precision operator and an FP32 preconditioner;
+  // FP64 and FP64_EMULATED the FP64-accurate operator.
+  cudaError_t iteration(int prec) {
     DevScalars* s = P->s;
+    const bool lowop = is_lowp(prec);
     cudaError_t e;
-    launches += 2;
+    ++launches;
     if (lowop) {
-      if ((e = op32(P->p, P->y, s, s)) != cudaSuccess) return e;
+      if ((e = op_lowp(prec, P->p, P->y, s, s)) != cudaSuccess) return e;
       if ((e = launch_update_precond<float>(UP_ITER, P->n, P->r, P->x, P->res, P->p, P->y, P->z,
                                             P->UV32, P->D32, s, P->red, st)) != cudaSuccess)
         return e;
-      return launch_pupdate<float>(P->n, P->r, P->z, P->p, P->pop32, s, st);
+      return pupdate_lowp(prec);
     }
-    if ((e = opwide(emul, CM_APPLY, P->p, P->y, s, s, 1)) != cudaSuccess) return e;
+    if ((e = opwide(prec == CPHIFI_FP64_EMULATED, CM_APPLY, P->p, P->y, s, s, 1)) != cudaSuccess)
+      return e;
     if ((e = launch_update_precond<double>(UP_ITER, P->n, P->r, P->x, P->res, P->p, P->y, P->z,
                                            P->UV, P->D64, s, P->red, st)) != cudaSuccess)
       return e;
-    return launch_pupdate<double>(P->n, P->r, P->z, P->p, nullptr, s, st);
+    ++launches;
+    return launch_pupdate<double>(P->n, P->r, P->z, P->p, nullptr, nullptr, P->n, nullptr, s, st);
   }
 
   // FP64-accurate true residual of x, then a restart from it (p = z).
-  cudaError_t true_residual_restart(bool lowop, bool emul) {
+  cudaError_t true_residual_restart(int prec) {
     DevScalars* s = P->s;
     cudaError_t e;
-    if ((e = opwide(emul, CM_RESID, P->x, P->res, s, nullptr, lowop ? 2 : 1)) != cudaSuccess)
+    if ((e = opwide(prec != CPHIFI_FP64, CM_RESID, P->x, P->res, s, nullptr,
+                    is_lowp(prec) ? 2 : 1)) != cudaSuccess)
       return e;
-    return restart(lowop);
+    return restart(prec);
   }
-  cudaError_t restart(bool lowop) {
+  cudaError_t restart(int prec) {
     DevScalars* s = P->s;
     cudaError_t e;
-    launches += 2;
-    if (lowop) {
+    ++launches;
+    if (is_lowp(prec)) {
       if ((e = launch_update_precond<float>(UP_RESTART, P->n, P->r, P->x, P->res, P->p, P->y,
                                             P->z, P->UV32, P->D32, s, P->red, st)) != cudaSuccess)
         return e;
-      return launch_pupdate<float>(P->n, P->r, P->z, P->p, P->pop32, s, st);
+      return pupdate_lowp(prec);
     }
     if ((e = launch_update_precond<double>(UP_RESTART, P->n, P->r, P->x, P->res, P->p, P->y, P->z,
                                            P->UV, P->D64, s, P->red, st)) != cudaSuccess)
       return e;
-    return launch_pupdate<double>(P->n, P->r, P->z, P->p, nullptr, s, st);
+    ++launches;
+    return launch_pupdate<double>(P->n, P->r, P->z, P->p, nullptr, nullptr, P->n, nullptr, s, st);
   }
 };
 
@@ -915,8 +1025,6 @@ int check_params(cphifi_ctx* ctx, const cphifi_params* prm) {
   if (prm->max_iter < 0) return fail(ctx, CPHIFI_E_INVALID_ARG, "max_iter must be >= 0");
   if (prm->precision < CPHIFI_FP64 || prm->precision > CPHIFI_FP64_EMULATED)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
-  if (prm->precision == CPHIFI_MIXED_TF32 || prm->precision == CPHIFI_MIXED_BF16)
-    return fail(ctx, CPHIFI_E_UNSUPPORTED, "tensor-core operator not built");
   return CPHIFI_OK;
 }
 
@@ -961,8 +1069,11 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
   // mixed: FP32 operator inside PCG, stop only on the FP64-accurate true
   // residual (restart every k_replace); emul: the FP64-accurate steps run in
   // double-float arithmetic (every mode but FP64).
-  const bool mixed = prm->precision == CPHIFI_MIXED_FP32;
-  const bool emul = prm->precision != CPHIFI_FP64;
+  const int prec = prm->precision;
+  const bool mixed = is_lowp(prec);
+  const bool emul = prec != CPHIFI_FP64;
+  if ((prec == CPHIFI_MIXED_TF32 || prec == CPHIFI_MIXED_BF16) && !P->kern->tc)
+    return fail(ctx, CPHIFI_E_UNSUPPORTED, "tensor-core products unavailable for this kernel");
   if ((rc = emul ? ensure_lowp(P) : ensure_fp64(P)) != CPHIFI_OK) return rc;
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = ctx->stream;
@@ -991,7 +1102,8 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
     CK(cudaMemsetAsync(P->x, 0, nr * sizeof(double), st));
     CK(cudaMemcpyAsync(P->res, P->bbar, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
-  CK(L.restart(mixed));
+  if (P->tc_err) CK(cudaMemsetAsync(P->tc_err, 0, sizeof(int), st));
+  CK(L.restart(prec));
   CK(cudaEventRecord(ctx->phase[1], st));
   DevScalars* hs = ctx->h_scalars;
   CK(cudaMemcpyAsync(hs, P->s, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
@@ -1012,8 +1124,8 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
       const int left = prm->max_iter - hs->iter;
       if (left <= 0) break;
       const int m = std::min(cycle, left);
-      for (int k = 0; k < m; ++k) CK(L.iteration(mixed, emul));
-      if (mixed) CK(L.true_residual_restart(true, emul));
+      for (int k = 0; k < m; ++k) CK(L.iteration(prec));
+      if (mixed) CK(L.true_residual_restart(prec));
       CK(cudaMemcpyAsync(hs, P->s, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       if (hs->status) break;
@@ -1024,7 +1136,7 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
       if (hs->done) {
         // FP64-accurate operator: the recurrence met tol; confirm with the
         // true residual and restart from it if it does not (refinement).
-        CK(L.true_residual_restart(false, emul));
+        CK(L.true_residual_restart(prec));
         CK(cudaMemcpyAsync(hs, P->s, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if (hs->status) break;
@@ -1047,7 +1159,14 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
   CK(L.ux(emul, P->x, Wdev, P->s));
   if (mem != CPHIFI_MEM_DEVICE) CK(download(W_out, Wdev, nr * sizeof(double), mem, st));
   CK(cudaEventRecord(ctx->phase[3], st));
+  int tcerr = 0;
+  if (P->tc_err) CK(cudaMemcpyAsync(&tcerr, P->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (tcerr) {
+    status = CPHIFI_E_TIMEOUT;  // a bounded wait in a tensor-core product expired
+    ctx->last_error = "tensor-core product: a bounded wait expired (error code " +
+                      std::to_string(tcerr) + ")";
+  }
   auto t1 = std::chrono::steady_clock::now();
   if (stats) {
     memset(stats, 0, sizeof(*stats));
@@ -1077,7 +1196,7 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
       stats->gemm64_launches = (int)tm.gemm64.size();
     }
   }
-  if (status != CPHIFI_OK)
+  if (status != CPHIFI_OK && status != CPHIFI_E_TIMEOUT)
     ctx->last_error = std::string("solve: ") + cphifi_status_string(status);
   return status;
 }
@@ -1130,10 +1249,10 @@ extern "C" int cphifi_problem_matvec(cphifi_problem* P, int precision, double la
                                      const double* X, double* Y, int mem) {
   if (!P || !X || !Y) return CPHIFI_E_INVALID_ARG;
   cphifi_ctx* ctx = P->ctx;
-  if (precision == CPHIFI_MIXED_TF32 || precision == CPHIFI_MIXED_BF16)
-    return fail(ctx, CPHIFI_E_UNSUPPORTED, "tensor-core operator not built");
   if (precision < CPHIFI_FP64 || precision > CPHIFI_FP64_EMULATED)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
+  if ((precision == CPHIFI_MIXED_TF32 || precision == CPHIFI_MIXED_BF16) && !P->kern->tc)
+    return fail(ctx, CPHIFI_E_UNSUPPORTED, "tensor-core products unavailable for this kernel");
   Enter guard(ctx);
   int rc;
   if ((rc = precision == CPHIFI_FP64 ? ensure_fp64(P) : ensure_lowp(P)) != CPHIFI_OK) return rc;
@@ -1149,9 +1268,12 @@ extern "C" int cphifi_problem_matvec(cphifi_problem* P, int precision, double la
   // xbar = U_K' X, then the operator in the eigenbasis, then Y = U_K ybar
   CK(L.gemm64(false, nullptr, P->tmp64, (double*)P->cpart, nullptr, 0));
   CK(L.combine<double, double>(CM_STORE, (double*)P->cpart, nullptr, nullptr, P->tmp64b, P->s2, nullptr));
-  if (precision == CPHIFI_MIXED_FP32) {
-    CK(launch_convert<double, float>(P->tmp64b, P->pop32, (int64_t)nr, st));
-    CK(L.op32(P->tmp64b, P->y, P->s2, nullptr));
+  if (is_lowp(precision)) {
+    CK(launch_scale_to<double, float>(P->tmp64b, P->kern->dK, P->n, (int64_t)nr, P->pop32, P->ldt, st));
+    if (precision == CPHIFI_MIXED_BF16)
+      CK(launch_scale_to<double, __nv_bfloat16>(P->tmp64b, P->kern->dK, P->n, (int64_t)nr, P->pop16,
+                                                P->ldt, st));
+    CK(L.op_lowp(precision, P->tmp64b, P->y, P->s2, nullptr));
   } else {
     CK(L.opwide(precision == CPHIFI_FP64_EMULATED, CM_APPLY, P->tmp64b, P->y, P->s2, nullptr, 0));
   }

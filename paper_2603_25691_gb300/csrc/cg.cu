@@ -376,10 +376,14 @@ template cudaError_t launch_update_precond<float>(int, int, int, double*, double
                                                   cudaStream_t);
 
 // -------------------------------------------------- direction update ------
-// p = z + beta p, and the next product's operand pop = p in type TB.
+// p = z + beta p, and the operand of the next product in the low-precision
+// types: pop = TB(scale[i] p(i, j)) (the D_K row scale of the eigenbasis
+// operator folded in; scale may be NULL) with leading dimension ldp, and the
+// same in BF16 when pop16 is set.
 template <typename TB>
 __global__ void pupdate_kernel(int n, int r, const double* __restrict__ z, double* __restrict__ p,
-                               TB* __restrict__ pop, DevScalars* s) {
+                               TB* __restrict__ pop, const double* __restrict__ scale,
+                               int64_t ldp, __nv_bfloat16* __restrict__ pop16, DevScalars* s) {
   if (dev_skip(s)) return;
   const double beta = s->beta;
   const int64_t total = (int64_t)n * r;
@@ -387,22 +391,26 @@ __global__ void pupdate_kernel(int n, int r, const double* __restrict__ z, doubl
        t += (int64_t)gridDim.x * blockDim.x) {
     const double v = z[t] + beta * p[t];
     p[t] = v;
-    if (pop) pop[t] = (TB)v;
+    const int64_t i = t % n, j = t / n;
+    const double sv = scale ? scale[i] * v : v;
+    if (pop) pop[j * ldp + i] = (TB)sv;
+    if (pop16) pop16[j * ldp + i] = __double2bfloat16(sv);
   }
 }
 
 template <typename TB>
-cudaError_t launch_pupdate(int n, int r, const double* z, double* p, TB* pop, DevScalars* s,
-                           cudaStream_t st) {
+cudaError_t launch_pupdate(int n, int r, const double* z, double* p, TB* pop, const double* scale,
+                           int64_t ldp, __nv_bfloat16* pop16, DevScalars* s, cudaStream_t st) {
   const int blocks = vec_blocks((int64_t)n * r);
-  pupdate_kernel<TB><<<blocks, 256, 0, st>>>(n, r, z, p, pop, s);
+  pupdate_kernel<TB><<<blocks, 256, 0, st>>>(n, r, z, p, pop, scale, ldp, pop16, s);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_pupdate<double>(int, int, const double*, double*, double*, DevScalars*,
+template cudaError_t launch_pupdate<double>(int, int, const double*, double*, double*,
+                                            const double*, int64_t, __nv_bfloat16*, DevScalars*,
                                             cudaStream_t);
-template cudaError_t launch_pupdate<float>(int, int, const double*, double*, float*, DevScalars*,
-                                           cudaStream_t);
+template cudaError_t launch_pupdate<float>(int, int, const double*, double*, float*, const double*,
+                                           int64_t, __nv_bfloat16*, DevScalars*, cudaStream_t);
 
 // ---------------------------------------------------- small utilities -----
 // Y(i,:) = ((X(i,:) U_V) .* D(i,:)) U_V' (the r x r part of Eq. fx), FP64.

@@ -3,6 +3,8 @@
 // return the cudaError_t of the launch.
 #pragma once
 
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -119,6 +121,27 @@ cudaError_t launch_join_df(const float* hi, const float* lo, int64_t total, doub
 cudaError_t launch_split_df(const double* X, const double* scale, int64_t rows, int64_t total,
                             float* hi, float* lo, cudaStream_t st);
 
+// ------------------------------------------------------------ tc_gemm.cu ---
+// tcgen05 products C_split = A B (TF32 or BF16 operands, FP32 accumulation);
+// A and B are K-major and described by TMA tensor maps (tc_make_map).
+bool tc_available(int n);
+cudaError_t tc_make_map(CUtensorMap* map, const void* base, bool bf16, uint64_t inner,
+                        uint64_t outer, uint64_t row_stride_bytes, uint32_t box_outer);
+int tc_pad_cols(int ncols);
+int tc_pick_split(int n, int num_sms);
+cudaError_t launch_tc_gemm(bool bf16, const CUtensorMap& ma, const CUtensorMap& mb, float* C,
+                           int64_t ldc, int64_t split_stride, int n, int ncols, int nsplit,
+                           const DevScalars* skip, int* err, cudaStream_t st);
+// U_K -> T copy with leading dimension ldo, transposed (row-major U_K) or not.
+template <typename T>
+cudaError_t launch_uk_copy(const double* U, int n, int64_t ldo, bool transpose, T* out,
+                           cudaStream_t st);
+// out(i, j) = T(scale[i] X(i, j)) at j*ldo + i for an n x r column-major X
+// (ld n; scale may be NULL).
+template <typename TS, typename T>
+cudaError_t launch_scale_to(const TS* X, const double* scale, int64_t rows, int64_t total, T* out,
+                            int64_t ldo, cudaStream_t st);
+
 // ----------------------------------------------------------------- cg.cu ---
 cudaError_t launch_gram(const double* const* factors_dev, const int64_t* sizes_host,
                         int d_other, int r, double* V, cudaStream_t st);
@@ -150,9 +173,12 @@ cudaError_t launch_update_precond(int mode, int n, int r, double* x, double* rre
                                   const double* p, const double* y, double* z,
                                   const TP* UV, const TP* D, DevScalars* s,
                                   RedScratch red, cudaStream_t st);
-// p = z + beta p; and the operand of the next n x n product, in type TB.
+// p = z + beta p; and the operand of the next n x n product, in type TB:
+// pop(i, j) = TB(scale[i] p(i, j)) at j*ldp + i (scale may be NULL), plus a
+// BF16 copy when pop16 is set.
 template <typename TB>
 cudaError_t launch_pupdate(int n, int r, const double* z, double* p, TB* pop,
+                           const double* scale, int64_t ldp, __nv_bfloat16* pop16,
                            DevScalars* s, cudaStream_t st);
 cudaError_t launch_precond_only(int n, int r, const double* X, double* Y,
                                 const double* UV, const double* D, cudaStream_t st);
