@@ -327,6 +327,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"mixed_tf32": "tf32 products + f32 gather, f64 CG, df64 residuals",
                       "mixed_bf16": "bf16 products + f32 gather, f64 CG, df64 residuals",
+                      "mixed_tf32x3": "3-term split-tf32 products + f32 gather, f64 CG, df64 residuals",
                       "mixed_fp32": "f32 operator, f64 CG, df64 residuals",
                       "fp64_emulated": "df64 (fp32-pair) operator, f64 CG",
                       "fp64": "f64"}[args.precision],

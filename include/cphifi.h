@@ -67,6 +67,9 @@ enum { CPHIFI_MEM_HOST = 0, CPHIFI_MEM_DEVICE = 1 };
  *  MIXED_TF32    : as MIXED_FP32 with the two n x n products on the tensor
  *                  cores in TF32 (FP32 accumulate).
  *  MIXED_BF16    : as MIXED_TF32 with BF16 operands.
+ *  MIXED_TF32X3  : as MIXED_TF32 with each operand split into two TF32 parts
+ *                  (hi + lo) and the product accumulated as hi*hi + hi*lo +
+ *                  lo*hi on the tensor cores: near-FP32 accuracy.
  *  FP64_EMULATED : every step FP64-accurate in double-float arithmetic (pairs
  *                  of FP32 numbers, 48-bit significand, error-free TwoSum /
  *                  TwoProd transforms) on the FP32 units.
@@ -78,7 +81,8 @@ typedef enum cphifi_precision {
   CPHIFI_MIXED_FP32 = 1,
   CPHIFI_MIXED_TF32 = 2,
   CPHIFI_MIXED_BF16 = 3,
-  CPHIFI_FP64_EMULATED = 4
+  CPHIFI_FP64_EMULATED = 4,
+  CPHIFI_MIXED_TF32X3 = 5
 } cphifi_precision;
 
 /* Problem-creation flags. */

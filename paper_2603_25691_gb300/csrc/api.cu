@@ -65,7 +65,8 @@ struct cphifi_kernel {
   int64_t ldt = 0;
   float *A1f = nullptr, *A2f = nullptr;
   __nv_bfloat16 *A1b = nullptr, *A2b = nullptr;
-  CUtensorMap mA1f, mA2f, mA1b, mA2b;
+  float *A1h = nullptr, *A1l = nullptr, *A2h = nullptr, *A2l = nullptr;  // 3-term TF32 split
+  CUtensorMap mA1f, mA2f, mA1b, mA2b, mA1h, mA1l, mA2h, mA2l;
   double* dK = nullptr;    // n
   size_t bytes = 0;
 };
@@ -114,7 +115,8 @@ struct cphifi_problem {
   // TMA maps for the tensor-core modes.
   int64_t ldt = 0;
   __nv_bfloat16 *pop16 = nullptr, *y116 = nullptr;
-  CUtensorMap mBpf, mBpb, mByf, mByb;
+  float *poph = nullptr, *popl = nullptr, *y1h = nullptr, *y1l = nullptr;  // 3-term TF32 split
+  CUtensorMap mBpf, mBpb, mByf, mByb, mBph, mBpl, mByh, mByl;
   int nsplittc = 1;
   int* tc_err = nullptr;
   void* cpart = nullptr;  // max(nsplit64, nsplit32, nsplitdf) x n x r doubles
@@ -417,7 +419,8 @@ extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
     if (kern->UK32) cudaFree(kern->UK32);
     if (kern->UKlo) cudaFree(kern->UKlo);
     if (kern->dK) cudaFree(kern->dK);
-    for (void* a : {(void*)kern->A1f, (void*)kern->A2f, (void*)kern->A1b, (void*)kern->A2b})
+    for (void* a : {(void*)kern->A1f, (void*)kern->A2f, (void*)kern->A1b, (void*)kern->A2b,
+                    (void*)kern->A1h, (void*)kern->A1l, (void*)kern->A2h, (void*)kern->A2l})
       if (a) cudaFree(a);
     if (err) cudaFree(err);
     delete kern;
@@ -446,13 +449,17 @@ extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
   if (tc_available((int)n)) {
     const int64_t ldt = (n + 7) / 8 * 8;
     const size_t cnt = (size_t)n * ldt;
-    tc_bytes = cnt * (2 * sizeof(float) + 2 * sizeof(__nv_bfloat16));
+    tc_bytes = cnt * (6 * sizeof(float) + 2 * sizeof(__nv_bfloat16));
     if (ctx->budget && ctx->in_use + bytes + tc_bytes > ctx->budget) {
       tc_bytes = 0;  // no room: the tensor-core modes stay unavailable
     } else if (cudaMalloc(&kern->A1f, cnt * sizeof(float)) == cudaSuccess &&
                cudaMalloc(&kern->A2f, cnt * sizeof(float)) == cudaSuccess &&
                cudaMalloc(&kern->A1b, cnt * sizeof(__nv_bfloat16)) == cudaSuccess &&
                cudaMalloc(&kern->A2b, cnt * sizeof(__nv_bfloat16)) == cudaSuccess &&
+               cudaMalloc(&kern->A1h, cnt * sizeof(float)) == cudaSuccess &&
+               cudaMalloc(&kern->A1l, cnt * sizeof(float)) == cudaSuccess &&
+               cudaMalloc(&kern->A2h, cnt * sizeof(float)) == cudaSuccess &&
+               cudaMalloc(&kern->A2l, cnt * sizeof(float)) == cudaSuccess &&
                launch_uk_copy<float>(kern->UK64, (int)n, ldt, true, kern->A1f, st) == cudaSuccess &&
                launch_uk_copy<float>(kern->UK64, (int)n, ldt, false, kern->A2f, st) == cudaSuccess &&
                launch_uk_copy<__nv_bfloat16>(kern->UK64, (int)n, ldt, true, kern->A1b, st) == cudaSuccess &&
@@ -461,6 +468,12 @@ extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
                tc_make_map(&kern->mA2f, kern->A2f, false, n, n, ldt * 4, 128) == cudaSuccess &&
                tc_make_map(&kern->mA1b, kern->A1b, true, n, n, ldt * 2, 128) == cudaSuccess &&
                tc_make_map(&kern->mA2b, kern->A2b, true, n, n, ldt * 2, 128) == cudaSuccess &&
+               launch_tf32_split(kern->A1f, kern->A1h, kern->A1l, (int64_t)cnt, st) == cudaSuccess &&
+               launch_tf32_split(kern->A2f, kern->A2h, kern->A2l, (int64_t)cnt, st) == cudaSuccess &&
+               tc_make_map(&kern->mA1h, kern->A1h, false, n, n, ldt * 4, 128) == cudaSuccess &&
+               tc_make_map(&kern->mA1l, kern->A1l, false, n, n, ldt * 4, 128) == cudaSuccess &&
+               tc_make_map(&kern->mA2h, kern->A2h, false, n, n, ldt * 4, 128) == cudaSuccess &&
+               tc_make_map(&kern->mA2l, kern->A2l, false, n, n, ldt * 4, 128) == cudaSuccess &&
                cudaStreamSynchronize(st) == cudaSuccess) {
       kern->tc = true;
       kern->ldt = ldt;
@@ -487,7 +500,8 @@ extern "C" int cphifi_kernel_destroy(cphifi_kernel* kern) {
   cudaFree(kern->UK32);
   cudaFree(kern->UKlo);
   cudaFree(kern->dK);
-  for (void* a : {(void*)kern->A1f, (void*)kern->A2f, (void*)kern->A1b, (void*)kern->A2b})
+  for (void* a : {(void*)kern->A1f, (void*)kern->A2f, (void*)kern->A1b, (void*)kern->A2b,
+                  (void*)kern->A1h, (void*)kern->A1l, (void*)kern->A2h, (void*)kern->A2l})
     if (a) cudaFree(a);
   ctx->in_use -= std::min(ctx->in_use, kern->bytes);
   cudaSetDevice(prev);
@@ -644,6 +658,10 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   if (kern->tc) {
     PCK(dalloc(P, &P->pop16, (size_t)P->ldt * r));
     PCK(dalloc(P, &P->y116, (size_t)P->ldt * r));
+    for (float** v : {&P->poph, &P->popl, &P->y1h, &P->y1l}) {
+      PCK(dalloc(P, v, (size_t)P->ldt * r));
+      PCK(cudaMemsetAsync(*v, 0, (size_t)P->ldt * r * sizeof(float), st));
+    }
     PCK(dalloc(P, &P->tc_err, 1));
     PCK(cudaMemsetAsync(P->tc_err, 0, sizeof(int), st));
     const uint32_t np = (uint32_t)tc_pad_cols(r);
@@ -651,6 +669,10 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
     PCK(tc_make_map(&P->mByf, P->y132, false, n, r, P->ldt * 4, np));
     PCK(tc_make_map(&P->mBpb, P->pop16, true, n, r, P->ldt * 2, np));
     PCK(tc_make_map(&P->mByb, P->y116, true, n, r, P->ldt * 2, np));
+    PCK(tc_make_map(&P->mBph, P->poph, false, n, r, P->ldt * 4, np));
+    PCK(tc_make_map(&P->mBpl, P->popl, false, n, r, P->ldt * 4, np));
+    PCK(tc_make_map(&P->mByh, P->y1h, false, n, r, P->ldt * 4, np));
+    PCK(tc_make_map(&P->mByl, P->y1l, false, n, r, P->ldt * 4, np));
   }
   PCK(dalloc(P, (double**)&P->cpart, (size_t)nsplit * nr));
   PCK(dalloc(P, &P->red.partials, (size_t)kRedMaxBlocks * kRedSlots));
@@ -780,7 +802,11 @@ extern "C" size_t cphifi_problem_bytes(const cphifi_problem* P) { return P ? P->
 namespace {
 
 bool is_lowp(int prec) {
-  return prec == CPHIFI_MIXED_FP32 || prec == CPHIFI_MIXED_TF32 || prec == CPHIFI_MIXED_BF16;
+  return prec == CPHIFI_MIXED_FP32 || prec == CPHIFI_MIXED_TF32 || prec == CPHIFI_MIXED_BF16 ||
+         prec == CPHIFI_MIXED_TF32X3;
+}
+bool is_tc(int prec) {
+  return prec == CPHIFI_MIXED_TF32 || prec == CPHIFI_MIXED_BF16 || prec == CPHIFI_MIXED_TF32X3;
 }
 
 struct Launcher {
@@ -819,14 +845,26 @@ struct Launcher {
     ++launches;
     return e;
   }
-  // Tensor-core product (tcgen05): g1 = U_K pop, else U_K' y1; TF32 or BF16.
-  cudaError_t gemm_tc(bool g1, bool bf16, float* out_part, const DevScalars* skip) {
+  // Tensor-core product (tcgen05): g1 = U_K pop, else U_K' y1; TF32, BF16,
+  // or the 3-term split TF32 (x3).
+  cudaError_t gemm_tc(bool g1, bool bf16, bool x3, float* out_part, const DevScalars* skip) {
     const cphifi_kernel* K = P->kern;
-    const CUtensorMap& ma = g1 ? (bf16 ? K->mA1b : K->mA1f) : (bf16 ? K->mA2b : K->mA2f);
-    const CUtensorMap& mb = g1 ? (bf16 ? P->mBpb : P->mBpf) : (bf16 ? P->mByb : P->mByf);
+    const CUtensorMap* ma;
+    const CUtensorMap* mb;
+    const CUtensorMap* mal = nullptr;
+    const CUtensorMap* mbl = nullptr;
+    if (x3) {
+      ma = g1 ? &K->mA1h : &K->mA2h;
+      mal = g1 ? &K->mA1l : &K->mA2l;
+      mb = g1 ? &P->mBph : &P->mByh;
+      mbl = g1 ? &P->mBpl : &P->mByl;
+    } else {
+      ma = g1 ? (bf16 ? &K->mA1b : &K->mA1f) : (bf16 ? &K->mA2b : &K->mA2f);
+      mb = g1 ? (bf16 ? &P->mBpb : &P->mBpf) : (bf16 ? &P->mByb : &P->mByf);
+    }
     cudaEvent_t b = tm ? tm->begin() : nullptr;
-    cudaError_t e = launch_tc_gemm(bf16, ma, mb, out_part, P->n, split_stride(), P->n, P->r,
-                                   P->nsplittc, skip, P->tc_err, st);
+    cudaError_t e = launch_tc_gemm(bf16, *ma, *mb, mal, mbl, out_part, P->n, split_stride(), P->n,
+                                   P->r, P->nsplittc, skip, P->tc_err, st);
     if (tm) tm->end(b, tm->gemm);
     ++launches;
     return e;
@@ -909,12 +947,19 @@ struct Launcher {
   // D_K xin in the operand type; FP32 SIMT products, or tcgen05 TF32/BF16.
   cudaError_t op_lowp(int prec, const double* xin, double* out, DevScalars* s,
                       const DevScalars* skip) {
-    const bool tc = prec == CPHIFI_MIXED_TF32 || prec == CPHIFI_MIXED_BF16;
+    const bool x3 = prec == CPHIFI_MIXED_TF32X3;
+    const bool tc = prec == CPHIFI_MIXED_TF32 || prec == CPHIFI_MIXED_BF16 || x3;
     const bool bf = prec == CPHIFI_MIXED_BF16;
     float* Cp = (float*)P->cpart;
     const int ns = tc ? P->nsplittc : P->nsplit32;
     cudaError_t e;
-    e = tc ? gemm_tc(true, bf, Cp, skip) : gemm32(true, nullptr, P->pop32, P->ldt, Cp, skip);
+    if (x3) {
+      ++launches;
+      if ((e = launch_tf32_split_block(P->pop32, P->ldt, P->n, (int64_t)P->n * P->r, P->poph,
+                                       P->popl, P->ldt, skip, st)) != cudaSuccess)
+        return e;
+    }
+    e = tc ? gemm_tc(true, bf, x3, Cp, skip) : gemm32(true, nullptr, P->pop32, P->ldt, Cp, skip);
     if (e != cudaSuccess) return e;
     if ((e = combine<float, float>(CM_STORE, Cp, nullptr, nullptr, P->xh32, s, skip, ns)) != cudaSuccess) return e;
     // Yhat1 with leading dimension ldt (the product operand), dense for the
@@ -927,7 +972,13 @@ struct Launcher {
                                                      P->y116, P->ldt, st)) != cudaSuccess)
         return e;
     }
-    e = tc ? gemm_tc(false, bf, Cp, skip) : gemm32(false, nullptr, P->y132, P->ldt, Cp, skip);
+    if (x3) {
+      ++launches;
+      if ((e = launch_tf32_split_block(P->y132, P->ldt, P->n, (int64_t)P->n * P->r, P->y1h,
+                                       P->y1l, P->ldt, skip, st)) != cudaSuccess)
+        return e;
+    }
+    e = tc ? gemm_tc(false, bf, x3, Cp, skip) : gemm32(false, nullptr, P->y132, P->ldt, Cp, skip);
     if (e != cudaSuccess) return e;
     return combine<float, double>(CM_APPLY, Cp, xin, nullptr, out, s, skip, ns);
   }
@@ -1023,7 +1074,7 @@ int check_params(cphifi_ctx* ctx, const cphifi_params* prm) {
   if (!(prm->tol > 0.0) || !std::isfinite(prm->tol))
     return fail(ctx, CPHIFI_E_INVALID_ARG, "tol must be finite and > 0");
   if (prm->max_iter < 0) return fail(ctx, CPHIFI_E_INVALID_ARG, "max_iter must be >= 0");
-  if (prm->precision < CPHIFI_FP64 || prm->precision > CPHIFI_FP64_EMULATED)
+  if (prm->precision < CPHIFI_FP64 || prm->precision > CPHIFI_MIXED_TF32X3)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
   return CPHIFI_OK;
 }
@@ -1072,7 +1123,7 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
   const int prec = prm->precision;
   const bool mixed = is_lowp(prec);
   const bool emul = prec != CPHIFI_FP64;
-  if ((prec == CPHIFI_MIXED_TF32 || prec == CPHIFI_MIXED_BF16) && !P->kern->tc)
+  if (is_tc(prec) && !P->kern->tc)
     return fail(ctx, CPHIFI_E_UNSUPPORTED, "tensor-core products unavailable for this kernel");
   if ((rc = emul ? ensure_lowp(P) : ensure_fp64(P)) != CPHIFI_OK) return rc;
   auto t0 = std::chrono::steady_clock::now();
@@ -1249,9 +1300,9 @@ extern "C" int cphifi_problem_matvec(cphifi_problem* P, int precision, double la
                                      const double* X, double* Y, int mem) {
   if (!P || !X || !Y) return CPHIFI_E_INVALID_ARG;
   cphifi_ctx* ctx = P->ctx;
-  if (precision < CPHIFI_FP64 || precision > CPHIFI_FP64_EMULATED)
+  if (precision < CPHIFI_FP64 || precision > CPHIFI_MIXED_TF32X3)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
-  if ((precision == CPHIFI_MIXED_TF32 || precision == CPHIFI_MIXED_BF16) && !P->kern->tc)
+  if (is_tc(precision) && !P->kern->tc)
     return fail(ctx, CPHIFI_E_UNSUPPORTED, "tensor-core products unavailable for this kernel");
   Enter guard(ctx);
   int rc;
@@ -1288,7 +1339,7 @@ extern "C" int cphifi_problem_gds(cphifi_problem* P, int precision, const double
                                   int mem) {
   if (!P || !Xhat || !Y1) return CPHIFI_E_INVALID_ARG;
   cphifi_ctx* ctx = P->ctx;
-  if (precision < CPHIFI_FP64 || precision > CPHIFI_FP64_EMULATED)
+  if (precision < CPHIFI_FP64 || precision > CPHIFI_MIXED_TF32X3)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
   Enter guard(ctx);
   int rc;

@@ -129,9 +129,18 @@ cudaError_t tc_make_map(CUtensorMap* map, const void* base, bool bf16, uint64_t 
                         uint64_t outer, uint64_t row_stride_bytes, uint32_t box_outer);
 int tc_pad_cols(int ncols);
 int tc_pick_split(int n, int num_sms);
-cudaError_t launch_tc_gemm(bool bf16, const CUtensorMap& ma, const CUtensorMap& mb, float* C,
-                           int64_t ldc, int64_t split_stride, int n, int ncols, int nsplit,
+// mal/mbl (TF32 only, may be NULL): maps of the lo parts of a 3-term split
+// product A_hi B_hi + A_hi B_lo + A_lo B_hi.
+cudaError_t launch_tc_gemm(bool bf16, const CUtensorMap& ma, const CUtensorMap& mb,
+                           const CUtensorMap* mal, const CUtensorMap* mbl, float* C, int64_t ldc,
+                           int64_t split_stride, int n, int ncols, int nsplit,
                            const DevScalars* skip, int* err, cudaStream_t st);
+// TF32 hi/lo split (hi = x with 13 low bits cleared, lo = x - hi).
+cudaError_t launch_tf32_split(const float* src, float* hi, float* lo, int64_t total,
+                              cudaStream_t st);
+cudaError_t launch_tf32_split_block(const float* x, int64_t ldx, int64_t rows, int64_t total,
+                                    float* hi, float* lo, int64_t ldo, const DevScalars* skip,
+                                    cudaStream_t st);
 // U_K -> T copy with leading dimension ldo, transposed (row-major U_K) or not.
 template <typename T>
 cudaError_t launch_uk_copy(const double* U, int n, int64_t ldo, bool transpose, T* out,

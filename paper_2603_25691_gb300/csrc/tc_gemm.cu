@@ -125,19 +125,25 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 
 }  // namespace
 
-template <typename T, int NP>
+// SPLIT3 (TF32 only): the operands come as hi + lo pairs of TF32 values
+// (tensor maps tmAl, tmBl for the lo parts) and each k step accumulates
+// A_hi B_hi + A_hi B_lo + A_lo B_hi: the 3-term split product, accurate to
+// about 2^-21 instead of TF32's 2^-11.
+template <typename T, int NP, bool SPLIT3>
 __global__ void __launch_bounds__(kTcBlock, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ CUtensorMap tmAl, const __grid_constant__ CUtensorMap tmBl,
                float* __restrict__ C, int64_t ldc, int64_t split_stride, int n, int ncols,
                int kchunk, const DevScalars* skip, int* err) {
   if (dev_skip(skip)) return;
   constexpr int BK = 128 / (int)sizeof(T);            // k per 128-byte slab
   constexpr int A_BYTES = 128 * 128;                  // 128 rows x 128 bytes
   constexpr int B_BYTES = NP * 128;
-  constexpr int STAGE = A_BYTES + B_BYTES;
+  constexpr int STAGE = (A_BYTES + B_BYTES) * (SPLIT3 ? 2 : 1);
+  constexpr int kStages = SPLIT3 ? 4 : kTcStages;
   constexpr uint32_t TMEM_COLS = NP <= 32 ? 32 : (NP <= 64 ? 64 : 128);
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t full_bar[kTcStages], empty_bar[kTcStages], done_bar;
+  __shared__ uint64_t full_bar[kTcStages], empty_bar[kTcStages], done_bar;  // kStages used
   __shared__ uint32_t tmem_slot;
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
 
@@ -148,7 +154,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   const int nslab = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kTcStages; ++s) {
+    for (int s = 0; s < kStages; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
@@ -172,27 +178,39 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (warp == 0 && lane == 0) {
       // producer: TMA ring
       for (int c = 0; c < nslab; ++c) {
-        const int s = c % kTcStages;
-        const uint32_t ph = (uint32_t)(c / kTcStages) & 1u;
-        if (c >= kTcStages && !mbar_wait(&empty_bar[s], ph ^ 1u, err, 1)) break;
+        const int s = c % kStages;
+        const uint32_t ph = (uint32_t)(c / kStages) & 1u;
+        if (c >= kStages && !mbar_wait(&empty_bar[s], ph ^ 1u, err, 1)) break;
         uint8_t* st = smem + s * STAGE;
         mbar_expect_tx(&full_bar[s], STAGE);
         tma_load_2d(st, &tmA, kbeg + c * BK, m0, &full_bar[s]);
         tma_load_2d(st + A_BYTES, &tmB, kbeg + c * BK, 0, &full_bar[s]);
+        if (SPLIT3) {
+          tma_load_2d(st + A_BYTES + B_BYTES, &tmAl, kbeg + c * BK, m0, &full_bar[s]);
+          tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tmBl, kbeg + c * BK, 0, &full_bar[s]);
+        }
       }
     } else if (warp == 1 && lane == 0) {
       // MMA issuer
       const uint32_t id = idesc<T>(NP);
       for (int c = 0; c < nslab; ++c) {
-        const int s = c % kTcStages;
-        const uint32_t ph = (uint32_t)(c / kTcStages) & 1u;
+        const int s = c % kStages;
+        const uint32_t ph = (uint32_t)(c / kStages) & 1u;
         if (!mbar_wait(&full_bar[s], ph, err, 2)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint8_t* st = smem + s * STAGE;
+        const uint8_t* ah = st;
+        const uint8_t* bh = st + A_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < 128 / 32; ++kk)
-          mma<T>(tmem, sdesc(st + kk * 32), sdesc(st + A_BYTES + kk * 32), id,
-                 (c > 0 || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < 128 / 32; ++kk) {
+          mma<T>(tmem, sdesc(ah + kk * 32), sdesc(bh + kk * 32), id, (c > 0 || kk > 0) ? 1u : 0u);
+          if (SPLIT3) {
+            const uint8_t* al = st + A_BYTES + B_BYTES;
+            const uint8_t* bl = st + 2 * A_BYTES + B_BYTES;
+            mma<T>(tmem, sdesc(ah + kk * 32), sdesc(bl + kk * 32), id, 1u);
+            mma<T>(tmem, sdesc(al + kk * 32), sdesc(bh + kk * 32), id, 1u);
+          }
+        }
         mma_commit(&empty_bar[s]);
       }
       mma_commit(&done_bar);
@@ -287,15 +305,17 @@ int tc_pick_split(int n, int num_sms) {
   return s < 1 ? 1 : s;
 }
 
-template <typename T, int NP>
-static cudaError_t tc_launch(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int64_t ldc,
-                             int64_t split_stride, int n, int ncols, int nsplit,
-                             const DevScalars* skip, int* err, cudaStream_t st) {
-  constexpr int STAGE = 128 * 128 + NP * 128;
-  const size_t smem = (size_t)kTcStages * STAGE + 1024;
+template <typename T, int NP, bool SPLIT3>
+static cudaError_t tc_launch(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mal,
+                             const CUtensorMap& mbl, float* C, int64_t ldc, int64_t split_stride,
+                             int n, int ncols, int nsplit, const DevScalars* skip, int* err,
+                             cudaStream_t st) {
+  constexpr int STAGE = (128 * 128 + NP * 128) * (SPLIT3 ? 2 : 1);
+  constexpr int kStages = SPLIT3 ? 4 : kTcStages;
+  const size_t smem = (size_t)kStages * STAGE + 1024;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<T, NP>,
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<T, NP, SPLIT3>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
@@ -304,23 +324,32 @@ static cudaError_t tc_launch(const CUtensorMap& ma, const CUtensorMap& mb, float
   int kchunk = (n + nsplit - 1) / nsplit;
   kchunk = (kchunk + BK - 1) / BK * BK;
   const dim3 grid((n + 127) / 128, nsplit);
-  tc_gemm_kernel<T, NP><<<grid, kTcBlock, smem, st>>>(ma, mb, C, ldc, split_stride, n, ncols,
-                                                      kchunk, skip, err);
+  tc_gemm_kernel<T, NP, SPLIT3><<<grid, kTcBlock, smem, st>>>(ma, mb, mal, mbl, C, ldc,
+                                                              split_stride, n, ncols, kchunk,
+                                                              skip, err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_gemm(bool bf16, const CUtensorMap& ma, const CUtensorMap& mb, float* C,
-                           int64_t ldc, int64_t split_stride, int n, int ncols, int nsplit,
+cudaError_t launch_tc_gemm(bool bf16, const CUtensorMap& ma, const CUtensorMap& mb,
+                           const CUtensorMap* mal, const CUtensorMap* mbl, float* C, int64_t ldc,
+                           int64_t split_stride, int n, int ncols, int nsplit,
                            const DevScalars* skip, int* err, cudaStream_t st) {
   const int np = tc_pad_cols(ncols);
-#define CPHIFI_TC(NPV)                                                                       \
-  return bf16 ? tc_launch<__nv_bfloat16, NPV>(ma, mb, C, ldc, split_stride, n, ncols, nsplit, \
-                                              skip, err, st)                                  \
-              : tc_launch<float, NPV>(ma, mb, C, ldc, split_stride, n, ncols, nsplit, skip,   \
-                                      err, st)
-  if (np == 16) CPHIFI_TC(16);
-  if (np == 32) CPHIFI_TC(32);
-  if (np == 48) CPHIFI_TC(48);
+  const bool split3 = !bf16 && mal && mbl;
+  const CUtensorMap& al = split3 ? *mal : ma;
+  const CUtensorMap& bl = split3 ? *mbl : mb;
+#define CPHIFI_TC(NPV)                                                                        \
+  if (bf16)                                                                                   \
+    return tc_launch<__nv_bfloat16, NPV, false>(ma, mb, al, bl, C, ldc, split_stride, n,      \
+                                                ncols, nsplit, skip, err, st);                \
+  if (split3)                                                                                 \
+    return tc_launch<float, NPV, true>(ma, mb, al, bl, C, ldc, split_stride, n, ncols, nsplit, \
+                                       skip, err, st);                                        \
+  return tc_launch<float, NPV, false>(ma, mb, al, bl, C, ldc, split_stride, n, ncols, nsplit,  \
+                                      skip, err, st)
+  if (np == 16) { CPHIFI_TC(16); }
+  if (np == 32) { CPHIFI_TC(32); }
+  if (np == 48) { CPHIFI_TC(48); }
   CPHIFI_TC(64);
 #undef CPHIFI_TC
 }
@@ -359,6 +388,63 @@ cudaError_t launch_uk_copy(const double* U, int n, int64_t ldo, bool transpose, 
 template cudaError_t launch_uk_copy<float>(const double*, int, int64_t, bool, float*, cudaStream_t);
 template cudaError_t launch_uk_copy<__nv_bfloat16>(const double*, int, int64_t, bool,
                                                    __nv_bfloat16*, cudaStream_t);
+
+// TF32 split: hi = x with the 13 low significand bits cleared (a TF32 value),
+// lo = x - hi (exact in FP32; its TF32 rounding loses ~2^-21 of x).
+__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
+  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+  lo = x - hi;
+}
+
+// hi/lo TF32 split of U_K copies, in place for hi (a) and into lo.
+__global__ void tf32_split_kernel(float* __restrict__ a, float* __restrict__ lo, int64_t total) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    float h, l;
+    tf32_split(a[t], h, l);
+    a[t] = h;
+    lo[t] = l;
+  }
+}
+
+cudaError_t launch_tf32_split(const float* src, float* hi, float* lo, int64_t total,
+                              cudaStream_t st) {
+  if (total == 0) return cudaSuccess;
+  if (src != hi) {
+    cudaError_t e = cudaMemcpyAsync(hi, src, total * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  int64_t b = (total + 255) / 256;
+  if (b > 4096) b = 4096;
+  tf32_split_kernel<<<(int)b, 256, 0, st>>>(hi, lo, total);
+  return cudaGetLastError();
+}
+
+// Strided hi/lo TF32 split of an n x r block (ld ldx) into hi/lo (ld ldo).
+__global__ void tf32_split_block_kernel(const float* __restrict__ x, int64_t ldx, int64_t rows,
+                                        int64_t total, float* __restrict__ hi,
+                                        float* __restrict__ lo, int64_t ldo,
+                                        const DevScalars* skip) {
+  if (dev_skip(skip)) return;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % rows, j = t / rows;
+    float h, l;
+    tf32_split(x[j * ldx + i], h, l);
+    hi[j * ldo + i] = h;
+    lo[j * ldo + i] = l;
+  }
+}
+
+cudaError_t launch_tf32_split_block(const float* x, int64_t ldx, int64_t rows, int64_t total,
+                                    float* hi, float* lo, int64_t ldo, const DevScalars* skip,
+                                    cudaStream_t st) {
+  if (total == 0) return cudaSuccess;
+  int64_t b = (total + 255) / 256;
+  if (b > 2048) b = 2048;
+  tf32_split_block_kernel<<<(int)b, 256, 0, st>>>(x, ldx, rows, total, hi, lo, ldo, skip);
+  return cudaGetLastError();
+}
 
 // out = T(scale[i] * X(i, j)) for an n x r column-major block (scale may be
 // NULL): the B operand of the tensor-core products.

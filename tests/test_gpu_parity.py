@@ -123,6 +123,8 @@ def test_matvec(case):
         # tensor-core operand rounding: TF32 2^-11, BF16 2^-8 per element
         assert rel(prob.matvec(X, lam, rho, "mixed_tf32"), ref) <= 4e-3
         assert rel(prob.matvec(X, lam, rho, "mixed_bf16"), ref) <= 3e-2
+        # 3-term split TF32: about 2^-21 per operand element
+        assert rel(prob.matvec(X, lam, rho, "mixed_tf32x3"), ref) <= 2e-5
 
 
 def test_preconditioner(case):
@@ -147,7 +149,8 @@ def _gate(p, W, tol, Wd=None):
                                            ("mixed_fp32", 1e-6), ("mixed_fp32", 1e-8),
                                            ("mixed_fp32", 1e-10), ("mixed_tf32", 1e-6),
                                            ("mixed_tf32", 1e-8), ("mixed_bf16", 1e-6),
-                                           ("mixed_bf16", 1e-8)])
+                                           ("mixed_bf16", 1e-8), ("mixed_tf32x3", 1e-6),
+                                           ("mixed_tf32x3", 1e-10)])
 def test_solve_c1_workload(ctx, pkg, precision, tol):
     """n=100, 20x30, q=6000, r=5, lambda=1e-4, rho=1e-6 (planted, 1% noise)."""
     p = synth.workload("c1_fp64_n100_q6e3_r5", seed=0)
@@ -208,7 +211,8 @@ def test_unsorted_equals_sorted(ctx, pkg):
 def test_deterministic(ctx, pkg):
     p = synth.planted_problem(9, 70, (15, 16), 8000, 12, bandwidth=0.1, lam=1e-4, rho=1e-6)
     kern, prob = make(ctx, pkg, p)
-    for prec in ("fp64", "mixed_fp32", "fp64_emulated", "mixed_tf32", "mixed_bf16"):
+    for prec in ("fp64", "mixed_fp32", "fp64_emulated", "mixed_tf32", "mixed_bf16",
+                 "mixed_tf32x3"):
         W1, s1 = prob.solve(p.lam, p.rho, 1e-9, 500, precision=prec)
         W2, s2 = prob.solve(p.lam, p.rho, 1e-9, 500, precision=prec)
         np.testing.assert_array_equal(W1, W2)
