@@ -43,7 +43,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--precision", default="mixed_tf32")
+    ap.add_argument("--precision", default="mixed_fp32")
+    ap.add_argument("--sweep", default="mixed_tf32x3,mixed_tf32,mixed_bf16,fp64_emulated",
+                    help="other operator arithmetics timed on the same data (2 steps each)")
     ap.add_argument("--q", type=int, default=0, help="override q (smaller runs)")
     ap.add_argument("--n", type=int, default=0, help="override n (smaller runs)")
     ap.add_argument("--no-fp64", action="store_true")
@@ -306,6 +308,27 @@ def main():
                 "iterations": s64["iterations"], "rel_residual": s64["rel_residual"],
                 "status": s64["status"]}
 
+    # ---- the other operator arithmetics on the same problem (tensor cores etc.)
+    sweep = {}
+    for prec in [x for x in args.sweep.split(",") if x and x != args.precision]:
+        sts = [step(prec, profile=True) for _ in range(1)]   # warm
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sts = [step(prec, profile=True) for _ in range(2)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 2
+        it = sum(x["iterations"] for x in sts) / 2
+        itms = sum(x["iter_ms"] for x in sts) / 2
+        gm = sum(x["gemm_ms"] for x in sts)
+        gl = 2 * sum(x["iterations"] for x in sts)  # executed products (2 per iteration)
+        sweep[prec] = {"value": q * it / (itms / 1e3), "solves_per_s": 1e3 / ms,
+                       "iterations": it, "iter_phase_ms": itms,
+                       "rel_residual": sts[-1]["rel_residual"], "status": sts[-1]["status"],
+                       "gemm_avg_ms": gm / max(1, gl)}
+
     # ---- end to end through the public API with host buffers (pinned)
     e2e = None
     if not args.no_e2e:
@@ -353,6 +376,7 @@ def main():
                          "bytes_per_launch": gds_bytes_per_launch,
                          "avg_launch_ms": gds_ms / max(1, gds_exec)},
             "fp64_path": fp64,
+            "precision_sweep": sweep,
             "mixed_vs_fp64_solves": (solves_per_s / fp64["solves_per_s"]) if fp64 else None,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary(),
             "gpu_launches": int(launches),
