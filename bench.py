@@ -310,7 +310,7 @@ def main():
 
     # ---- the other operator arithmetics on the same problem (tensor cores etc.)
     sweep = {}
-    for prec in [x for x in args.sweep.split(",") if x and x != args.precision]:
+    for prec in [x for x in args.sweep.split(",") if x and x not in ("none", args.precision)]:
         sts = [step(prec, profile=True) for _ in range(1)]   # warm
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
