@@ -444,6 +444,23 @@ __device__ __forceinline__ void store_row(const PieceList& pl, int p, int seg, i
   }
 }
 
+// Factor row part (CPL consecutive columns of row `off`, row-major hi/lo):
+// 16-byte loads when the row and the lane's column block are 16-byte aligned.
+template <int CPL>
+__device__ __forceinline__ void load_row_part(const float* __restrict__ base, bool vec,
+                                              float (&v)[CPL]) {
+  if (CPL % 4 == 0 && vec) {
+#pragma unroll
+    for (int c = 0; c < CPL; c += 4) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(base + c));
+      v[c] = t.x; v[c + 1] = t.y; v[c + 2] = t.z; v[c + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) v[c] = __ldg(base + c);
+  }
+}
+
 template <int RP, int LPO>
 __global__ void __launch_bounds__(256)
 zhat_mttkrp_kernel(PieceList pl, const int32_t* __restrict__ perm, const int32_t* __restrict__ oidx,
@@ -452,10 +469,13 @@ zhat_mttkrp_kernel(PieceList pl, const int32_t* __restrict__ perm, const int32_t
                    const double* __restrict__ vals, float* __restrict__ zhi,
                    float* __restrict__ zlo, double* __restrict__ z64,
                    double* __restrict__ partial, double* __restrict__ B, int64_t ldb, int* err) {
-  constexpr int OPW = 32 / LPO, CPL = RP / LPO;
+  constexpr int OPW = 32 / LPO, CPL = RP / LPO, UN = 1;
   const int lane = threadIdx.x & 31, sub = lane / OPW, o = lane % OPW;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  // 16-byte factor-row loads need r % 4 == 0 (rows start on 16 bytes) and a
+  // whole lane block inside the row
+  const bool vec = (r % 4 == 0) && ((sub + 1) * CPL <= r);
   int bad = 0;
   for (int w = gw; w < pl.nwarps; w += nwarps) {
     const int p_end = pl.warp_first[w + 1];
@@ -465,36 +485,61 @@ zhat_mttkrp_kernel(PieceList pl, const int32_t* __restrict__ perm, const int32_t
       df acc[CPL];
 #pragma unroll
       for (int c = 0; c < CPL; ++c) acc[c] = df{0.f, 0.f};
-      for (int l = b + o; l < e; l += OPW) {
-        const int64_t src = perm ? (int64_t)perm[l] : (int64_t)l;
-        const df t = df_from_double(vals[src]);
-        df z[CPL];
-        for (int m = 0; m < d_other; ++m) {
-          const int32_t im = oidx[src * d_other + m];
-          const int64_t nm = sizes[m];
-          const bool ok = im >= 0 && im < nm;
-          bad |= ok ? 0 : 1;
-          const int64_t off = ok ? im : 0;
-          // factors' hi/lo parts are row-major: the lane's columns of row
-          // im are contiguous (one or two cache lines per row)
-          const float* rh = fhi[m] + off * r + sub * CPL;
-          const float* rl = flo[m] + off * r + sub * CPL;
+      for (int l0 = b + o; l0 < e; l0 += UN * OPW) {
+        int64_t src[UN];
+        bool live[UN];
 #pragma unroll
-          for (int c = 0; c < CPL; ++c) {
-            const int j = sub * CPL + c;
-            df f{0.f, 0.f};
-            if (ok && j < r) f = df{rh[c], rl[c]};
-            z[c] = m == 0 ? f : df_mul(z[c], f);
+        for (int u = 0; u < UN; ++u) {
+          const int l = l0 + u * OPW;
+          live[u] = l < e;
+          src[u] = live[u] ? (perm ? (int64_t)perm[l] : (int64_t)l) : 0;
+        }
+        df t[UN];
+#pragma unroll
+        for (int u = 0; u < UN; ++u) t[u] = live[u] ? df_from_double(vals[src[u]]) : df{0.f, 0.f};
+        df z[UN][CPL];
+        for (int m = 0; m < d_other; ++m) {
+          const int64_t nm = sizes[m];
+          int32_t im[UN];
+#pragma unroll
+          for (int u = 0; u < UN; ++u) im[u] = live[u] ? oidx[src[u] * d_other + m] : 0;
+#pragma unroll
+          for (int u = 0; u < UN; ++u) {
+            const bool ok = im[u] >= 0 && im[u] < nm;
+            bad |= (live[u] && !ok) ? 1 : 0;
+            const int64_t off = (ok ? im[u] : 0) * (int64_t)r + sub * CPL;
+            float h[CPL], lo[CPL];
+            if (vec) {
+              load_row_part<CPL>(fhi[m] + off, true, h);
+              load_row_part<CPL>(flo[m] + off, true, lo);
+            } else {
+#pragma unroll
+              for (int c = 0; c < CPL; ++c) {
+                const bool in = sub * CPL + c < r;
+                h[c] = in ? __ldg(fhi[m] + off + c) : 0.f;
+                lo[c] = in ? __ldg(flo[m] + off + c) : 0.f;
+              }
+            }
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+              const df f{ok ? h[c] : 0.f, ok ? lo[c] : 0.f};
+              z[u][c] = m == 0 ? f : df_mul(z[u][c], f);
+            }
           }
         }
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-          const int j = sub * CPL + c;
-          if (j < r) {
-            const int64_t zi = zidx(l, j, r);
-            if (zhi) { zhi[zi] = z[c].hi; zlo[zi] = z[c].lo; }
-            if (z64) z64[zi] = df_to_double(z[c]);
-            df_acc_prod(acc[c], t, z[c]);
+        for (int u = 0; u < UN; ++u) {
+          if (!live[u]) continue;
+          const int l = l0 + u * OPW;
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            const int j = sub * CPL + c;
+            if (j < r) {
+              const int64_t zi = zidx(l, j, r);
+              if (zhi) { zhi[zi] = z[u][c].hi; zlo[zi] = z[u][c].lo; }
+              if (z64) z64[zi] = df_to_double(z[u][c]);
+              df_acc_prod(acc[c], t[u], z[u][c]);
+            }
           }
         }
       }
