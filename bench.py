@@ -51,6 +51,13 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch", type=int, default=256,
+                    help="uneven subproblems in the batched run (0: skip)")
+    ap.add_argument("--serve-rates", default="200,1000",
+                    help="Poisson arrival rates (req/s) of the serving run ('' : skip)")
+    ap.add_argument("--slots", type=int, default=16, help="requests running at once")
+    ap.add_argument("--serve-requests", type=int, default=300,
+                    help="requests per serving rate (at most ~2 s of arrivals)")
     return ap.parse_args()
 
 
@@ -212,6 +219,152 @@ def run_e2e(args, pkg, ctx, kern, p):
             "d2h_bytes_per_step": int(n * r * 8), "solves_per_s": e2e_steps / te2e}
 
 
+class BatchInputs:
+    """Device-resident inputs of uneven subproblems and their kernels (eig(K)
+    is the one-time per-kernel setup: computed here, outside any timing)."""
+
+    def __init__(self, pkg, ctx, dev, specs):
+        import torch
+        import synth
+        self.specs = specs
+        self.kerns = {}
+        self.items = []
+        for sp in specs:
+            p = synth.batch_problem(sp)
+            key = (p.n, sp["kernel"])
+            if key not in self.kerns:
+                dK, UK = np.linalg.eigh(p.K)
+                self.kerns[key] = ctx.kernel_create(p.n, UK, dK)
+            self.items.append(self.upload(p, self.kerns[key], dev))
+
+    @staticmethod
+    def upload(p, kern, dev):
+        import torch
+        return dict(
+            p=p, kern=kern, q=p.q, n=p.n, r=p.r,
+            f=[torch.from_numpy(np.asfortranarray(F).ravel(order="F")).to(dev) for F in p.factors],
+            k=torch.from_numpy(p.kidx).to(dev),
+            o=torch.from_numpy(np.ascontiguousarray(p.oidx).ravel()).to(dev),
+            v=torch.from_numpy(p.vals).to(dev),
+            W=torch.empty(p.n * p.r, dtype=torch.float64, device=dev))
+
+    def close(self):
+        for k in self.kerns.values():
+            k.close()
+
+
+def submit_item(pkg, ctx, it, precision):
+    p = it["p"]
+    return pkg.submit(ctx, it["kern"], it["f"], it["k"], it["o"], it["v"], p.r, p.lam, p.rho, TOL,
+                      max_iter=1000, precision=precision, sorted_obs=True, out=it["W"])
+
+
+def run_batch(args, pkg, ctx, dev, seed):
+    """All subproblems submitted at once; every request's PCG runs on its own
+    stream (CUDA-graph chunks) as slots and HBM free up.  Timed on the host
+    clock from the first submit to the last completion, with the device idle
+    on both sides."""
+    import torch
+    import synth
+    B = BatchInputs(pkg, ctx, dev, synth.batch_specs(seed, args.batch))
+    items = B.items
+    for it in items[:16]:  # warm-up: module loads, pools, pinned slots
+        submit_item(pkg, ctx, it, args.precision).wait()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reqs = [submit_item(pkg, ctx, it, args.precision) for it in items]
+    done_t = {}
+    by_ticket = {r_.ticket: r_ for r_ in reqs}
+    while len(done_t) < len(reqs):
+        _, _, done = ctx.poll(done_cap=64)
+        now = time.perf_counter()
+        for t in done:
+            done_t[t] = now
+    res = [r_.wait() for r_ in reqs]
+    torch.cuda.synchronize()
+    elapsed = time.perf_counter() - t0
+    stats = [st for _, st in res]
+    ok = sum(1 for st in stats if st["status"] == 0)
+    obs_iter = sum(it["q"] * st["iterations"] for it, st in zip(items, stats))
+    lat = sorted(1e3 * (done_t[r_.ticket] - t0) for r_ in reqs)
+    pct = lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))]
+    launches = sum(st["kernel_launches"] + st["setup_launches"] for st in stats)
+    # The plain FP64 GPU path, one subproblem at a time, same inputs and tolerance.
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    it64 = 0
+    for it in items:
+        p = it["p"]
+        _, st = pkg.solve(ctx, it["kern"], it["f"], it["k"], it["o"], it["v"], p.r, p.lam, p.rho,
+                          TOL, max_iter=1000, precision="fp64", sorted_obs=True, out=it["W"])
+        it64 += st["iterations"]
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t1
+    out = {"workload": f"c4_batch_{len(items)}_uneven", "precision": args.precision, "tol": TOL,
+           "requests": len(items), "sum_q": int(sum(it["q"] for it in items)),
+           "n_grid": list(synth.BATCH_N_GRID), "kernels": len(B.kerns),
+           "elapsed_ms": 1e3 * elapsed, "solves_per_s": len(items) / elapsed,
+           "obs_iter_per_s": obs_iter / elapsed, "converged": ok,
+           "max_rel_residual": max(st["rel_residual"] for st in stats),
+           "completion_ms": {"p50": pct(0.5), "p99": pct(0.99), "max": lat[-1]},
+           "fp64_one_at_a_time": {"solves_per_s": len(items) / t64, "elapsed_ms": 1e3 * t64,
+                                  "iterations": it64},
+           "speedup_vs_fp64_one_at_a_time": t64 / elapsed,
+           "gpu_launches": int(launches), "slots": args.slots}
+    B.close()
+    return out
+
+
+def run_serve(args, pkg, ctx, dev, seed, big_kern, big_p):
+    """Poisson arrivals of subproblems sized as the batch (plus 5% large ones,
+    n = 8000, q = 2e7, r = 40); each is submitted at its arrival time and its
+    latency runs from the arrival to the poll that sees it complete."""
+    import torch
+    import synth
+    rates = [float(x) for x in args.serve_rates.split(",") if x]
+    pool = BatchInputs(pkg, ctx, dev, synth.batch_specs(seed + 7, 64))
+    big = BatchInputs.upload(big_p, big_kern, dev) if big_p is not None else None
+    rng = np.random.default_rng(seed)
+    out = []
+    for it in pool.items[:8]:
+        submit_item(pkg, ctx, it, args.precision).wait()
+    for rate in rates:
+        nreq = int(min(args.serve_requests, max(20, 2.0 * rate)))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
+        which = [big if (big is not None and rng.uniform() < 0.05) else
+                 pool.items[int(rng.integers(len(pool.items)))] for _ in range(nreq)]
+        # distinct output buffers: requests in flight may share an instance
+        outs = [torch.empty_like(it["W"]) for it in which]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k = 0
+        tick = {}
+        done_t = {}
+        while len(done_t) < nreq:
+            now = time.perf_counter() - t0
+            while k < nreq and arrivals[k] <= now:
+                it = dict(which[k])
+                it["W"] = outs[k]
+                rq = submit_item(pkg, ctx, it, args.precision)
+                tick[rq.ticket] = (k, rq)
+                k += 1
+            _, _, done = ctx.poll(done_cap=256)
+            now = time.perf_counter() - t0
+            for t in done:
+                done_t[tick[t][0]] = now
+        sts = [rq.wait()[1] for _, rq in tick.values()]
+        lat = sorted(1e3 * (done_t[i] - arrivals[i]) for i in range(nreq))
+        pct = lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))]
+        span = max(done_t.values()) - arrivals[0]
+        out.append({"rate_req_s": rate, "requests": nreq,
+                    "large": int(sum(1 for it in which if it is big)),
+                    "solves_per_s": nreq / span, "p50_ms": pct(0.5), "p99_ms": pct(0.99),
+                    "max_ms": lat[-1],
+                    "converged": sum(1 for st in sts if st["status"] == 0)})
+    pool.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -239,6 +392,7 @@ def main():
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream)
     kern = ctx.kernel_create(n, UK, dK)
+    ctx.set_slots(args.slots)
 
     def step(precision, profile=False, device=True):
         lowp = precision != "fp64"
@@ -334,6 +488,19 @@ def main():
     if not args.no_e2e:
         e2e = run_e2e(args, pkg, ctx, kern, p)
 
+    # ---- batched uneven subproblems, then a served Poisson stream
+    batched = None
+    if args.batch > 0:
+        batched = run_batch(args, pkg, ctx, dev, seed=1000 + rank)
+    serving = None
+    if args.serve_rates:
+        import synth
+        big_p = None
+        if n == 8000 and p.r == 40:
+            big_p = synth.planted_problem(2000 + rank, 8000, (400, 500), 20_000_000, 40,
+                                          bandwidth=0.1)
+        serving = run_serve(args, pkg, ctx, dev, 3000 + rank, kern if big_p else None, big_p)
+
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -378,6 +545,7 @@ def main():
             "fp64_path": fp64,
             "precision_sweep": sweep,
             "mixed_vs_fp64_solves": (solves_per_s / fp64["solves_per_s"]) if fp64 else None,
+            "batched": batched, "serving": serving,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary(),
             "gpu_launches": int(launches),
         }

@@ -63,7 +63,11 @@ enum { CPHIFI_MEM_HOST = 0, CPHIFI_MEM_DEVICE = 1 };
  *  FP64          : every step in FP64 (FP64 FMA units).
  *  MIXED_FP32    : operator in FP32 (FP32 products, FP32 gather-dot/scatter);
  *                  every k_replace iterations an FP64-accurate true residual
- *                  restarts PCG, and only it decides convergence.
+ *                  is formed, and only it decides convergence.  PCG restarts
+ *                  from it (p = M^{-1} r) when the recurrence residual has met
+ *                  the tolerance or fallen below half the true residual (the
+ *                  low-precision operator's error then dominates), and
+ *                  otherwise runs on with its Krylov space intact.
  *  MIXED_TF32    : as MIXED_FP32 with the two n x n products on the tensor
  *                  cores in TF32 (FP32 accumulate).
  *  MIXED_BF16    : as MIXED_TF32 with BF16 operands.
@@ -98,7 +102,7 @@ typedef struct cphifi_params {
   double tol;         /* stop when ||b - A w|| / ||b|| <= tol                 */
   int32_t max_iter;   /* bound on PCG iterations over all restarts            */
   int32_t precision;  /* cphifi_precision                                      */
-  int32_t k_replace;  /* mixed: FP64 true residual + restart every k (>= 1)   */
+  int32_t k_replace;  /* mixed: FP64 true-residual check every k (>= 1)      */
   int32_t check_every;/* FP64: iterations between host convergence polls (>=1)*/
   int32_t profile;    /* 1: time every n x n product and gather-dot/scatter  */
   int32_t reserved;
@@ -129,6 +133,7 @@ typedef struct cphifi_stats {
                                 updates, preconditioner, FP64 true residuals
                                 and restarts), i.e. the iteration phase        */
   double final_ms;           /* CUDA-event time: W = U_K Wbar and its copy    */
+  double queue_ms;           /* submitted requests: wait for admission (host) */
 } cphifi_stats;
 
 typedef struct cphifi_ctx cphifi_ctx;
@@ -212,6 +217,53 @@ int cphifi_solve(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
                  const int32_t* oidx, const double* vals, uint32_t flags,
                  const cphifi_params* params, const double* W0, double* W_out,
                  int mem, cphifi_stats* stats);
+
+/* ---- batches of independent solves: submit / poll / wait ------------------
+ * Each kernel-mode subproblem of §4.4 (one tensor, one kernel mode, one ALS
+ * sweep) is an independent PCG solve; many of them can share the GPU.  A
+ * submitted request holds the arguments of cphifi_solve.  It is admitted --
+ * its problem created on a stream of its own, its PCG started -- as soon as
+ * fewer than `max_active` requests run and its device footprint fits the
+ * context's HBM budget next to the running ones; requests are admitted in
+ * submission order.  Admitted requests advance concurrently on their own
+ * streams: each PCG chunk (k_replace iterations and the true-residual check
+ * of §4.4 mixed mode) is replayed from a CUDA graph captured on first use,
+ * and the host only looks at a request between chunks.
+ *
+ * cphifi_submit   queues a request and returns its ticket at once.  The
+ *                 caller keeps every buffer it names (factors, observation
+ *                 lists, W0, W_out) alive and unchanged until cphifi_wait
+ *                 returns for that ticket.  Device-memory inputs are read
+ *                 in order after the work the caller queued on the stream set
+ *                 by cphifi_ctx_set_stream before the submit.  A request whose
+ *                 footprint exceeds the budget even alone completes with
+ *                 CPHIFI_E_ADMISSION.  Argument errors return at once.
+ * cphifi_poll     advances every request without blocking.  Optional
+ *                 outputs: the numbers running and queued, and up to
+ *                 `done_cap` tickets (oldest first) that completed since they
+ *                 were last listed and have not been waited for; cphifi_wait
+ *                 on them returns at once.
+ * cphifi_wait     advances all requests until the ticket completes, or until
+ *                 `timeout_us` microseconds pass (negative: no limit), which
+ *                 returns CPHIFI_E_TIMEOUT and leaves the request running.
+ *                 On completion it writes W_out (already written when it
+ *                 returns), fills `stats` (queue_ms: the wait for admission;
+ *                 setup_ms: the host time of the problem's creation) and
+ *                 returns the solve's status; the ticket is then released.
+ * cphifi_ctx_set_slots sets max_active (1..1024, default 16).
+ * Destroying the context releases requests that were never waited for. */
+typedef uint64_t cphifi_ticket;
+int cphifi_ctx_set_slots(cphifi_ctx* ctx, int max_active);
+int cphifi_submit(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
+                  const int64_t* other_sizes, const double* const* factors,
+                  int32_t r, int64_t q, const int32_t* kidx,
+                  const int32_t* oidx, const double* vals, uint32_t flags,
+                  const cphifi_params* params, const double* W0, double* W_out,
+                  int mem, cphifi_ticket* ticket);
+int cphifi_poll(cphifi_ctx* ctx, int32_t* n_active, int32_t* n_pending,
+                cphifi_ticket* done, int32_t done_cap, int32_t* n_done);
+int cphifi_wait(cphifi_ctx* ctx, cphifi_ticket ticket, int64_t timeout_us,
+                cphifi_stats* stats);
 
 /* ---- the steps of the path, one call each (for checking each step) ------
  * All n x r arrays are column-major in memory kind `mem`. */

@@ -67,7 +67,7 @@ class Stats(ctypes.Structure):
                 ("gemm64_launches", ctypes.c_int32), ("gemm64_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("setup_launches", ctypes.c_int64),
                 ("rhs_ms", ctypes.c_double), ("iter_ms", ctypes.c_double),
-                ("final_ms", ctypes.c_double)]
+                ("final_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -111,6 +111,16 @@ _SIG = {
                                               ctypes.c_int]),
     "cphifi_problem_gram": (ctypes.c_int, [_P, _P, _P, _P]),
     "cphifi_problem_order": (ctypes.c_int, [_P, _P, _P]),
+    "cphifi_ctx_set_slots": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cphifi_submit": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32,
+                                     ctypes.c_int64, _P, _P, _P, ctypes.c_uint32,
+                                     ctypes.POINTER(Params), _P, _P, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_uint64)]),
+    "cphifi_poll": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32,
+                                   ctypes.POINTER(ctypes.c_int32)]),
+    "cphifi_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(Stats)]),
     "cphifi_gds_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P,
                                           ctypes.c_int64, _P, _P, _P,
                                           ctypes.POINTER(ctypes.c_char_p)]),
@@ -209,6 +219,21 @@ class Context:
             self.h = None
 
     __del__ = close
+
+    def set_slots(self, max_active: int) -> None:
+        """cphifi_ctx_set_slots: how many submitted requests run at once."""
+        _check(self.h, lib().cphifi_ctx_set_slots(self.h, int(max_active)), "ctx_set_slots")
+
+    def poll(self, done_cap: int = 0):
+        """cphifi_poll: advance all submitted requests.  Returns (active,
+        pending), or (active, pending, completed tickets) when done_cap > 0."""
+        a, p, nd = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        buf = (ctypes.c_uint64 * max(done_cap, 1))()
+        _check(self.h, lib().cphifi_poll(self.h, ctypes.byref(a), ctypes.byref(p), buf,
+                                         int(done_cap), ctypes.byref(nd)), "poll")
+        if done_cap > 0:
+            return a.value, p.value, list(buf[:nd.value])
+        return a.value, p.value
 
     def kernel_create(self, n: int, UK, DK, K=None) -> "Kernel":
         return Kernel(self, n, UK, DK, K)
@@ -405,6 +430,56 @@ def solve(ctx: Context, kernel: Kernel, factors, kidx, oidx, vals, r: int, lam: 
     if rc not in (OK, E_NOT_CONVERGED):
         _check(ctx.h, rc, "solve")
     return wb.obj, st.as_dict()
+
+
+class Request:
+    """A submitted solve (cphifi_submit); keeps its buffers alive until wait()."""
+
+    def __init__(self, ctx, ticket, bufs, out):
+        self.ctx, self.ticket, self._bufs, self.out = ctx, ticket, bufs, out
+        self.result = None
+
+    def wait(self, timeout_us: int = -1):
+        """cphifi_wait: returns (W, stats); raises CphifiError(E_TIMEOUT) if
+        the request is still running after `timeout_us` (it keeps running)."""
+        if self.result is not None:
+            return self.result
+        st = Stats()
+        rc = lib().cphifi_wait(self.ctx.h, ctypes.c_uint64(self.ticket), int(timeout_us),
+                               ctypes.byref(st))
+        if rc == E_TIMEOUT:
+            _check(self.ctx.h, rc, "wait")
+        self._bufs = None
+        self.result = (self.out, st.as_dict())
+        if rc not in (OK, E_NOT_CONVERGED):
+            _check(self.ctx.h, rc, "request")
+        return self.result
+
+
+def submit(ctx: Context, kernel: Kernel, factors, kidx, oidx, vals, r: int, lam: float,
+           rho: float, tol: float, max_iter: int = 1000, precision="fp64", sorted_obs=False,
+           k_replace=10, check_every=8, W0=None, out=None) -> Request:
+    """cphifi_submit: queue one solve; returns a Request whose wait() gives (W, stats)."""
+    fb, sizes = _factor_bufs(factors, r)
+    k, o, v = _obs_bufs(kidx, oidx, vals)
+    prm = make_params(lam, rho, tol, max_iter, precision, k_replace, check_every, False)
+    n = kernel.n
+    if out is None:
+        out = np.empty((n, r), order="F") if k.mem == MEM_HOST else None
+        if out is None:
+            import torch
+            out = torch.empty(n * r, dtype=torch.float64, device="cuda")
+    wb = _Buf(out, np.float64, colmajor=not _is_torch(out))
+    w0 = _Buf(W0, np.float64, colmajor=True) if W0 is not None else None
+    sizes_arr = (ctypes.c_int64 * len(sizes))(*sizes)
+    fptrs = (ctypes.c_void_p * len(fb))(*[b.ptr for b in fb])
+    flags = OBS_SORTED if sorted_obs else 0
+    t = ctypes.c_uint64()
+    rc = lib().cphifi_submit(ctx.h, kernel.h, len(fb), sizes_arr, fptrs, int(r), k.numel, k.ptr,
+                             o.ptr, v.ptr, flags, ctypes.byref(prm), w0.ptr if w0 else None,
+                             wb.ptr, k.mem, ctypes.byref(t))
+    _check(ctx.h, rc, "submit")
+    return Request(ctx, t.value, (fb, k, o, v, wb, w0, sizes_arr, fptrs, prm), wb.obj)
 
 
 def gds_noalloc(n: int, r: int, q: int, row_ptr, zhat, ldz: int, Xhat, Y1, stream=None):

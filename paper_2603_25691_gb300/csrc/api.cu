@@ -19,7 +19,10 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <deque>
 #include <map>
+#include <memory>
+#include <thread>
 #include <string>
 #include <utility>
 #include <vector>
@@ -28,6 +31,9 @@
 #include "launch.h"
 
 using namespace cphifi;
+
+struct Request;
+static void requests_clear(cphifi_ctx* ctx);
 
 struct cphifi_ctx {
   int device = 0;
@@ -40,17 +46,32 @@ struct cphifi_ctx {
   std::string last_error;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   DevScalars* h_scalars = nullptr;  // pinned
-  std::vector<cudaEvent_t> ev_pool;
   // Device blocks released by destroyed problems, by size: a new problem of a
   // similar shape reuses them instead of paying cudaMalloc/cudaFree (and the
   // device synchronisation cudaFree implies) on every solve.
   std::multimap<size_t, void*> pool;
   size_t pool_bytes = 0;
+  // Pinned host slots (one per problem: its scalars and the tensor-core error
+  // word) carved from page-locked slabs, and a free list of CUDA events, so
+  // that creating a problem pins no memory and creates no event.
+  std::vector<void*> pinned_slabs;
+  std::vector<char*> pinned_free;
+  std::vector<cudaEvent_t> events_free;
   cudaEvent_t phase[4] = {nullptr, nullptr, nullptr, nullptr};  // solve phase marks
   // Side stream for small serial work (Gram, eig(V)) that overlaps the
   // bandwidth-bound Zhat pass on the main stream.
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // Submitted requests (cphifi_submit): admitted FIFO while a slot (stream)
+  // and the HBM budget allow, advanced by cphifi_poll / cphifi_wait.
+  uint64_t next_ticket = 1;
+  int max_active = 16;
+  std::vector<cudaStream_t> slot_stream;
+  std::vector<bool> slot_busy;
+  std::deque<Request*> pending;
+  std::vector<Request*> active;
+  std::map<uint64_t, Request*> requests;
+  std::vector<uint64_t> done_unreported;  // completed, not yet listed by poll
 };
 
 struct cphifi_kernel {
@@ -108,6 +129,7 @@ struct cphifi_problem {
   double *x = nullptr, *res = nullptr, *z = nullptr, *p = nullptr, *y = nullptr,
          *bbar = nullptr, *xh64 = nullptr, *y164 = nullptr, *tmp64 = nullptr,
          *tmp64b = nullptr, *D64 = nullptr;
+  double* tres = nullptr;  // true residual of the mixed modes' periodic check
   float *pop32 = nullptr, *xh32 = nullptr, *y132 = nullptr, *D32 = nullptr;
   float *Bhi = nullptr, *Blo = nullptr;  // double-float product operand
   // Low-precision product operands pop (D_K P̄) and y1 (Ŷ1) use leading
@@ -119,6 +141,12 @@ struct cphifi_problem {
   CUtensorMap mBpf, mBpb, mByf, mByb, mBph, mBpl, mByh, mByl;
   int nsplittc = 1;
   int* tc_err = nullptr;
+  // Stream, pinned scalar copy and phase events of this problem's solves (the
+  // context's stream for the synchronous calls, a pool stream for submitted
+  // requests).
+  cudaStream_t st = nullptr;
+  DevScalars* hs = nullptr;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   void* cpart = nullptr;  // max(nsplit64, nsplit32, nsplitdf) x n x r doubles
   int nsplit64 = 1, nsplit32 = 1, nsplitdf = 1;  // splits of the k range per product kind
   RedScratch red{};
@@ -226,7 +254,38 @@ cudaError_t dalloc(cphifi_problem* P, T** out, size_t count) {
   return cudaSuccess;
 }
 
+constexpr size_t kPinnedSlot = 256;
+constexpr int kPinnedPerSlab = 64;
+static_assert(sizeof(DevScalars) + 16 <= kPinnedSlot, "pinned slot too small");
+
+cudaError_t pinned_get(cphifi_ctx* ctx, void** out) {
+  if (ctx->pinned_free.empty()) {
+    void* slab = nullptr;
+    cudaError_t e = cudaMallocHost(&slab, kPinnedSlot * kPinnedPerSlab);
+    if (e != cudaSuccess) return e;
+    ctx->pinned_slabs.push_back(slab);
+    for (int k = kPinnedPerSlab - 1; k >= 0; --k)
+      ctx->pinned_free.push_back((char*)slab + k * kPinnedSlot);
+  }
+  *out = ctx->pinned_free.back();
+  ctx->pinned_free.pop_back();
+  return cudaSuccess;
+}
+
+cudaError_t event_get(cphifi_ctx* ctx, cudaEvent_t* out) {
+  if (!ctx->events_free.empty()) {
+    *out = ctx->events_free.back();
+    ctx->events_free.pop_back();
+    return cudaSuccess;
+  }
+  return cudaEventCreate(out);
+}
+
 void free_problem(cphifi_problem* P) {
+  if (P->hs) P->ctx->pinned_free.push_back((char*)P->hs);
+  P->hs = nullptr;
+  for (auto& e : P->ev)
+    if (e) { P->ctx->events_free.push_back(e); e = nullptr; }
   for (auto& a : P->allocs) pool_release(P->ctx, a.first, a.second);
   P->ctx->in_use -= std::min(P->ctx->in_use, P->bytes);
   P->allocs.clear();
@@ -270,29 +329,32 @@ cudaError_t download(void* dst, const void* src, size_t bytes, int mem, cudaStre
 
 // Launch timing: pairs of events around selected launches.
 struct Timer {
-  cphifi_ctx* ctx;
+  cudaStream_t st;
   bool on;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gds, gemm, gds64, gemm64;
-  size_t used = 0;
-  Timer(cphifi_ctx* c, bool enabled) : ctx(c), on(enabled) {}
+  std::vector<cudaEvent_t> pool;
+  Timer(cudaStream_t s, bool enabled) : st(s), on(enabled) {}
+  ~Timer() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+  Timer(const Timer&) = delete;
+  Timer& operator=(const Timer&) = delete;
   cudaEvent_t ev() {
-    if (used == ctx->ev_pool.size()) {
-      cudaEvent_t e;
-      cudaEventCreate(&e);
-      ctx->ev_pool.push_back(e);
-    }
-    return ctx->ev_pool[used++];
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    pool.push_back(e);
+    return e;
   }
   cudaEvent_t begin() {
     if (!on) return nullptr;
     cudaEvent_t e = ev();
-    cudaEventRecord(e, ctx->stream);
+    cudaEventRecord(e, st);
     return e;
   }
   void end(cudaEvent_t b, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v) {
     if (!on) return;
     cudaEvent_t e = ev();
-    cudaEventRecord(e, ctx->stream);
+    cudaEventRecord(e, st);
     v.push_back({b, e});
   }
   static double total(const std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v) {
@@ -360,8 +422,8 @@ extern "C" int cphifi_ctx_destroy(cphifi_ctx* ctx) {
   cudaGetDevice(&prev);
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  requests_clear(ctx);
   pool_trim(ctx);
-  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   for (auto e : ctx->phase)
     if (e) cudaEventDestroy(e);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
@@ -373,6 +435,8 @@ extern "C" int cphifi_ctx_destroy(cphifi_ctx* ctx) {
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
   if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
+  for (auto e : ctx->events_free) cudaEventDestroy(e);
+  for (auto p : ctx->pinned_slabs) cudaFreeHost(p);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   cudaSetDevice(prev);
   delete ctx;
@@ -521,17 +585,37 @@ static size_t problem_footprint(int64_t n, int64_t q, int r, int d_other,
   b += (n + 1) * sizeof(int64_t) + 4 * n * sizeof(int32_t) + (n + 1) * sizeof(int32_t);
   b += (size_t)npieces_max * (3 * sizeof(int32_t) + 64 * sizeof(double));
   for (int m = 0; m < d_other; ++m) b += (size_t)sizes[m] * r * sizeof(double);
-  b += 12 * nr * sizeof(double) + 4 * nr * sizeof(float);
+  b += 13 * nr * sizeof(double) + 4 * nr * sizeof(float);
   b += (size_t)nsplit * nr * sizeof(double);
   b += (size_t)kRedMaxBlocks * kRedSlots * sizeof(double);
   return b;
 }
 
-extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
-                                     const int64_t* other_sizes, const double* const* factors,
-                                     int32_t r, int64_t q, const int32_t* kidx,
-                                     const int32_t* oidx, const double* vals, uint32_t flags,
-                                     int mem, cphifi_problem** out) {
+// Device bytes a problem holds (`need`) and the temporaries of its creation
+// (`tmp`), for admission against the context's HBM budget.
+static void problem_need(const cphifi_ctx* ctx, int n, bool tc, int32_t d_other,
+                         const std::vector<int64_t>& sizes, int32_t r, int64_t q, uint32_t flags,
+                         size_t* need, size_t* tmp) {
+  const int64_t W = std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 16, (q + 63) / 64));
+  const int64_t npieces_max = (int64_t)n + W + 1;
+  const int nsplit = std::max(
+      std::max(gemm_pick_split<double, double>(n, ctx->num_sms), gemm_pick_split<float, float>(n, ctx->num_sms)),
+      std::max(gemm_df_pick_split(n, ctx->num_sms), tc ? tc_pick_split(n, ctx->num_sms) : 1));
+  const bool need64 = (flags & CPHIFI_NEED_FP64) || !(flags & CPHIFI_NEED_LOWP);
+  const bool lowp = (flags & CPHIFI_NEED_LOWP) || !(flags & CPHIFI_NEED_FP64);
+  *need = problem_footprint(n, q, r, d_other, sizes, lowp, nsplit, npieces_max) +
+          (need64 ? (size_t)zhat_elems(q, r) * sizeof(double) : 0);
+  *tmp = (size_t)q * (sizeof(int32_t) * (1 + d_other) + sizeof(double) * 2 + sizeof(uint32_t)) +
+         radix_sort_tmp_bytes(q);
+}
+
+// Problem creation on stream `st` (the context's stream for the public call, a
+// pool stream for submitted requests).
+static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
+                             const int64_t* other_sizes, const double* const* factors, int32_t r,
+                             int64_t q, const int32_t* kidx, const int32_t* oidx,
+                             const double* vals, uint32_t flags, int mem, cudaStream_t st,
+                             cphifi_problem** out) {
   if (!ctx || !out) return CPHIFI_E_INVALID_ARG;
   *out = nullptr;
   if (!kern || kern->ctx != ctx) return fail(ctx, CPHIFI_E_INVALID_ARG, "kernel of another context");
@@ -566,10 +650,8 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   // mixed modes; neither flag set means both.
   const bool need64 = (flags & CPHIFI_NEED_FP64) || !(flags & CPHIFI_NEED_LOWP);
   const bool lowp = (flags & CPHIFI_NEED_LOWP) || !(flags & CPHIFI_NEED_FP64);
-  const size_t need = problem_footprint(n, q, r, d_other, sizes, lowp, nsplit, npieces_max) +
-                      (need64 ? (size_t)zhat_elems(q, r) * sizeof(double) : 0);
-  const size_t tmp_need = (size_t)q * (sizeof(int32_t) * (1 + d_other) + sizeof(double) * 2 +
-                                       sizeof(uint32_t)) + radix_sort_tmp_bytes(q);
+  size_t need = 0, tmp_need = 0;
+  problem_need(ctx, n, kern->tc, d_other, sizes, r, q, flags, &need, &tmp_need);
   if (ctx->budget && ctx->in_use + need + tmp_need > ctx->budget)
     return fail(ctx, CPHIFI_E_ADMISSION, "problem footprint exceeds the HBM budget");
   auto t0 = std::chrono::steady_clock::now();
@@ -582,6 +664,7 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   P->q = q;
   P->sizes = sizes;
   P->gamma = (double)q / ((double)n * M);
+  P->st = st;
   P->nsplit64 = nsplit64;
   P->nsplit32 = nsplit32;
   P->nsplitdf = nsplitdf;
@@ -589,7 +672,6 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   P->ldt = kern->tc ? kern->ldt : n;
   P->nwarps = W;
   P->obs_per_warp = L;
-  cudaStream_t st = ctx->stream;
   std::vector<std::pair<void*, size_t>> temps;
   auto tmp_alloc = [&](size_t bytes) -> void* {
     void* p = nullptr;
@@ -648,7 +730,7 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   PCK(dalloc(P, &P->err, 4));
   PCK(dalloc(P, &P->Bm, nr));
   for (double** v : {&P->x, &P->res, &P->z, &P->p, &P->y, &P->bbar, &P->xh64, &P->y164,
-                     &P->tmp64, &P->tmp64b, &P->D64})
+                     &P->tmp64, &P->tmp64b, &P->D64, &P->tres})
     PCK(dalloc(P, v, nr));
   for (float** v : {&P->xh32, &P->D32, &P->Bhi, &P->Blo}) PCK(dalloc(P, v, nr));
   PCK(dalloc(P, &P->pop32, (size_t)P->ldt * r));
@@ -680,6 +762,13 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
   PCK(dalloc(P, &P->s, 1));
   PCK(dalloc(P, &P->s2, 1));
   PCK(cudaMemsetAsync(P->red.ticket, 0, 4 * sizeof(unsigned), st));
+  // pinned: the scalars, then the tensor-core error word
+  {
+    void* h = nullptr;
+    PCK(pinned_get(ctx, &h));
+    P->hs = (DevScalars*)h;
+  }
+  for (auto& e : P->ev) PCK(event_get(ctx, &e));
   PCK(cudaMemsetAsync(P->seg_ticket, 0, n * sizeof(unsigned), st));
   PCK(cudaMemsetAsync(P->err, 0, sizeof(int), st));
   PCK(cudaMemsetAsync(P->info, 0, sizeof(int), st));
@@ -783,13 +872,23 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
 #undef PCK
 }
 
+extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
+                                     const int64_t* other_sizes, const double* const* factors,
+                                     int32_t r, int64_t q, const int32_t* kidx,
+                                     const int32_t* oidx, const double* vals, uint32_t flags,
+                                     int mem, cphifi_problem** out) {
+  if (!ctx) return CPHIFI_E_INVALID_ARG;
+  return problem_create_on(ctx, kern, d_other, other_sizes, factors, r, q, kidx, oidx, vals,
+                           flags, mem, ctx->stream, out);
+}
+
 extern "C" int cphifi_problem_destroy(cphifi_problem* P) {
   if (!P) return CPHIFI_E_INVALID_ARG;
   cphifi_ctx* ctx = P->ctx;
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(ctx->device);
-  cudaStreamSynchronize(ctx->stream);
+  cudaStreamSynchronize(P->st);
   free_problem(P);
   cudaSetDevice(prev);
   delete P;
@@ -1047,6 +1146,18 @@ struct Launcher {
       return e;
     return restart(prec);
   }
+  // Mixed modes: FP64-accurate true residual into tres (convergence decided
+  // on it); the recurrence is left as it is.
+  cudaError_t true_residual_check(int prec) {
+    return opwide(true, CM_TRUE, P->x, P->tres, P->s, nullptr, 2);
+  }
+  // The checked true residual replaces the recurrence residual; restart.
+  cudaError_t adopt_restart(int prec) {
+    ++launches;
+    cudaError_t e = launch_adopt_residual(P->tres, P->res, (int64_t)P->n * P->r, P->s, st);
+    if (e != cudaSuccess) return e;
+    return restart(prec);
+  }
   cudaError_t restart(int prec) {
     DevScalars* s = P->s;
     cudaError_t e;
@@ -1090,7 +1201,7 @@ int ensure_lowp(cphifi_problem* P) {
     return fail(ctx, CPHIFI_E_ADMISSION, "hi/lo operator data exceeds the HBM budget");
   CK(dalloc(P, &P->zhi, elems));
   CK(dalloc(P, &P->zlo, elems));
-  CK(launch_split_df(P->z64, nullptr, (int64_t)elems, (int64_t)elems, P->zhi, P->zlo, ctx->stream));
+  CK(launch_split_df(P->z64, nullptr, (int64_t)elems, (int64_t)elems, P->zhi, P->zlo, P->st));
   return CPHIFI_OK;
 }
 
@@ -1101,125 +1212,257 @@ int ensure_fp64(cphifi_problem* P) {
   if (ctx->budget && ctx->in_use + elems * sizeof(double) > ctx->budget)
     return fail(ctx, CPHIFI_E_ADMISSION, "FP64 operator data exceeds the HBM budget");
   CK(dalloc(P, &P->z64, elems));
-  CK(launch_join_df(P->zhi, P->zlo, (int64_t)elems, P->z64, ctx->stream));
+  CK(launch_join_df(P->zhi, P->zlo, (int64_t)elems, P->z64, P->st));
   return CPHIFI_OK;
 }
 
 }  // namespace
 
-extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm, const double* W0,
-                                    double* W_out, int mem, cphifi_stats* stats) {
-  if (!P) return CPHIFI_E_INVALID_ARG;
-  cphifi_ctx* ctx = P->ctx;
-  int rc = check_params(ctx, prm);
-  if (rc != CPHIFI_OK) return rc;
-  if (!W_out) return fail(ctx, CPHIFI_E_INVALID_ARG, "null W_out");
-  if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
-    return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
-  Enter guard(ctx);
-  // mixed: FP32 operator inside PCG, stop only on the FP64-accurate true
-  // residual (restart every k_replace); emul: the FP64-accurate steps run in
-  // double-float arithmetic (every mode but FP64).
-  const int prec = prm->precision;
-  const bool mixed = is_lowp(prec);
-  const bool emul = prec != CPHIFI_FP64;
-  if (is_tc(prec) && !P->kern->tc)
-    return fail(ctx, CPHIFI_E_UNSUPPORTED, "tensor-core products unavailable for this kernel");
-  if ((rc = emul ? ensure_lowp(P) : ensure_fp64(P)) != CPHIFI_OK) return rc;
-  auto t0 = std::chrono::steady_clock::now();
-  cudaStream_t st = ctx->stream;
-  const int n = P->n, r = P->r;
-  const size_t nr = (size_t)n * r;
-  Timer tm(ctx, prm->profile != 0);
-  Launcher L{P, st, &tm};
-
-  DevScalars h{};
-  h.tol2 = prm->tol * prm->tol;
-  h.lam = prm->lambda;
-  h.rho = prm->rho;
-  h.max_iter = prm->max_iter;
-  h.mode = mixed ? 1 : 0;
-  CK(cudaEventRecord(ctx->phase[0], st));
-  CK(cudaMemcpyAsync(P->s, &h, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
-  CK(launch_build_D(P->kern->dK, P->dV, n, r, P->gamma, prm->lambda, prm->rho, P->D64, P->D32, st));
-  // right-hand side in the eigenbasis: bbar = D_K U_K' B, and ||bbar||^2
-  CK(L.utb(emul, CM_DK_NORM, P->Bm, P->bbar, P->s));
-  // start: x = U_K' W0 (or 0) and its true residual
-  if (W0) {
-    CK(upload(P->tmp64, W0, nr * sizeof(double), mem, st));
-    CK(L.utb(emul, CM_STORE, P->tmp64, P->x, P->s));
-    CK(L.opwide(emul, CM_RESID, P->x, P->res, P->s, nullptr, 0));
-  } else {
-    CK(cudaMemsetAsync(P->x, 0, nr * sizeof(double), st));
-    CK(cudaMemcpyAsync(P->res, P->bbar, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  }
-  if (P->tc_err) CK(cudaMemsetAsync(P->tc_err, 0, sizeof(int), st));
-  CK(L.restart(prec));
-  CK(cudaEventRecord(ctx->phase[1], st));
-  DevScalars* hs = ctx->h_scalars;
-  CK(cudaMemcpyAsync(hs, P->s, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-
-  int status = CPHIFI_OK;
+// One PCG solve as a resumable sequence of device work (§4.4): begin() queues
+// the right-hand side and the start; each advance() runs when the previous
+// step's work (and its copy of the device scalars) has finished, decides from
+// the scalars, and queues the next step.  The synchronous solve loops over it;
+// submitted requests interleave the steps of many solves on their own
+// streams.  Between steps the host reads a few scalars; nothing else.
+struct SolveRun {
+  enum Stage { INIT, CHUNK, CONFIRM, LASTRES, FINAL, DONE };
+  cphifi_problem* P;
+  cphifi_params prm;
+  const double* W0;
+  double* W_out;
+  int mem;
+  int prec;
+  bool mixed, emul;
+  cudaStream_t st;
+  Timer tm;
+  Launcher L;
+  Stage stage = INIT;
   bool converged = false;
-  if (hs->bb == 0.0) {
-    converged = true;  // b = 0: W = 0 solves the system exactly
-    CK(cudaMemsetAsync(P->x, 0, nr * sizeof(double), st));
-  } else if (W0 && hs->done) {
-    converged = true;  // the warm start already meets the tolerance
-  } else {
-    const int cycle = mixed ? std::max(1, prm->k_replace) : std::max(1, prm->check_every);
-    // Every pass either adds iterations or ends the loop; the bound is a
-    // second guarantee that the host loop terminates.
-    for (int64_t pass = 0; pass <= (int64_t)prm->max_iter + 2; ++pass) {
-      const int left = prm->max_iter - hs->iter;
-      if (left <= 0) break;
-      const int m = std::min(cycle, left);
-      for (int k = 0; k < m; ++k) CK(L.iteration(prec));
-      if (mixed) CK(L.true_residual_restart(prec));
-      CK(cudaMemcpyAsync(hs, P->s, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      if (hs->status) break;
-      if (mixed) {
-        if (hs->done) { converged = true; break; }
-        continue;
-      }
-      if (hs->done) {
-        // FP64-accurate operator: the recurrence met tol; confirm with the
-        // true residual and restart from it if it does not (refinement).
-        CK(L.true_residual_restart(prec));
-        CK(cudaMemcpyAsync(hs, P->s, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (hs->status) break;
-        if (hs->done) { converged = true; break; }
-      }
+  int status = CPHIFI_OK;
+  int64_t pass = 0;
+  int tcerr = 0;
+  std::chrono::steady_clock::time_point t0;
+  // CUDA graphs of the iteration chunk (launch-bound small problems):
+  // captured on first use per chunk length; profiling runs launch directly.
+  bool use_graphs;
+  std::vector<std::pair<int, cudaGraphExec_t>> graphs;
+  std::vector<int64_t> graph_launches;  // kernels captured in each graph
+
+  SolveRun(cphifi_problem* p, const cphifi_params& pr, const double* w0, double* wout, int m,
+           bool graphs_ok)
+      : P(p), prm(pr), W0(w0), W_out(wout), mem(m), prec(pr.precision),
+        mixed(is_lowp(pr.precision)), emul(pr.precision != CPHIFI_FP64), st(p->st),
+        tm(p->st, pr.profile != 0), L{p, p->st, &tm},
+        use_graphs(graphs_ok && pr.profile == 0) {}
+  ~SolveRun() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.second);
+  }
+  SolveRun(const SolveRun&) = delete;
+  SolveRun& operator=(const SolveRun&) = delete;
+
+  cphifi_ctx* ctx() const { return P->ctx; }
+  int* tc_word() const { return reinterpret_cast<int*>(P->hs + 1); }
+  int err(cudaError_t e, const char* what) {
+    ctx()->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    status = CPHIFI_E_DEVICE;
+    stage = DONE;
+    return CPHIFI_E_DEVICE;
+  }
+#define SR_CK(...)                                   \
+  do {                                               \
+    cudaError_t e_ = (__VA_ARGS__);                  \
+    if (e_ != cudaSuccess) return err(e_, #__VA_ARGS__); \
+  } while (0)
+
+  // Queue the copy of the device scalars and the event that marks the end of
+  // the queued step.
+  int mark() {
+    SR_CK(cudaMemcpyAsync(P->hs, P->s, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+    SR_CK(cudaEventRecord(P->ev[4], st));
+    return CPHIFI_OK;
+  }
+  bool ready() const { return stage == DONE || cudaEventQuery(P->ev[4]) != cudaErrorNotReady; }
+  int wait_ready() {
+    if (stage == DONE) return CPHIFI_OK;
+    SR_CK(cudaEventSynchronize(P->ev[4]));
+    return CPHIFI_OK;
+  }
+
+  int begin() {
+    t0 = std::chrono::steady_clock::now();
+    const int n = P->n, r = P->r;
+    const size_t nr = (size_t)n * r;
+    DevScalars h{};
+    h.tol2 = prm.tol * prm.tol;
+    h.lam = prm.lambda;
+    h.rho = prm.rho;
+    h.max_iter = prm.max_iter;
+    h.mode = mixed ? 1 : 0;
+    SR_CK(cudaEventRecord(P->ev[0], st));
+    SR_CK(cudaMemcpyAsync(P->s, &h, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
+    SR_CK(launch_build_D(P->kern->dK, P->dV, n, r, P->gamma, prm.lambda, prm.rho, P->D64, P->D32, st));
+    // right-hand side in the eigenbasis: bbar = D_K U_K' B, and ||bbar||^2
+    SR_CK(L.utb(emul, CM_DK_NORM, P->Bm, P->bbar, P->s));
+    // start: x = U_K' W0 (or 0) and its true residual
+    if (W0) {
+      SR_CK(upload(P->tmp64, W0, nr * sizeof(double), mem, st));
+      SR_CK(L.utb(emul, CM_STORE, P->tmp64, P->x, P->s));
+      SR_CK(L.opwide(emul, CM_RESID, P->x, P->res, P->s, nullptr, 0));
+    } else {
+      SR_CK(cudaMemsetAsync(P->x, 0, nr * sizeof(double), st));
+      SR_CK(cudaMemcpyAsync(P->res, P->bbar, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
-    if (!converged && !hs->status) {
-      // final true residual of the returned iterate
-      CK(L.opwide(emul, CM_RESID, P->x, P->res, P->s, nullptr, 0));
-      CK(cudaMemcpyAsync(hs, P->s, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      if (hs->done) converged = true;
+    if (P->tc_err) SR_CK(cudaMemsetAsync(P->tc_err, 0, sizeof(int), st));
+    SR_CK(L.restart(prec));
+    SR_CK(cudaEventRecord(P->ev[1], st));
+    stage = INIT;
+    return mark();
+  }
+
+  // m PCG iterations (plus, in the mixed modes, the FP64-accurate true
+  // residual and restart that close every cycle).
+  int queue_chunk(int m) {
+    if (!use_graphs) {
+      for (int k = 0; k < m; ++k) SR_CK(L.iteration(prec));
+      if (mixed) SR_CK(L.true_residual_check(prec));
+      return CPHIFI_OK;
     }
+    cudaGraphExec_t ex = nullptr;
+    int64_t nl = 0;
+    for (size_t k = 0; k < graphs.size(); ++k)
+      if (graphs[k].first == m) { ex = graphs[k].second; nl = graph_launches[k]; }
+    if (!ex) {
+      cudaGraph_t g = nullptr;
+      const int64_t before = L.launches;
+      SR_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaSuccess;
+      for (int k = 0; k < m && e == cudaSuccess; ++k) e = L.iteration(prec);
+      if (e == cudaSuccess && mixed) e = L.true_residual_check(prec);
+      cudaError_t e2 = cudaStreamEndCapture(st, &g);
+      nl = L.launches - before;
+      L.launches = before;
+      if (e != cudaSuccess) return err(e, "capturing the iteration chunk");
+      SR_CK(e2);
+      e = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      SR_CK(e);
+      graphs.push_back({m, ex});
+      graph_launches.push_back(nl);
+    }
+    SR_CK(cudaGraphLaunch(ex, st));
+    L.launches += nl;
+    return CPHIFI_OK;
+  }
+
+  int queue_final() {
+    const size_t nr = (size_t)P->n * P->r;
+    SR_CK(cudaEventRecord(P->ev[2], st));
+    double* Wdev = (mem == CPHIFI_MEM_DEVICE) ? W_out : P->tmp64;
+    SR_CK(L.ux(emul, P->x, Wdev, P->s));
+    if (mem != CPHIFI_MEM_DEVICE) SR_CK(download(W_out, Wdev, nr * sizeof(double), mem, st));
+    SR_CK(cudaEventRecord(P->ev[3], st));
+    if (P->tc_err)
+      SR_CK(cudaMemcpyAsync(tc_word(), P->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    stage = FINAL;
+    return mark();
+  }
+
+  // The scalars of the finished step decide the next one.
+  int advance() {
+    const DevScalars* hs = P->hs;
+    switch (stage) {
+      case INIT:
+        if (hs->bb == 0.0) {  // b = 0: W = 0 solves the system exactly
+          converged = true;
+          SR_CK(cudaMemsetAsync(P->x, 0, (size_t)P->n * P->r * sizeof(double), st));
+          return queue_final();
+        }
+        if (W0 && hs->done) {  // the warm start already meets the tolerance
+          converged = true;
+          return queue_final();
+        }
+        stage = CHUNK;
+        return next_chunk();
+      case CHUNK:
+        if (hs->status) return finish_loop();
+        if (mixed) {
+          if (hs->done) { converged = true; return finish_loop(); }
+          // Restart from the true residual when the recurrence has stopped
+          // (it met the tolerance, or max_iter) or has drifted below the true
+          // residual by more than a factor 2: the low-precision operator's
+          // error then dominates.  Otherwise PCG runs on with its Krylov
+          // space intact.
+          if (hs->inner_done || hs->rr < 0.25 * hs->true_rr) {
+            if (prm.max_iter - hs->iter <= 0) return last_residual();
+            SR_CK(L.adopt_restart(prec));
+          }
+          return next_chunk();
+        }
+        if (hs->done) {
+          // FP64-accurate operator: the recurrence met tol; confirm with the
+          // true residual and restart from it if it does not (refinement).
+          SR_CK(L.true_residual_restart(prec));
+          stage = CONFIRM;
+          return mark();
+        }
+        return next_chunk();
+      case CONFIRM:
+        if (hs->status) return finish_loop();
+        if (hs->done) { converged = true; return finish_loop(); }
+        stage = CHUNK;
+        return next_chunk();
+      case LASTRES:
+        if (hs->done) converged = true;
+        return finish_loop();
+      case FINAL: {
+        tcerr = P->tc_err ? *tc_word() : 0;
+        if (tcerr) {
+          status = CPHIFI_E_TIMEOUT;  // a bounded wait in a tensor-core product expired
+          ctx()->last_error = "tensor-core product: a bounded wait expired (error code " +
+                              std::to_string(tcerr) + ")";
+        }
+        stage = DONE;
+        return CPHIFI_OK;
+      }
+      case DONE:
+        return CPHIFI_OK;
+    }
+    return CPHIFI_OK;
+  }
+
+  int next_chunk() {
+    const DevScalars* hs = P->hs;
+    const int cycle = mixed ? std::max(1, prm.k_replace) : std::max(1, prm.check_every);
+    const int left = prm.max_iter - hs->iter;
+    // Every chunk adds iterations or the loop ends; the pass bound is a second
+    // guarantee that it terminates.
+    if (left <= 0 || ++pass > (int64_t)prm.max_iter + 2) return last_residual();
+    const int m = std::min(cycle, left);
+    int rc = queue_chunk(m);
+    if (rc != CPHIFI_OK) return rc;
+    stage = CHUNK;
+    return mark();
+  }
+
+  // max_iter reached: the true residual of the returned iterate.
+  int last_residual() {
+    if (P->hs->status) return finish_loop();
+    SR_CK(L.opwide(emul, CM_RESID, P->x, P->res, P->s, nullptr, 0));
+    stage = LASTRES;
+    return mark();
+  }
+
+  int finish_loop() {
+    const DevScalars* hs = P->hs;
     if (hs->status) status = hs->status;
     else if (!converged) status = CPHIFI_E_NOT_CONVERGED;
+    return queue_final();
   }
-  // W = U_K Wbar
-  CK(cudaEventRecord(ctx->phase[2], st));
-  double* Wdev = (mem == CPHIFI_MEM_DEVICE) ? W_out : P->tmp64;
-  CK(L.ux(emul, P->x, Wdev, P->s));
-  if (mem != CPHIFI_MEM_DEVICE) CK(download(W_out, Wdev, nr * sizeof(double), mem, st));
-  CK(cudaEventRecord(ctx->phase[3], st));
-  int tcerr = 0;
-  if (P->tc_err) CK(cudaMemcpyAsync(&tcerr, P->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  if (tcerr) {
-    status = CPHIFI_E_TIMEOUT;  // a bounded wait in a tensor-core product expired
-    ctx->last_error = "tensor-core product: a bounded wait expired (error code " +
-                      std::to_string(tcerr) + ")";
-  }
-  auto t1 = std::chrono::steady_clock::now();
-  if (stats) {
+#undef SR_CK
+
+  void fill(cphifi_stats* stats) {
+    auto t1 = std::chrono::steady_clock::now();
+    const DevScalars* hs = P->hs;
     memset(stats, 0, sizeof(*stats));
     stats->status = status;
     stats->iterations = hs->iter;
@@ -1233,9 +1476,9 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
     stats->kernel_launches = L.launches;
     stats->setup_launches = P->create_launches;
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, ctx->phase[0], ctx->phase[1]) == cudaSuccess) stats->rhs_ms = ms;
-    if (cudaEventElapsedTime(&ms, ctx->phase[1], ctx->phase[2]) == cudaSuccess) stats->iter_ms = ms;
-    if (cudaEventElapsedTime(&ms, ctx->phase[2], ctx->phase[3]) == cudaSuccess) stats->final_ms = ms;
+    if (cudaEventElapsedTime(&ms, P->ev[0], P->ev[1]) == cudaSuccess) stats->rhs_ms = ms;
+    if (cudaEventElapsedTime(&ms, P->ev[1], P->ev[2]) == cudaSuccess) stats->iter_ms = ms;
+    if (cudaEventElapsedTime(&ms, P->ev[2], P->ev[3]) == cudaSuccess) stats->final_ms = ms;
     if (tm.on) {
       stats->gds_ms = Timer::total(tm.gds);
       stats->gds_launches = (int)tm.gds.size();
@@ -1247,9 +1490,41 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
       stats->gemm64_launches = (int)tm.gemm64.size();
     }
   }
-  if (status != CPHIFI_OK && status != CPHIFI_E_TIMEOUT)
-    ctx->last_error = std::string("solve: ") + cphifi_status_string(status);
-  return status;
+};
+
+// Checks that do not touch the device, then the operator data the precision
+// needs.
+static int solve_prepare(cphifi_problem* P, const cphifi_params* prm, double* W_out, int mem) {
+  cphifi_ctx* ctx = P->ctx;
+  int rc = check_params(ctx, prm);
+  if (rc != CPHIFI_OK) return rc;
+  if (!W_out) return fail(ctx, CPHIFI_E_INVALID_ARG, "null W_out");
+  if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
+  const int prec = prm->precision;
+  if (is_tc(prec) && !P->kern->tc)
+    return fail(ctx, CPHIFI_E_UNSUPPORTED, "tensor-core products unavailable for this kernel");
+  return prec != CPHIFI_FP64 ? ensure_lowp(P) : ensure_fp64(P);
+}
+
+extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm, const double* W0,
+                                    double* W_out, int mem, cphifi_stats* stats) {
+  if (!P) return CPHIFI_E_INVALID_ARG;
+  cphifi_ctx* ctx = P->ctx;
+  Enter guard(ctx);
+  int rc = solve_prepare(P, prm, W_out, mem);
+  if (rc != CPHIFI_OK) return rc;
+  SolveRun run(P, *prm, W0, W_out, mem, /*graphs_ok=*/false);
+  rc = run.begin();
+  while (rc == CPHIFI_OK && run.stage != SolveRun::DONE) {
+    if ((rc = run.wait_ready()) != CPHIFI_OK) break;
+    rc = run.advance();
+  }
+  if (rc != CPHIFI_OK) return rc;
+  if (stats) run.fill(stats);
+  if (run.status != CPHIFI_OK && run.status != CPHIFI_E_TIMEOUT)
+    ctx->last_error = std::string("solve: ") + cphifi_status_string(run.status);
+  return run.status;
 }
 
 extern "C" int cphifi_solve(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
@@ -1275,12 +1550,271 @@ extern "C" int cphifi_solve(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t 
   return rc;
 }
 
+// ------------------------------------------------ submitted requests -----
+struct Request {
+  uint64_t id = 0;
+  const cphifi_kernel* kern = nullptr;
+  int32_t d_other = 0;
+  std::vector<int64_t> sizes;
+  std::vector<const double*> factors;
+  int32_t r = 0;
+  int64_t q = 0;
+  const int32_t* kidx = nullptr;
+  const int32_t* oidx = nullptr;
+  const double* vals = nullptr;
+  uint32_t flags = 0;
+  cphifi_params prm{};
+  const double* W0 = nullptr;
+  double* W_out = nullptr;
+  int mem = 0;
+  size_t need = 0;
+  enum { PENDING, ACTIVE, DONE } state = PENDING;
+  cphifi_problem* P = nullptr;
+  std::unique_ptr<SolveRun> run;
+  cudaEvent_t ev_submit = nullptr;  // inputs ready (caller's stream order)
+  int slot = -1;
+  int status = CPHIFI_OK;
+  std::string error;
+  cphifi_stats stats{};
+  std::chrono::steady_clock::time_point t_submit, t_admit, t_created;
+};
+
+namespace {
+
+void request_finish(cphifi_ctx* ctx, Request* R, int status) {
+  if (R->run) {
+    if (status == CPHIFI_OK && R->run->stage == SolveRun::DONE) {
+      R->run->fill(&R->stats);
+      status = R->run->status;
+    }
+    R->run.reset();
+  }
+  R->stats.status = status;
+  R->stats.queue_ms =
+      std::chrono::duration<double, std::milli>(R->t_admit - R->t_submit).count();
+  R->stats.setup_ms =
+      std::chrono::duration<double, std::milli>(R->t_created - R->t_admit).count();
+  if (status != CPHIFI_OK && R->error.empty()) R->error = ctx->last_error;
+  if (R->P) {
+    cphifi_problem_destroy(R->P);
+    R->P = nullptr;
+  }
+  if (R->slot >= 0) {
+    ctx->slot_busy[R->slot] = false;
+    R->slot = -1;
+  }
+  if (R->ev_submit) {
+    cudaEventDestroy(R->ev_submit);
+    R->ev_submit = nullptr;
+  }
+  R->status = status;
+  R->state = Request::DONE;
+  ctx->done_unreported.push_back(R->id);
+}
+
+// Advance every active request whose queued step has finished; admit
+// pending requests while a slot and the HBM budget allow.  Returns whether
+// anything changed.
+bool progress(cphifi_ctx* ctx) {
+  bool moved = false;
+  for (size_t k = 0; k < ctx->active.size();) {
+    Request* R = ctx->active[k];
+    int rc = CPHIFI_OK;
+    if (R->run->ready()) {
+      moved = true;
+      rc = R->run->advance();
+    }
+    if (rc != CPHIFI_OK || R->run->stage == SolveRun::DONE) {
+      request_finish(ctx, R, rc);
+      ctx->active.erase(ctx->active.begin() + k);
+      moved = true;
+    } else {
+      ++k;
+    }
+  }
+  while (!ctx->pending.empty() && (int)ctx->active.size() < ctx->max_active) {
+    Request* R = ctx->pending.front();
+    if (ctx->budget && ctx->in_use + R->need > ctx->budget) {
+      if (ctx->active.empty()) {  // cannot fit even alone
+        ctx->pending.pop_front();
+        R->error = "request footprint exceeds the HBM budget";
+        request_finish(ctx, R, CPHIFI_E_ADMISSION);
+        moved = true;
+        continue;
+      }
+      break;  // wait for memory to free up
+    }
+    int slot = -1;
+    for (int k = 0; k < (int)ctx->slot_busy.size(); ++k)
+      if (!ctx->slot_busy[k]) { slot = k; break; }
+    if (slot < 0) {
+      cudaStream_t stn = nullptr;
+      if (cudaStreamCreateWithFlags(&stn, cudaStreamNonBlocking) != cudaSuccess) break;
+      ctx->slot_stream.push_back(stn);
+      ctx->slot_busy.push_back(false);
+      slot = (int)ctx->slot_stream.size() - 1;
+    }
+    ctx->pending.pop_front();
+    moved = true;
+    R->t_admit = std::chrono::steady_clock::now();
+    ctx->slot_busy[slot] = true;
+    R->slot = slot;
+    int rc = cudaStreamWaitEvent(ctx->slot_stream[slot], R->ev_submit, 0) == cudaSuccess
+                 ? (int)CPHIFI_OK
+                 : fail(ctx, CPHIFI_E_DEVICE, "ordering the request after its inputs");
+    if (rc == CPHIFI_OK)
+      rc = problem_create_on(ctx, R->kern, R->d_other, R->sizes.data(), R->factors.data(), R->r,
+                               R->q, R->kidx, R->oidx, R->vals, R->flags, R->mem,
+                               ctx->slot_stream[slot], &R->P);
+    R->t_created = std::chrono::steady_clock::now();
+    if (rc == CPHIFI_OK) rc = solve_prepare(R->P, &R->prm, R->W_out, R->mem);
+    if (rc == CPHIFI_OK) {
+      R->run.reset(new SolveRun(R->P, R->prm, R->W0, R->W_out, R->mem, /*graphs_ok=*/true));
+      rc = R->run->begin();
+    }
+    if (rc != CPHIFI_OK) {
+      request_finish(ctx, R, rc);
+      continue;
+    }
+    R->state = Request::ACTIVE;
+    ctx->active.push_back(R);
+  }
+  return moved;
+}
+
+}  // namespace
+
+static void requests_clear(cphifi_ctx* ctx) {
+  for (auto& kv : ctx->requests) {
+    Request* R = kv.second;
+    if (R->P) cudaStreamSynchronize(R->P->st);
+    if (R->state != Request::DONE) request_finish(ctx, R, CPHIFI_E_INVALID_ARG);
+    delete R;
+  }
+  ctx->requests.clear();
+  ctx->pending.clear();
+  ctx->active.clear();
+  ctx->done_unreported.clear();
+  for (auto stn : ctx->slot_stream) cudaStreamDestroy(stn);
+  ctx->slot_stream.clear();
+  ctx->slot_busy.clear();
+}
+
+extern "C" int cphifi_ctx_set_slots(cphifi_ctx* ctx, int max_active) {
+  if (!ctx || max_active < 1 || max_active > 1024) return CPHIFI_E_INVALID_ARG;
+  ctx->max_active = max_active;
+  return CPHIFI_OK;
+}
+
+extern "C" int cphifi_submit(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
+                             const int64_t* other_sizes, const double* const* factors, int32_t r,
+                             int64_t q, const int32_t* kidx, const int32_t* oidx,
+                             const double* vals, uint32_t flags, const cphifi_params* params,
+                             const double* W0, double* W_out, int mem, cphifi_ticket* ticket) {
+  if (!ctx || !ticket) return CPHIFI_E_INVALID_ARG;
+  *ticket = 0;
+  int rc = check_params(ctx, params);
+  if (rc != CPHIFI_OK) return rc;
+  if (!kern || kern->ctx != ctx) return fail(ctx, CPHIFI_E_INVALID_ARG, "kernel of another context");
+  if (d_other < 1 || d_other > 16 || !other_sizes || !factors)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "bad other modes");
+  if (r < 1 || r > kMaxRank || q < 0 || q >= (int64_t(1) << 31))
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "r or q out of range");
+  if (!W_out) return fail(ctx, CPHIFI_E_INVALID_ARG, "null W_out");
+  if (q > 0 && (!kidx || !oidx || !vals)) return fail(ctx, CPHIFI_E_INVALID_ARG, "null observation list");
+  for (int m = 0; m < d_other; ++m)
+    if (other_sizes[m] < 1 || other_sizes[m] > (int64_t(1) << 31) - 1 || !factors[m])
+      return fail(ctx, CPHIFI_E_INVALID_ARG, "bad other-mode size or null factor");
+  if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
+  Enter guard(ctx);
+  Request* R = new Request();
+  R->id = ctx->next_ticket++;
+  R->kern = kern;
+  R->d_other = d_other;
+  R->sizes.assign(other_sizes, other_sizes + d_other);
+  R->factors.assign(factors, factors + d_other);
+  R->r = r;
+  R->q = q;
+  R->kidx = kidx;
+  R->oidx = oidx;
+  R->vals = vals;
+  R->flags = flags | (params->precision == CPHIFI_FP64 ? CPHIFI_NEED_FP64 : CPHIFI_NEED_LOWP);
+  R->prm = *params;
+  R->W0 = W0;
+  R->W_out = W_out;
+  R->mem = mem;
+  R->t_submit = R->t_admit = R->t_created = std::chrono::steady_clock::now();
+  {
+    size_t need = 0, tmp = 0;
+    problem_need(ctx, kern->n, kern->tc, d_other, R->sizes, r, q, R->flags, &need, &tmp);
+    R->need = need + tmp;
+  }
+  if (cudaEventCreateWithFlags(&R->ev_submit, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(R->ev_submit, ctx->stream) != cudaSuccess) {
+    if (R->ev_submit) cudaEventDestroy(R->ev_submit);
+    delete R;
+    return fail(ctx, CPHIFI_E_DEVICE, "recording the submit event");
+  }
+  ctx->requests[R->id] = R;
+  ctx->pending.push_back(R);
+  *ticket = R->id;
+  progress(ctx);
+  return CPHIFI_OK;
+}
+
+extern "C" int cphifi_poll(cphifi_ctx* ctx, int32_t* n_active, int32_t* n_pending,
+                           cphifi_ticket* done, int32_t done_cap, int32_t* n_done) {
+  if (!ctx || done_cap < 0 || (done_cap > 0 && !done)) return CPHIFI_E_INVALID_ARG;
+  Enter guard(ctx);
+  progress(ctx);
+  if (n_active) *n_active = (int32_t)ctx->active.size();
+  if (n_pending) *n_pending = (int32_t)ctx->pending.size();
+  // Tickets that completed since they were last listed, oldest first.
+  auto& du = ctx->done_unreported;
+  size_t k = 0, m = 0;
+  for (; k < du.size() && (int32_t)m < done_cap; ++k) {
+    if (ctx->requests.count(du[k])) done[m++] = du[k];
+  }
+  du.erase(du.begin(), du.begin() + k);
+  if (n_done) *n_done = (int32_t)m;
+  return CPHIFI_OK;
+}
+
+extern "C" int cphifi_wait(cphifi_ctx* ctx, cphifi_ticket ticket, int64_t timeout_us,
+                           cphifi_stats* stats) {
+  if (!ctx) return CPHIFI_E_INVALID_ARG;
+  auto it = ctx->requests.find(ticket);
+  if (it == ctx->requests.end()) return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown ticket");
+  Request* R = it->second;
+  Enter guard(ctx);
+  const auto t0 = std::chrono::steady_clock::now();
+  while (R->state != Request::DONE) {
+    const bool moved = progress(ctx);
+    if (R->state == Request::DONE) break;
+    if (timeout_us >= 0) {
+      const auto us = std::chrono::duration_cast<std::chrono::microseconds>(
+                          std::chrono::steady_clock::now() - t0).count();
+      if (us >= timeout_us) return fail(ctx, CPHIFI_E_TIMEOUT, "request still running");
+    }
+    if (!moved) std::this_thread::sleep_for(std::chrono::microseconds(10));
+  }
+  if (stats) *stats = R->stats;
+  const int status = R->status;
+  auto& du = ctx->done_unreported;
+  du.erase(std::remove(du.begin(), du.end(), ticket), du.end());
+  if (status != CPHIFI_OK) ctx->last_error = R->error;
+  ctx->requests.erase(it);
+  delete R;
+  return status;
+}
+
 // ------------------------------------------------- step-by-step calls -----
 extern "C" int cphifi_problem_rhs(cphifi_problem* P, double* B_out, double* b_out, int mem) {
   if (!P) return CPHIFI_E_INVALID_ARG;
   cphifi_ctx* ctx = P->ctx;
   Enter guard(ctx);
-  cudaStream_t st = ctx->stream;
+  cudaStream_t st = P->st;
   const size_t nr = (size_t)P->n * P->r;
   Launcher L{P, st, nullptr};
   if (B_out) CK(download(B_out, P->Bm, nr * sizeof(double), mem, st));
@@ -1307,7 +1841,7 @@ extern "C" int cphifi_problem_matvec(cphifi_problem* P, int precision, double la
   Enter guard(ctx);
   int rc;
   if ((rc = precision == CPHIFI_FP64 ? ensure_fp64(P) : ensure_lowp(P)) != CPHIFI_OK) return rc;
-  cudaStream_t st = ctx->stream;
+  cudaStream_t st = P->st;
   const size_t nr = (size_t)P->n * P->r;
   Launcher L{P, st, nullptr};
   DevScalars h{};
@@ -1344,7 +1878,7 @@ extern "C" int cphifi_problem_gds(cphifi_problem* P, int precision, const double
   Enter guard(ctx);
   int rc;
   if ((rc = precision == CPHIFI_FP64 ? ensure_fp64(P) : ensure_lowp(P)) != CPHIFI_OK) return rc;
-  cudaStream_t st = ctx->stream;
+  cudaStream_t st = P->st;
   const size_t nr = (size_t)P->n * P->r;
   Launcher L{P, st, nullptr};
   CK(upload(P->xh64, Xhat, nr * sizeof(double), mem, st));
@@ -1368,7 +1902,7 @@ extern "C" int cphifi_problem_precond(cphifi_problem* P, double lambda, double r
   cphifi_ctx* ctx = P->ctx;
   if (!(rho > 0.0) || !(lambda >= 0.0)) return fail(ctx, CPHIFI_E_INVALID_ARG, "lambda/rho");
   Enter guard(ctx);
-  cudaStream_t st = ctx->stream;
+  cudaStream_t st = P->st;
   const size_t nr = (size_t)P->n * P->r;
   Launcher L{P, st, nullptr};
   CK(launch_build_D(P->kern->dK, P->dV, P->n, P->r, P->gamma, lambda, rho, P->D64, P->D32, st));
@@ -1387,7 +1921,7 @@ extern "C" int cphifi_problem_gram(cphifi_problem* P, double* V, double* DV, dou
   if (!P) return CPHIFI_E_INVALID_ARG;
   cphifi_ctx* ctx = P->ctx;
   Enter guard(ctx);
-  cudaStream_t st = ctx->stream;
+  cudaStream_t st = P->st;
   const size_t rr = (size_t)P->r * P->r;
   if (V) CK(cudaMemcpyAsync(V, P->V, rr * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (DV) CK(cudaMemcpyAsync(DV, P->dV, P->r * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1400,7 +1934,7 @@ extern "C" int cphifi_problem_order(cphifi_problem* P, int32_t* perm, int64_t* r
   if (!P) return CPHIFI_E_INVALID_ARG;
   cphifi_ctx* ctx = P->ctx;
   Enter guard(ctx);
-  cudaStream_t st = ctx->stream;
+  cudaStream_t st = P->st;
   if (perm) CK(cudaMemcpyAsync(perm, P->perm, P->q * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   if (row_ptr)
     CK(cudaMemcpyAsync(row_ptr, P->row_ptr, (P->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));

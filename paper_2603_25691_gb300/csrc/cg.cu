@@ -174,9 +174,9 @@ cudaError_t launch_build_D(const double* dK, const double* dV, int n, int r, dou
 
 // ------------------------------------------------- operator epilogue ------
 // Sums the split partial products and applies the elementwise tail.  CM_APPLY
-// also forms (p, Ap) and, in its last block, alpha = rz / pAp; CM_RESID forms
-// ||b - A x||^2 and, in its last block, decides convergence on the FP64 true
-// residual.
+// also forms (p, Ap) and, in its last block, alpha = rz / pAp; CM_RESID and
+// CM_TRUE form ||b - A x||^2 and, in their last block, decide convergence on
+// the FP64 true residual (CM_RESID also makes it the recurrence residual).
 static int vec_blocks(int64_t total) {
   int64_t b = (total + 255) / 256;
   if (b > kRedMaxBlocks) b = kRedMaxBlocks;
@@ -190,7 +190,7 @@ combine_kernel(int mode, const TC* __restrict__ C, int64_t split_stride, int nsp
                const double* __restrict__ dK, const double* __restrict__ V,
                const double* __restrict__ Bv, TO* __restrict__ out, DevScalars* s,
                RedScratch red, const DevScalars* skip) {
-  if (mode != CM_RESID && dev_skip(skip)) return;
+  if (mode != CM_RESID && mode != CM_TRUE && dev_skip(skip)) return;
   const int64_t total = (int64_t)n * r;
   double lam = 0.0, rho = 0.0;
   if (s) { lam = s->lam; rho = s->rho; }
@@ -218,7 +218,7 @@ combine_kernel(int mode, const TC* __restrict__ C, int64_t split_stride, int nsp
     }
     out[t] = (TO)o;
   }
-  if (mode == CM_APPLY || mode == CM_RESID || mode == CM_DK_NORM) {
+  if (mode == CM_APPLY || mode == CM_RESID || mode == CM_TRUE || mode == CM_DK_NORM) {
     double tot[1];
     if (grid_sum_last<1>(acc, red, tot)) {
       if (mode == CM_DK_NORM) {
@@ -233,14 +233,33 @@ combine_kernel(int mode, const TC* __restrict__ C, int64_t split_stride, int nsp
         s->alpha = a;
       } else {
         s->true_rr = tot[0];
-        s->rr = tot[0];
+        if (mode == CM_RESID) {
+          s->rr = tot[0];
+          s->inner_done = 0;
+        }
         s->true_evals += 1;
-        s->inner_done = 0;
         if (!isfinite(tot[0])) { s->status = 5; s->done = 1; }
         else if (s->status == 0) s->done = (tot[0] <= s->tol2 * s->bb) ? 1 : 0;
       }
     }
   }
+}
+
+__global__ void adopt_residual_kernel(const double* __restrict__ tres, double* __restrict__ res,
+                                      int64_t count, DevScalars* s) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
+       t += (int64_t)gridDim.x * blockDim.x)
+    res[t] = tres[t];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    s->rr = s->true_rr;
+    s->inner_done = 0;
+  }
+}
+
+cudaError_t launch_adopt_residual(const double* tres, double* res, int64_t count, DevScalars* s,
+                                  cudaStream_t st) {
+  adopt_residual_kernel<<<vec_blocks(count), 256, 0, st>>>(tres, res, count, s);
+  return cudaGetLastError();
 }
 
 template <typename TC, typename TO>

@@ -165,8 +165,14 @@ enum CombineMode {
   CM_DK = 1,     // out = dK .* sum_s C_s
   CM_APPLY = 2,  // out = dK .* sum_s C_s + (lam dK + rho) .* V; pAp -> alpha
   CM_RESID = 3,  // out = Bv - (dK .* sum_s C_s + (lam dK + rho) .* V); ||out||^2 -> true residual
-  CM_DK_NORM = 4 // out = dK .* sum_s C_s; ||out||^2 -> bb (the right-hand side)
+  CM_DK_NORM = 4, // out = dK .* sum_s C_s; ||out||^2 -> bb (the right-hand side)
+  CM_TRUE = 5     // as CM_RESID into a separate buffer: sets true_rr and the
+                  // convergence flag, leaves the recurrence (rr, inner_done) alone
 };
+// res = tres, rr = true_rr, inner_done = 0: the true residual of CM_TRUE
+// replaces the recurrence residual (before a restart).
+cudaError_t launch_adopt_residual(const double* tres, double* res, int64_t count, DevScalars* s,
+                                  cudaStream_t st);
 template <typename TC, typename TO>
 cudaError_t launch_combine(int mode, const TC* C, int64_t split_stride, int nsplit,
                            int n, int r, const double* dK, const double* V,

@@ -202,6 +202,47 @@ WORKLOADS = {
 }
 
 
+# Kernel sizes of the batched / served streams: n is drawn log-uniform on
+# [50, 2000] and snapped to this 16-point log grid, so that kernels (and their
+# one-time eigendecompositions) are shared between instances, as the kernel
+# mode of one tensor is across ALS sweeps.
+BATCH_N_GRID = tuple(int(round(50 * (40.0 ** (k / 15.0)))) for k in range(16))
+
+
+def batch_specs(seed: int, count: int = 256):
+    """Instance shapes of a batch of uneven kernel-mode subproblems.
+
+    n ~ logU[50, 2000] (snapped to BATCH_N_GRID), M ~ logU[100, 5e4] split into
+    two finite modes of about sqrt(M) rows each, q ~ logU[1e3, 1e6] capped at
+    floor(0.5 n M), r uniform in {4, 8, 16, 32}, Gaussian or Matern-3/2 kernel
+    (bandwidth 0.1) with probability 1/2 each.  Returns a list of dicts with
+    keys n, other_sizes, q, r, kernel, seed.
+    """
+    rng = np.random.default_rng(seed)
+    grid = np.array(BATCH_N_GRID, dtype=np.float64)
+    out = []
+    for k in range(count):
+        n_raw = np.exp(rng.uniform(np.log(50.0), np.log(2000.0)))
+        n = int(grid[np.argmin(np.abs(np.log(grid) - np.log(n_raw)))])
+        M = np.exp(rng.uniform(np.log(100.0), np.log(5e4)))
+        n1 = max(1, int(round(np.sqrt(M))))
+        n2 = max(1, int(round(M / n1)))
+        q = int(round(np.exp(rng.uniform(np.log(1e3), np.log(1e6)))))
+        q = min(q, (n * n1 * n2) // 2)
+        r = int(rng.choice([4, 8, 16, 32]))
+        kernel = "gaussian" if rng.uniform() < 0.5 else "matern32"
+        out.append(dict(n=n, other_sizes=(n1, n2), q=q, r=r, kernel=kernel,
+                        seed=int(rng.integers(1 << 31))))
+    return out
+
+
+def batch_problem(spec: dict, lam: float = 1e-4, rho: float = 1e-6) -> Problem:
+    """The planted subproblem of one batch_specs entry (sorted observations)."""
+    return planted_problem(spec["seed"], spec["n"], spec["other_sizes"], spec["q"],
+                           spec["r"], kernel=spec["kernel"], bandwidth=0.1, lam=lam,
+                           rho=rho)
+
+
 def workload(name: str, seed: int = 0, **over) -> Problem:
     kw = dict(WORKLOADS[name])
     kw.update(over)

@@ -50,3 +50,35 @@ def test_context_without_gpu_is_an_error(libpath):
     import paper_2603_25691_gb300 as pkg
     with pytest.raises(pkg.CphifiError):
         pkg.Context(0)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # The binding's ctypes mirrors of cphifi_params / cphifi_stats must have the
+    # header's size and field offsets (a C program compiled from the header
+    # prints them).
+    import ctypes
+
+    import paper_2603_25691_gb300 as pkg
+    fields = {"cphifi_params": pkg.Params, "cphifi_stats": pkg.Stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cphifi.h"',
+             "int main(void) {"]
+    for cname, py in fields.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            # (a C member named like a Python keyword has a trailing _ in ctypes)
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f.rstrip("_")}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = {}
+    for line in out.splitlines():
+        c, f, v = line.split()
+        got[(c, f)] = int(v)
+    for cname, py in fields.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)

@@ -307,3 +307,33 @@ def test_device_pointers(ctx, pkg):
     res = O.relative_residual(p.K, p.factors, p.kidx, p.oidx, p.vals, p.lam, p.rho, Wh)
     assert st["status"] == 0 and res <= 1e-10
     kern.close()
+
+
+# Slowly converging instances of the uneven batch: Matern-3/2 kernels with few
+# observations per unknown (q ~ 1e3 for n r ~ 3e3 .. 3e4), where FP64 PCG
+# needs hundreds of iterations and the preconditioner's density weight gamma
+# is small.  The mixed modes must still reach the tolerance on the oracle's
+# FP64 true residual, restarting only when the low-precision recurrence
+# drifts.
+HARD = {
+    "matern_n105_q1040_r32": dict(n=105, other_sizes=(58, 58), q=1040, r=32, kernel="matern32",
+                                  seed=845932451),
+    "matern_n1223_q1107_r32": dict(n=1223, other_sizes=(61, 60), q=1107, r=32,
+                                   kernel="matern32", seed=546953866),
+    "matern_n457_q2429_r32": dict(n=457, other_sizes=(62, 62), q=2429, r=32, kernel="matern32",
+                                  seed=1745629169),
+}
+
+
+@pytest.mark.parametrize("name", list(HARD))
+@pytest.mark.parametrize("prec", ["mixed_fp32", "mixed_tf32x3", "fp64_emulated"])
+def test_slow_instances_reach_tolerance(ctx, pkg, name, prec):
+    p = synth.batch_problem(HARD[name])
+    dK, UK = np.linalg.eigh(p.K)
+    kern = ctx.kernel_create(p.n, UK, dK)
+    W, st = pkg.solve(ctx, kern, p.factors, p.kidx, p.oidx, p.vals, p.r, p.lam, p.rho, 1e-6,
+                      max_iter=6000, precision=prec, sorted_obs=True)
+    res = O.relative_residual(p.K, p.factors, p.kidx, p.oidx, p.vals, p.lam, p.rho, W)
+    assert st["status"] == 0, st
+    assert res <= 1e-6, (res, st)
+    kern.close()
