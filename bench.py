@@ -34,6 +34,7 @@ METRIC = "kernel-mode PCG obs*iter/s & solves/s, mixed vs FP64 at 1e-6 rel err; 
 UNIT = "obs*iter/s"
 WORKLOAD = "c3_mixed_n8000_q5e7_r40"
 TOL = 1e-6
+MAX_ITER_BATCH = 5000
 
 
 def parse():
@@ -256,7 +257,8 @@ class BatchInputs:
 def submit_item(pkg, ctx, it, precision):
     p = it["p"]
     return pkg.submit(ctx, it["kern"], it["f"], it["k"], it["o"], it["v"], p.r, p.lam, p.rho, TOL,
-                      max_iter=1000, precision=precision, sorted_obs=True, out=it["W"])
+                      max_iter=MAX_ITER_BATCH, precision=precision, sorted_obs=True,
+                      out=it["W"])
 
 
 def run_batch(args, pkg, ctx, dev, seed):
@@ -296,7 +298,8 @@ def run_batch(args, pkg, ctx, dev, seed):
     for it in items:
         p = it["p"]
         _, st = pkg.solve(ctx, it["kern"], it["f"], it["k"], it["o"], it["v"], p.r, p.lam, p.rho,
-                          TOL, max_iter=1000, precision="fp64", sorted_obs=True, out=it["W"])
+                          TOL, max_iter=MAX_ITER_BATCH, precision="fp64", sorted_obs=True,
+                          out=it["W"])
         it64 += st["iterations"]
     torch.cuda.synchronize()
     t64 = time.perf_counter() - t1
@@ -310,7 +313,9 @@ def run_batch(args, pkg, ctx, dev, seed):
            "fp64_one_at_a_time": {"solves_per_s": len(items) / t64, "elapsed_ms": 1e3 * t64,
                                   "iterations": it64},
            "speedup_vs_fp64_one_at_a_time": t64 / elapsed,
-           "gpu_launches": int(launches), "slots": args.slots}
+           "gpu_launches": int(launches), "slots": args.slots,
+           "host_create_ms_sum": sum(st["setup_ms"] for st in stats),
+           "iterations": int(sum(st["iterations"] for st in stats))}
     B.close()
     return out
 

@@ -57,6 +57,10 @@ struct cphifi_ctx {
   std::vector<void*> pinned_slabs;
   std::vector<char*> pinned_free;
   std::vector<cudaEvent_t> events_free;
+  // Temporaries of asynchronous problem creations, returned to the pool once
+  // the event recorded after their last use has completed.
+  std::vector<std::pair<cudaEvent_t, std::vector<std::pair<void*, size_t>>>> deferred;
+  size_t deferred_bytes = 0;
   cudaEvent_t phase[4] = {nullptr, nullptr, nullptr, nullptr};  // solve phase marks
   // Side stream for small serial work (Gram, eig(V)) that overlaps the
   // bandwidth-bound Zhat pass on the main stream.
@@ -281,6 +285,37 @@ cudaError_t event_get(cphifi_ctx* ctx, cudaEvent_t* out) {
   return cudaEventCreate(out);
 }
 
+// Returns deferred temporaries whose last use has completed (all of them,
+// after a wait, when `wait` is set).
+void deferred_collect(cphifi_ctx* ctx, bool wait) {
+  auto& d = ctx->deferred;
+  size_t k = 0;
+  for (size_t i = 0; i < d.size(); ++i) {
+    // after a wait the entry is released whatever the query says
+    const bool done = wait ? (cudaEventSynchronize(d[i].first), true)
+                           : cudaEventQuery(d[i].first) == cudaSuccess;
+    if (done) {
+      for (auto& t : d[i].second) {
+        pool_release(ctx, t.first, t.second);
+        ctx->deferred_bytes -= std::min(ctx->deferred_bytes, t.second);
+      }
+      ctx->events_free.push_back(d[i].first);
+    } else {
+      if (k != i) d[k] = std::move(d[i]);  // (a self-move would empty the list)
+      ++k;
+    }
+  }
+  d.resize(k);
+  if (d.empty()) ctx->deferred_bytes = 0;
+}
+
+const char* input_error_text(int herr) {
+  if (herr & 1) return "observation index out of range";
+  if (herr & 2) return "non-finite observation value or factor entry";
+  if (herr & 4) return "CPHIFI_OBS_SORTED set but kidx is not sorted";
+  return "invalid observation data";
+}
+
 void free_problem(cphifi_problem* P) {
   if (P->hs) P->ctx->pinned_free.push_back((char*)P->hs);
   P->hs = nullptr;
@@ -423,6 +458,7 @@ extern "C" int cphifi_ctx_destroy(cphifi_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   requests_clear(ctx);
+  deferred_collect(ctx, true);
   pool_trim(ctx);
   for (auto e : ctx->phase)
     if (e) cudaEventDestroy(e);
@@ -611,11 +647,16 @@ static void problem_need(const cphifi_ctx* ctx, int n, bool tc, int32_t d_other,
 
 // Problem creation on stream `st` (the context's stream for the public call, a
 // pool stream for submitted requests).
+// With `async` set (submitted requests) nothing waits for the device: input
+// errors stay in the problem's error word, which the kernels after the
+// validation check before touching memory and the solve reads at its first
+// step; the piece arrays are sized by their upper bound; the temporaries go
+// back to the pool once an event after their last use has completed.
 static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
                              const int64_t* other_sizes, const double* const* factors, int32_t r,
                              int64_t q, const int32_t* kidx, const int32_t* oidx,
                              const double* vals, uint32_t flags, int mem, cudaStream_t st,
-                             cphifi_problem** out) {
+                             bool async, cphifi_problem** out) {
   if (!ctx || !out) return CPHIFI_E_INVALID_ARG;
   *out = nullptr;
   if (!kern || kern->ctx != ctx) return fail(ctx, CPHIFI_E_INVALID_ARG, "kernel of another context");
@@ -822,10 +863,13 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
   PCK(cudaMemcpyAsync(keys, kidx_d, (size_t)q * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
   PCK(launch_iota(P->perm, q, st));
   int herr = 0;
-  PCK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  PCK(cudaStreamSynchronize(st));
-  if (herr & 1) return bail(CPHIFI_E_INVALID_ARG, "observation index out of range");
-  if (herr & 2) return bail(CPHIFI_E_INVALID_ARG, "non-finite observation value or factor entry");
+  if (!async) {
+    PCK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PCK(cudaStreamSynchronize(st));
+    if (herr & 1) return bail(CPHIFI_E_INVALID_ARG, "observation index out of range");
+    if (herr & 2) return bail(CPHIFI_E_INVALID_ARG, "non-finite observation value or factor entry");
+  }
+  const int* gate = async ? P->err : nullptr;
   if (!(flags & CPHIFI_OBS_SORTED) && q > 1) {
     void* rtmp = tmp_alloc(radix_sort_tmp_bytes(q));
     if (!rtmp) return bail(CPHIFI_E_OOM, "temporary allocation failed");
@@ -837,18 +881,24 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
   {
     void* stmp = tmp_alloc(exclusive_scan_tmp_bytes(n));
     if (!stmp) return bail(CPHIFI_E_OOM, "temporary allocation failed");
-    PCK(launch_piece_counts(P->row_ptr, n, L, P->seg_count, st));
+    PCK(launch_piece_counts(P->row_ptr, n, L, P->seg_count, gate, st));
     PCK(exclusive_scan_i32(P->seg_count, P->seg_first, n, stmp, exclusive_scan_tmp_bytes(n), st));
     int np = 0;
-    PCK(cudaMemcpyAsync(&np, P->seg_first + n, sizeof(int), cudaMemcpyDeviceToHost, st));
-    PCK(cudaStreamSynchronize(st));
+    if (async) {
+      np = q > 0 ? (int)npieces_max : 0;  // the exact count stays on the device
+    } else {
+      PCK(cudaMemcpyAsync(&np, P->seg_first + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+      PCK(cudaStreamSynchronize(st));
+    }
     P->npieces = np;
     PCK(dalloc(P, &P->pseg, np));
     PCK(dalloc(P, &P->pbeg, np));
     PCK(dalloc(P, &P->pend, np));
     PCK(dalloc(P, (double**)&P->gds_partial, (size_t)np * 64));
-    PCK(launch_piece_fill(P->row_ptr, n, L, P->seg_first, P->seg_count, P->pseg, P->pbeg, P->pend, st));
-    PCK(launch_warp_first(P->pbeg, np, L, W, P->warp_first, st));
+    PCK(launch_piece_fill(P->row_ptr, n, L, P->seg_first, P->seg_count, P->pseg, P->pbeg,
+                          P->pend, gate, st));
+    PCK(launch_warp_first(P->pbeg, np, async ? P->seg_first + n : nullptr, L, W, P->warp_first,
+                          gate, st));
   }
 
   // ---- Zhat (hi/lo) fused with the right-hand side MTTKRP; Gram, eig(V)
@@ -856,16 +906,23 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
                P->warp_first, P->npieces, P->nwarps};
   PCK(launch_zhat_mttkrp(pl, (flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm, oidx_d, d_other,
                          P->fhi_dev, P->flo_dev, P->sizes_dev, r, vals_d, P->zhi, P->zlo,
-                         P->z64, (double*)P->gds_partial, P->Bm, n, P->err, st));
+                         P->z64, (double*)P->gds_partial, P->Bm, n, P->err, gate, st));
   PCK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
-  PCK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  PCK(cudaStreamSynchronize(st));
-  if (herr & 4) return bail(CPHIFI_E_INVALID_ARG, "CPHIFI_OBS_SORTED set but kidx is not sorted");
-  if (herr) return bail(CPHIFI_E_INVALID_ARG, "invalid observation data");
-  PCK(cudaStreamSynchronize(st));  // the temporaries are free to reuse only after the work
-  for (auto& t : temps) pool_release(ctx, t.first, t.second);
-  temps.clear();
-  PCK(cudaStreamSynchronize(st));
+  if (async) {
+    cudaEvent_t ev = nullptr;
+    PCK(event_get(ctx, &ev));
+    PCK(cudaEventRecord(ev, st));
+    for (auto& t : temps) ctx->deferred_bytes += t.second;
+    ctx->deferred.push_back({ev, std::move(temps)});
+    temps.clear();
+  } else {
+    PCK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PCK(cudaStreamSynchronize(st));
+    if (herr) return bail(CPHIFI_E_INVALID_ARG, input_error_text(herr));
+    // the temporaries are free to reuse only after the work (synchronized above)
+    for (auto& t : temps) pool_release(ctx, t.first, t.second);
+    temps.clear();
+  }
   (void)t0;
   *out = P;
   return CPHIFI_OK;
@@ -879,7 +936,7 @@ extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
                                      int mem, cphifi_problem** out) {
   if (!ctx) return CPHIFI_E_INVALID_ARG;
   return problem_create_on(ctx, kern, d_other, other_sizes, factors, r, q, kidx, oidx, vals,
-                           flags, mem, ctx->stream, out);
+                           flags, mem, ctx->stream, /*async=*/false, out);
 }
 
 extern "C" int cphifi_problem_destroy(cphifi_problem* P) {
@@ -1262,6 +1319,7 @@ struct SolveRun {
 
   cphifi_ctx* ctx() const { return P->ctx; }
   int* tc_word() const { return reinterpret_cast<int*>(P->hs + 1); }
+  int* err_word() const { return reinterpret_cast<int*>(P->hs + 1) + 1; }
   int err(cudaError_t e, const char* what) {
     ctx()->last_error = std::string(what) + ": " + cudaGetErrorString(e);
     status = CPHIFI_E_DEVICE;
@@ -1316,6 +1374,8 @@ struct SolveRun {
     SR_CK(L.restart(prec));
     SR_CK(cudaEventRecord(P->ev[1], st));
     stage = INIT;
+    *err_word() = 0;
+    SR_CK(cudaMemcpyAsync(err_word(), P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     return mark();
   }
 
@@ -1372,6 +1432,12 @@ struct SolveRun {
     const DevScalars* hs = P->hs;
     switch (stage) {
       case INIT:
+        if (*err_word()) {  // input errors of an asynchronous creation
+          status = CPHIFI_E_INVALID_ARG;
+          ctx()->last_error = input_error_text(*err_word());
+          stage = DONE;
+          return CPHIFI_OK;
+        }
         if (hs->bb == 0.0) {  // b = 0: W = 0 solves the system exactly
           converged = true;
           SR_CK(cudaMemsetAsync(P->x, 0, (size_t)P->n * P->r * sizeof(double), st));
@@ -1617,6 +1683,7 @@ void request_finish(cphifi_ctx* ctx, Request* R, int status) {
 // anything changed.
 bool progress(cphifi_ctx* ctx) {
   bool moved = false;
+  deferred_collect(ctx, false);
   for (size_t k = 0; k < ctx->active.size();) {
     Request* R = ctx->active[k];
     int rc = CPHIFI_OK;
@@ -1634,7 +1701,12 @@ bool progress(cphifi_ctx* ctx) {
   }
   while (!ctx->pending.empty() && (int)ctx->active.size() < ctx->max_active) {
     Request* R = ctx->pending.front();
-    if (ctx->budget && ctx->in_use + R->need > ctx->budget) {
+    deferred_collect(ctx, false);
+    if (ctx->budget && ctx->in_use + ctx->deferred_bytes + R->need > ctx->budget) {
+      if (ctx->active.empty() && !ctx->deferred.empty()) {
+        deferred_collect(ctx, true);  // empties the list: runs once per request
+        continue;
+      }
       if (ctx->active.empty()) {  // cannot fit even alone
         ctx->pending.pop_front();
         R->error = "request footprint exceeds the HBM budget";
@@ -1665,7 +1737,7 @@ bool progress(cphifi_ctx* ctx) {
     if (rc == CPHIFI_OK)
       rc = problem_create_on(ctx, R->kern, R->d_other, R->sizes.data(), R->factors.data(), R->r,
                                R->q, R->kidx, R->oidx, R->vals, R->flags, R->mem,
-                               ctx->slot_stream[slot], &R->P);
+                               ctx->slot_stream[slot], /*async=*/true, &R->P);
     R->t_created = std::chrono::steady_clock::now();
     if (rc == CPHIFI_OK) rc = solve_prepare(R->P, &R->prm, R->W_out, R->mem);
     if (rc == CPHIFI_OK) {

@@ -34,14 +34,18 @@ cudaError_t launch_row_ptr(const uint32_t* sorted_keys, int64_t q, int n,
                            int64_t* row_ptr, cudaStream_t st);
 // Pieces: the kernel-index segments cut at multiples of L (each warp of the
 // gather-dot/scatter owns L sorted observations); every index owns >= 1 piece.
+// A non-null `gate` that reads nonzero (an input error found by an earlier
+// kernel) makes these kernels, and the Zhat build, return without touching
+// memory: their inputs cannot be trusted to stay in range.
 cudaError_t launch_piece_counts(const int64_t* row_ptr, int n, int64_t L,
-                                int32_t* seg_count, cudaStream_t st);
+                                int32_t* seg_count, const int* gate, cudaStream_t st);
 cudaError_t launch_piece_fill(const int64_t* row_ptr, int n, int64_t L,
                               const int32_t* seg_first, const int32_t* seg_count,
                               int32_t* pseg, int32_t* pbeg, int32_t* pend,
+                              const int* gate, cudaStream_t st);
+cudaError_t launch_warp_first(const int32_t* pbeg, int npieces, const int32_t* np_dev,
+                              int64_t L, int W, int32_t* warp_first, const int* gate,
                               cudaStream_t st);
-cudaError_t launch_warp_first(const int32_t* pbeg, int npieces, int64_t L, int W,
-                              int32_t* warp_first, cudaStream_t st);
 // Exclusive scan of int32 counts into int32 offsets (out has n+1 entries).
 cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n,
                                void* tmp, size_t tmp_bytes, cudaStream_t st);
@@ -88,7 +92,7 @@ cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const i
                                int d_other, const float* const* fhi, const float* const* flo,
                                const int64_t* sizes_dev, int r, const double* vals,
                                float* zhi, float* zlo, double* z64, double* partial, double* B,
-                               int64_t ldb, int* err, cudaStream_t st);
+                               int64_t ldb, int* err, const int* gate, cudaStream_t st);
 
 // -------------------------------------------------------------- dense.cu ---
 // Skinny product C = op(A) diag(s) B for A n x n (op = identity when a_trans

@@ -220,10 +220,10 @@ extern "C" int cphifi_gds_noalloc(int32_t n, int32_t r, int64_t q, const int64_t
   // The tickets must start at zero; the last piece of an index resets its own,
   // but a call that was cut short could leave stale counts behind.
   if (e == cudaSuccess) e = cudaMemsetAsync(seg_ticket, 0, sizeof(unsigned) * n, st);
-  if (e == cudaSuccess) e = launch_piece_counts(row_ptr, n, L, seg_count, st);
+  if (e == cudaSuccess) e = launch_piece_counts(row_ptr, n, L, seg_count, nullptr, st);
   if (e == cudaSuccess) e = exclusive_scan_i32(seg_count, seg_first, n, scan_tmp, kScanBytes, st);
   if (e == cudaSuccess)
-    e = launch_piece_fill(row_ptr, n, L, seg_first, seg_count, pseg, pbeg, pend, st);
+    e = launch_piece_fill(row_ptr, n, L, seg_first, seg_count, pseg, pbeg, pend, nullptr, st);
   if (e == cudaSuccess) {
     noalloc_warp_first_kernel<<<(W + 1 + 255) / 256, 256, 0, st>>>(pbeg, seg_first, n, L, W,
                                                                   warp_first);

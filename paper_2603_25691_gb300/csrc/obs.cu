@@ -306,25 +306,25 @@ cudaError_t launch_row_ptr(const uint32_t* sorted_keys, int64_t q, int n, int64_
 // observation range of one warp: every warp then owns exactly L sorted
 // observations (the last one fewer) whatever the segment lengths are.
 __global__ void piece_counts_kernel(const int64_t* __restrict__ row_ptr, int n, int64_t L,
-                                    int32_t* seg_count) {
+                                    int32_t* seg_count, const int* gate) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || (gate && *gate)) return;
   const int64_t b = row_ptr[i], e = row_ptr[i + 1];
   seg_count[i] = e > b ? (int32_t)((e - 1) / L - b / L + 1) : 1;
 }
 
 cudaError_t launch_piece_counts(const int64_t* row_ptr, int n, int64_t L, int32_t* seg_count,
-                                cudaStream_t st) {
-  piece_counts_kernel<<<(n + 255) / 256, 256, 0, st>>>(row_ptr, n, L, seg_count);
+                                const int* gate, cudaStream_t st) {
+  piece_counts_kernel<<<(n + 255) / 256, 256, 0, st>>>(row_ptr, n, L, seg_count, gate);
   return cudaGetLastError();
 }
 
 __global__ void piece_fill_kernel(const int64_t* __restrict__ row_ptr, int n, int64_t L,
                                   const int32_t* __restrict__ seg_first,
                                   const int32_t* __restrict__ seg_count, int32_t* pseg,
-                                  int32_t* pbeg, int32_t* pend) {
+                                  int32_t* pbeg, int32_t* pend, const int* gate) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || (gate && *gate)) return;
   const int64_t b = row_ptr[i], e = row_ptr[i + 1];
   const int c = seg_count[i];
   const int64_t k0 = b / L;
@@ -342,18 +342,22 @@ __global__ void piece_fill_kernel(const int64_t* __restrict__ row_ptr, int n, in
 
 cudaError_t launch_piece_fill(const int64_t* row_ptr, int n, int64_t L, const int32_t* seg_first,
                               const int32_t* seg_count, int32_t* pseg, int32_t* pbeg,
-                              int32_t* pend, cudaStream_t st) {
+                              int32_t* pend, const int* gate, cudaStream_t st) {
   piece_fill_kernel<<<(n + 255) / 256, 256, 0, st>>>(row_ptr, n, L, seg_first, seg_count, pseg,
-                                                     pbeg, pend);
+                                                     pbeg, pend, gate);
   return cudaGetLastError();
 }
 
 // warp_first[w] = first piece starting at or after w*L (w < W); warp_first[W]
-// = npieces, so warp w owns pieces [warp_first[w], warp_first[w+1]).
-__global__ void warp_first_kernel(const int32_t* __restrict__ pbeg, int npieces, int64_t L, int W,
-                                  int32_t* warp_first) {
+// = npieces, so warp w owns pieces [warp_first[w], warp_first[w+1]).  With
+// np_dev set, npieces is read from the device (the piece-count scan's total,
+// clamped to the allocated npieces) instead.
+__global__ void warp_first_kernel(const int32_t* __restrict__ pbeg, int npieces,
+                                  const int32_t* np_dev, int64_t L, int W, int32_t* warp_first,
+                                  const int* gate) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w > W) return;
+  if (w > W || (gate && *gate)) return;
+  if (np_dev) npieces = min(npieces, *np_dev);
   if (w == W) { warp_first[W] = npieces; return; }
   const int64_t v = (int64_t)w * L;
   int lo = 0, hi = npieces;
@@ -364,9 +368,10 @@ __global__ void warp_first_kernel(const int32_t* __restrict__ pbeg, int npieces,
   warp_first[w] = lo;
 }
 
-cudaError_t launch_warp_first(const int32_t* pbeg, int npieces, int64_t L, int W,
-                              int32_t* warp_first, cudaStream_t st) {
-  warp_first_kernel<<<(W + 1 + 255) / 256, 256, 0, st>>>(pbeg, npieces, L, W, warp_first);
+cudaError_t launch_warp_first(const int32_t* pbeg, int npieces, const int32_t* np_dev, int64_t L,
+                              int W, int32_t* warp_first, const int* gate, cudaStream_t st) {
+  warp_first_kernel<<<(W + 1 + 255) / 256, 256, 0, st>>>(pbeg, npieces, np_dev, L, W,
+                                                         warp_first, gate);
   return cudaGetLastError();
 }
 
@@ -468,7 +473,9 @@ zhat_mttkrp_kernel(PieceList pl, const int32_t* __restrict__ perm, const int32_t
                    const float* const* __restrict__ flo, const int64_t* __restrict__ sizes, int r,
                    const double* __restrict__ vals, float* __restrict__ zhi,
                    float* __restrict__ zlo, double* __restrict__ z64,
-                   double* __restrict__ partial, double* __restrict__ B, int64_t ldb, int* err) {
+                   double* __restrict__ partial, double* __restrict__ B, int64_t ldb, int* err,
+                   const int* gate) {
+  if (gate && *gate) return;  // invalid input found earlier: touch nothing
   constexpr int OPW = 32 / LPO, CPL = RP / LPO, UN = 1;
   const int lane = threadIdx.x & 31, sub = lane / OPW, o = lane % OPW;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -557,13 +564,13 @@ cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const i
                                int d_other, const float* const* fhi, const float* const* flo,
                                const int64_t* sizes_dev, int r, const double* vals, float* zhi,
                                float* zlo, double* z64, double* partial, double* B, int64_t ldb,
-                               int* err, cudaStream_t st) {
+                               int* err, const int* gate, cudaStream_t st) {
   if (pl.npieces == 0 || pl.nwarps == 0) return cudaSuccess;
   const int blocks = (pl.nwarps + 7) / 8;
 #define CPHIFI_ZM(RPV, LPOV)                                                                  \
   zhat_mttkrp_kernel<RPV, LPOV><<<blocks, 256, 0, st>>>(pl, perm, oidx, d_other, fhi, flo,   \
                                                          sizes_dev, r, vals, zhi, zlo, z64,  \
-                                                         partial, B, ldb, err)
+                                                         partial, B, ldb, err, gate)
   if (r <= 8) CPHIFI_ZM(8, 1);
   else if (r <= 16) CPHIFI_ZM(16, 1);
   else if (r <= 32) CPHIFI_ZM(32, 2);

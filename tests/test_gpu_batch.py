@@ -15,7 +15,8 @@ import pytest
 import oracle as O
 import synth
 
-pytestmark = pytest.mark.gpu
+# every test here drives host-side request loops: bound each one
+pytestmark = [pytest.mark.gpu, pytest.mark.timeout(300)]
 
 
 @pytest.fixture(scope="module")
@@ -209,3 +210,34 @@ def test_poll_lists_completed_tickets(pkg, batch):
         W, st = r_.wait(timeout_us=0)  # already complete: returns at once
         np.testing.assert_array_equal(W, Wa)
     assert ctx.poll(done_cap=8) == (0, 0, [])
+
+
+def test_invalid_inputs_fail_the_request_only(pkg, batch):
+    # A submitted problem is created without waiting on the device; its input
+    # errors surface when the request completes, and the requests around it
+    # are unaffected.
+    ctx, probs, kerns, alone = batch
+    p, prec, tol = probs[0]
+    bad_k = p.kidx.copy()
+    bad_k[len(bad_k) // 2] = p.n + 3
+    order = np.argsort(p.kidx, kind="stable")
+    unsorted_k = p.kidx[order][::-1].copy()
+    unsorted_o = p.oidx[order][::-1].copy()
+    unsorted_v = p.vals[order][::-1].copy()
+    r0 = pkg.submit(ctx, kerns[0], p.factors, p.kidx, p.oidx, p.vals, p.r, p.lam, p.rho, tol,
+                    max_iter=2000, precision=prec)
+    r1 = pkg.submit(ctx, kerns[0], p.factors, bad_k, p.oidx, p.vals, p.r, p.lam, p.rho, tol,
+                    max_iter=2000, precision=prec)
+    r2 = pkg.submit(ctx, kerns[0], p.factors, unsorted_k, unsorted_o, unsorted_v, p.r, p.lam,
+                    p.rho, tol, max_iter=2000, precision=prec, sorted_obs=True)
+    r3 = pkg.submit(ctx, kerns[0], p.factors, p.kidx, p.oidx, p.vals, p.r, p.lam, p.rho, tol,
+                    max_iter=2000, precision=prec)
+    with pytest.raises(pkg.CphifiError) as e:
+        r1.wait()
+    assert e.value.status == pkg.E_INVALID_ARG and "out of range" in str(e.value)
+    with pytest.raises(pkg.CphifiError) as e:
+        r2.wait()
+    assert e.value.status == pkg.E_INVALID_ARG and "not sorted" in str(e.value)
+    for rq in (r0, r3):
+        W, st = rq.wait()
+        np.testing.assert_array_equal(W, alone[0][0])
