@@ -34,6 +34,10 @@ METRIC = "kernel-mode PCG obs*iter/s & solves/s, mixed vs FP64 at 1e-6 rel err; 
 UNIT = "obs*iter/s"
 WORKLOAD = "c3_mixed_n8000_q5e7_r40"
 TOL = 1e-6
+# DRAM bytes (read + write) per observation of the FP32 gather-dot/scatter
+# launch at r = 40, from one ncu capture of the same kernel at n = 2000,
+# q = 5e6 (813.1 MB per launch); traffic grows in proportion to q.
+GDS32_TRAFFIC_PER_OBS_R40 = 813.13e6 / 5e6
 MAX_ITER_BATCH = 5000
 
 
@@ -542,7 +546,9 @@ def main():
                 "iteration": iter_phase_ms / args.steps,
                 "final": sum(s["final_ms"] for s in stats) / args.steps},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "frac": (achieved / peak) if achieved else None,
+                         "traffic": (GDS32_TRAFFIC_PER_OBS_R40 * q
+                                     if r == 40 and args.precision == "mixed_fp32" else None),
                          "kernel": "gds_kernel<float> (gather-dot/scatter, Eqs. vl/yhat1)",
                          "peak_source": f"{peak_kind} hbm_gbs",
                          "bytes_per_launch": gds_bytes_per_launch,
