@@ -466,7 +466,19 @@ __device__ __forceinline__ void load_row_part(const float* __restrict__ base, bo
   }
 }
 
-template <int RP, int LPO>
+// Observations a warp stages at a time: their other-mode indices, values and
+// (unsorted input) source positions are copied to shared memory with
+// coalesced loads, so the latency of those HBM reads is paid once per window
+// instead of once per observation.
+constexpr int kZWin = 128;
+
+__host__ __device__ constexpr size_t zhat_warp_smem(int d_other) {
+  return (size_t)kZWin * (sizeof(double) + sizeof(int32_t) * (1 + d_other));
+}
+
+// W64: also store Zhat in FP64 (a template flag, so the FP64 conversions are
+// not executed, even speculatively, when only the FP32 pair is stored).
+template <int RP, int LPO, bool W64>
 __global__ void __launch_bounds__(256)
 zhat_mttkrp_kernel(PieceList pl, const int32_t* __restrict__ perm, const int32_t* __restrict__ oidx,
                    int d_other, const float* const* __restrict__ fhi,
@@ -476,76 +488,91 @@ zhat_mttkrp_kernel(PieceList pl, const int32_t* __restrict__ perm, const int32_t
                    double* __restrict__ partial, double* __restrict__ B, int64_t ldb, int* err,
                    const int* gate) {
   if (gate && *gate) return;  // invalid input found earlier: touch nothing
-  constexpr int OPW = 32 / LPO, CPL = RP / LPO, UN = 1;
+  constexpr int OPW = 32 / LPO, CPL = RP / LPO;
+  extern __shared__ __align__(16) unsigned char zsm[];
   const int lane = threadIdx.x & 31, sub = lane / OPW, o = lane % OPW;
+  const int wib = threadIdx.x >> 5;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned char* wsm = zsm + (size_t)wib * zhat_warp_smem(d_other);
+  double* vals_s = reinterpret_cast<double*>(wsm);
+  int32_t* src_s = reinterpret_cast<int32_t*>(vals_s + kZWin);
+  int32_t* oidx_s = src_s + kZWin;
   // 16-byte factor-row loads need r % 4 == 0 (rows start on 16 bytes) and a
   // whole lane block inside the row
   const bool vec = (r % 4 == 0) && ((sub + 1) * CPL <= r);
   int bad = 0;
   for (int w = gw; w < pl.nwarps; w += nwarps) {
-    const int p_end = pl.warp_first[w + 1];
-    for (int p = pl.warp_first[w]; p < p_end; ++p) {
+    const int p_first = pl.warp_first[w], p_end = pl.warp_first[w + 1];
+    if (p_first >= p_end) continue;
+    const int wend = pl.end[p_end - 1];  // piece ends are non-decreasing
+    int win_lo = 0, win_hi = 0;
+    for (int p = p_first; p < p_end; ++p) {
       const int seg = pl.seg[p];
       const int b = pl.beg[p], e = pl.end[p];
       df acc[CPL];
 #pragma unroll
       for (int c = 0; c < CPL; ++c) acc[c] = df{0.f, 0.f};
-      for (int l0 = b + o; l0 < e; l0 += UN * OPW) {
-        int64_t src[UN];
-        bool live[UN];
-#pragma unroll
-        for (int u = 0; u < UN; ++u) {
-          const int l = l0 + u * OPW;
-          live[u] = l < e;
-          src[u] = live[u] ? (perm ? (int64_t)perm[l] : (int64_t)l) : 0;
+      for (int base = b; base < e; base += OPW) {
+        if (base < win_lo || min(base + OPW, e) > win_hi) {  // warp-uniform
+          // stage observations [base, hi) of this warp's range
+          const int hi = min(base + kZWin, wend), cnt = hi - base;
+          __syncwarp();
+          if (perm) {
+            for (int k = lane; k < cnt; k += 32) src_s[k] = perm[base + k];
+            __syncwarp();
+            for (int k = lane; k < cnt * d_other; k += 32) {
+              const int sidx = k / d_other, m = k - sidx * d_other;
+              oidx_s[k] = oidx[(int64_t)src_s[sidx] * d_other + m];
+            }
+            for (int k = lane; k < cnt; k += 32) vals_s[k] = vals[src_s[k]];
+          } else {
+            const int32_t* og = oidx + (int64_t)base * d_other;
+            for (int k = lane; k < cnt * d_other; k += 32) oidx_s[k] = og[k];
+            for (int k = lane; k < cnt; k += 32) vals_s[k] = vals[base + k];
+          }
+          __syncwarp();
+          win_lo = base;
+          win_hi = hi;
         }
-        df t[UN];
-#pragma unroll
-        for (int u = 0; u < UN; ++u) t[u] = live[u] ? df_from_double(vals[src[u]]) : df{0.f, 0.f};
-        df z[UN][CPL];
+        const int l = base + o;
+        const bool live = l < e;
+        const int sl = live ? l - win_lo : 0;
+        const df t = live ? df_from_double(vals_s[sl]) : df{0.f, 0.f};
+        df z[CPL];
         for (int m = 0; m < d_other; ++m) {
           const int64_t nm = sizes[m];
-          int32_t im[UN];
-#pragma unroll
-          for (int u = 0; u < UN; ++u) im[u] = live[u] ? oidx[src[u] * d_other + m] : 0;
-#pragma unroll
-          for (int u = 0; u < UN; ++u) {
-            const bool ok = im[u] >= 0 && im[u] < nm;
-            bad |= (live[u] && !ok) ? 1 : 0;
-            const int64_t off = (ok ? im[u] : 0) * (int64_t)r + sub * CPL;
-            float h[CPL], lo[CPL];
-            if (vec) {
-              load_row_part<CPL>(fhi[m] + off, true, h);
-              load_row_part<CPL>(flo[m] + off, true, lo);
-            } else {
-#pragma unroll
-              for (int c = 0; c < CPL; ++c) {
-                const bool in = sub * CPL + c < r;
-                h[c] = in ? __ldg(fhi[m] + off + c) : 0.f;
-                lo[c] = in ? __ldg(flo[m] + off + c) : 0.f;
-              }
-            }
+          const int32_t im = live ? oidx_s[sl * d_other + m] : 0;
+          const bool ok = im >= 0 && im < nm;
+          bad |= (live && !ok) ? 1 : 0;
+          const int64_t off = (ok ? im : 0) * (int64_t)r + sub * CPL;
+          float h[CPL], lo[CPL];
+          if (vec) {
+            load_row_part<CPL>(fhi[m] + off, true, h);
+            load_row_part<CPL>(flo[m] + off, true, lo);
+          } else {
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {
-              const df f{ok ? h[c] : 0.f, ok ? lo[c] : 0.f};
-              z[u][c] = m == 0 ? f : df_mul(z[u][c], f);
+              const bool in = sub * CPL + c < r;
+              h[c] = in ? __ldg(fhi[m] + off + c) : 0.f;
+              lo[c] = in ? __ldg(flo[m] + off + c) : 0.f;
             }
           }
-        }
 #pragma unroll
-        for (int u = 0; u < UN; ++u) {
-          if (!live[u]) continue;
-          const int l = l0 + u * OPW;
+          for (int c = 0; c < CPL; ++c) {
+            const df f{ok ? h[c] : 0.f, ok ? lo[c] : 0.f};
+            z[c] = m == 0 ? f : df_mul(z[c], f);
+          }
+        }
+        if (live) {
 #pragma unroll
           for (int c = 0; c < CPL; ++c) {
             const int j = sub * CPL + c;
             if (j < r) {
               const int64_t zi = zidx(l, j, r);
-              if (zhi) { zhi[zi] = z[u][c].hi; zlo[zi] = z[u][c].lo; }
-              if (z64) z64[zi] = df_to_double(z[u][c]);
-              df_acc_prod(acc[c], t[u], z[u][c]);
+              if (zhi) { zhi[zi] = z[c].hi; zlo[zi] = z[c].lo; }
+              if constexpr (W64) z64[zi] = df_to_double(z[c]);
+              df_acc_prod(acc[c], t, z[c]);
             }
           }
         }
@@ -560,25 +587,47 @@ zhat_mttkrp_kernel(PieceList pl, const int32_t* __restrict__ perm, const int32_t
   if (bad) atomicOr(err, 1);
 }
 
+template <int RP, int LPO, bool W64>
+static cudaError_t zhat_launch(const PieceList& pl, int blocks, size_t smem, const int32_t* perm,
+                               const int32_t* oidx, int d_other, const float* const* fhi,
+                               const float* const* flo, const int64_t* sizes_dev, int r,
+                               const double* vals, float* zhi, float* zlo, double* z64,
+                               double* partial, double* B, int64_t ldb, int* err,
+                               const int* gate, cudaStream_t st) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(zhat_mttkrp_kernel<RP, LPO, W64>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  zhat_mttkrp_kernel<RP, LPO, W64><<<blocks, 256, smem, st>>>(pl, perm, oidx, d_other, fhi, flo,
+                                                         sizes_dev, r, vals, zhi, zlo, z64,
+                                                         partial, B, ldb, err, gate);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const int32_t* oidx,
                                int d_other, const float* const* fhi, const float* const* flo,
                                const int64_t* sizes_dev, int r, const double* vals, float* zhi,
                                float* zlo, double* z64, double* partial, double* B, int64_t ldb,
                                int* err, const int* gate, cudaStream_t st) {
   if (pl.npieces == 0 || pl.nwarps == 0) return cudaSuccess;
+  if (d_other < 1 || d_other > 16) return cudaErrorInvalidValue;
   const int blocks = (pl.nwarps + 7) / 8;
-#define CPHIFI_ZM(RPV, LPOV)                                                                  \
-  zhat_mttkrp_kernel<RPV, LPOV><<<blocks, 256, 0, st>>>(pl, perm, oidx, d_other, fhi, flo,   \
-                                                         sizes_dev, r, vals, zhi, zlo, z64,  \
-                                                         partial, B, ldb, err, gate)
+  const size_t smem = 8 * zhat_warp_smem(d_other);
+#define CPHIFI_ZM(RPV, LPOV)                                                                    \
+  return z64 ? zhat_launch<RPV, LPOV, true>(pl, blocks, smem, perm, oidx, d_other, fhi, flo,     \
+                                            sizes_dev, r, vals, zhi, zlo, z64, partial, B, ldb,  \
+                                            err, gate, st)                                       \
+             : zhat_launch<RPV, LPOV, false>(pl, blocks, smem, perm, oidx, d_other, fhi, flo,    \
+                                             sizes_dev, r, vals, zhi, zlo, z64, partial, B, ldb, \
+                                             err, gate, st)
   if (r <= 8) CPHIFI_ZM(8, 1);
-  else if (r <= 16) CPHIFI_ZM(16, 1);
-  else if (r <= 32) CPHIFI_ZM(32, 2);
-  else if (r <= 48) CPHIFI_ZM(48, 4);
-  else if (r <= 64) CPHIFI_ZM(64, 4);
-  else return cudaErrorInvalidValue;
+  if (r <= 16) CPHIFI_ZM(16, 1);
+  if (r <= 32) CPHIFI_ZM(32, 2);
+  if (r <= 48) CPHIFI_ZM(48, 4);
+  if (r <= 64) CPHIFI_ZM(64, 4);
 #undef CPHIFI_ZM
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------ gather-dot / scatter ----
