@@ -120,10 +120,9 @@ struct cphifi_problem {
   void* gds_partial = nullptr;  // npieces x 64 doubles
   // factors and their Gram
   std::vector<double*> factors;
-  std::vector<float*> fhi, flo;  // factors as double-float pairs
+  std::vector<float*> fhl;  // factors as row-major interleaved double-float pairs
   double** factors_dev = nullptr;
-  float** fhi_dev = nullptr;
-  float** flo_dev = nullptr;
+  float** fhl_dev = nullptr;
   int64_t* sizes_dev = nullptr;
   double *V = nullptr, *dV = nullptr, *UV = nullptr;
   float* UV32 = nullptr;
@@ -752,16 +751,13 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
   PCK(dalloc(P, &P->seg_count, n));
   PCK(dalloc(P, &P->seg_ticket, n));
   PCK(dalloc(P, &P->factors_dev, d_other));
-  PCK(dalloc(P, &P->fhi_dev, d_other));
-  PCK(dalloc(P, &P->flo_dev, d_other));
+  PCK(dalloc(P, &P->fhl_dev, d_other));
   PCK(dalloc(P, &P->sizes_dev, d_other));
   P->factors.resize(d_other);
-  P->fhi.resize(d_other);
-  P->flo.resize(d_other);
+  P->fhl.resize(d_other);
   for (int m = 0; m < d_other; ++m) {
     PCK(dalloc(P, &P->factors[m], (size_t)sizes[m] * r));
-    PCK(dalloc(P, &P->fhi[m], (size_t)sizes[m] * r));
-    PCK(dalloc(P, &P->flo[m], (size_t)sizes[m] * r));
+    PCK(dalloc(P, &P->fhl[m], (size_t)sizes[m] * r * 2));
   }
   PCK(dalloc(P, &P->V, r * r));
   PCK(dalloc(P, &P->dV, r));
@@ -817,16 +813,14 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
   // ---- factors
   PCK(cudaMemcpyAsync(P->factors_dev, P->factors.data(), d_other * sizeof(double*),
                       cudaMemcpyHostToDevice, st));
-  PCK(cudaMemcpyAsync(P->fhi_dev, P->fhi.data(), d_other * sizeof(float*),
-                      cudaMemcpyHostToDevice, st));
-  PCK(cudaMemcpyAsync(P->flo_dev, P->flo.data(), d_other * sizeof(float*),
+  PCK(cudaMemcpyAsync(P->fhl_dev, P->fhl.data(), d_other * sizeof(float*),
                       cudaMemcpyHostToDevice, st));
   PCK(cudaMemcpyAsync(P->sizes_dev, sizes.data(), d_other * sizeof(int64_t),
                       cudaMemcpyHostToDevice, st));
   for (int m = 0; m < d_other; ++m) {
     PCK(upload(P->factors[m], factors[m], (size_t)sizes[m] * r * sizeof(double), mem, st));
     PCK(launch_validate_dense(P->factors[m], sizes[m] * r, P->err, st));
-    PCK(launch_split_rows_df(P->factors[m], sizes[m], r, P->fhi[m], P->flo[m], st));
+    PCK(launch_split_rows_df(P->factors[m], sizes[m], r, P->fhl[m], st));
   }
 
   // ---- Gram V (§3) and eig(V) (Eq. eigV) on the side stream: they need only
@@ -905,8 +899,9 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
   PieceList pl{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket,
                P->warp_first, P->npieces, P->nwarps};
   PCK(launch_zhat_mttkrp(pl, (flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm, oidx_d, d_other,
-                         P->fhi_dev, P->flo_dev, P->sizes_dev, r, vals_d, P->zhi, P->zlo,
-                         P->z64, (double*)P->gds_partial, P->Bm, n, P->err, gate, st));
+                         P->fhl_dev, P->sizes_dev, r, vals_d, P->zhi, P->zlo,
+                         P->z64, (double*)P->gds_partial, P->Bm, n, P->err, gate,
+                         ctx->num_sms, q, st));
   PCK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
   if (async) {
     cudaEvent_t ev = nullptr;

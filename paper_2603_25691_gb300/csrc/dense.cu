@@ -300,25 +300,24 @@ cudaError_t launch_split_df(const double* X, const double* scale, int64_t rows, 
 }
 
 __global__ void split_rows_df_kernel(const double* __restrict__ X, int64_t rows, int cols,
-                                     float* __restrict__ hi, float* __restrict__ lo) {
+                                     float2* __restrict__ hl) {
   const int64_t total = rows * cols;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = t / cols;
     const int j = (int)(t % cols);
     const df d = df_from_double(X[i + rows * j]);
-    hi[t] = d.hi;
-    lo[t] = d.lo;
+    hl[t] = make_float2(d.hi, d.lo);
   }
 }
 
-cudaError_t launch_split_rows_df(const double* X, int64_t rows, int cols, float* hi, float* lo,
+cudaError_t launch_split_rows_df(const double* X, int64_t rows, int cols, float* hl,
                                  cudaStream_t st) {
   const int64_t total = rows * cols;
   if (total == 0) return cudaSuccess;
   int64_t b = (total + 255) / 256;
   if (b > 4096) b = 4096;
-  split_rows_df_kernel<<<(int)b, 256, 0, st>>>(X, rows, cols, hi, lo);
+  split_rows_df_kernel<<<(int)b, 256, 0, st>>>(X, rows, cols, reinterpret_cast<float2*>(hl));
   return cudaGetLastError();
 }
 

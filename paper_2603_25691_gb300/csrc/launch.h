@@ -58,8 +58,7 @@ __host__ __device__ __forceinline__ int64_t zidx(int64_t l, int j, int r) {
 __host__ __device__ __forceinline__ int64_t zhat_elems(int64_t q, int r) {
   return ((q + 31) >> 5) * 32 * (int64_t)r;
 }
-// Gather-dot/scatter (Eqs. vl and yhat1).  with_dot = false computes the
-// sparse MTTKRP B(i,:) = sum t_l Zhat(l,:) with t taken from `tvals`.
+// Gather-dot/scatter (Eqs. vl and yhat1) over the piece decomposition.
 struct PieceList {
   const int32_t* seg;
   const int32_t* beg;
@@ -84,15 +83,17 @@ cudaError_t launch_gds_df(const PieceList& pl, const float* zhi, const float* zl
                           const double* Xh, int64_t xld, double* partial, double* Y,
                           int64_t yld, const DevScalars* skip, cudaStream_t st);
 // Zhat (Eq. zhat) in sorted order, computed in double-float from the factors'
-// hi/lo parts (row-major n_m x r, see launch_split_rows_df), written as hi/lo FP32 pairs and/or FP64 (either may be NULL),
-// fused with the MTTKRP B(i,:) = sum_{i_l = i} t_l Zhat(l,:) (B column-major,
-// ld ldb, FP64 result).  perm = NULL: input already sorted.  Bad indices set
-// *err bit 1.
+// interleaved hi/lo rows (fhl[m], see launch_split_rows_df) and written as
+// hi/lo FP32 pairs and/or FP64 (zhi/zlo or z64 may be NULL, not both); then
+// the MTTKRP B(i,:) = sum_{i_l = i} t_l Zhat(l,:) (B column-major, ld ldb,
+// FP64-accurate) as the weights mode of the gather-dot/scatter.  perm = NULL:
+// input already sorted.  Bad indices set *err bit 1 (the MTTKRP then skips).
 cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const int32_t* oidx,
-                               int d_other, const float* const* fhi, const float* const* flo,
+                               int d_other, const float* const* fhl,
                                const int64_t* sizes_dev, int r, const double* vals,
                                float* zhi, float* zlo, double* z64, double* partial, double* B,
-                               int64_t ldb, int* err, const int* gate, cudaStream_t st);
+                               int64_t ldb, int* err, const int* gate, int num_sms, int64_t q,
+                               cudaStream_t st);
 
 // -------------------------------------------------------------- dense.cu ---
 // Skinny product C = op(A) diag(s) B for A n x n (op = identity when a_trans
@@ -114,9 +115,10 @@ cudaError_t launch_gemm_df(const float* Ahi, const float* Alo, int64_t lda, bool
                            int64_t ldc, int64_t split_stride, int n, int ncols, int nsplit,
                            const DevScalars* skip, cudaStream_t st);
 int gemm_df_pick_split(int n, int num_sms);
-// Row-major hi/lo split of a column-major rows x cols matrix X:
-// hi[i*cols + j] + lo[i*cols + j] = X[i + rows*j].
-cudaError_t launch_split_rows_df(const double* X, int64_t rows, int cols, float* hi, float* lo,
+// Row-major interleaved hi/lo split of a column-major rows x cols matrix X:
+// hl[2 (i*cols + j)] + hl[2 (i*cols + j) + 1] = X[i + rows*j] (a 32-byte sector
+// holds 4 consecutive elements of a row, hi and lo together).
+cudaError_t launch_split_rows_df(const double* X, int64_t rows, int cols, float* hl,
                                  cudaStream_t st);
 // out[t] = hi[t] + lo[t] in FP64.
 cudaError_t launch_join_df(const float* hi, const float* lo, int64_t total, double* out,

@@ -466,168 +466,81 @@ __device__ __forceinline__ void load_row_part(const float* __restrict__ base, bo
   }
 }
 
-// Observations a warp stages at a time: their other-mode indices, values and
-// (unsorted input) source positions are copied to shared memory with
-// coalesced loads, so the latency of those HBM reads is paid once per window
-// instead of once per observation.
-constexpr int kZWin = 128;
-
-__host__ __device__ constexpr size_t zhat_warp_smem(int d_other) {
-  return (size_t)kZWin * (sizeof(double) + sizeof(int32_t) * (1 + d_other));
-}
-
+// One lane per observation, tiles of 32 sorted observations taken grid-stride
+// by the warps: every column of a Zhat tile is written by one coalesced
+// 128-byte store per array.  Each lane walks the columns in groups of 4
+// (16-byte factor-row loads) and forms the double-float product over the
+// other modes.  No per-lane state survives a tile, so registers stay few and
+// the launch fills the SMs (the gathers from L2 need many warps in flight).
 // W64: also store Zhat in FP64 (a template flag, so the FP64 conversions are
 // not executed, even speculatively, when only the FP32 pair is stored).
-template <int RP, int LPO, bool W64>
+template <bool W64>
 __global__ void __launch_bounds__(256)
-zhat_mttkrp_kernel(PieceList pl, const int32_t* __restrict__ perm, const int32_t* __restrict__ oidx,
-                   int d_other, const float* const* __restrict__ fhi,
-                   const float* const* __restrict__ flo, const int64_t* __restrict__ sizes, int r,
-                   const double* __restrict__ vals, float* __restrict__ zhi,
-                   float* __restrict__ zlo, double* __restrict__ z64,
-                   double* __restrict__ partial, double* __restrict__ B, int64_t ldb, int* err,
-                   const int* gate) {
+zhat_build_kernel(int64_t q, const int32_t* __restrict__ perm, const int32_t* __restrict__ oidx,
+                  int d_other, const float* const* __restrict__ fhl,
+                  const int64_t* __restrict__ sizes, int r,
+                  float* __restrict__ zhi, float* __restrict__ zlo, double* __restrict__ z64,
+                  int* err, const int* gate) {
   if (gate && *gate) return;  // invalid input found earlier: touch nothing
-  constexpr int OPW = 32 / LPO, CPL = RP / LPO;
-  extern __shared__ __align__(16) unsigned char zsm[];
-  const int lane = threadIdx.x & 31, sub = lane / OPW, o = lane % OPW;
-  const int wib = threadIdx.x >> 5;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  unsigned char* wsm = zsm + (size_t)wib * zhat_warp_smem(d_other);
-  double* vals_s = reinterpret_cast<double*>(wsm);
-  int32_t* src_s = reinterpret_cast<int32_t*>(vals_s + kZWin);
-  int32_t* oidx_s = src_s + kZWin;
-  // 16-byte factor-row loads need r % 4 == 0 (rows start on 16 bytes) and a
-  // whole lane block inside the row
-  const bool vec = (r % 4 == 0) && ((sub + 1) * CPL <= r);
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t ntiles = (q + 31) >> 5;
+  const bool vec = (r % 4 == 0);  // 16-byte aligned factor rows
   int bad = 0;
-  for (int w = gw; w < pl.nwarps; w += nwarps) {
-    const int p_first = pl.warp_first[w], p_end = pl.warp_first[w + 1];
-    if (p_first >= p_end) continue;
-    const int wend = pl.end[p_end - 1];  // piece ends are non-decreasing
-    int win_lo = 0, win_hi = 0;
-    for (int p = p_first; p < p_end; ++p) {
-      const int seg = pl.seg[p];
-      const int b = pl.beg[p], e = pl.end[p];
-      df acc[CPL];
+  for (int64_t tile = gw; tile < ntiles; tile += nw) {
+    const int64_t l = tile * 32 + lane;
+    if (l >= q) continue;
+    const int64_t src = perm ? (int64_t)perm[l] : l;
+    const int32_t* im = oidx + src * d_other;
+    bool ok = true;
+    for (int m = 0; m < d_other; ++m) {
+      const int32_t v = __ldg(im + m);
+      ok = ok && v >= 0 && v < sizes[m];
+    }
+    bad |= ok ? 0 : 1;
+    const int64_t base = tile * 32 * (int64_t)r + lane;
+    for (int j0 = 0; j0 < r; j0 += 4) {
+      df z[4];
+      for (int m = 0; m < d_other; ++m) {
+        const int64_t off = (ok ? (int64_t)__ldg(im + m) : 0) * r + j0;
+        float h[4], lo[4];
+        if (vec) {  // columns j0..j0+3 as (hi, lo) pairs: one 32-byte sector
+          const float4* p4 = reinterpret_cast<const float4*>(fhl[m] + 2 * off);
+          const float4 a = __ldg(p4), c = __ldg(p4 + 1);
+          h[0] = a.x; lo[0] = a.y; h[1] = a.z; lo[1] = a.w;
+          h[2] = c.x; lo[2] = c.y; h[3] = c.z; lo[3] = c.w;
+        } else {
+          const float2* p2 = reinterpret_cast<const float2*>(fhl[m]) + off;
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) acc[c] = df{0.f, 0.f};
-      for (int base = b; base < e; base += OPW) {
-        if (base < win_lo || min(base + OPW, e) > win_hi) {  // warp-uniform
-          // stage observations [base, hi) of this warp's range
-          const int hi = min(base + kZWin, wend), cnt = hi - base;
-          __syncwarp();
-          if (perm) {
-            for (int k = lane; k < cnt; k += 32) src_s[k] = perm[base + k];
-            __syncwarp();
-            for (int k = lane; k < cnt * d_other; k += 32) {
-              const int sidx = k / d_other, m = k - sidx * d_other;
-              oidx_s[k] = oidx[(int64_t)src_s[sidx] * d_other + m];
-            }
-            for (int k = lane; k < cnt; k += 32) vals_s[k] = vals[src_s[k]];
-          } else {
-            const int32_t* og = oidx + (int64_t)base * d_other;
-            for (int k = lane; k < cnt * d_other; k += 32) oidx_s[k] = og[k];
-            for (int k = lane; k < cnt; k += 32) vals_s[k] = vals[base + k];
-          }
-          __syncwarp();
-          win_lo = base;
-          win_hi = hi;
-        }
-        const int l = base + o;
-        const bool live = l < e;
-        const int sl = live ? l - win_lo : 0;
-        const df t = live ? df_from_double(vals_s[sl]) : df{0.f, 0.f};
-        df z[CPL];
-        for (int m = 0; m < d_other; ++m) {
-          const int64_t nm = sizes[m];
-          const int32_t im = live ? oidx_s[sl * d_other + m] : 0;
-          const bool ok = im >= 0 && im < nm;
-          bad |= (live && !ok) ? 1 : 0;
-          const int64_t off = (ok ? im : 0) * (int64_t)r + sub * CPL;
-          float h[CPL], lo[CPL];
-          if (vec) {
-            load_row_part<CPL>(fhi[m] + off, true, h);
-            load_row_part<CPL>(flo[m] + off, true, lo);
-          } else {
-#pragma unroll
-            for (int c = 0; c < CPL; ++c) {
-              const bool in = sub * CPL + c < r;
-              h[c] = in ? __ldg(fhi[m] + off + c) : 0.f;
-              lo[c] = in ? __ldg(flo[m] + off + c) : 0.f;
-            }
-          }
-#pragma unroll
-          for (int c = 0; c < CPL; ++c) {
-            const df f{ok ? h[c] : 0.f, ok ? lo[c] : 0.f};
-            z[c] = m == 0 ? f : df_mul(z[c], f);
+          for (int u = 0; u < 4; ++u) {
+            const bool in = j0 + u < r;
+            const float2 v = in ? __ldg(p2 + u) : make_float2(0.f, 0.f);
+            h[u] = v.x;
+            lo[u] = v.y;
           }
         }
-        if (live) {
 #pragma unroll
-          for (int c = 0; c < CPL; ++c) {
-            const int j = sub * CPL + c;
-            if (j < r) {
-              const int64_t zi = zidx(l, j, r);
-              if (zhi) { zhi[zi] = z[c].hi; zlo[zi] = z[c].lo; }
-              if constexpr (W64) z64[zi] = df_to_double(z[c]);
-              df_acc_prod(acc[c], t, z[c]);
-            }
-          }
+        for (int u = 0; u < 4; ++u) {
+          const df f{ok ? h[u] : 0.f, ok ? lo[u] : 0.f};
+          z[u] = m == 0 ? f : df_mul(z[u], f);
         }
       }
-      double accd[CPL];
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) accd[c] = df_to_double(df_norm(acc[c]));
-      reduce_row<double, RP, LPO>(accd);
-      store_row<double, RP, LPO>(pl, p, seg, r, accd, partial, B, ldb);
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + u;
+        if (j < r) {
+          const int64_t zi = base + 32 * (int64_t)j;
+          if (zhi) {
+            __stcs(zhi + zi, z[u].hi);
+            __stcs(zlo + zi, z[u].lo);
+          }
+          if constexpr (W64) __stcs(z64 + zi, df_to_double(z[u]));
+        }
+      }
     }
   }
   if (bad) atomicOr(err, 1);
-}
-
-template <int RP, int LPO, bool W64>
-static cudaError_t zhat_launch(const PieceList& pl, int blocks, size_t smem, const int32_t* perm,
-                               const int32_t* oidx, int d_other, const float* const* fhi,
-                               const float* const* flo, const int64_t* sizes_dev, int r,
-                               const double* vals, float* zhi, float* zlo, double* z64,
-                               double* partial, double* B, int64_t ldb, int* err,
-                               const int* gate, cudaStream_t st) {
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(zhat_mttkrp_kernel<RP, LPO, W64>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  zhat_mttkrp_kernel<RP, LPO, W64><<<blocks, 256, smem, st>>>(pl, perm, oidx, d_other, fhi, flo,
-                                                         sizes_dev, r, vals, zhi, zlo, z64,
-                                                         partial, B, ldb, err, gate);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const int32_t* oidx,
-                               int d_other, const float* const* fhi, const float* const* flo,
-                               const int64_t* sizes_dev, int r, const double* vals, float* zhi,
-                               float* zlo, double* z64, double* partial, double* B, int64_t ldb,
-                               int* err, const int* gate, cudaStream_t st) {
-  if (pl.npieces == 0 || pl.nwarps == 0) return cudaSuccess;
-  if (d_other < 1 || d_other > 16) return cudaErrorInvalidValue;
-  const int blocks = (pl.nwarps + 7) / 8;
-  const size_t smem = 8 * zhat_warp_smem(d_other);
-#define CPHIFI_ZM(RPV, LPOV)                                                                    \
-  return z64 ? zhat_launch<RPV, LPOV, true>(pl, blocks, smem, perm, oidx, d_other, fhi, flo,     \
-                                            sizes_dev, r, vals, zhi, zlo, z64, partial, B, ldb,  \
-                                            err, gate, st)                                       \
-             : zhat_launch<RPV, LPOV, false>(pl, blocks, smem, perm, oidx, d_other, fhi, flo,    \
-                                             sizes_dev, r, vals, zhi, zlo, z64, partial, B, ldb, \
-                                             err, gate, st)
-  if (r <= 8) CPHIFI_ZM(8, 1);
-  if (r <= 16) CPHIFI_ZM(16, 1);
-  if (r <= 32) CPHIFI_ZM(32, 2);
-  if (r <= 48) CPHIFI_ZM(48, 4);
-  if (r <= 64) CPHIFI_ZM(64, 4);
-#undef CPHIFI_ZM
-  return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------ gather-dot / scatter ----
@@ -668,7 +581,10 @@ __device__ __forceinline__ float acc_out(float a) { return a; }
 __device__ __forceinline__ double acc_out(double a) { return a; }
 __device__ __forceinline__ double acc_out(df a) { return df_to_double(df_norm(a)); }
 
-template <int MODE, int RP, int LPO>
+// WTS (weights mode, the sparse MTTKRP B = T Z of §4): xbar_l is the given
+// weight t_l (wts[wperm[l]], or wts[l] without a permutation) instead of the
+// dot product, so Y(i,:) = sum_{i_l = i} t_l Zhat(l,:).
+template <int MODE, int RP, int LPO, bool WTS>
 __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __restrict__ zhi,
                                                   const float* __restrict__ zlo,
                                                   const double* __restrict__ z64, int r,
@@ -676,10 +592,13 @@ __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __r
                                                   int64_t xld,
                                                   typename GdsTypes<MODE>::IO* __restrict__ partial,
                                                   typename GdsTypes<MODE>::IO* __restrict__ Y,
-                                                  int64_t yld, const DevScalars* skip) {
+                                                  int64_t yld, const DevScalars* skip,
+                                                  const double* __restrict__ wts,
+                                                  const int32_t* __restrict__ wperm,
+                                                  const int* gate) {
   using IO = typename GdsTypes<MODE>::IO;
   using Acc = typename GdsTypes<MODE>::Acc;
-  if (dev_skip(skip)) return;
+  if (dev_skip(skip) || (gate && *gate)) return;
   constexpr int OPW = 32 / LPO, CPL = RP / LPO;
   __shared__ Acc xs[8][RP];
   const int lane = threadIdx.x & 31, sub = lane / OPW, o = lane % OPW;
@@ -691,13 +610,15 @@ __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __r
     for (int p = pl.warp_first[w]; p < p_end; ++p) {
       const int seg = pl.seg[p];
       const int b = pl.beg[p], e = pl.end[p];
-      __syncwarp();
-      for (int j = lane; j < RP; j += 32) {
-        const IO v = j < r ? Xh[(int64_t)j * xld + seg] : IO(0);
-        if constexpr (MODE == GDS_DF) xs[wib][j] = df_from_double(v);
-        else xs[wib][j] = v;
+      if constexpr (!WTS) {
+        __syncwarp();
+        for (int j = lane; j < RP; j += 32) {
+          const IO v = j < r ? Xh[(int64_t)j * xld + seg] : IO(0);
+          if constexpr (MODE == GDS_DF) xs[wib][j] = df_from_double(v);
+          else xs[wib][j] = v;
+        }
+        __syncwarp();
       }
-      __syncwarp();
       Acc acc[CPL];
 #pragma unroll
       for (int c = 0; c < CPL; ++c) acc[c] = acc_zero(Acc());
@@ -717,10 +638,15 @@ __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __r
           else z[c] = ld ? df{__ldcs(zhi + base + 32 * j), __ldcs(zlo + base + 32 * j)}
                          : df{0.f, 0.f};
         }
+        Acc xb;
+        if constexpr (WTS) {
+          const double t = act ? wts[wperm ? (int64_t)wperm[l] : (int64_t)l] : 0.0;
+          if constexpr (MODE == GDS_DF) xb = df_from_double(t);
+          else xb = (Acc)t;
+        } else {
         Acc dot = acc_zero(Acc());
 #pragma unroll
         for (int c = 0; c < CPL; ++c) acc_fma(dot, xs[wib][sub * CPL + c], z[c]);
-        Acc xb;
         if constexpr (MODE == GDS_DF) {
           df d = df_norm(dot);
           // sum the partial dots of the LPO lanes of this observation
@@ -734,6 +660,7 @@ __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __r
         } else {
           xb = LPO > 1 ? sum_over_subs<Acc, LPO>(dot) : dot;
         }
+        }
 #pragma unroll
         for (int c = 0; c < CPL; ++c) acc_fma(acc[c], xb, z[c]);
       }
@@ -746,15 +673,28 @@ __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __r
   }
 }
 
+struct GdsWeights {
+  const double* wts = nullptr;    // non-null: weights mode
+  const int32_t* wperm = nullptr;
+  const int* gate = nullptr;
+};
+
 template <int MODE, int RP, int LPO>
 static cudaError_t gds_dispatch(const PieceList& pl, const float* zhi, const float* zlo,
                                 const double* z64, int r, const typename GdsTypes<MODE>::IO* Xh,
                                 int64_t xld, typename GdsTypes<MODE>::IO* partial,
                                 typename GdsTypes<MODE>::IO* Y, int64_t yld,
-                                const DevScalars* skip, cudaStream_t st) {
+                                const DevScalars* skip, cudaStream_t st,
+                                const GdsWeights& wt = GdsWeights()) {
   const int blocks = (pl.nwarps + 7) / 8;
-  gds_kernel<MODE, RP, LPO><<<blocks, 256, 0, st>>>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y,
-                                                    yld, skip);
+  if (wt.wts)
+    gds_kernel<MODE, RP, LPO, true><<<blocks, 256, 0, st>>>(pl, zhi, zlo, z64, r, Xh, xld, partial,
+                                                            Y, yld, skip, wt.wts, wt.wperm,
+                                                            wt.gate);
+  else
+    gds_kernel<MODE, RP, LPO, false><<<blocks, 256, 0, st>>>(pl, zhi, zlo, z64, r, Xh, xld,
+                                                             partial, Y, yld, skip, nullptr,
+                                                             nullptr, nullptr);
   return cudaGetLastError();
 }
 
@@ -765,15 +705,50 @@ static cudaError_t gds_by_rank(const PieceList& pl, const float* zhi, const floa
                                const double* z64, int r, const typename GdsTypes<MODE>::IO* Xh,
                                int64_t xld, typename GdsTypes<MODE>::IO* partial,
                                typename GdsTypes<MODE>::IO* Y, int64_t yld,
-                               const DevScalars* skip, cudaStream_t st) {
+                               const DevScalars* skip, cudaStream_t st,
+                               const GdsWeights& wt = GdsWeights()) {
   if (pl.npieces == 0 || pl.nwarps == 0) return cudaSuccess;
   constexpr bool wide = MODE != GDS_F32;
-  if (r <= 8) return gds_dispatch<MODE, 8, 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st);
-  if (r <= 16) return gds_dispatch<MODE, 16, 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st);
-  if (r <= 32) return gds_dispatch<MODE, 32, wide ? 2 : 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st);
-  if (r <= 48) return gds_dispatch<MODE, 48, wide ? 4 : 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st);
-  if (r <= 64) return gds_dispatch<MODE, 64, wide ? 4 : 2>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st);
+  if (r <= 8) return gds_dispatch<MODE, 8, 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
+  if (r <= 16) return gds_dispatch<MODE, 16, 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
+  if (r <= 32) return gds_dispatch<MODE, 32, wide ? 2 : 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
+  if (r <= 48) return gds_dispatch<MODE, 48, wide ? 4 : 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
+  if (r <= 64) return gds_dispatch<MODE, 64, wide ? 4 : 2>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
   return cudaErrorInvalidValue;
+}
+
+// Zhat, then the sparse MTTKRP B = T Z as the weights mode of the
+// gather-dot/scatter (double-float from hi + lo, or FP64 from z64).
+cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const int32_t* oidx,
+                               int d_other, const float* const* fhl,
+                               const int64_t* sizes_dev, int r, const double* vals, float* zhi,
+                               float* zlo, double* z64, double* partial, double* B, int64_t ldb,
+                               int* err, const int* gate, int num_sms, int64_t q,
+                               cudaStream_t st) {
+  if (q == 0 || pl.npieces == 0 || pl.nwarps == 0) return cudaSuccess;
+  if (d_other < 1 || d_other > 16 || r < 1 || r > 64 || (!zhi && !z64) || (zhi && !zlo))
+    return cudaErrorInvalidValue;
+  const int64_t tiles = (q + 31) / 32;
+  int64_t blocks = (tiles + 7) / 8;
+  const int64_t cap = (int64_t)num_sms * 8;  // 8 resident 256-thread blocks per SM
+  if (blocks > cap) blocks = cap;
+  if (z64)
+    zhat_build_kernel<true><<<(int)blocks, 256, 0, st>>>(q, perm, oidx, d_other, fhl,
+                                                         sizes_dev, r, zhi, zlo, z64, err, gate);
+  else
+    zhat_build_kernel<false><<<(int)blocks, 256, 0, st>>>(q, perm, oidx, d_other, fhl,
+                                                          sizes_dev, r, zhi, zlo, z64, err, gate);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  GdsWeights wt;
+  wt.wts = vals;
+  wt.wperm = perm;
+  wt.gate = err;  // no MTTKRP over invalid indices (the build flags them)
+  if (zhi)
+    return gds_by_rank<GDS_DF>(pl, zhi, zlo, nullptr, r, nullptr, 0, partial, B, ldb, nullptr, st,
+                               wt);
+  return gds_by_rank<GDS_F64>(pl, nullptr, nullptr, z64, r, nullptr, 0, partial, B, ldb, nullptr,
+                              st, wt);
 }
 
 cudaError_t launch_gds_f32(const PieceList& pl, const float* zhi, int r, const float* Xh,
