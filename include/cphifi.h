@@ -95,6 +95,9 @@ typedef enum cphifi_precision {
 #define CPHIFI_NEED_LOWP 0x4u   /* build the hi/lo FP32 operator data (other
                                    modes); neither flag: both are built; a mode
                                    whose data is missing builds it on first use */
+#define CPHIFI_KEEP_OBS 0x8u    /* keep the observation lists on the device in
+                                   sorted order: needed by the alternating-fit
+                                   calls (set_factors, update_factor, fit) */
 
 typedef struct cphifi_params {
   double lambda;      /* RKHS regularisation, >= 0 (§2)                       */
@@ -295,6 +298,53 @@ int cphifi_problem_gram(cphifi_problem* prob, double* V, double* DV,
  * row_ptr[i+1]).  Host memory only; either may be NULL. */
 int cphifi_problem_order(cphifi_problem* prob, int32_t* perm,
                          int64_t* row_ptr);
+
+/* ---- the alternating fit around the kernel-mode solve (§2) ----------------
+ * The CP-HIFI model (§2) is a rank-r CP tensor whose kernel-mode factor is
+ * A_k = K W and whose other (finite) modes have plain factors A_m; it is fit
+ * by alternating over the modes (§2, Eq. cp-hifi-subproblem).  The kernel
+ * mode is the PCG solve above; a finite mode has no regulariser (R_m = 0,
+ * §2), so its update is the CP-ALS step for incomplete data: with
+ * z_l = A_k(i_l,:) o prod_{m' != m} A_m'(i_m'^l,:), row i of A_m solves the
+ * r x r normal equations G_i a = h_i, G_i = sum z_l z_l', h_i = sum t_l z_l
+ * over the observations with i_m^l = i (FP64 sums, Cholesky).  The paper
+ * only cites this step as known; this library adds 1e-12 trace(G_i) to the
+ * diagonal of rows with fewer than r observations and leaves rows without
+ * observations (or whose G_i is not positive definite after that) unchanged.
+ * These calls need a problem created with CPHIFI_KEEP_OBS.
+ *
+ * cphifi_problem_set_factors: replaces the finite factors (n_m x r,
+ *   column-major, memory kind mem) and rebuilds what depends on them (Zhat,
+ *   the MTTKRP B, V, eig(V)); the observation order is kept.
+ * cphifi_problem_update_factor: the CP-ALS update of finite mode m for the
+ *   kernel weights W (n x r): A_k = U_K (D_K o (U_K' W)) in FP64, the
+ *   normal equations, Cholesky.  The new factor replaces the problem's
+ *   (and is copied to A_out, n_m x r, when A_out is not NULL); the data that
+ *   depend on it are rebuilt before the next solve.
+ * cphifi_problem_fit: for the model (K W, the problem's factors), the sums
+ *   sum_l (t_l - m_l)^2 and sum_l t_l^2 in FP64 (either output may be NULL).
+ * cphifi_als: the alternating fit.  Creates a problem (CPHIFI_KEEP_OBS
+ *   added to flags), then per sweep: the kernel-mode PCG solve (params;
+ *   warm started from the previous W, or from W_io when `warm` is set),
+ *   the finite modes in order, and the relative fit error
+ *   ||t - m|| / ||t|| into err_out[sweep] (err_out holds `sweeps` values).
+ *   Stops after `sweeps` sweeps or when the error changes by less than
+ *   als_tol (§5: tolerance on the change in the ALS error).  factors_io
+ *   (d_other pointers, each n_m x r) are read as the start and overwritten
+ *   with the fitted factors; W_io (n x r) receives the fitted weights.  All
+ *   in memory kind mem.  *sweeps_done (may be NULL) gets the number of
+ *   sweeps run; `stats` (may be NULL) the last kernel-mode solve's stats. */
+int cphifi_problem_set_factors(cphifi_problem* prob, const double* const* factors, int mem);
+int cphifi_problem_update_factor(cphifi_problem* prob, int32_t mode, const double* W,
+                                 double* A_out, int mem);
+int cphifi_problem_fit(cphifi_problem* prob, const double* W, int mem, double* res2,
+                       double* t2);
+int cphifi_als(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
+               const int64_t* other_sizes, double* const* factors_io, int32_t r,
+               int64_t q, const int32_t* kidx, const int32_t* oidx, const double* vals,
+               uint32_t flags, const cphifi_params* params, int32_t sweeps, double als_tol,
+               int32_t warm, double* W_io, double* err_out, int32_t* sweeps_done, int mem,
+               cphifi_stats* stats);
 
 /* ---- allocation-free entry point -----------------------------------------
  * cphifi_gds_noalloc: the gather-dot/scatter product of the solver, FP64,

@@ -47,6 +47,7 @@ PRECISIONS = {"fp64": FP64, "mixed_fp32": MIXED_FP32, "mixed_tf32": MIXED_TF32,
               "mixed_bf16": MIXED_BF16, "fp64_emulated": FP64_EMULATED,
               "mixed_tf32x3": MIXED_TF32X3}
 NEED_FP64 = 0x2
+KEEP_OBS = 0x8
 
 
 class Params(ctypes.Structure):
@@ -112,6 +113,15 @@ _SIG = {
     "cphifi_problem_gram": (ctypes.c_int, [_P, _P, _P, _P]),
     "cphifi_problem_order": (ctypes.c_int, [_P, _P, _P]),
     "cphifi_ctx_set_slots": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cphifi_problem_set_factors": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "cphifi_problem_update_factor": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int]),
+    "cphifi_problem_fit": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]),
+    "cphifi_als": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_int64,
+                                  _P, _P, _P, ctypes.c_uint32, ctypes.POINTER(Params),
+                                  ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P, _P,
+                                  ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
+                                  ctypes.POINTER(Stats)]),
     "cphifi_submit": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32,
                                      ctypes.c_int64, _P, _P, _P, ctypes.c_uint32,
                                      ctypes.POINTER(Params), _P, _P, ctypes.c_int,
@@ -285,9 +295,10 @@ class Problem:
     """cphifi_problem_create: one subproblem (sort, Zhat, Gram, eig(V), B)."""
 
     def __init__(self, ctx: Context, kernel: Kernel, factors, kidx, oidx, vals, r: int,
-                 sorted_obs: bool = False, lowp: bool | None = None):
+                 sorted_obs: bool = False, lowp: bool | None = None, keep_obs: bool = False):
         # lowp: True = build only the hi/lo data of the mixed/emulated modes,
-        # False = only the FP64 data, None = both.
+        # False = only the FP64 data, None = both.  keep_obs: keep the sorted
+        # observation lists (needed by the alternating-fit calls).
         self.ctx, self.kernel, self.r = ctx, kernel, int(r)
         self.n = kernel.n
         fb, sizes = _factor_bufs(factors, self.r)
@@ -299,7 +310,7 @@ class Problem:
         self.sizes = sizes
         sizes_arr = (ctypes.c_int64 * len(sizes))(*sizes)
         fptrs = (ctypes.c_void_p * len(fb))(*[b.ptr for b in fb])
-        flags = (OBS_SORTED if sorted_obs else 0)
+        flags = (OBS_SORTED if sorted_obs else 0) | (KEEP_OBS if keep_obs else 0)
         if lowp is True:
             flags |= NEED_LOWP
         elif lowp is False:
@@ -386,6 +397,31 @@ class Problem:
                                                      UV.ctypes.data), "problem_gram")
         return V, DV, UV
 
+    def set_factors(self, factors) -> None:
+        """cphifi_problem_set_factors: new finite factors (host arrays)."""
+        fb = [_Buf(F, np.float64, colmajor=True) for F in factors]
+        fptrs = (ctypes.c_void_p * len(fb))(*[b.ptr for b in fb])
+        _check(self.ctx.h, lib().cphifi_problem_set_factors(self.h, fptrs, MEM_HOST),
+               "problem_set_factors")
+
+    def update_factor(self, mode: int, W):
+        """cphifi_problem_update_factor: the CP-ALS update of finite mode
+        `mode` for weights W; returns the new factor (n_m, r)."""
+        w = _Buf(W, np.float64, colmajor=True)
+        A = np.empty((self.sizes[mode], self.r), order="F")
+        _check(self.ctx.h, lib().cphifi_problem_update_factor(self.h, int(mode), w.ptr,
+                                                              A.ctypes.data, MEM_HOST),
+               "problem_update_factor")
+        return A
+
+    def fit(self, W):
+        """cphifi_problem_fit: (sum (t - m)^2, sum t^2) of the model K W."""
+        w = _Buf(W, np.float64, colmajor=True)
+        r2, t2 = ctypes.c_double(), ctypes.c_double()
+        _check(self.ctx.h, lib().cphifi_problem_fit(self.h, w.ptr, MEM_HOST, ctypes.byref(r2),
+                                                    ctypes.byref(t2)), "problem_fit")
+        return r2.value, t2.value
+
     def order(self):
         """cphifi_problem_order: (perm, row_ptr) of the stable sort by kernel index."""
         perm = np.empty(self.q, dtype=np.int32)
@@ -430,6 +466,33 @@ def solve(ctx: Context, kernel: Kernel, factors, kidx, oidx, vals, r: int, lam: 
     if rc not in (OK, E_NOT_CONVERGED):
         _check(ctx.h, rc, "solve")
     return wb.obj, st.as_dict()
+
+
+def als(ctx: Context, kernel: Kernel, factors, kidx, oidx, vals, r: int, lam: float, rho: float,
+        tol: float, sweeps: int, als_tol: float = 0.0, max_iter: int = 1000, precision="fp64",
+        sorted_obs=False, k_replace=10, check_every=8, W0=None):
+    """cphifi_als on host arrays: the alternating fit (§2).  `factors` is the
+    start; returns (W, fitted factors, fit errors per sweep, last solve's stats)."""
+    facs = [np.array(F, dtype=np.float64, order="F") for F in factors]
+    k, o, v = _obs_bufs(kidx, oidx, vals)
+    if k.mem != MEM_HOST:
+        raise ValueError("als() takes host arrays")
+    n = kernel.n
+    W = np.zeros((n, r), order="F") if W0 is None else np.array(W0, dtype=np.float64, order="F")
+    sizes = [F.shape[0] for F in facs]
+    sizes_arr = (ctypes.c_int64 * len(sizes))(*sizes)
+    fptrs = (ctypes.c_void_p * len(facs))(*[F.ctypes.data for F in facs])
+    prm = make_params(lam, rho, tol, max_iter, precision, k_replace, check_every, False)
+    errs = np.zeros(sweeps)
+    done = ctypes.c_int32()
+    st = Stats()
+    rc = lib().cphifi_als(ctx.h, kernel.h, len(facs), sizes_arr, fptrs, int(r), k.numel, k.ptr,
+                          o.ptr, v.ptr, OBS_SORTED if sorted_obs else 0, ctypes.byref(prm),
+                          int(sweeps), float(als_tol), 1 if W0 is not None else 0,
+                          W.ctypes.data, errs.ctypes.data, ctypes.byref(done), MEM_HOST,
+                          ctypes.byref(st))
+    _check(ctx.h, rc, "als")
+    return W, facs, errs[:done.value], st.as_dict()
 
 
 class Request:

@@ -157,6 +157,19 @@ struct cphifi_problem {
   DevScalars* s2 = nullptr;   // scalars of the step-by-step calls
   int* err = nullptr;
   int64_t create_launches = 0;
+  // alternating fit (CPHIFI_KEEP_OBS): observation lists in the sorted order,
+  // per-finite-mode sort (built on first use), A_k = K W, and whether the
+  // factors changed since Zhat / B / V were built.
+  bool keep_obs = false;
+  int32_t* kidx_s = nullptr;
+  int32_t* oidx_s = nullptr;
+  double* vals_s = nullptr;
+  std::vector<int32_t*> perm_m;
+  std::vector<int64_t*> rowp_m;
+  double* Ak = nullptr;
+  double* fit2 = nullptr;  // 2 doubles
+  int* nfail = nullptr;
+  bool stale = false;
 };
 
 // ------------------------------------------------------------ helpers -----
@@ -642,6 +655,9 @@ static void problem_need(const cphifi_ctx* ctx, int n, bool tc, int32_t d_other,
           (need64 ? (size_t)zhat_elems(q, r) * sizeof(double) : 0);
   *tmp = (size_t)q * (sizeof(int32_t) * (1 + d_other) + sizeof(double) * 2 + sizeof(uint32_t)) +
          radix_sort_tmp_bytes(q);
+  if (flags & CPHIFI_KEEP_OBS)  // sorted observation lists + A_k
+    *need += (size_t)q * (sizeof(int32_t) * (1 + d_other) + sizeof(double)) +
+             (size_t)n * r * sizeof(double);
 }
 
 // Problem creation on stream `st` (the context's stream for the public call, a
@@ -902,6 +918,19 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
                          P->fhl_dev, P->sizes_dev, r, vals_d, P->zhi, P->zlo,
                          P->z64, (double*)P->gds_partial, P->Bm, n, P->err, gate,
                          ctx->num_sms, q, st));
+  if (flags & CPHIFI_KEEP_OBS) {
+    P->keep_obs = true;
+    PCK(dalloc(P, &P->kidx_s, (size_t)q));
+    PCK(dalloc(P, &P->oidx_s, (size_t)q * d_other));
+    PCK(dalloc(P, &P->vals_s, (size_t)q));
+    PCK(dalloc(P, &P->Ak, (size_t)n * r));
+    PCK(dalloc(P, &P->fit2, 2));
+    PCK(dalloc(P, &P->nfail, 4));
+    P->perm_m.assign(d_other, nullptr);
+    P->rowp_m.assign(d_other, nullptr);
+    PCK(launch_keep_obs(q, d_other, keys, (flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm,
+                        oidx_d, vals_d, P->kidx_s, P->oidx_s, P->vals_s, gate, st));
+  }
   PCK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
   if (async) {
     cudaEvent_t ev = nullptr;
@@ -1555,6 +1584,127 @@ struct SolveRun {
 
 // Checks that do not touch the device, then the operator data the precision
 // needs.
+// ------------------------------------------------ alternating fit (§2) ----
+// Rebuilds what depends on the finite factors (their double-float rows, V,
+// eig(V), Zhat, the MTTKRP B) from the kept sorted observation lists; the
+// order, pieces and density are unchanged.  Synchronous; input errors (a
+// non-finite factor) give CPHIFI_E_INVALID_ARG.
+static int problem_rebuild(cphifi_problem* P) {
+  cphifi_ctx* ctx = P->ctx;
+  cudaStream_t st = P->st;
+  const int r = P->r, d = P->d_other;
+  CK(cudaMemsetAsync(P->err, 0, sizeof(int), st));
+  for (int m = 0; m < d; ++m) {
+    CK(launch_validate_dense(P->factors[m], P->sizes[m] * r, P->err, st));
+    CK(launch_split_rows_df(P->factors[m], P->sizes[m], r, P->fhl[m], st));
+  }
+  CK(launch_gram(P->factors_dev, P->sizes_dev, d, r, P->V, st));
+  CK(launch_jacobi_eig(P->V, r, P->dV, P->UV, 60, P->info, st));
+  CK(launch_convert<double, float>(P->UV, P->UV32, (int64_t)r * r, st));
+  const PieceList pl{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket,
+                     P->warp_first, P->npieces, P->nwarps};
+  CK(launch_zhat_mttkrp(pl, nullptr, P->oidx_s, d, P->fhl_dev, P->sizes_dev, r, P->vals_s,
+                        P->zhi, P->zlo, P->z64, (double*)P->gds_partial, P->Bm, P->n, P->err,
+                        nullptr, ctx->num_sms, P->q, st));
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (herr) return fail(ctx, CPHIFI_E_INVALID_ARG, input_error_text(herr));
+  P->stale = false;
+  return CPHIFI_OK;
+}
+
+// A_k = K W = U_K (D_K o (U_K' W)) in FP64 into P->Ak; W is a device n x r
+// array (column-major).
+static cudaError_t kernel_factor(cphifi_problem* P, const double* Wd) {
+  Launcher L{P, P->st, nullptr};
+  double* Cp = (double*)P->cpart;
+  cudaError_t e = L.gemm64(false, nullptr, Wd, Cp, nullptr, 0);
+  if (e == cudaSuccess) e = L.combine<double, double>(CM_STORE, Cp, nullptr, nullptr, P->tmp64b,
+                                                      P->s2, nullptr, P->nsplit64);
+  if (e == cudaSuccess) e = L.gemm64(true, P->kern->dK, P->tmp64b, Cp, nullptr, 0);
+  if (e == cudaSuccess) e = L.combine<double, double>(CM_STORE, Cp, nullptr, nullptr, P->Ak, P->s2,
+                                                      nullptr, P->nsplit64);
+  return e;
+}
+
+// W (host or device) into P->tmp64, then A_k.
+static int load_weights(cphifi_problem* P, const double* W, int mem) {
+  cphifi_ctx* ctx = P->ctx;
+  if (!W) return fail(ctx, CPHIFI_E_INVALID_ARG, "null W");
+  if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
+  CK(upload(P->tmp64, W, (size_t)P->n * P->r * sizeof(double), mem, P->st));
+  CK(launch_validate_dense(P->tmp64, (int64_t)P->n * P->r, P->err, P->st));
+  CK(kernel_factor(P, P->tmp64));
+  return CPHIFI_OK;
+}
+
+static int update_factor(cphifi_problem* P, int m, const double* W, double* A_out, int mem) {
+  cphifi_ctx* ctx = P->ctx;
+  if (!P->keep_obs) return fail(ctx, CPHIFI_E_INVALID_ARG, "problem created without CPHIFI_KEEP_OBS");
+  if (m < 0 || m >= P->d_other) return fail(ctx, CPHIFI_E_INVALID_ARG, "mode out of range");
+  cudaStream_t st = P->st;
+  const int64_t q = P->q;
+  const int64_t nm = P->sizes[m];
+  if (nm > (int64_t(1) << 30)) return fail(ctx, CPHIFI_E_UNSUPPORTED, "finite mode too large");
+  CK(cudaMemsetAsync(P->err, 0, sizeof(int), st));
+  if (!P->perm_m[m]) {  // the mode-m order of the observations, once
+    CK(dalloc(P, &P->perm_m[m], (size_t)std::max<int64_t>(q, 1)));
+    CK(dalloc(P, &P->rowp_m[m], (size_t)nm + 1));
+    void* keys = nullptr;
+    void* rtmp = nullptr;
+    size_t gk = 0, gr = 0;
+    CK(pool_alloc(ctx, (size_t)std::max<int64_t>(q, 1) * sizeof(uint32_t), &keys, &gk));
+    cudaError_t e = pool_alloc(ctx, radix_sort_tmp_bytes(q), &rtmp, &gr);
+    if (e == cudaSuccess) e = launch_mode_keys(q, P->d_other, m, P->oidx_s, (uint32_t*)keys, st);
+    if (e == cudaSuccess) e = launch_iota(P->perm_m[m], q, st);
+    if (e == cudaSuccess && q > 1)
+      e = radix_sort_pairs((uint32_t*)keys, P->perm_m[m], q, bits_for((int)nm), rtmp, st);
+    if (e == cudaSuccess) e = launch_row_ptr((const uint32_t*)keys, q, (int)nm, P->rowp_m[m], st);
+    cudaStreamSynchronize(st);
+    if (rtmp) pool_release(ctx, rtmp, gr);
+    pool_release(ctx, keys, gk);
+    CK(e);
+  }
+  int rc = load_weights(P, W, mem);
+  if (rc != CPHIFI_OK) return rc;
+  CK(cudaMemsetAsync(P->nfail, 0, sizeof(int), st));
+  CK(launch_als_rows((int)nm, m, P->d_other, P->r, P->n, P->rowp_m[m], P->perm_m[m], P->kidx_s,
+                     P->oidx_s, P->vals_s, P->Ak, (const double* const*)P->factors_dev,
+                     P->sizes_dev, P->factors[m], P->nfail, ctx->num_sms, st));
+  if (A_out) CK(download(A_out, P->factors[m], (size_t)nm * P->r * sizeof(double), mem, st));
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  P->stale = true;
+  if (herr) return fail(ctx, CPHIFI_E_INVALID_ARG, "non-finite weight W");
+  return CPHIFI_OK;
+}
+
+static int problem_fit(cphifi_problem* P, const double* W, int mem, double* res2, double* t2) {
+  cphifi_ctx* ctx = P->ctx;
+  if (!P->keep_obs) return fail(ctx, CPHIFI_E_INVALID_ARG, "problem created without CPHIFI_KEEP_OBS");
+  cudaStream_t st = P->st;
+  CK(cudaMemsetAsync(P->err, 0, sizeof(int), st));
+  int rc = load_weights(P, W, mem);
+  if (rc != CPHIFI_OK) return rc;
+  double h[2] = {0.0, 0.0};
+  if (P->q > 0) {
+    CK(launch_fit(P->q, P->d_other, P->r, P->n, P->kidx_s, P->oidx_s, P->vals_s, P->Ak,
+                  (const double* const*)P->factors_dev, P->sizes_dev, P->red, P->fit2,
+                  ctx->num_sms, st));
+    CK(cudaMemcpyAsync(h, P->fit2, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (herr) return fail(ctx, CPHIFI_E_INVALID_ARG, "non-finite weight W");
+  if (res2) *res2 = h[0];
+  if (t2) *t2 = h[1];
+  return CPHIFI_OK;
+}
+
 static int solve_prepare(cphifi_problem* P, const cphifi_params* prm, double* W_out, int mem) {
   cphifi_ctx* ctx = P->ctx;
   int rc = check_params(ctx, prm);
@@ -1562,6 +1712,10 @@ static int solve_prepare(cphifi_problem* P, const cphifi_params* prm, double* W_
   if (!W_out) return fail(ctx, CPHIFI_E_INVALID_ARG, "null W_out");
   if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
+  if (P->stale) {
+    const int rc = problem_rebuild(P);
+    if (rc != CPHIFI_OK) return rc;
+  }
   const int prec = prm->precision;
   if (is_tc(prec) && !P->kern->tc)
     return fail(ctx, CPHIFI_E_UNSUPPORTED, "tensor-core products unavailable for this kernel");
@@ -1982,6 +2136,118 @@ extern "C" int cphifi_problem_precond(cphifi_problem* P, double lambda, double r
   CK(download(Y, P->tmp64b, nr * sizeof(double), mem, st));
   CK(cudaStreamSynchronize(st));
   return CPHIFI_OK;
+}
+
+extern "C" int cphifi_problem_set_factors(cphifi_problem* P, const double* const* factors,
+                                          int mem) {
+  if (!P) return CPHIFI_E_INVALID_ARG;
+  cphifi_ctx* ctx = P->ctx;
+  if (!P->keep_obs) return fail(ctx, CPHIFI_E_INVALID_ARG, "problem created without CPHIFI_KEEP_OBS");
+  if (!factors) return fail(ctx, CPHIFI_E_INVALID_ARG, "null factors");
+  if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
+  for (int m = 0; m < P->d_other; ++m)
+    if (!factors[m]) return fail(ctx, CPHIFI_E_INVALID_ARG, "null factor");
+  Enter guard(ctx);
+  for (int m = 0; m < P->d_other; ++m)
+    CK(upload(P->factors[m], factors[m], (size_t)P->sizes[m] * P->r * sizeof(double), mem, P->st));
+  return problem_rebuild(P);
+}
+
+extern "C" int cphifi_problem_update_factor(cphifi_problem* P, int32_t mode, const double* W,
+                                            double* A_out, int mem) {
+  if (!P) return CPHIFI_E_INVALID_ARG;
+  Enter guard(P->ctx);
+  return update_factor(P, mode, W, A_out, mem);
+}
+
+extern "C" int cphifi_problem_fit(cphifi_problem* P, const double* W, int mem, double* res2,
+                                  double* t2) {
+  if (!P) return CPHIFI_E_INVALID_ARG;
+  Enter guard(P->ctx);
+  return problem_fit(P, W, mem, res2, t2);
+}
+
+extern "C" int cphifi_als(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
+                          const int64_t* other_sizes, double* const* factors_io, int32_t r,
+                          int64_t q, const int32_t* kidx, const int32_t* oidx, const double* vals,
+                          uint32_t flags, const cphifi_params* params, int32_t sweeps,
+                          double als_tol, int32_t warm, double* W_io, double* err_out,
+                          int32_t* sweeps_done, int mem, cphifi_stats* stats) {
+  if (!ctx) return CPHIFI_E_INVALID_ARG;
+  int rc = check_params(ctx, params);
+  if (rc != CPHIFI_OK) return rc;
+  if (sweeps < 1 || !W_io || !err_out || !factors_io || !(als_tol >= 0.0))
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "bad sweeps, tolerance or output pointers");
+  if (sweeps_done) *sweeps_done = 0;
+  flags |= CPHIFI_KEEP_OBS |
+           (params->precision == CPHIFI_FP64 ? CPHIFI_NEED_FP64 : CPHIFI_NEED_LOWP);
+  cphifi_problem* P = nullptr;
+  rc = cphifi_problem_create(ctx, kern, d_other, other_sizes, (const double* const*)factors_io, r,
+                             q, kidx, oidx, vals, flags, mem, &P);
+  if (rc != CPHIFI_OK) return rc;
+  Enter guard(ctx);
+  const int n = P->n;
+  double* Wd = nullptr;   // the current weights on the device
+  size_t gw = 0;
+  if (pool_alloc(ctx, (size_t)n * r * sizeof(double), (void**)&Wd, &gw) != cudaSuccess) {
+    cphifi_problem_destroy(P);
+    return fail(ctx, CPHIFI_E_OOM, "weights allocation failed");
+  }
+  bool have_w = false;
+  if (warm) {
+    if (upload(Wd, W_io, (size_t)n * r * sizeof(double), mem, P->st) != cudaSuccess) rc = CPHIFI_E_DEVICE;
+    have_w = true;
+  }
+  int s = 0;
+  cphifi_stats st_last{};
+  for (; rc == CPHIFI_OK && s < sweeps; ++s) {
+    // kernel mode (§4): PCG from the previous weights
+    rc = solve_prepare(P, params, Wd, CPHIFI_MEM_DEVICE);
+    if (rc != CPHIFI_OK) break;
+    {
+      SolveRun run(P, *params, have_w ? Wd : nullptr, Wd, CPHIFI_MEM_DEVICE, false);
+      rc = run.begin();
+      while (rc == CPHIFI_OK && run.stage != SolveRun::DONE) {
+        if ((rc = run.wait_ready()) != CPHIFI_OK) break;
+        rc = run.advance();
+      }
+      if (rc == CPHIFI_OK) {
+        run.fill(&st_last);
+        if (run.status != CPHIFI_OK && run.status != CPHIFI_E_NOT_CONVERGED) rc = run.status;
+      }
+    }
+    if (rc != CPHIFI_OK) break;
+    have_w = true;
+    // finite modes in order (§2)
+    for (int m = 0; m < d_other && rc == CPHIFI_OK; ++m)
+      rc = update_factor(P, m, Wd, nullptr, CPHIFI_MEM_DEVICE);
+    if (rc != CPHIFI_OK) break;
+    double r2 = 0.0, t2 = 0.0;
+    rc = problem_fit(P, Wd, CPHIFI_MEM_DEVICE, &r2, &t2);
+    if (rc != CPHIFI_OK) break;
+    err_out[s] = t2 > 0 ? std::sqrt(r2 / t2) : std::sqrt(r2);
+    if (sweeps_done) *sweeps_done = s + 1;
+    if (als_tol > 0 && s > 0 && std::fabs(err_out[s - 1] - err_out[s]) < als_tol) {
+      ++s;
+      break;
+    }
+  }
+  if (rc == CPHIFI_OK) {
+    if (download(W_io, Wd, (size_t)n * r * sizeof(double), mem, P->st) != cudaSuccess)
+      rc = CPHIFI_E_DEVICE;
+    for (int m = 0; m < d_other && rc == CPHIFI_OK; ++m)
+      if (download(factors_io[m], P->factors[m], (size_t)P->sizes[m] * r * sizeof(double), mem,
+                   P->st) != cudaSuccess)
+        rc = CPHIFI_E_DEVICE;
+    if (cudaStreamSynchronize(P->st) != cudaSuccess) rc = CPHIFI_E_DEVICE;
+    if (rc != CPHIFI_OK) fail(ctx, rc, "copying the fitted model out");
+  }
+  if (stats) *stats = st_last;
+  cudaStreamSynchronize(P->st);
+  pool_release(ctx, Wd, gw);
+  cphifi_problem_destroy(P);
+  return rc;
 }
 
 extern "C" int cphifi_problem_gram(cphifi_problem* P, double* V, double* DV, double* UV) {

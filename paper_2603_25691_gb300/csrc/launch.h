@@ -208,4 +208,28 @@ cudaError_t launch_convert(const TS* src, TD* dst, int64_t count, cudaStream_t s
 cudaError_t launch_scale_rows(const double* dK, const double* X, double* Y,
                               int n, int r, cudaStream_t st);
 
+// ---------------------------------------------------------------- als.cu ---
+// The alternating fit (§2).  keep_obs: kidx_s = sorted keys, and the
+// other-mode indices / values of observation perm[l] (l without perm) in the
+// sorted order.  mode_keys: keys[l] = oidx_s[l d_other + m].  als_rows: the
+// CP-ALS update of finite mode m (r x r normal equations per row of A_m,
+// FP64, Cholesky; Ak = K W, n x r; factors/sizes: device arrays of the
+// d_other factor pointers (column-major n_m x r) and sizes; writes Anew, may
+// alias factors[m]; *nfail counts rows with observations kept unchanged).
+// fit: out[0] = sum (t - m)^2, out[1] = sum t^2 of the model.
+cudaError_t launch_keep_obs(int64_t q, int d_other, const uint32_t* keys, const int32_t* perm,
+                            const int32_t* oidx, const double* vals, int32_t* kidx_s,
+                            int32_t* oidx_s, double* vals_s, const int* gate, cudaStream_t st);
+cudaError_t launch_mode_keys(int64_t q, int d_other, int m, const int32_t* oidx_s, uint32_t* keys,
+                             cudaStream_t st);
+cudaError_t launch_als_rows(int n_m, int m, int d_other, int r, int n, const int64_t* row_ptr_m,
+                            const int32_t* perm_m, const int32_t* kidx_s, const int32_t* oidx_s,
+                            const double* vals_s, const double* Ak, const double* const* factors,
+                            const int64_t* sizes, double* Anew, int* nfail, int num_sms,
+                            cudaStream_t st);
+cudaError_t launch_fit(int64_t q, int d_other, int r, int n, const int32_t* kidx_s,
+                       const int32_t* oidx_s, const double* vals_s, const double* Ak,
+                       const double* const* factors, const int64_t* sizes, RedScratch red,
+                       double* out, int num_sms, cudaStream_t st);
+
 }  // namespace cphifi
