@@ -165,9 +165,10 @@ const char* cphifi_status_string(int status);
  * K      : n x n symmetric PSD kernel matrix, column-major; may be NULL when
  *          UK and DK are given (the solver works in K's eigenbasis).
  * UK, DK : K = UK diag(DK) UK' with UK orthogonal (n x n, column-major,
- *          column j = eigenvector j) and DK the n eigenvalues.  Computing them
- *          (e.g. LAPACK dsyevd) is the caller's one-time setup; passing NULL
- *          returns CPHIFI_E_UNSUPPORTED.  Tiny negative eigenvalues are
+ *          column j = eigenvector j) and DK the n eigenvalues.  Pass both, or
+ *          neither: then the library computes them from K on the device
+ *          (FP64 symmetric divide-and-conquer, cuSOLVER dsyevd; the lower
+ *          triangle of K is read; n <= 46340).  Tiny negative eigenvalues are
  *          clamped to 0 inside the preconditioner only.
  * The library keeps FP64 and FP32 copies of UK on the device. */
 int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,

@@ -253,15 +253,27 @@ class Kernel:
     """cphifi_kernel_create: the kernel matrix's eigendecomposition (Eq. eigK)."""
 
     def __init__(self, ctx: Context, n: int, UK, DK, K=None):
+        # UK = DK = None: the library computes eig(K) on the device from K.
         self.ctx = ctx
         self.n = int(n)
+        h = ctypes.c_void_p()
+        if UK is None and DK is None:
+            if K is None:
+                raise ValueError("pass K or its eigendecomposition (UK, DK)")
+            k = _Buf(K, np.float64, colmajor=True)
+            if k.numel != self.n * self.n:
+                raise ValueError("K must be n x n")
+            rc = lib().cphifi_kernel_create(ctx.h, self.n, k.ptr, None, None, k.mem,
+                                            ctypes.byref(h))
+            _check(ctx.h, rc, "kernel_create")
+            self.h = h
+            return
         u = _Buf(UK, np.float64, colmajor=True)
         d = _Buf(DK, np.float64)
         if u.mem != d.mem:
             raise ValueError("UK and DK must live in the same memory kind")
         if u.numel != self.n * self.n or d.numel != self.n:
             raise ValueError("UK must be n x n and DK length n")
-        h = ctypes.c_void_p()
         rc = lib().cphifi_kernel_create(ctx.h, self.n, None, u.ptr, d.ptr, u.mem, ctypes.byref(h))
         _check(ctx.h, rc, "kernel_create")
         self.h = h

@@ -13,6 +13,7 @@
 // rounded U_K stays symmetric positive definite because U_K appears on both
 // sides.  W = U_K Wbar at the end.
 #include <cuda_runtime.h>
+#include <cusolverDn.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -37,6 +38,7 @@ static void requests_clear(cphifi_ctx* ctx);
 
 struct cphifi_ctx {
   int device = 0;
+  cusolverDnHandle_t solver = nullptr;  // device eig(K), created on first use
   int num_sms = 1;
   cudaStream_t stream = nullptr;
   cudaStream_t user_stream = nullptr;
@@ -471,6 +473,7 @@ extern "C" int cphifi_ctx_destroy(cphifi_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   requests_clear(ctx);
   deferred_collect(ctx, true);
+  if (ctx->solver) cusolverDnDestroy(ctx->solver);
   pool_trim(ctx);
   for (auto e : ctx->phase)
     if (e) cudaEventDestroy(e);
@@ -505,16 +508,69 @@ extern "C" const char* cphifi_last_error(const cphifi_ctx* ctx) {
 }
 
 // ------------------------------------------------------------ kernel ------
+// Symmetric eigendecomposition A = U diag(w) U' in FP64 on the device (the
+// one-time eig(K) of Eq. eigK): cuSOLVER's divide-and-conquer dsyevd on the
+// context's stream, A (n x n column-major, lower triangle read) overwritten
+// by U, eigenvalues ascending into w.  Synchronous.
+static int sym_eig_device(cphifi_ctx* ctx, int n, double* A, double* w, cudaStream_t st,
+                          std::string* why) {
+  if (!ctx->solver) {
+    if (cusolverDnCreate(&ctx->solver) != CUSOLVER_STATUS_SUCCESS) {
+      ctx->solver = nullptr;
+      *why = "cusolverDnCreate failed";
+      return CPHIFI_E_DEVICE;
+    }
+  }
+  if (cusolverDnSetStream(ctx->solver, st) != CUSOLVER_STATUS_SUCCESS) {
+    *why = "cusolverDnSetStream failed";
+    return CPHIFI_E_DEVICE;
+  }
+  int lwork = 0;
+  if (cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                                  A, n, w, &lwork) != CUSOLVER_STATUS_SUCCESS) {
+    *why = "cusolverDnDsyevd_bufferSize failed";
+    return CPHIFI_E_DEVICE;
+  }
+  double* work = nullptr;
+  int* info = nullptr;
+  if (cudaMalloc(&work, (size_t)std::max(lwork, 1) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&info, sizeof(int)) != cudaSuccess) {
+    if (work) cudaFree(work);
+    *why = "workspace allocation for the eigensolver failed";
+    return CPHIFI_E_OOM;
+  }
+  int hinfo = 0;
+  const cusolverStatus_t cs = cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR,
+                                               CUBLAS_FILL_MODE_LOWER, n, A, n, w, work, lwork,
+                                               info);
+  const cudaError_t e1 = cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st);
+  const cudaError_t e2 = cudaStreamSynchronize(st);
+  cudaFree(work);
+  cudaFree(info);
+  if (cs != CUSOLVER_STATUS_SUCCESS || e1 != cudaSuccess || e2 != cudaSuccess) {
+    *why = "cusolverDnDsyevd failed";
+    return CPHIFI_E_DEVICE;
+  }
+  if (hinfo != 0) {
+    *why = "the eigensolver did not converge (info " + std::to_string(hinfo) + ")";
+    return CPHIFI_E_INVALID_ARG;
+  }
+  return CPHIFI_OK;
+}
+
 extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
                                     const double* UK, const double* DK, int mem,
                                     cphifi_kernel** out) {
-  (void)K;
   if (!ctx || !out) return CPHIFI_E_INVALID_ARG;
   *out = nullptr;
   if (n < 1 || n > (1 << 20)) return fail(ctx, CPHIFI_E_INVALID_ARG, "n out of range");
-  if (!UK || !DK)
-    return fail(ctx, CPHIFI_E_UNSUPPORTED,
-                "the eigendecomposition of K must be passed (UK, DK)");
+  const bool device_eig = !UK && !DK;
+  if (device_eig && !K)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "either K or its eigendecomposition (UK, DK) is needed");
+  if (!device_eig && (!UK || !DK))
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "UK and DK are passed together");
+  if (device_eig && n > 46340)
+    return fail(ctx, CPHIFI_E_UNSUPPORTED, "n too large for the device eigensolver");
   if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
   const size_t nn = (size_t)n * n;
@@ -546,8 +602,20 @@ extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
     return cleanup(CPHIFI_E_OOM, "cudaMalloc failed for the kernel matrix");
   cudaStream_t st = ctx->stream;
   int herr = 0;
-  if (upload(kern->UK64, UK, nn * sizeof(double), mem, st) != cudaSuccess ||
-      upload(kern->dK, DK, n * sizeof(double), mem, st) != cudaSuccess ||
+  if (device_eig) {  // K = U_K diag(D_K) U_K' on the device (Eq. eigK), FP64
+    if (upload(kern->UK64, K, nn * sizeof(double), mem, st) != cudaSuccess ||
+        cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess ||
+        launch_validate_dense(kern->UK64, (int64_t)nn, err, st) != cudaSuccess ||
+        cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return cleanup(CPHIFI_E_DEVICE, "uploading K failed");
+    if (herr) return cleanup(CPHIFI_E_INVALID_ARG, "non-finite entry in K");
+    std::string why;
+    const int rc = sym_eig_device(ctx, (int)n, kern->UK64, kern->dK, st, &why);
+    if (rc != CPHIFI_OK) return cleanup(rc, why);
+  }
+  if ((!device_eig && (upload(kern->UK64, UK, nn * sizeof(double), mem, st) != cudaSuccess ||
+                       upload(kern->dK, DK, n * sizeof(double), mem, st) != cudaSuccess)) ||
       cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess ||
       launch_validate_dense(kern->UK64, (int64_t)nn, err, st) != cudaSuccess ||
       launch_validate_dense(kern->dK, n, err, st) != cudaSuccess ||

@@ -337,3 +337,29 @@ def test_slow_instances_reach_tolerance(ctx, pkg, name, prec):
     assert st["status"] == 0, st
     assert res <= 1e-6, (res, st)
     kern.close()
+
+
+def test_kernel_from_K_with_device_eigensolver(ctx, pkg):
+    # eig(K) computed on the device (Eq. eigK) gives the same solve as the
+    # host eigendecomposition: the oracle's FP64 residual meets the tolerance
+    # and the fitted values agree (W is invariant to the eigenvector basis).
+    p = synth.planted_problem(21, 120, (20, 30), 6000, 5, bandwidth=0.1, lam=1e-4, rho=1e-6)
+    kd = ctx.kernel_create(p.n, None, None, K=p.K)
+    dK, UK = np.linalg.eigh(p.K)
+    kh = ctx.kernel_create(p.n, UK, dK)
+    Wd, sd = pkg.solve(ctx, kd, p.factors, p.kidx, p.oidx, p.vals, p.r, p.lam, p.rho, 1e-10,
+                       2000, sorted_obs=True)
+    Wh, sh = pkg.solve(ctx, kh, p.factors, p.kidx, p.oidx, p.vals, p.r, p.lam, p.rho, 1e-10,
+                       2000, sorted_obs=True)
+    assert sd["status"] == 0
+    assert O.relative_residual(p.K, p.factors, p.kidx, p.oidx, p.vals, p.lam, p.rho, Wd) <= 1e-10
+    Zh = O.zhat(p.factors, p.oidx)
+    fd, fh = O.fitted_values(p.K, Wd, p.kidx, Zh), O.fitted_values(p.K, Wh, p.kidx, Zh)
+    assert rel(fd, fh) <= 1e-9
+    bad = p.K.copy()
+    bad[3, 4] = np.nan
+    with pytest.raises(pkg.CphifiError) as e:
+        ctx.kernel_create(p.n, None, None, K=bad)
+    assert e.value.status == pkg.E_INVALID_ARG
+    kd.close()
+    kh.close()
