@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--als-ranks", default="20",
                     help="ranks of the alternating-fit run (n=2000, 200x300, q=6e6; '' : skip)")
     ap.add_argument("--als-sweeps", type=int, default=20)
+    ap.add_argument("--no-paper-shapes", action="store_true",
+                    help="skip the runs on the paper's vortex / Miranda shapes")
     ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests per serving rate (at most ~2 s of arrivals)")
     return ap.parse_args()
@@ -377,6 +379,53 @@ def run_serve(args, pkg, ctx, dev, seed, big_kern, big_p):
     return out
 
 
+# Stand-ins for the paper's unaligned experiments (§5.2): mode sizes of the
+# vortex (199 x 449 x 151, Gaussian sigma = (4, 4, 3)) and Miranda (256 x 256
+# x 269, sigma = (1, 1, 2)) tensors on integer grids, q = 50,000 uniform
+# observations, lambda = 0.1, rho = 1e-6, tol 1e-6, at most 75 iterations,
+# r in {5, 10, ..., 50}.  The data values are planted (the datasets are not
+# available).  Each mode in turn is the kernel mode, the other two finite.
+PAPER_SHAPES = {"vortex": ((199, 449, 151), (4.0, 4.0, 3.0)),
+                "miranda": ((256, 256, 269), (1.0, 1.0, 2.0))}
+
+
+def run_paper_shapes(args, pkg, ctx, seed):
+    import synth
+    out = {}
+    for name, (dims, sig) in PAPER_SHAPES.items():
+        rows = []
+        for k in range(3):
+            n = dims[k]
+            other = tuple(dims[m] for m in range(3) if m != k)
+            x = synth.grid_points(n, integer=True)
+            K = synth.gaussian_kernel(x, sig[k])
+            dK, UK = np.linalg.eigh(K)
+            kern = ctx.kernel_create(n, UK, dK)
+            for r in range(5, 51, 5):
+                p = synth.planted_problem(seed + 97 * k + r, n, other, 50_000, r, bandwidth=sig[k],
+                                          integer_grid=True, lam=0.1, rho=1e-6)
+                for prec in ("fp64", "mixed_fp32"):
+                    t0 = time.perf_counter()
+                    W, st = pkg.solve(ctx, kern, p.factors, p.kidx, p.oidx, p.vals, r, p.lam,
+                                      p.rho, 1e-6, 75, precision=prec, sorted_obs=True)
+                    ms = 1e3 * (time.perf_counter() - t0)
+                    rows.append({"mode": k, "n": n, "r": r, "precision": prec, "ms": ms,
+                                 "iterations": st["iterations"], "status": st["status"],
+                                 "rel_residual": st["rel_residual"]})
+            kern.close()
+        summ = {}
+        for prec in ("fp64", "mixed_fp32"):
+            sel = [x for x in rows if x["precision"] == prec]
+            summ[prec] = {"solves": len(sel), "mean_ms": float(np.mean([x["ms"] for x in sel])),
+                          "max_ms": float(np.max([x["ms"] for x in sel])),
+                          "converged": int(sum(1 for x in sel if x["status"] == 0)),
+                          "max_iterations": int(max(x["iterations"] for x in sel)),
+                          "sweep_ms_r25": float(sum(x["ms"] for x in sel if x["r"] == 25))}
+        out[name] = {"dims": dims, "sigma": sig, "q": 50_000, "lambda": 0.1, "rho": 1e-6,
+                     "tol": 1e-6, "max_iter": 75, "summary": summ}
+    return out
+
+
 def run_als(args, pkg, ctx, seed):
     """The full alternating fit (§2) on the device: kernel mode n = 2000
     (Gaussian, bandwidth 0.1), finite modes 200 x 300 updated by CP-ALS rows,
@@ -547,6 +596,11 @@ def main():
                                           bandwidth=0.1)
         serving = run_serve(args, pkg, ctx, dev, 3000 + rank, kern if big_p else None, big_p)
 
+    # ---- the paper's unaligned experiment shapes (one-shot solves, host inputs)
+    paper = None
+    if not args.no_paper_shapes:
+        paper = run_paper_shapes(args, pkg, ctx, seed=5000 + rank)
+
     # ---- the alternating fit (kernel mode + finite modes), FP64
     als_runs = None
     if args.als_ranks:
@@ -598,7 +652,7 @@ def main():
             "fp64_path": fp64,
             "precision_sweep": sweep,
             "mixed_vs_fp64_solves": (solves_per_s / fp64["solves_per_s"]) if fp64 else None,
-            "batched": batched, "serving": serving, "als": als_runs,
+            "batched": batched, "serving": serving, "als": als_runs, "paper_shapes": paper,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary(),
             "gpu_launches": int(launches),
         }
