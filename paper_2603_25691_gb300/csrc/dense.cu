@@ -92,17 +92,126 @@ gemm_skinny_kernel(const TA* __restrict__ A, int64_t lda, const double* __restri
   }
 }
 
+// FP32 version with a larger register tile: 256 rows per block, each thread
+// 8 rows (ty + 32 m) x tn columns, so a k step costs 8 + tn shared loads for
+// 8 tn multiply-adds; the next slab of A and B is fetched into registers
+// while the current one is multiplied (one __syncthreads per slab).
+constexpr int kF32BM = 256, kF32BK = 16;
+
+template <bool ATRANS, bool SCALEB, int TNMAX>
+__global__ void __launch_bounds__(256)
+gemm_f32_kernel(const float* __restrict__ A, int64_t lda, const double* __restrict__ sk,
+                const float* __restrict__ B, int64_t ldb, float* __restrict__ C, int64_t ldc,
+                int64_t split_stride, int n, int ncols, int kchunk, const DevScalars* skip) {
+  if (dev_skip(skip)) return;
+  constexpr int BM = kF32BM, BK = kF32BK, TM = BM / 32;
+  constexpr int AL = BM * BK / 256;  // A values each thread stages per slab (16)
+  constexpr int BL = BK * 64 / 256;  // B values each thread stages per slab (4)
+  __shared__ float As[2][BK][BM + 4];
+  __shared__ float Bs[2][BK][64];
+  const int tid = threadIdx.x;
+  const int ty = tid & 31, tx = tid >> 5;
+  const int i0 = blockIdx.x * BM;  // columns tx*TNMAX .. +TNMAX-1 (< 64)
+  const int kbeg = blockIdx.y * kchunk;
+  const int kend = min(n, kbeg + kchunk);
+  float acc[TM][TNMAX];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TNMAX; ++b) acc[a][b] = 0.f;
+  float ra[AL], rb[BL];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < AL; ++u) {
+      const int idx = tid + 256 * u;
+      int ii, kk;
+      if (ATRANS) { ii = idx % BM; kk = idx / BM; } else { kk = idx % BK; ii = idx / BK; }
+      const int i = i0 + ii, k = k0 + kk;
+      ra[u] = (i < n && k < kend)
+                  ? __ldg(ATRANS ? A + (int64_t)k * lda + i : A + (int64_t)i * lda + k)
+                  : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < BL; ++u) {
+      const int idx = tid + 256 * u;
+      const int kk = idx % BK, j = idx / BK;
+      const int k = k0 + kk;
+      float v = 0.f;
+      if (k < kend && j < ncols) {
+        v = __ldg(B + (int64_t)j * ldb + k);
+        if (SCALEB) v = (float)((double)v * sk[k]);
+      }
+      rb[u] = v;
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < AL; ++u) {
+      const int idx = tid + 256 * u;
+      int ii, kk;
+      if (ATRANS) { ii = idx % BM; kk = idx / BM; } else { kk = idx % BK; ii = idx / BK; }
+      As[buf][kk][ii] = ra[u];
+    }
+#pragma unroll
+    for (int u = 0; u < BL; ++u) {
+      const int idx = tid + 256 * u;
+      Bs[buf][idx % BK][idx / BK] = rb[u];
+    }
+  };
+  if (kbeg < kend) {
+    fetch(kbeg);
+    stash(0);
+  }
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    const bool more = k0 + BK < kend;
+    if (more) fetch(k0 + BK);  // in flight during the multiply below
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float a[TM], b[TNMAX];
+#pragma unroll
+      for (int m = 0; m < TM; ++m) a[m] = As[buf][kk][ty + 32 * m];
+#pragma unroll
+      for (int c = 0; c < TNMAX; ++c) b[c] = Bs[buf][kk][tx * TNMAX + c];
+#pragma unroll
+      for (int m = 0; m < TM; ++m)
+#pragma unroll
+        for (int c = 0; c < TNMAX; ++c) acc[m][c] = fmaf(a[m], b[c], acc[m][c]);
+    }
+    if (more) stash(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+  float* Cs = C + (int64_t)blockIdx.y * split_stride;
+#pragma unroll
+  for (int m = 0; m < TM; ++m) {
+    const int i = i0 + ty + 32 * m;
+    if (i >= n) continue;
+#pragma unroll
+    for (int c = 0; c < TNMAX; ++c) {
+      const int j = tx * TNMAX + c;
+      if (j < ncols) Cs[(int64_t)j * ldc + i] = acc[m][c];
+    }
+  }
+}
+
 // Split of the k range: the grid is (ceil(n/128) row tiles) x nsplit blocks;
 // pick nsplit so that the blocks fill whole waves of the resident slots
 // (SMs x blocks per SM) as evenly as possible -- a grid of 1.04 waves runs
 // as long as two.
 template <typename TA, typename TC>
 int gemm_pick_split(int n, int num_sms) {
+  constexpr bool f32 = sizeof(TC) == 4;
   int occ = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gemm_skinny_kernel<TA, TC, true, true>, 256, 0);
+  if (f32)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gemm_f32_kernel<true, true, 5>, 256, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gemm_skinny_kernel<TA, TC, true, true>, 256, 0);
   if (occ < 1) occ = 1;
   const int64_t slots = (int64_t)num_sms * occ;
-  const int mt = (n + 127) / 128;
+  const int bm = f32 ? kF32BM : 128;
+  const int mt = (n + bm - 1) / bm;
   int smax = (n + 31) / 32;
   if (smax > 32) smax = 32;
   int best = 1;
@@ -128,6 +237,32 @@ cudaError_t launch_gemm_skinny(const TA* A, int64_t lda, bool a_trans, const dou
   if (ncols > 64) return cudaErrorInvalidValue;
   int kchunk = (n + nsplit - 1) / nsplit;
   kchunk = (kchunk + 31) / 32 * 32;
+  if constexpr (sizeof(TA) == 4 && sizeof(TC) == 4) {
+    const dim3 g((n + kF32BM - 1) / kF32BM, nsplit);
+    const float* Af = reinterpret_cast<const float*>(A);
+    const float* Bf = reinterpret_cast<const float*>(B);
+    float* Cf = reinterpret_cast<float*>(C);
+    const int tn = (ncols + 7) / 8;
+#define CPHIFI_F32(TNV)                                                                           \
+  do {                                                                                            \
+    if (a_trans) {                                                                                \
+      if (scale_k) gemm_f32_kernel<true, true, TNV><<<g, 256, 0, st>>>(Af, lda, scale_k, Bf, ldb, Cf, ldc, split_stride, n, ncols, kchunk, skip);   \
+      else gemm_f32_kernel<true, false, TNV><<<g, 256, 0, st>>>(Af, lda, scale_k, Bf, ldb, Cf, ldc, split_stride, n, ncols, kchunk, skip);         \
+    } else {                                                                                      \
+      if (scale_k) gemm_f32_kernel<false, true, TNV><<<g, 256, 0, st>>>(Af, lda, scale_k, Bf, ldb, Cf, ldc, split_stride, n, ncols, kchunk, skip);  \
+      else gemm_f32_kernel<false, false, TNV><<<g, 256, 0, st>>>(Af, lda, scale_k, Bf, ldb, Cf, ldc, split_stride, n, ncols, kchunk, skip);        \
+    }                                                                                             \
+  } while (0)
+    if (tn <= 1) CPHIFI_F32(1);
+    else if (tn <= 2) CPHIFI_F32(2);
+    else if (tn <= 3) CPHIFI_F32(3);
+    else if (tn <= 4) CPHIFI_F32(4);
+    else if (tn <= 5) CPHIFI_F32(5);
+    else if (tn <= 6) CPHIFI_F32(6);
+    else CPHIFI_F32(8);
+#undef CPHIFI_F32
+    return cudaGetLastError();
+  }
   const dim3 grid((n + 127) / 128, nsplit);
   if (a_trans) {
     if (scale_k)
@@ -163,8 +298,7 @@ gemm_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo, int
   __shared__ float Bsh[BK][64], Bsl[BK][64];
   const int tid = threadIdx.x;
   const int ty = tid & 31, tx = tid >> 5;
-  const int tn = (ncols + 7) / 8;
-  const int i0 = blockIdx.x * BM;
+  const int i0 = blockIdx.x * BM;  // columns tx*TNMAX .. +TNMAX-1 (< 64)
   const int kbeg = blockIdx.y * kchunk;
   const int kend = min(n, kbeg + kchunk);
   df acc[TM][TNMAX];
@@ -205,12 +339,12 @@ gemm_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo, int
       for (int m = 0; m < TM; ++m) a[m] = df{Ash[kk][ty + 32 * m], Asl[kk][ty + 32 * m]};
 #pragma unroll
       for (int c = 0; c < TNMAX; ++c)
-        b[c] = c < tn ? df{Bsh[kk][tx * tn + c], Bsl[kk][tx * tn + c]} : df{0.f, 0.f};
+        b[c] = df{Bsh[kk][tx * TNMAX + c], Bsl[kk][tx * TNMAX + c]};
 #pragma unroll
       for (int m = 0; m < TM; ++m)
 #pragma unroll
         for (int c = 0; c < TNMAX; ++c)
-          if (c < tn) df_acc_prod(acc[m][c], a[m], b[c]);
+          df_acc_prod(acc[m][c], a[m], b[c]);
     }
     __syncthreads();
   }
@@ -221,8 +355,8 @@ gemm_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo, int
     if (i >= n) continue;
 #pragma unroll
     for (int c = 0; c < TNMAX; ++c) {
-      const int j = tx * tn + c;
-      if (c < tn && j < ncols) Cs[(int64_t)j * ldc + i] = df_to_double(df_norm(acc[m][c]));
+      const int j = tx * TNMAX + c;
+      if (j < ncols) Cs[(int64_t)j * ldc + i] = df_to_double(df_norm(acc[m][c]));
     }
   }
 }
