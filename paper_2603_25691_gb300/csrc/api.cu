@@ -721,8 +721,8 @@ static void problem_need(const cphifi_ctx* ctx, int n, bool tc, int32_t d_other,
   const bool lowp = (flags & CPHIFI_NEED_LOWP) || !(flags & CPHIFI_NEED_FP64);
   *need = problem_footprint(n, q, r, d_other, sizes, lowp, nsplit, npieces_max) +
           (need64 ? (size_t)zhat_elems(q, r) * sizeof(double) : 0);
-  *tmp = (size_t)q * (sizeof(int32_t) * (1 + d_other) + sizeof(double) * 2 + sizeof(uint32_t)) +
-         radix_sort_tmp_bytes(q);
+  *tmp = (size_t)q * (sizeof(int32_t) * (1 + d_other) + sizeof(double) * 3 + sizeof(uint32_t)) +
+         radix_sort_tmp_bytes(q);  // index/value copies, sort keys, double-float values
   if (flags & CPHIFI_KEEP_OBS)  // sorted observation lists + A_k
     *need += (size_t)q * (sizeof(int32_t) * (1 + d_other) + sizeof(double)) +
              (size_t)n * r * sizeof(double);
@@ -979,13 +979,18 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
                           gate, st));
   }
 
-  // ---- Zhat (hi/lo) fused with the right-hand side MTTKRP; Gram, eig(V)
+  // ---- Zhat, then the right-hand side MTTKRP
+  float* tdf_tmp = nullptr;
+  if (P->zhi) {
+    tdf_tmp = (float*)tmp_alloc((size_t)std::max<int64_t>(q, 1) * 2 * sizeof(float));
+    if (!tdf_tmp) return bail(CPHIFI_E_OOM, "temporary allocation failed");
+  }
   PieceList pl{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket,
                P->warp_first, P->npieces, P->nwarps};
   PCK(launch_zhat_mttkrp(pl, (flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm, oidx_d, d_other,
                          P->fhl_dev, P->sizes_dev, r, vals_d, P->zhi, P->zlo,
                          P->z64, (double*)P->gds_partial, P->Bm, n, P->err, gate,
-                         ctx->num_sms, q, st));
+                         ctx->num_sms, q, tdf_tmp, st));
   if (flags & CPHIFI_KEEP_OBS) {
     P->keep_obs = true;
     PCK(dalloc(P, &P->kidx_s, (size_t)q));
@@ -1671,12 +1676,20 @@ static int problem_rebuild(cphifi_problem* P) {
   CK(launch_convert<double, float>(P->UV, P->UV32, (int64_t)r * r, st));
   const PieceList pl{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket,
                      P->warp_first, P->npieces, P->nwarps};
-  CK(launch_zhat_mttkrp(pl, nullptr, P->oidx_s, d, P->fhl_dev, P->sizes_dev, r, P->vals_s,
-                        P->zhi, P->zlo, P->z64, (double*)P->gds_partial, P->Bm, P->n, P->err,
-                        nullptr, ctx->num_sms, P->q, st));
+  void* tdf = nullptr;
+  size_t gt = 0;
+  if (P->zhi) CK(pool_alloc(ctx, (size_t)std::max<int64_t>(P->q, 1) * 2 * sizeof(float), &tdf, &gt));
+  const cudaError_t ez = launch_zhat_mttkrp(pl, nullptr, P->oidx_s, d, P->fhl_dev, P->sizes_dev,
+                                            r, P->vals_s, P->zhi, P->zlo, P->z64,
+                                            (double*)P->gds_partial, P->Bm, P->n, P->err, nullptr,
+                                            ctx->num_sms, P->q, (float*)tdf, st);
   int herr = 0;
-  CK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  cudaError_t ec = cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  const cudaError_t es = cudaStreamSynchronize(st);
+  if (tdf) pool_release(ctx, tdf, gt);
+  CK(ez);
+  CK(ec);
+  CK(es);
   if (herr) return fail(ctx, CPHIFI_E_INVALID_ARG, input_error_text(herr));
   P->stale = false;
   return CPHIFI_OK;

@@ -88,12 +88,14 @@ cudaError_t launch_gds_df(const PieceList& pl, const float* zhi, const float* zl
 // the MTTKRP B(i,:) = sum_{i_l = i} t_l Zhat(l,:) (B column-major, ld ldb,
 // FP64-accurate) as the weights mode of the gather-dot/scatter.  perm = NULL:
 // input already sorted.  Bad indices set *err bit 1 (the MTTKRP then skips).
+// tdf_tmp: 2 q floats of scratch (the values as double-float pairs in the
+// sorted order) when zhi is set; unused otherwise.
 cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const int32_t* oidx,
                                int d_other, const float* const* fhl,
                                const int64_t* sizes_dev, int r, const double* vals,
                                float* zhi, float* zlo, double* z64, double* partial, double* B,
                                int64_t ldb, int* err, const int* gate, int num_sms, int64_t q,
-                               cudaStream_t st);
+                               float* tdf_tmp, cudaStream_t st);
 
 // -------------------------------------------------------------- dense.cu ---
 // Skinny product C = op(A) diag(s) B for A n x n (op = identity when a_trans

@@ -480,7 +480,8 @@ zhat_build_kernel(int64_t q, const int32_t* __restrict__ perm, const int32_t* __
                   int d_other, const float* const* __restrict__ fhl,
                   const int64_t* __restrict__ sizes, int r,
                   float* __restrict__ zhi, float* __restrict__ zlo, double* __restrict__ z64,
-                  int* err, const int* gate) {
+                  const double* __restrict__ vals, float2* __restrict__ tdf, int* err,
+                  const int* gate) {
   if (gate && *gate) return;  // invalid input found earlier: touch nothing
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -492,6 +493,10 @@ zhat_build_kernel(int64_t q, const int32_t* __restrict__ perm, const int32_t* __
     const int64_t l = tile * 32 + lane;
     if (l >= q) continue;
     const int64_t src = perm ? (int64_t)perm[l] : l;
+    if (tdf) {  // the observed value as a double-float pair, in the sorted order
+      const df t = df_from_double(vals[src]);
+      tdf[l] = make_float2(t.hi, t.lo);
+    }
     const int32_t* im = oidx + src * d_other;
     bool ok = true;
     for (int m = 0; m < d_other; ++m) {
@@ -595,6 +600,7 @@ __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __r
                                                   int64_t yld, const DevScalars* skip,
                                                   const double* __restrict__ wts,
                                                   const int32_t* __restrict__ wperm,
+                                                  const float2* __restrict__ wdf,
                                                   const int* gate) {
   using IO = typename GdsTypes<MODE>::IO;
   using Acc = typename GdsTypes<MODE>::Acc;
@@ -640,9 +646,13 @@ __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __r
         }
         Acc xb;
         if constexpr (WTS) {
-          const double t = act ? wts[wperm ? (int64_t)wperm[l] : (int64_t)l] : 0.0;
-          if constexpr (MODE == GDS_DF) xb = df_from_double(t);
-          else xb = (Acc)t;
+          if constexpr (MODE == GDS_DF) {
+            const float2 t2 = act ? __ldcs(wdf + l) : make_float2(0.f, 0.f);
+            xb = df{t2.x, t2.y};
+          } else {
+            const double t = act ? wts[wperm ? (int64_t)wperm[l] : (int64_t)l] : 0.0;
+            xb = (Acc)t;
+          }
         } else {
         Acc dot = acc_zero(Acc());
 #pragma unroll
@@ -674,8 +684,9 @@ __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __r
 }
 
 struct GdsWeights {
-  const double* wts = nullptr;    // non-null: weights mode
+  const double* wts = nullptr;    // non-null: weights mode (FP64 weights, wperm order)
   const int32_t* wperm = nullptr;
+  const float2* wdf = nullptr;    // double-float weights in the sorted order (GDS_DF)
   const int* gate = nullptr;
 };
 
@@ -687,14 +698,14 @@ static cudaError_t gds_dispatch(const PieceList& pl, const float* zhi, const flo
                                 const DevScalars* skip, cudaStream_t st,
                                 const GdsWeights& wt = GdsWeights()) {
   const int blocks = (pl.nwarps + 7) / 8;
-  if (wt.wts)
+  if (wt.wts || wt.wdf)
     gds_kernel<MODE, RP, LPO, true><<<blocks, 256, 0, st>>>(pl, zhi, zlo, z64, r, Xh, xld, partial,
                                                             Y, yld, skip, wt.wts, wt.wperm,
-                                                            wt.gate);
+                                                            wt.wdf, wt.gate);
   else
     gds_kernel<MODE, RP, LPO, false><<<blocks, 256, 0, st>>>(pl, zhi, zlo, z64, r, Xh, xld,
                                                              partial, Y, yld, skip, nullptr,
-                                                             nullptr, nullptr);
+                                                             nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 
@@ -723,9 +734,11 @@ cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const i
                                int d_other, const float* const* fhl,
                                const int64_t* sizes_dev, int r, const double* vals, float* zhi,
                                float* zlo, double* z64, double* partial, double* B, int64_t ldb,
-                               int* err, const int* gate, int num_sms, int64_t q,
+                               int* err, const int* gate, int num_sms, int64_t q, float* tdf_tmp,
                                cudaStream_t st) {
   if (q == 0 || pl.npieces == 0 || pl.nwarps == 0) return cudaSuccess;
+  float2* tdf = zhi ? reinterpret_cast<float2*>(tdf_tmp) : nullptr;
+  if (zhi && !tdf) return cudaErrorInvalidValue;
   if (d_other < 1 || d_other > 16 || r < 1 || r > 64 || (!zhi && !z64) || (zhi && !zlo))
     return cudaErrorInvalidValue;
   const int64_t tiles = (q + 31) / 32;
@@ -734,15 +747,18 @@ cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const i
   if (blocks > cap) blocks = cap;
   if (z64)
     zhat_build_kernel<true><<<(int)blocks, 256, 0, st>>>(q, perm, oidx, d_other, fhl,
-                                                         sizes_dev, r, zhi, zlo, z64, err, gate);
+                                                         sizes_dev, r, zhi, zlo, z64, vals, tdf,
+                                                         err, gate);
   else
     zhat_build_kernel<false><<<(int)blocks, 256, 0, st>>>(q, perm, oidx, d_other, fhl,
-                                                          sizes_dev, r, zhi, zlo, z64, err, gate);
+                                                          sizes_dev, r, zhi, zlo, z64, vals, tdf,
+                                                          err, gate);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   GdsWeights wt;
   wt.wts = vals;
   wt.wperm = perm;
+  wt.wdf = tdf;
   wt.gate = err;  // no MTTKRP over invalid indices (the build flags them)
   if (zhi)
     return gds_by_rank<GDS_DF>(pl, zhi, zlo, nullptr, r, nullptr, 0, partial, B, ldb, nullptr, st,
