@@ -294,6 +294,7 @@ gemm_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo, int
                int kchunk, const DevScalars* skip) {
   if (dev_skip(skip)) return;
   constexpr int BM = 128, BK = 16, TM = BM / 32;
+  constexpr int AL = BM * BK / 256, BL = BK * 64 / 256;  // staged values per thread
   __shared__ float Ash[BK][BM + 1], Asl[BK][BM + 1];
   __shared__ float Bsh[BK][64], Bsl[BK][64];
   const int tid = threadIdx.x;
@@ -306,32 +307,62 @@ gemm_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo, int
   for (int a = 0; a < TM; ++a)
 #pragma unroll
     for (int b = 0; b < TNMAX; ++b) acc[a][b] = df{0.f, 0.f};
-  for (int k0 = kbeg; k0 < kend; k0 += BK) {
-    for (int idx = tid; idx < BM * BK; idx += 256) {
+  // the next slab is fetched into registers while the current one is used
+  float rah[AL], ral[AL], rbh[BL], rbl[BL];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < AL; ++u) {
+      const int idx = tid + 256 * u;
       int ii, kk;
       if (ATRANS) { ii = idx % BM; kk = idx / BM; } else { kk = idx % BK; ii = idx / BK; }
       const int i = i0 + ii, k = k0 + kk;
       float h = 0.f, l = 0.f;
       if (i < n && k < kend) {
         const int64_t off = ATRANS ? (int64_t)k * lda + i : (int64_t)i * lda + k;
-        h = Ahi[off];
-        l = Alo[off];
+        h = __ldg(Ahi + off);
+        l = __ldg(Alo + off);
       }
-      Ash[kk][ii] = h;
-      Asl[kk][ii] = l;
+      rah[u] = h;
+      ral[u] = l;
     }
-    for (int idx = tid; idx < BK * 64; idx += 256) {
+#pragma unroll
+    for (int u = 0; u < BL; ++u) {
+      const int idx = tid + 256 * u;
       const int kk = idx % BK, j = idx / BK;
       const int k = k0 + kk;
       float h = 0.f, l = 0.f;
       if (k < kend && j < ncols) {
-        h = Bhi[(int64_t)j * ldb + k];
-        l = Blo[(int64_t)j * ldb + k];
+        h = __ldg(Bhi + (int64_t)j * ldb + k);
+        l = __ldg(Blo + (int64_t)j * ldb + k);
       }
-      Bsh[kk][j] = h;
-      Bsl[kk][j] = l;
+      rbh[u] = h;
+      rbl[u] = l;
     }
-    __syncthreads();
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int u = 0; u < AL; ++u) {
+      const int idx = tid + 256 * u;
+      int ii, kk;
+      if (ATRANS) { ii = idx % BM; kk = idx / BM; } else { kk = idx % BK; ii = idx / BK; }
+      Ash[kk][ii] = rah[u];
+      Asl[kk][ii] = ral[u];
+    }
+#pragma unroll
+    for (int u = 0; u < BL; ++u) {
+      const int idx = tid + 256 * u;
+      Bsh[idx % BK][idx / BK] = rbh[u];
+      Bsl[idx % BK][idx / BK] = rbl[u];
+    }
+  };
+  if (kbeg < kend) {
+    fetch(kbeg);
+    stash();
+  }
+  __syncthreads();
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    const bool more = k0 + BK < kend;
+    if (more) fetch(k0 + BK);
 #pragma unroll 4
     for (int kk = 0; kk < BK; ++kk) {
       df a[TM], b[TNMAX];
@@ -346,6 +377,8 @@ gemm_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo, int
         for (int c = 0; c < TNMAX; ++c)
           df_acc_prod(acc[m][c], a[m], b[c]);
     }
+    __syncthreads();
+    if (more) stash();
     __syncthreads();
   }
   double* Cs = C + (int64_t)blockIdx.y * split_stride;
