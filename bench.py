@@ -640,7 +640,12 @@ def main():
                 "setup": (elapsed_ms / args.steps) - sum(s["rhs_ms"] + s["iter_ms"] + s["final_ms"] for s in stats) / args.steps,
                 "rhs": sum(s["rhs_ms"] for s in stats) / args.steps,
                 "iteration": iter_phase_ms / args.steps,
-                "final": sum(s["final_ms"] for s in stats) / args.steps},
+                "final": sum(s["final_ms"] for s in stats) / args.steps,
+                # inside the iteration phase (CUDA events around each launch):
+                "iter_gds": sum(s["gds_ms"] for s in stats) / args.steps,
+                "iter_products": sum(s["gemm_ms"] for s in stats) / args.steps,
+                "iter_true_residual_gds": sum(s["gds64_ms"] for s in stats) / args.steps,
+                "iter_true_residual_products": sum(s["gemm64_ms"] for s in stats) / args.steps},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None,
                          "traffic": (GDS32_TRAFFIC_PER_OBS_R40 * q

@@ -111,7 +111,9 @@ struct cphifi_problem {
   int32_t* perm = nullptr;
   int64_t* row_ptr = nullptr;
   double* z64 = nullptr;  // Zhat in FP64 (the FP64 operator)
-  float* zhi = nullptr;   // Zhat = zhi + zlo (FP32 pair, mixed modes); zhi = FP32 operator
+  // Zhat as an FP32 pair (mixed and double-float modes): one array of tiles
+  // [hi block | lo block] (tile stride 64 r); zhi points at it, zlo = zhi + 32 r.
+  float* zhi = nullptr;
   float* zlo = nullptr;
   int32_t *pseg = nullptr, *pbeg = nullptr, *pend = nullptr, *seg_first = nullptr,
           *seg_count = nullptr, *warp_first = nullptr;
@@ -826,8 +828,8 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
   PCK(dalloc(P, &P->perm, q));
   PCK(dalloc(P, &P->row_ptr, n + 1));
   if (lowp) {
-    PCK(dalloc(P, &P->zhi, (size_t)zhat_elems(q, r)));
-    PCK(dalloc(P, &P->zlo, (size_t)zhat_elems(q, r)));
+    PCK(dalloc(P, &P->zhi, (size_t)zhat_elems(q, r) * 2));
+    P->zlo = P->zhi + 32 * (int64_t)r;
   }
   if (need64) PCK(dalloc(P, &P->z64, (size_t)zhat_elems(q, r)));
   PCK(dalloc(P, &P->warp_first, (size_t)W + 1));
@@ -1353,9 +1355,9 @@ int ensure_lowp(cphifi_problem* P) {
   const size_t elems = (size_t)zhat_elems(P->q, P->r);
   if (ctx->budget && ctx->in_use + 2 * elems * sizeof(float) > ctx->budget)
     return fail(ctx, CPHIFI_E_ADMISSION, "hi/lo operator data exceeds the HBM budget");
-  CK(dalloc(P, &P->zhi, elems));
-  CK(dalloc(P, &P->zlo, elems));
-  CK(launch_split_df(P->z64, nullptr, (int64_t)elems, (int64_t)elems, P->zhi, P->zlo, P->st));
+  CK(dalloc(P, &P->zhi, elems * 2));
+  P->zlo = P->zhi + 32 * (int64_t)P->r;
+  CK(launch_zhat_split(P->z64, P->q, P->r, P->zhi, P->st));
   return CPHIFI_OK;
 }
 
@@ -1366,7 +1368,7 @@ int ensure_fp64(cphifi_problem* P) {
   if (ctx->budget && ctx->in_use + elems * sizeof(double) > ctx->budget)
     return fail(ctx, CPHIFI_E_ADMISSION, "FP64 operator data exceeds the HBM budget");
   CK(dalloc(P, &P->z64, elems));
-  CK(launch_join_df(P->zhi, P->zlo, (int64_t)elems, P->z64, P->st));
+  CK(launch_zhat_join(P->zhi, P->q, P->r, P->z64, P->st));
   return CPHIFI_OK;
 }
 

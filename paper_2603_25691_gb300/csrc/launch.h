@@ -51,13 +51,20 @@ cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n,
                                void* tmp, size_t tmp_bytes, cudaStream_t st);
 size_t exclusive_scan_tmp_bytes(int64_t n);
 // Zhat storage: tiles of 32 sorted observations, each a 32 x r column-major
-// block; (l, j) lives at zidx(l, j, r).  Buffers hold zhat_elems(q, r) values.
-__host__ __device__ __forceinline__ int64_t zidx(int64_t l, int j, int r) {
-  return (l >> 5) * (32 * (int64_t)r) + 32 * (int64_t)j + (l & 31);
+// block; (l, j) lives at zidx(l, j, ts) with tile stride ts.  The FP64 copy
+// has ts = 32 r; the FP32 pair is one array whose tiles hold the hi block
+// then the lo block (ts = 64 r, lo = hi + 32 r), so a pass over the hi parts
+// alone keeps touching the same pages as one over both.  A buffer holds
+// zhat_elems(q, r) values per part.
+__host__ __device__ __forceinline__ int64_t zidx(int64_t l, int j, int64_t ts) {
+  return (l >> 5) * ts + 32 * (int64_t)j + (l & 31);
 }
 __host__ __device__ __forceinline__ int64_t zhat_elems(int64_t q, int r) {
   return ((q + 31) >> 5) * 32 * (int64_t)r;
 }
+// Conversions between the FP64 copy and the interleaved FP32 pair.
+cudaError_t launch_zhat_split(const double* z64, int64_t q, int r, float* zhl, cudaStream_t st);
+cudaError_t launch_zhat_join(const float* zhl, int64_t q, int r, double* z64, cudaStream_t st);
 // Gather-dot/scatter (Eqs. vl and yhat1) over the piece decomposition.
 struct PieceList {
   const int32_t* seg;

@@ -504,7 +504,8 @@ zhat_build_kernel(int64_t q, const int32_t* __restrict__ perm, const int32_t* __
       ok = ok && v >= 0 && v < sizes[m];
     }
     bad |= ok ? 0 : 1;
-    const int64_t base = tile * 32 * (int64_t)r + lane;
+    const int64_t base = tile * 64 * (int64_t)r + lane;     // hi tile; lo = +32 r
+    const int64_t base64 = tile * 32 * (int64_t)r + lane;   // FP64 copy
     for (int j0 = 0; j0 < r; j0 += 4) {
       df z[4];
       for (int m = 0; m < d_other; ++m) {
@@ -535,12 +536,12 @@ zhat_build_kernel(int64_t q, const int32_t* __restrict__ perm, const int32_t* __
       for (int u = 0; u < 4; ++u) {
         const int j = j0 + u;
         if (j < r) {
-          const int64_t zi = base + 32 * (int64_t)j;
           if (zhi) {
+            const int64_t zi = base + 32 * (int64_t)j;
             __stcs(zhi + zi, z[u].hi);
-            __stcs(zlo + zi, z[u].lo);
+            __stcs(zhi + zi + 32 * r, z[u].lo);
           }
-          if constexpr (W64) __stcs(z64 + zi, df_to_double(z[u]));
+          if constexpr (W64) __stcs(z64 + base64 + 32 * (int64_t)j, df_to_double(z[u]));
         }
       }
     }
@@ -633,7 +634,8 @@ __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __r
       for (int l0 = b; l0 < e; l0 += OPW) {
         const int l = l0 + o;
         const bool act = l < e;
-        const int64_t base = zidx(act ? l : b, 0, r);
+        // hi/lo pair: tile stride 64 r (lo block at +32 r); FP64: 32 r
+        const int64_t base = zidx(act ? l : b, 0, (MODE == GDS_F64 ? 32 : 64) * (int64_t)r);
         Acc z[CPL];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
@@ -641,7 +643,7 @@ __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __r
           const bool ld = act && j < r;
           if constexpr (MODE == GDS_F32) z[c] = ld ? __ldcs(zhi + base + 32 * j) : 0.f;
           else if constexpr (MODE == GDS_F64) z[c] = ld ? __ldcs(z64 + base + 32 * j) : 0.0;
-          else z[c] = ld ? df{__ldcs(zhi + base + 32 * j), __ldcs(zlo + base + 32 * j)}
+          else z[c] = ld ? df{__ldcs(zhi + base + 32 * j), __ldcs(zhi + base + 32 * (r + j))}
                          : df{0.f, 0.f};
         }
         Acc xb;
@@ -765,6 +767,47 @@ cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const i
                                wt);
   return gds_by_rank<GDS_F64>(pl, nullptr, nullptr, z64, r, nullptr, 0, partial, B, ldb, nullptr,
                               st, wt);
+}
+
+// Elementwise conversions between the FP64 Zhat and its interleaved FP32 pair.
+__global__ void zhat_split_kernel(const double* __restrict__ z64, int64_t total, int r,
+                                  float* __restrict__ zhl) {
+  const int64_t per = 32 * (int64_t)r;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t tile = t / per, in = t - tile * per;
+    const df d = df_from_double(z64[t]);
+    zhl[tile * 2 * per + in] = d.hi;
+    zhl[tile * 2 * per + per + in] = d.lo;
+  }
+}
+
+__global__ void zhat_join_kernel(const float* __restrict__ zhl, int64_t total, int r,
+                                 double* __restrict__ z64) {
+  const int64_t per = 32 * (int64_t)r;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t tile = t / per, in = t - tile * per;
+    z64[t] = (double)zhl[tile * 2 * per + in] + (double)zhl[tile * 2 * per + per + in];
+  }
+}
+
+cudaError_t launch_zhat_split(const double* z64, int64_t q, int r, float* zhl, cudaStream_t st) {
+  const int64_t total = zhat_elems(q, r);
+  if (total == 0) return cudaSuccess;
+  int64_t b = (total + 255) / 256;
+  if (b > 8192) b = 8192;
+  zhat_split_kernel<<<(int)b, 256, 0, st>>>(z64, total, r, zhl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zhat_join(const float* zhl, int64_t q, int r, double* z64, cudaStream_t st) {
+  const int64_t total = zhat_elems(q, r);
+  if (total == 0) return cudaSuccess;
+  int64_t b = (total + 255) / 256;
+  if (b > 8192) b = 8192;
+  zhat_join_kernel<<<(int)b, 256, 0, st>>>(zhl, total, r, z64);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gds_f32(const PieceList& pl, const float* zhi, int r, const float* Xh,
