@@ -36,8 +36,9 @@ WORKLOAD = "c3_mixed_n8000_q5e7_r40"
 TOL = 1e-6
 # DRAM bytes (read + write) per observation of the FP32 gather-dot/scatter
 # launch at r = 40, from one ncu capture of the same kernel at n = 2000,
-# q = 5e6 (813.1 MB per launch); traffic grows in proportion to q.
-GDS32_TRAFFIC_PER_OBS_R40 = 813.13e6 / 5e6
+# q = 5e6 (810.0 MB read + 3.6 MB written per launch); traffic grows in
+# proportion to q.
+GDS32_TRAFFIC_PER_OBS_R40 = 813.6e6 / 5e6
 MAX_ITER_BATCH = 5000
 
 
