@@ -909,14 +909,20 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
     PCK(launch_split_rows_df(P->factors[m], sizes[m], r, P->fhl[m], st));
   }
 
-  // ---- Gram V (§3) and eig(V) (Eq. eigV) on the side stream: they need only
-  // the factors and overlap the observation passes below.
-  PCK(cudaEventRecord(ctx->ev_fork, st));
-  PCK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
-  PCK(launch_gram(P->factors_dev, P->sizes_dev, d_other, r, P->V, ctx->side));
-  PCK(launch_jacobi_eig(P->V, r, P->dV, P->UV, 60, P->info, ctx->side));
-  PCK(launch_convert<double, float>(P->UV, P->UV32, (int64_t)r * r, ctx->side));
-  PCK(cudaEventRecord(ctx->ev_join, ctx->side));
+  // ---- Gram V (§3) and eig(V) (Eq. eigV): they need only the factors.  A
+  // synchronous creation runs them on the context's side stream, overlapping
+  // the observation passes below; an asynchronous one (a submitted request,
+  // already on a stream of its own) runs them in order on its stream, so that
+  // concurrent requests do not queue behind one shared side stream.
+  cudaStream_t gst = async ? st : ctx->side;
+  if (!async) {
+    PCK(cudaEventRecord(ctx->ev_fork, st));
+    PCK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  }
+  PCK(launch_gram(P->factors_dev, P->sizes_dev, d_other, r, P->V, gst));
+  PCK(launch_jacobi_eig(P->V, r, P->dV, P->UV, 60, P->info, gst));
+  PCK(launch_convert<double, float>(P->UV, P->UV32, (int64_t)r * r, gst));
+  if (!async) PCK(cudaEventRecord(ctx->ev_join, ctx->side));
 
   // ---- observations: copy, validate, sort by kernel index
   uint32_t* keys = (uint32_t*)tmp_alloc((size_t)q * sizeof(uint32_t));
@@ -1006,7 +1012,7 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
     PCK(launch_keep_obs(q, d_other, keys, (flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm,
                         oidx_d, vals_d, P->kidx_s, P->oidx_s, P->vals_s, gate, st));
   }
-  PCK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+  if (!async) PCK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
   if (async) {
     cudaEvent_t ev = nullptr;
     PCK(event_get(ctx, &ev));
