@@ -50,54 +50,46 @@ cudaError_t launch_gram(const double* const* factors_dev, const int64_t* sizes_d
 // to even, the extra index being an isolated zero.  Rotation of
 // Golub & Van Loan, Matrix Computations, §8.5 (symmetric Schur 2 x 2):
 // tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) / (|tau| + sqrt(1 + tau^2)),
-// c = 1/sqrt(1 + t^2), s = t c, then A <- J'AJ and Q <- QJ.  Stops when the
-// off-diagonal Frobenius norm is below 1e-14 ||A||_F or after max_sweeps
-// (info = 1 then).  The 1e-14 relative off-diagonal target is far below
-// what the preconditioner needs.  Eigenvalues are left unsorted.
-__global__ void jacobi_kernel(const double* __restrict__ Vin, int r, double* dV, double* UV,
-                              int max_sweeps, int* info) {
-  extern __shared__ double smj[];
-  const int R = r + (r & 1);
-  double* A = smj;              // R x R, A[i + R j]
-  double* Q = A + R * R;        // R x R
-  double* cs = Q + R * R;       // R/2 x 2
-  int* pq = (int*)(cs + R);     // R/2 x 2
-  __shared__ double red[64];  // block_sum<2> scratch: 2 x 32
-  __shared__ double off_s, nrm_s;
-  for (int t = threadIdx.x; t < R * R; t += blockDim.x) {
-    const int i = t % R, j = t / R;
-    A[t] = (i < r && j < r) ? Vin[i + (int64_t)r * j] : 0.0;
-    Q[t] = i == j ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  int sweep = 0;
-  for (; sweep <= max_sweeps; ++sweep) {
+// c = 1/sqrt(1 + t^2), s = t c, then A <- J'AJ and Q <- QJ.
+//
+// GB300 runs FP64 multiply-adds at 1/63 of the FP32 rate, and a sweep is
+// ~6 R^2 (R - 1) multiply-adds on one SM, so the sweeps first run in FP32
+// (to an off-diagonal Frobenius norm of ~1e-6 ||A||) and give a basis Q0;
+// then B = Q0' V Q0 is formed in FP64 -- diagonal up to the FP32 error -- and
+// FP64 sweeps on B, accumulating into Q = Q0 J, finish to an off-diagonal
+// norm below 1e-14 ||V||_F (quadratic convergence: one or two sweeps).
+// info = 1 if that target was not met within max_sweeps FP64 sweeps.
+// Eigenvalues are left unsorted.
+template <typename T>
+__device__ void jacobi_sweeps(T* A, T* Q, T* cs, int* pq, int R, int max_sweeps, double tol2,
+                              double* red, double* stats /* off, nrm */) {
+  for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
     double v[2] = {0.0, 0.0};
     for (int t = threadIdx.x; t < R * R; t += blockDim.x) {
       const int i = t % R, j = t / R;
-      v[1] += A[t] * A[t];
-      if (i != j) v[0] += A[t] * A[t];
+      const double a = (double)A[t];
+      v[1] += a * a;
+      if (i != j) v[0] += a * a;
     }
     block_sum<2>(v, red);
-    if (threadIdx.x == 0) { off_s = v[0]; nrm_s = v[1]; }
+    if (threadIdx.x == 0) { stats[0] = v[0]; stats[1] = v[1]; }
     __syncthreads();
-    if (off_s <= 1e-28 * nrm_s || off_s == 0.0) break;
-    if (sweep == max_sweeps) break;
+    if (stats[0] <= tol2 * stats[1] || stats[0] == 0.0 || sweep == max_sweeps) break;
     for (int round = 0; round < R - 1; ++round) {
       for (int k = threadIdx.x; k < R / 2; k += blockDim.x) {
         int a, b;
         if (k == 0) { a = R - 1; b = round; }
         else { a = (round + k) % (R - 1); b = (round - k + R - 1) % (R - 1); }
         const int p = min(a, b), q = max(a, b);
-        const double apq = A[p + R * q];
-        double c = 1.0, s = 0.0;
-        if (apq != 0.0) {
-          const double tau = (A[q + R * q] - A[p + R * p]) / (2.0 * apq);
-          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + t * t);
-          s = t * c;
+        const T apq = A[p + R * q];
+        T c = T(1), sn = T(0);
+        if (apq != T(0)) {
+          const T tau = (A[q + R * q] - A[p + R * p]) / (T(2) * apq);
+          const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+          c = T(1) / sqrt(T(1) + t * t);
+          sn = t * c;
         }
-        cs[2 * k] = c; cs[2 * k + 1] = s;
+        cs[2 * k] = c; cs[2 * k + 1] = sn;
         pq[2 * k] = p; pq[2 * k + 1] = q;
       }
       __syncthreads();
@@ -105,39 +97,111 @@ __global__ void jacobi_kernel(const double* __restrict__ Vin, int r, double* dV,
       for (int t = threadIdx.x; t < (R / 2) * R; t += blockDim.x) {
         const int k = t / R, col = t % R;
         const int p = pq[2 * k], q = pq[2 * k + 1];
-        const double c = cs[2 * k], s = cs[2 * k + 1];
-        const double ap = A[p + R * col], aq = A[q + R * col];
-        A[p + R * col] = c * ap - s * aq;
-        A[q + R * col] = s * ap + c * aq;
+        const T c = cs[2 * k], sn = cs[2 * k + 1];
+        const T ap = A[p + R * col], aq = A[q + R * col];
+        A[p + R * col] = c * ap - sn * aq;
+        A[q + R * col] = sn * ap + c * aq;
       }
       __syncthreads();
       // columns of A and Q: (AJ)(:,p) = c A(:,p) - s A(:,q); (AJ)(:,q) = s A(:,p) + c A(:,q)
       for (int t = threadIdx.x; t < (R / 2) * R; t += blockDim.x) {
         const int k = t / R, row = t % R;
         const int p = pq[2 * k], q = pq[2 * k + 1];
-        const double c = cs[2 * k], s = cs[2 * k + 1];
-        const double ap = A[row + R * p], aq = A[row + R * q];
-        A[row + R * p] = c * ap - s * aq;
-        A[row + R * q] = s * ap + c * aq;
-        const double qp = Q[row + R * p], qq = Q[row + R * q];
-        Q[row + R * p] = c * qp - s * qq;
-        Q[row + R * q] = s * qp + c * qq;
+        const T c = cs[2 * k], sn = cs[2 * k + 1];
+        const T ap = A[row + R * p], aq = A[row + R * q];
+        A[row + R * p] = c * ap - sn * aq;
+        A[row + R * q] = sn * ap + c * aq;
+        const T qp = Q[row + R * p], qq = Q[row + R * q];
+        Q[row + R * p] = c * qp - sn * qq;
+        Q[row + R * q] = sn * qp + c * qq;
       }
       __syncthreads();
     }
   }
+}
+
+__global__ void jacobi_kernel(const double* __restrict__ Vin, int r, double* dV, double* UV,
+                              int max_sweeps, int* info) {
+  extern __shared__ double smj[];
+  const int R = r + (r & 1);
+  double* A = smj;              // R x R, A[i + R j]
+  double* Q = A + R * R;        // R x R
+  double* Tm = Q + R * R;       // R x R (FP64 work)
+  double* cs = Tm + R * R;      // R/2 x 2
+  float* A32 = reinterpret_cast<float*>(cs + R);  // R x R
+  float* Q32 = A32 + R * R;                       // R x R
+  float* cs32 = Q32 + R * R;                      // R/2 x 2
+  int* pq = reinterpret_cast<int*>(cs32 + R);     // R/2 x 2
+  __shared__ double red[64];  // block_sum<2> scratch: 2 x 32
+  __shared__ double stats[2];
+  for (int t = threadIdx.x; t < R * R; t += blockDim.x) {
+    const int i = t % R, j = t / R;
+    const double v = (i < r && j < r) ? Vin[i + (int64_t)r * j] : 0.0;
+    A[t] = v;
+    A32[t] = (float)v;
+    Q32[t] = i == j ? 1.f : 0.f;
+  }
+  __syncthreads();
+  // FP32 sweeps: an approximate eigenbasis Q0
+  jacobi_sweeps<float>(A32, Q32, cs32, pq, R, 40, 1e-12, red, stats);
+  // Q0 is orthogonal only to FP32 accuracy: two Newton-Schulz steps
+  // Q <- Q (3 I - Q'Q) / 2 in FP64 take ||I - Q'Q|| from ~1e-7 to rounding.
+  for (int t = threadIdx.x; t < R * R; t += blockDim.x) Q[t] = (double)Q32[t];
+  __syncthreads();
+  for (int step = 0; step < 2; ++step) {
+    for (int t = threadIdx.x; t < R * R; t += blockDim.x) {  // Tm = (3 I - Q'Q) / 2
+      const int i = t % R, j = t / R;
+      double acc = 0.0;
+      for (int k = 0; k < R; ++k) acc = fma(Q[k + R * i], Q[k + R * j], acc);
+      Tm[t] = (i == j ? 1.5 : 0.0) - 0.5 * acc;
+    }
+    __syncthreads();
+    // Q <- Q Tm: every thread first computes its entries (at most
+    // R*R / blockDim = 16 for R <= 64 and 256 threads), then all write.
+    double qn[16];
+    int cnt = 0;
+    for (int t = threadIdx.x; t < R * R; t += blockDim.x, ++cnt) {
+      const int i = t % R, j = t / R;
+      double acc = 0.0;
+      for (int k = 0; k < R; ++k) acc = fma(Q[i + R * k], Tm[k + R * j], acc);
+      qn[cnt] = acc;
+    }
+    __syncthreads();
+    cnt = 0;
+    for (int t = threadIdx.x; t < R * R; t += blockDim.x, ++cnt) Q[t] = qn[cnt];
+    __syncthreads();
+  }
+  // B = Q' V Q in FP64 (V is still in A): Tm = V Q, then A = Q' Tm
+  for (int t = threadIdx.x; t < R * R; t += blockDim.x) {
+    const int i = t % R, j = t / R;
+    double acc = 0.0;
+    for (int k = 0; k < R; ++k) acc = fma(A[i + R * k], Q[k + R * j], acc);
+    Tm[t] = acc;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < R * R; t += blockDim.x) {
+    const int i = t % R, j = t / R;
+    double acc = 0.0;
+    for (int k = 0; k < R; ++k) acc = fma(Q[k + R * i], Tm[k + R * j], acc);
+    A[t] = acc;
+  }
+  __syncthreads();
+  // FP64 sweeps on B, rotations accumulated into Q = Q0 J
+  jacobi_sweeps<double>(A, Q, cs, pq, R, max_sweeps, 1e-28, red, stats);
   for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
     const int i = t % r, j = t / r;
     UV[t] = Q[i + R * j];
   }
   for (int t = threadIdx.x; t < r; t += blockDim.x) dV[t] = A[t + R * t];
-  if (threadIdx.x == 0) *info = (off_s <= 1e-28 * nrm_s || off_s == 0.0) ? 0 : 1;
+  if (threadIdx.x == 0)
+    *info = (stats[0] <= 1e-28 * stats[1] || stats[0] == 0.0) ? 0 : 1;
 }
 
 cudaError_t launch_jacobi_eig(const double* V, int r, double* dV, double* UV, int max_sweeps,
                               int* info, cudaStream_t st) {
   const int R = r + (r & 1);
-  const size_t smem = (size_t)(2 * R * R + R) * sizeof(double) + (size_t)R * sizeof(int);
+  const size_t smem = (size_t)(3 * R * R + R) * sizeof(double) +
+                      (size_t)(2 * R * R + R) * sizeof(float) + (size_t)R * sizeof(int);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
