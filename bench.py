@@ -79,6 +79,28 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_over_ranks(world, device, sums, maxes):
+    """Whole-job aggregation of independent replicas: `sums` are added over
+    the ranks (units processed), `maxes` take the slowest rank (times).  With
+    one rank the values are returned as they are."""
+    sums, maxes = [float(x) for x in sums], [float(x) for x in maxes]
+    if world == 1:
+        return sums, maxes
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(sums, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    u = torch.tensor(maxes, dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.MAX)
+    return t.tolist(), u.tolist()
+
+
+def replica_seed(rank: int, base: int = 0) -> int:
+    """Seed of rank `rank`'s independent subproblem (replicas only: no data
+    is exchanged between ranks)."""
+    return base + rank
+
+
 def make_problem(args, seed):
     import synth
     over = {}
@@ -474,7 +496,7 @@ def main():
     import paper_2603_25691_gb300 as pkg
 
     # ---- inputs (each rank: its own independent subproblem; replicas only)
-    p = make_problem(args, seed=rank)
+    p = make_problem(args, seed=replica_seed(rank))
     dK, UK = np.linalg.eigh(p.K)
     n, r, q = p.n, p.r, p.q
     dev = torch.device("cuda", local)
@@ -522,21 +544,15 @@ def main():
         torch.cuda.synchronize()
     elapsed_ms = ev0.elapsed_time(ev1)
     step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
     iters = sum(s["iterations"] for s in stats)
     iter_phase_ms = sum(s["iter_ms"] for s in stats)
-    if world > 1:
-        t = torch.tensor([iter_phase_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        iter_phase_ms = float(t.item())
     # The metric: observations x PCG iterations per second of iteration phase
     # (operator, updates, preconditioner, FP64 true residuals and restarts),
-    # summed over all ranks' independent problems.
-    value = q * iters * world / (iter_phase_ms / 1e3)
-    solves_per_s = args.steps * world / (elapsed_ms / 1e3)
+    # summed over all ranks' independent problems, over the slowest rank's time.
+    (job_obs_iter, job_solves), (elapsed_ms, iter_phase_ms) = reduce_over_ranks(
+        world, dev, [q * iters, args.steps], [elapsed_ms, iter_phase_ms])
+    value = job_obs_iter / (iter_phase_ms / 1e3)
+    solves_per_s = job_solves / (elapsed_ms / 1e3)
     gds_ms = sum(s["gds_ms"] for s in stats)
     gds_bytes_per_launch = q * r * 4 + 2 * n * r * 4  # Zhat (FP32 part) + Xhat rows + Yhat1
     gds_exec = iters
@@ -634,7 +650,7 @@ def main():
                        "l2": "inputs larger than L2"},
             "solves_per_s": solves_per_s,
             "latency_ms": {"p50": pct(0.5), "p99": pct(0.99), "steps": step_ms},
-            "step_obs_iter_per_s": q * iters * world / (elapsed_ms / 1e3),
+            "step_obs_iter_per_s": job_obs_iter / (elapsed_ms / 1e3),
             "iterations_per_solve": iters / args.steps,
             "rel_residual": [s["rel_residual"] for s in stats],
             "phases_ms_per_solve": {
