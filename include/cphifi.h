@@ -174,6 +174,8 @@ const char* cphifi_status_string(int status);
 int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
                          const double* UK, const double* DK, int mem,
                          cphifi_kernel** out);
+/* Fails with CPHIFI_E_INVALID_ARG while a submitted request that uses the
+ * kernel has not completed. */
 int cphifi_kernel_destroy(cphifi_kernel* kern);
 
 /* ---- one subproblem (§4: everything that depends on the observations) ---
@@ -236,8 +238,8 @@ int cphifi_solve(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
  *
  * cphifi_submit   queues a request and returns its ticket at once.  The
  *                 caller keeps every buffer it names (factors, observation
- *                 lists, W0, W_out) alive and unchanged until cphifi_wait
- *                 returns for that ticket.  Device-memory inputs are read
+ *                 lists, W0, W_out) and the kernel handle alive and unchanged
+ *                 until cphifi_wait returns for that ticket.  Device-memory inputs are read
  *                 in order after the work the caller queued on the stream set
  *                 by cphifi_ctx_set_stream before the submit.  A request whose
  *                 footprint exceeds the budget even alone completes with

@@ -279,11 +279,17 @@ class Kernel:
         self.h = h
 
     def close(self):
+        """cphifi_kernel_destroy (raises while submitted requests still use it)."""
         if getattr(self, "h", None):
-            lib().cphifi_kernel_destroy(self.h)
+            rc = lib().cphifi_kernel_destroy(self.h)
+            _check(self.ctx.h, rc, "kernel_destroy")
             self.h = None
 
-    __del__ = close
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _factor_bufs(factors, r):
@@ -554,7 +560,8 @@ def submit(ctx: Context, kernel: Kernel, factors, kidx, oidx, vals, r: int, lam:
                              o.ptr, v.ptr, flags, ctypes.byref(prm), w0.ptr if w0 else None,
                              wb.ptr, k.mem, ctypes.byref(t))
     _check(ctx.h, rc, "submit")
-    return Request(ctx, t.value, (fb, k, o, v, wb, w0, sizes_arr, fptrs, prm), wb.obj)
+    # the request keeps its buffers and the kernel handle alive until wait()
+    return Request(ctx, t.value, (kernel, fb, k, o, v, wb, w0, sizes_arr, fptrs, prm), wb.obj)
 
 
 def gds_noalloc(n: int, r: int, q: int, row_ptr, zhat, ldz: int, Xhat, Y1, stream=None):

@@ -671,9 +671,13 @@ extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
   return CPHIFI_OK;
 }
 
+static bool kernel_in_use(const cphifi_ctx* ctx, const cphifi_kernel* kern);
+
 extern "C" int cphifi_kernel_destroy(cphifi_kernel* kern) {
   if (!kern) return CPHIFI_E_INVALID_ARG;
   cphifi_ctx* ctx = kern->ctx;
+  if (kernel_in_use(ctx, kern))
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "kernel still used by submitted requests");
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(ctx->device);
@@ -1993,6 +1997,12 @@ bool progress(cphifi_ctx* ctx) {
 }
 
 }  // namespace
+
+static bool kernel_in_use(const cphifi_ctx* ctx, const cphifi_kernel* kern) {
+  for (const auto& kv : ctx->requests)
+    if (kv.second->kern == kern && kv.second->state != Request::DONE) return true;
+  return false;
+}
 
 static void requests_clear(cphifi_ctx* ctx) {
   for (auto& kv : ctx->requests) {

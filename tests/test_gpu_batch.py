@@ -241,3 +241,19 @@ def test_invalid_inputs_fail_the_request_only(pkg, batch):
     for rq in (r0, r3):
         W, st = rq.wait()
         np.testing.assert_array_equal(W, alone[0][0])
+
+
+def test_kernel_in_use_cannot_be_destroyed(pkg):
+    ctx = pkg.Context(0)
+    p, prec, tol = _problems()[1]
+    dK, UK = np.linalg.eigh(p.K)
+    k = ctx.kernel_create(p.n, UK, dK)
+    rq = pkg.submit(ctx, k, p.factors, p.kidx, p.oidx, p.vals, p.r, p.lam, p.rho, tol,
+                    max_iter=2000, precision=prec)
+    with pytest.raises(pkg.CphifiError) as e:
+        k.close()
+    assert e.value.status == pkg.E_INVALID_ARG
+    W, st = rq.wait()
+    assert st["status"] == pkg.OK
+    k.close()  # the request has completed: now it may go
+    ctx.close()
