@@ -736,11 +736,14 @@ static void problem_need(const cphifi_ctx* ctx, int n, bool tc, int32_t d_other,
 
 // Problem creation on stream `st` (the context's stream for the public call, a
 // pool stream for submitted requests).
-// With `async` set (submitted requests) nothing waits for the device: input
-// errors stay in the problem's error word, which the kernels after the
-// validation check before touching memory and the solve reads at its first
-// step; the piece arrays are sized by their upper bound; the temporaries go
-// back to the pool once an event after their last use has completed.
+// The device work is queued without host waits: the kernels after the input
+// validation check the problem's error word before touching memory, the piece
+// arrays take their upper bound (the exact count stays on the device).  A
+// synchronous creation then waits once, reads the error word and returns the
+// temporaries to the pool.  With `async` set (submitted requests) nothing
+// waits at all: the solve reads the error word at its first step and the
+// temporaries go back to the pool once an event after their last use has
+// completed.
 static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
                              const int64_t* other_sizes, const double* const* factors, int32_t r,
                              int64_t q, const int32_t* kidx, const int32_t* oidx,
@@ -952,14 +955,10 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
   PCK(launch_validate_obs(kidx_d, oidx_d, vals_d, q, n, d_other, P->sizes_dev, P->err, st));
   PCK(cudaMemcpyAsync(keys, kidx_d, (size_t)q * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
   PCK(launch_iota(P->perm, q, st));
+  // No host wait from here on: the kernels after the validation are gated on
+  // the error word, which a synchronous creation reads once at the end.
   int herr = 0;
-  if (!async) {
-    PCK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    PCK(cudaStreamSynchronize(st));
-    if (herr & 1) return bail(CPHIFI_E_INVALID_ARG, "observation index out of range");
-    if (herr & 2) return bail(CPHIFI_E_INVALID_ARG, "non-finite observation value or factor entry");
-  }
-  const int* gate = async ? P->err : nullptr;
+  const int* gate = P->err;
   if (!(flags & CPHIFI_OBS_SORTED) && q > 1) {
     void* rtmp = tmp_alloc(radix_sort_tmp_bytes(q));
     if (!rtmp) return bail(CPHIFI_E_OOM, "temporary allocation failed");
@@ -974,12 +973,7 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
     PCK(launch_piece_counts(P->row_ptr, n, L, P->seg_count, gate, st));
     PCK(exclusive_scan_i32(P->seg_count, P->seg_first, n, stmp, exclusive_scan_tmp_bytes(n), st));
     int np = 0;
-    if (async) {
-      np = q > 0 ? (int)npieces_max : 0;  // the exact count stays on the device
-    } else {
-      PCK(cudaMemcpyAsync(&np, P->seg_first + n, sizeof(int), cudaMemcpyDeviceToHost, st));
-      PCK(cudaStreamSynchronize(st));
-    }
+    np = q > 0 ? (int)npieces_max : 0;  // the exact count stays on the device
     P->npieces = np;
     PCK(dalloc(P, &P->pseg, np));
     PCK(dalloc(P, &P->pbeg, np));
@@ -987,8 +981,7 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
     PCK(dalloc(P, (double**)&P->gds_partial, (size_t)np * 64));
     PCK(launch_piece_fill(P->row_ptr, n, L, P->seg_first, P->seg_count, P->pseg, P->pbeg,
                           P->pend, gate, st));
-    PCK(launch_warp_first(P->pbeg, np, async ? P->seg_first + n : nullptr, L, W, P->warp_first,
-                          gate, st));
+    PCK(launch_warp_first(P->pbeg, np, P->seg_first + n, L, W, P->warp_first, gate, st));
   }
 
   // ---- Zhat, then the right-hand side MTTKRP
