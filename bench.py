@@ -101,6 +101,13 @@ def replica_seed(rank: int, base: int = 0) -> int:
     return base + rank
 
 
+def config_dict(args, p, world):
+    """The workload description shared by both arms' JSON lines."""
+    return {"workload": args.workload, "n": p.n, "other_sizes": p.other_sizes, "q": p.q,
+            "r": p.r, "lambda": p.lam, "rho": p.rho, "tol": TOL, "precision": args.precision,
+            "parallelism": f"replicas x{world}", "l2": "inputs larger than L2"}
+
+
 def make_problem(args, seed):
     import synth
     over = {}
@@ -217,8 +224,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic planted low rank (seeded)",
-            "config": {"workload": args.workload, "n": p.n, "other_sizes": p.other_sizes,
-                       "q": p.q, "r": p.r, "lambda": p.lam, "rho": p.rho},
+            "config": config_dict(args, p, world),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"one FP64 oracle PCG iteration (NumPy) per step on the "
                                        f"first {min(sample_q, p.q)} sorted observations, full n"},
@@ -644,10 +650,7 @@ def main():
                       "fp64_emulated": "df64 (fp32-pair) operator, f64 CG",
                       "fp64": "f64"}[args.precision],
             "data": "synthetic planted low rank (seeded), inputs larger than L2 (no flush)",
-            "config": {"workload": args.workload, "n": n, "other_sizes": p.other_sizes, "q": q,
-                       "r": r, "lambda": p.lam, "rho": p.rho, "tol": TOL,
-                       "precision": args.precision, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2"},
+            "config": config_dict(args, p, world),
             "solves_per_s": solves_per_s,
             "latency_ms": {"p50": pct(0.5), "p99": pct(0.99), "steps": step_ms},
             "step_obs_iter_per_s": job_obs_iter / (elapsed_ms / 1e3),
