@@ -8,10 +8,18 @@ tolerance 1e-6 on the FP64 true relative residual.  Synthetic data (seeded).
 
 A step is one subproblem through every step of the path: problem creation
 from device-resident inputs (validation, Zhat, row pointer, pieces, Gram,
-eig(V), MTTKRP) followed by the PCG solve (right-hand side, iterations, FP64
-true-residual restarts, W = U_K Wbar).  eig(K) is the one-time per-kernel
-setup and stays outside the timed region.  Zhat (8 GB in FP32) is far larger
-than the 129 MB L2, so no flush is needed between steps.
+eig(V), MTTKRP) followed by the PCG solve (right-hand side, iterations,
+FP64-accurate true residuals, W = U_K Wbar).  eig(K) is the one-time
+per-kernel setup and stays outside the timed region.  Zhat (16 GB as an FP32
+pair) is far larger than the 129 MB L2, so no flush is needed between steps.
+
+Besides the headline line's own fields, the same JSON line carries: the FP64
+path on the same workload, the other operator arithmetics (--sweep), the
+end-to-end rate through the one-shot call with pinned host buffers, a batch
+of 256 uneven subproblems submitted at once (--batch), Poisson-arrival
+serving (--serve-rates), the alternating fit of the full model (--als-ranks),
+the paper's vortex / Miranda shapes (--no-paper-shapes to skip), the FP64
+oracle on a bounded sample of the host cores, and nvidia-smi clocks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
