@@ -114,6 +114,7 @@ struct cphifi_problem {
   int32_t *pseg = nullptr, *pbeg = nullptr, *pend = nullptr, *seg_first = nullptr,
           *seg_count = nullptr, *warp_first = nullptr;
   unsigned* seg_ticket = nullptr;
+  unsigned* wctr = nullptr;  // dynamic work counters of the observation passes (2, zero)
   int npieces = 0;
   int nwarps = 1;     // warps of the gather-dot/scatter, L observations each
   int64_t obs_per_warp = 1;
@@ -888,6 +889,8 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
   }
   for (auto& e : P->ev) PCK(event_get(ctx, &e));
   PCK(cudaMemsetAsync(P->seg_ticket, 0, n * sizeof(unsigned), st));
+  PCK(dalloc(P, &P->wctr, 2));
+  PCK(cudaMemsetAsync(P->wctr, 0, 2 * sizeof(unsigned), st));
   PCK(cudaMemsetAsync(P->err, 0, sizeof(int), st));
   PCK(cudaMemsetAsync(P->info, 0, sizeof(int), st));
 
@@ -973,7 +976,7 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
     if (!tdf_tmp) return bail(CPHIFI_E_OOM, "temporary allocation failed");
   }
   PieceList pl{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket,
-               P->warp_first, P->npieces, P->nwarps};
+               P->warp_first, P->npieces, P->nwarps, P->wctr};
   PCK(launch_zhat_mttkrp(pl, (flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm, oidx_d, d_other,
                          P->fhl_dev, P->sizes_dev, r, vals_d, P->zhi, P->zlo,
                          P->z64, (double*)P->gds_partial, P->Bm, n, P->err, gate,
@@ -1056,7 +1059,7 @@ struct Launcher {
 
   PieceList pieces() const {
     return PieceList{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket,
-                     P->warp_first, P->npieces, P->nwarps};
+                     P->warp_first, P->npieces, P->nwarps, P->wctr};
   }
   int64_t split_stride() const { return (int64_t)P->n * P->r; }
 
@@ -1661,7 +1664,7 @@ static int problem_rebuild(cphifi_problem* P) {
   CK(launch_jacobi_eig(P->V, r, P->dV, P->UV, 60, P->info, st));
   CK(launch_convert<double, float>(P->UV, P->UV32, (int64_t)r * r, st));
   const PieceList pl{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket,
-                     P->warp_first, P->npieces, P->nwarps};
+                     P->warp_first, P->npieces, P->nwarps, P->wctr};
   void* tdf = nullptr;
   size_t gt = 0;
   if (P->zhi) CK(pool_alloc(ctx, (size_t)std::max<int64_t>(P->q, 1) * 2 * sizeof(float), &tdf, &gt));

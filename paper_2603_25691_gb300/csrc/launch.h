@@ -76,6 +76,12 @@ struct PieceList {
   const int32_t* warp_first;  // nwarps + 1
   int npieces;
   int nwarps;
+  // Optional dynamic assignment (2 counters, zero between launches): physical
+  // warps draw the ranges (and the Zhat build its tile chunks) from wctr[0],
+  // so blocks that start late -- their SM held by another stream's kernel --
+  // take less work instead of running their fixed share after all others.
+  // The last warp to finish resets both counters.  NULL: static shares.
+  unsigned* wctr = nullptr;
 };
 // Gather-dot/scatter in three arithmetics (all in the tiled Zhat layout):
 // FP32 reading Zhat's hi part (mixed operator), FP64 reading z64 (FP64

@@ -481,7 +481,7 @@ zhat_build_kernel(int64_t q, const int32_t* __restrict__ perm, const int32_t* __
                   const int64_t* __restrict__ sizes, int r,
                   float* __restrict__ zhi, float* __restrict__ zlo, double* __restrict__ z64,
                   const double* __restrict__ vals, float2* __restrict__ tdf, int* err,
-                  const int* gate) {
+                  const int* gate, unsigned* wctr) {
   if (gate && *gate) return;  // invalid input found earlier: touch nothing
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -489,7 +489,16 @@ zhat_build_kernel(int64_t q, const int32_t* __restrict__ perm, const int32_t* __
   const int64_t ntiles = (q + 31) >> 5;
   const bool vec = (r % 4 == 0);  // 16-byte aligned factor rows
   int bad = 0;
-  for (int64_t tile = gw; tile < ntiles; tile += nw) {
+  // tiles in chunks of 8, drawn from the counter (dynamic) or taken grid-stride
+  constexpr int64_t kChunk = 8;
+  auto draw = [&]() -> int64_t {
+    unsigned v = 0;
+    if (lane == 0) v = atomicAdd(&wctr[0], 1u);
+    return (int64_t)__shfl_sync(0xffffffffu, v, 0) * kChunk;
+  };
+  for (int64_t t0 = wctr ? draw() : gw * kChunk; t0 < ntiles;
+       t0 = wctr ? draw() : t0 + nw * kChunk)
+  for (int64_t tile = t0; tile < min(t0 + kChunk, ntiles); ++tile) {
     const int64_t l = tile * 32 + lane;
     if (l >= q) continue;
     const int64_t src = perm ? (int64_t)perm[l] : l;
@@ -547,6 +556,14 @@ zhat_build_kernel(int64_t q, const int32_t* __restrict__ perm, const int32_t* __
     }
   }
   if (bad) atomicOr(err, 1);
+  if (wctr && lane == 0) {  // the last warp out resets the counters
+    __threadfence();
+    if (atomicAdd(&wctr[1], 1u) == (unsigned)nw - 1) {
+      wctr[0] = 0u;
+      wctr[1] = 0u;
+      __threadfence();
+    }
+  }
 }
 
 // ------------------------------------------------ gather-dot / scatter ----
@@ -612,7 +629,13 @@ __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __r
   const int wib = threadIdx.x >> 5;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int w = gw; w < pl.nwarps; w += nwarps) {
+  // virtual warp ranges: drawn from the counter (dynamic) or w = gw + k nwarps
+  auto draw = [&]() -> int {
+    unsigned v = 0;
+    if (lane == 0) v = atomicAdd(&pl.wctr[0], 1u);
+    return (int)__shfl_sync(0xffffffffu, v, 0);
+  };
+  for (int w = pl.wctr ? draw() : gw; w < pl.nwarps; w = pl.wctr ? draw() : w + nwarps) {
     const int p_end = pl.warp_first[w + 1];
     for (int p = pl.warp_first[w]; p < p_end; ++p) {
       const int seg = pl.seg[p];
@@ -683,6 +706,14 @@ __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __r
       store_row<IO, RP, LPO>(pl, p, seg, r, accd, partial, Y, yld);
     }
   }
+  if (pl.wctr && lane == 0) {  // the last warp out resets the counters
+    __threadfence();
+    if (atomicAdd(&pl.wctr[1], 1u) == (unsigned)nwarps - 1) {
+      pl.wctr[0] = 0u;
+      pl.wctr[1] = 0u;
+      __threadfence();
+    }
+  }
 }
 
 struct GdsWeights {
@@ -750,11 +781,11 @@ cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const i
   if (z64)
     zhat_build_kernel<true><<<(int)blocks, 256, 0, st>>>(q, perm, oidx, d_other, fhl,
                                                          sizes_dev, r, zhi, zlo, z64, vals, tdf,
-                                                         err, gate);
+                                                         err, gate, pl.wctr);
   else
     zhat_build_kernel<false><<<(int)blocks, 256, 0, st>>>(q, perm, oidx, d_other, fhl,
                                                           sizes_dev, r, zhi, zlo, z64, vals, tdf,
-                                                          err, gate);
+                                                          err, gate, pl.wctr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   GdsWeights wt;
