@@ -449,25 +449,9 @@ __device__ __forceinline__ void store_row(const PieceList& pl, int p, int seg, i
   }
 }
 
-// Factor row part (CPL consecutive columns of row `off`, row-major hi/lo):
-// 16-byte loads when the row and the lane's column block are 16-byte aligned.
-template <int CPL>
-__device__ __forceinline__ void load_row_part(const float* __restrict__ base, bool vec,
-                                              float (&v)[CPL]) {
-  if (CPL % 4 == 0 && vec) {
-#pragma unroll
-    for (int c = 0; c < CPL; c += 4) {
-      const float4 t = __ldg(reinterpret_cast<const float4*>(base + c));
-      v[c] = t.x; v[c + 1] = t.y; v[c + 2] = t.z; v[c + 3] = t.w;
-    }
-  } else {
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) v[c] = __ldg(base + c);
-  }
-}
-
-// One lane per observation, tiles of 32 sorted observations taken grid-stride
-// by the warps: every column of a Zhat tile is written by one coalesced
+// One lane per observation, tiles of 32 sorted observations in chunks of 8
+// tiles that the warps draw from a counter (grid-stride when no counter is
+// given): every column of a Zhat tile is written by one coalesced
 // 128-byte store per array.  Each lane walks the columns in groups of 4
 // (16-byte factor-row loads) and forms the double-float product over the
 // other modes.  No per-lane state survives a tile, so registers stay few and
