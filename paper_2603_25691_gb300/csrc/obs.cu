@@ -449,6 +449,22 @@ __device__ __forceinline__ void store_row(const PieceList& pl, int p, int seg, i
   }
 }
 
+// Eight consecutive floats from read-only global memory in one 256-bit load
+// (sm_100 and later); p must be 32-byte aligned.  A lane's 32-byte sector
+// then takes one load instead of two: the factor-row gathers of the Zhat
+// build are bound by the L1 data stage.
+__device__ __forceinline__ void ldg_v8(const float* p, float (&v)[8]) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
+        "=f"(v[7])
+      : "l"(p));
+}
+
+// Resident 256-thread blocks per SM of the Zhat build (a register budget of
+// 40 per thread: with 32 the compiler spills to local memory, which shares the
+// L1 data path that the factor-row gathers saturate).
+constexpr int kBuildBlocksPerSM = 6;
+
 // One lane per observation, tiles of 32 sorted observations in chunks of 8
 // tiles that the warps draw from a counter (grid-stride when no counter is
 // given): every column of a Zhat tile is written by one coalesced
@@ -459,7 +475,7 @@ __device__ __forceinline__ void store_row(const PieceList& pl, int p, int seg, i
 // W64: also store Zhat in FP64 (a template flag, so the FP64 conversions are
 // not executed, even speculatively, when only the FP32 pair is stored).
 template <bool W64>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, kBuildBlocksPerSM)
 zhat_build_kernel(int64_t q, const int32_t* __restrict__ perm, const int32_t* __restrict__ oidx,
                   int d_other, const float* const* __restrict__ fhl,
                   const int64_t* __restrict__ sizes, int r,
@@ -471,7 +487,10 @@ zhat_build_kernel(int64_t q, const int32_t* __restrict__ perm, const int32_t* __
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t ntiles = (q + 31) >> 5;
-  const bool vec = (r % 4 == 0);  // 16-byte aligned factor rows
+  // 32-byte aligned groups of 4 (hi, lo) pairs: one 256-bit load each
+  bool vec = (r % 4 == 0);
+  for (int m = 0; m < d_other; ++m)
+    vec = vec && ((reinterpret_cast<uintptr_t>(fhl[m]) & 31) == 0);
   int bad = 0;
   // tiles in chunks of 8, drawn from the counter (dynamic) or taken grid-stride
   constexpr int64_t kChunk = 8;
@@ -505,10 +524,13 @@ zhat_build_kernel(int64_t q, const int32_t* __restrict__ perm, const int32_t* __
         const int64_t off = (ok ? (int64_t)__ldg(im + m) : 0) * r + j0;
         float h[4], lo[4];
         if (vec) {  // columns j0..j0+3 as (hi, lo) pairs: one 32-byte sector
-          const float4* p4 = reinterpret_cast<const float4*>(fhl[m] + 2 * off);
-          const float4 a = __ldg(p4), c = __ldg(p4 + 1);
-          h[0] = a.x; lo[0] = a.y; h[1] = a.z; lo[1] = a.w;
-          h[2] = c.x; lo[2] = c.y; h[3] = c.z; lo[3] = c.w;
+          float v[8];
+          ldg_v8(fhl[m] + 2 * off, v);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            h[u] = v[2 * u];
+            lo[u] = v[2 * u + 1];
+          }
         } else {
           const float2* p2 = reinterpret_cast<const float2*>(fhl[m]) + off;
 #pragma unroll
@@ -592,7 +614,7 @@ __device__ __forceinline__ double acc_out(df a) { return df_to_double(df_norm(a)
 // weight t_l (wts[wperm[l]], or wts[l] without a permutation) instead of the
 // dot product, so Y(i,:) = sum_{i_l = i} t_l Zhat(l,:).
 template <int MODE, int RP, int LPO, bool WTS>
-__global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __restrict__ zhi,
+__global__ void __launch_bounds__(256, 2) gds_kernel(PieceList pl, const float* __restrict__ zhi,
                                                   const float* __restrict__ zlo,
                                                   const double* __restrict__ z64, int r,
                                                   const typename GdsTypes<MODE>::IO* __restrict__ Xh,
@@ -636,14 +658,12 @@ __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __r
       Acc acc[CPL];
 #pragma unroll
       for (int c = 0; c < CPL; ++c) acc[c] = acc_zero(Acc());
-      // Every lane runs the same number of rounds so the cross-lane sums of
-      // the dot product see the whole warp.
-      for (int l0 = b; l0 < e; l0 += OPW) {
+      // Zhat values of the OPW observations of the round starting at l0
+      auto load = [&](int l0, Acc (&z)[CPL]) {
         const int l = l0 + o;
         const bool act = l < e;
         // hi/lo pair: tile stride 64 r (lo block at +32 r); FP64: 32 r
         const int64_t base = zidx(act ? l : b, 0, (MODE == GDS_F64 ? 32 : 64) * (int64_t)r);
-        Acc z[CPL];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
           const int j = sub * CPL + c;
@@ -652,6 +672,26 @@ __global__ void __launch_bounds__(256) gds_kernel(PieceList pl, const float* __r
           else if constexpr (MODE == GDS_F64) z[c] = ld ? __ldcs(z64 + base + 32 * j) : 0.0;
           else z[c] = ld ? df{__ldcs(zhi + base + 32 * j), __ldcs(zhi + base + 32 * (r + j))}
                          : df{0.f, 0.f};
+        }
+      };
+      // double-float with 4 lanes per observation (r > 32): the next round's
+      // values are loaded while this round's arithmetic (half of the pass's
+      // time) runs; with fewer lanes the extra registers would spill
+      constexpr bool kPrefetch = MODE == GDS_DF && LPO >= 4;
+      Acc zn[kPrefetch ? CPL : 1];
+      if constexpr (kPrefetch) load(b, zn);
+      // Every lane runs the same number of rounds so the cross-lane sums of
+      // the dot product see the whole warp.
+      for (int l0 = b; l0 < e; l0 += OPW) {
+        const int l = l0 + o;
+        const bool act = l < e;
+        Acc z[CPL];
+        if constexpr (kPrefetch) {
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) z[c] = zn[c];
+          if (l0 + OPW < e) load(l0 + OPW, zn);
+        } else {
+          load(l0, z);
         }
         Acc xb;
         if constexpr (WTS) {
@@ -760,7 +800,7 @@ cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const i
     return cudaErrorInvalidValue;
   const int64_t tiles = (q + 31) / 32;
   int64_t blocks = (tiles + 7) / 8;
-  const int64_t cap = (int64_t)num_sms * 8;  // 8 resident 256-thread blocks per SM
+  const int64_t cap = (int64_t)num_sms * kBuildBlocksPerSM;  // one resident wave
   if (blocks > cap) blocks = cap;
   if (z64)
     zhat_build_kernel<true><<<(int)blocks, 256, 0, st>>>(q, perm, oidx, d_other, fhl,
