@@ -767,7 +767,10 @@ static cudaError_t gds_dispatch(const PieceList& pl, const float* zhi, const flo
 }
 
 // Lanes per observation keep the per-lane registers (RP/LPO values of the
-// row and of the accumulator) within budget.
+// row and of the accumulator) within budget.  The FP32 pass has a 40-column
+// instance (at r = 40, n = 8000, q = 5e7: 1.37 ms per pass against 1.48 ms
+// with 48 columns); the double-float pass ran slower with 40 columns (5.5
+// against 4.5 ms), so the wide modes keep 48.
 template <int MODE>
 static cudaError_t gds_by_rank(const PieceList& pl, const float* zhi, const float* zlo,
                                const double* z64, int r, const typename GdsTypes<MODE>::IO* Xh,
@@ -780,6 +783,9 @@ static cudaError_t gds_by_rank(const PieceList& pl, const float* zhi, const floa
   if (r <= 8) return gds_dispatch<MODE, 8, 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
   if (r <= 16) return gds_dispatch<MODE, 16, 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
   if (r <= 32) return gds_dispatch<MODE, 32, wide ? 2 : 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
+  if constexpr (!wide) {
+    if (r <= 40) return gds_dispatch<MODE, 40, 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
+  }
   if (r <= 48) return gds_dispatch<MODE, 48, wide ? 4 : 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
   if (r <= 64) return gds_dispatch<MODE, 64, wide ? 4 : 2>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
   return cudaErrorInvalidValue;
