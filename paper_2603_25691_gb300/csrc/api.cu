@@ -90,6 +90,12 @@ struct cphifi_kernel {
   __nv_bfloat16 *A1b = nullptr, *A2b = nullptr;
   float *A1h = nullptr, *A1l = nullptr, *A2h = nullptr, *A2l = nullptr;  // 3-term TF32 split
   CUtensorMap mA1f, mA2f, mA1b, mA2b, mA1h, mA1l, mA2h, mA2l;
+  // BF16 slices of U_K and U_K' for the FP64-accurate tensor-core products
+  // (oz_gemm.cu) and their row exponents (n for U_K, then n for U_K').
+  bool oz = false;
+  __nv_bfloat16 *oz1 = nullptr, *oz2 = nullptr;
+  int* oze = nullptr;
+  CUtensorMap mOz1, mOz2;
   double* dK = nullptr;    // n
   size_t bytes = 0;
 };
@@ -143,6 +149,11 @@ struct cphifi_problem {
   __nv_bfloat16 *pop16 = nullptr, *y116 = nullptr;
   float *poph = nullptr, *popl = nullptr, *y1h = nullptr, *y1l = nullptr;  // 3-term TF32 split
   CUtensorMap mBpf, mBpb, mByf, mByb, mBph, mBpl, mByh, mByl;
+  // B slices of the FP64-accurate tensor-core products (when the kernel has
+  // U_K slices) and their column exponents
+  __nv_bfloat16* ozb = nullptr;
+  int* ozce = nullptr;
+  CUtensorMap mOzb;
   int nsplittc = 1;
   int* tc_err = nullptr;
   // Stream, pinned scalar copy and phase events of this problem's solves (the
@@ -580,7 +591,8 @@ extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
     if (kern->UKlo) cudaFree(kern->UKlo);
     if (kern->dK) cudaFree(kern->dK);
     for (void* a : {(void*)kern->A1f, (void*)kern->A2f, (void*)kern->A1b, (void*)kern->A2b,
-                    (void*)kern->A1h, (void*)kern->A1l, (void*)kern->A2h, (void*)kern->A2l})
+                    (void*)kern->A1h, (void*)kern->A1l, (void*)kern->A2h, (void*)kern->A2l,
+                    (void*)kern->oz1, (void*)kern->oz2, (void*)kern->oze})
       if (a) cudaFree(a);
     if (err) cudaFree(err);
     delete kern;
@@ -653,10 +665,27 @@ extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
       cudaGetLastError();
       return cleanup(CPHIFI_E_DEVICE, "building the tensor-core copies of U_K failed");
     }
+    // slices for the FP64-accurate products, when the budget has room (else
+    // those products stay on the double-float SIMT kernel)
+    const size_t oz_bytes = oz_uk_bytes((int)n, ldt);
+    if (!ctx->budget || ctx->in_use + bytes + tc_bytes + oz_bytes <= ctx->budget) {
+      const size_t sb = (size_t)oz_mpad((int)n) * ldt * 7 * sizeof(__nv_bfloat16);
+      if (cudaMalloc(&kern->oz1, sb) == cudaSuccess && cudaMalloc(&kern->oz2, sb) == cudaSuccess &&
+          cudaMalloc(&kern->oze, 2 * (size_t)n * sizeof(int)) == cudaSuccess &&
+          launch_oz_uk(kern->UK64, (int)n, ldt, kern->oz1, kern->oz2, kern->oze, st) == cudaSuccess &&
+          oz_make_maps(kern->oz1, kern->oz2, (int)n, ldt, &kern->mOz1, &kern->mOz2) == cudaSuccess &&
+          cudaStreamSynchronize(st) == cudaSuccess) {
+        kern->oz = true;
+        tc_bytes += oz_bytes;
+      } else {
+        cudaGetLastError();
+        return cleanup(CPHIFI_E_DEVICE, "building the tensor-core slices of U_K failed");
+      }
+    }
   }
   cudaFree(err);
   kern->bytes = bytes + (kern->tc ? tc_bytes : 0);
-  ctx->in_use += bytes;
+  ctx->in_use += kern->bytes;
   *out = kern;
   return CPHIFI_OK;
 }
@@ -677,7 +706,8 @@ extern "C" int cphifi_kernel_destroy(cphifi_kernel* kern) {
   cudaFree(kern->UKlo);
   cudaFree(kern->dK);
   for (void* a : {(void*)kern->A1f, (void*)kern->A2f, (void*)kern->A1b, (void*)kern->A2b,
-                  (void*)kern->A1h, (void*)kern->A1l, (void*)kern->A2h, (void*)kern->A2l})
+                  (void*)kern->A1h, (void*)kern->A1l, (void*)kern->A2h, (void*)kern->A2l,
+                  (void*)kern->oz1, (void*)kern->oz2, (void*)kern->oze})
     if (a) cudaFree(a);
   ctx->in_use -= std::min(ctx->in_use, kern->bytes);
   cudaSetDevice(prev);
@@ -716,7 +746,8 @@ static void problem_need(const cphifi_ctx* ctx, int n, bool tc, int32_t d_other,
   const bool need64 = (flags & CPHIFI_NEED_FP64) || !(flags & CPHIFI_NEED_LOWP);
   const bool lowp = (flags & CPHIFI_NEED_LOWP) || !(flags & CPHIFI_NEED_FP64);
   *need = problem_footprint(n, q, r, d_other, sizes, lowp, nsplit, npieces_max) +
-          (need64 ? (size_t)zhat_elems(q, r) * sizeof(double) : 0);
+          (need64 ? (size_t)zhat_elems(q, r) * sizeof(double) : 0) +
+          (tc ? oz_b_bytes(r, ((int64_t)n + 7) / 8 * 8) : 0);  // B slices
   *tmp = (size_t)q * (sizeof(int32_t) * (1 + d_other) + sizeof(double) * 3 + sizeof(uint32_t)) +
          radix_sort_tmp_bytes(q);  // index/value copies, sort keys, double-float values
   if (flags & CPHIFI_KEEP_OBS)  // sorted observation lists + A_k
@@ -766,7 +797,7 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
   const int64_t npieces_max = (int64_t)n + W + 1;
   const int nsplit64 = gemm_pick_split<double, double>(n, ctx->num_sms);
   const int nsplit32 = gemm_pick_split<float, float>(n, ctx->num_sms);
-  const int nsplitdf = gemm_df_pick_split(n, ctx->num_sms);
+  const int nsplitdf = kern->oz ? oz_pick_split(n, ctx->num_sms) : gemm_df_pick_split(n, ctx->num_sms);
   const int nsplittc = kern->tc ? tc_pick_split(n, ctx->num_sms) : 1;
   const int nsplit = std::max(std::max(nsplit64, nsplit32), std::max(nsplitdf, nsplittc));
   // Operator data: FP64 Zhat for the FP64 operator, hi/lo FP32 pairs for the
@@ -874,6 +905,13 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
     PCK(tc_make_map(&P->mBpl, P->popl, false, n, r, P->ldt * 4, np));
     PCK(tc_make_map(&P->mByh, P->y1h, false, n, r, P->ldt * 4, np));
     PCK(tc_make_map(&P->mByl, P->y1l, false, n, r, P->ldt * 4, np));
+    if (kern->oz) {
+      const size_t cnt = (size_t)7 * np * P->ldt;
+      PCK(dalloc(P, &P->ozb, cnt));
+      PCK(cudaMemsetAsync(P->ozb, 0, cnt * sizeof(__nv_bfloat16), st));
+      PCK(dalloc(P, &P->ozce, 64));
+      PCK(oz_make_b_map(P->ozb, n, r, P->ldt, &P->mOzb));
+    }
   }
   PCK(dalloc(P, (double**)&P->cpart, (size_t)nsplit * nr));
   PCK(dalloc(P, &P->red.partials, (size_t)kRedMaxBlocks * kRedSlots));
@@ -1115,6 +1153,19 @@ struct Launcher {
   // partial products of op(U_K) diag(scale) B over nsplitdf splits.
   cudaError_t gemm_df(bool a_trans, const double* scale, const double* B, double* out_part,
                       const DevScalars* skip, int cat) {
+    if (P->ozb) {  // tensor cores, from BF16 slices of both operands
+      const cphifi_kernel* K = P->kern;
+      cudaError_t e = launch_oz_b(B, scale, P->n, P->r, P->n, P->ldt, P->ozb, P->ozce, skip, st);
+      ++launches;
+      if (e != cudaSuccess) return e;
+      cudaEvent_t b = cat && tm ? tm->begin() : nullptr;
+      e = launch_oz_gemm(a_trans ? K->mOz1 : K->mOz2, a_trans ? K->oze : K->oze + P->n, P->mOzb,
+                         P->ozce, out_part, P->n, split_stride(), P->n, P->r, P->nsplitdf, skip,
+                         P->tc_err, st);
+      if (cat && tm) tm->end(b, cat == 1 ? tm->gemm : tm->gemm64);
+      ++launches;
+      return e;
+    }
     cudaError_t e = launch_split_df(B, scale, P->n, (int64_t)P->n * P->r, P->Bhi, P->Blo, st);
     ++launches;
     if (e != cudaSuccess) return e;
@@ -1444,6 +1495,7 @@ struct SolveRun {
     h.mode = mixed ? 1 : 0;
     SR_CK(cudaEventRecord(P->ev[0], st));
     SR_CK(cudaMemcpyAsync(P->s, &h, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
+    if (P->tc_err) SR_CK(cudaMemsetAsync(P->tc_err, 0, sizeof(int), st));
     SR_CK(launch_build_D(P->kern->dK, P->dV, n, r, P->gamma, prm.lambda, prm.rho, P->D64, P->D32, st));
     // right-hand side in the eigenbasis: bbar = D_K U_K' B, and ||bbar||^2
     SR_CK(L.utb(emul, CM_DK_NORM, P->Bm, P->bbar, P->s));
@@ -1456,7 +1508,6 @@ struct SolveRun {
       SR_CK(cudaMemsetAsync(P->x, 0, nr * sizeof(double), st));
       SR_CK(cudaMemcpyAsync(P->res, P->bbar, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
-    if (P->tc_err) SR_CK(cudaMemsetAsync(P->tc_err, 0, sizeof(int), st));
     SR_CK(L.restart(prec));
     SR_CK(cudaEventRecord(P->ev[1], st));
     stage = INIT;

@@ -156,6 +156,31 @@ cudaError_t launch_tc_gemm(bool bf16, const CUtensorMap& ma, const CUtensorMap& 
                            const CUtensorMap* mal, const CUtensorMap* mbl, float* C, int64_t ldc,
                            int64_t split_stride, int n, int ncols, int nsplit,
                            const DevScalars* skip, int* err, cudaStream_t st);
+// ------------------------------------------------------------ oz_gemm.cu ---
+// FP64-accurate products op(U_K) B on the tensor cores from 7 BF16 slices of
+// each operand (error-free splitting, exact group sums in TMEM).  U_K slices:
+// a1 (rows of U_K), a2 (rows of U_K'), BF16 [7][oz_mpad(n)][ldt] each, with
+// the row exponents e[0..n) (a1) and e[n..2n) (a2).  B slices: BF16
+// [7][tc_pad_cols(r)][ldt] with column exponents cexp[0..r).  C_split gets
+// FP64 partial products over nsplit ranges of k (oz_pick_split).
+int64_t oz_mpad(int n);
+size_t oz_uk_bytes(int n, int64_t ldt);
+size_t oz_b_bytes(int r, int64_t ldt);
+cudaError_t launch_oz_uk(const double* U, int n, int64_t ldt, __nv_bfloat16* a1, __nv_bfloat16* a2,
+                         int* e, cudaStream_t st);
+cudaError_t oz_make_maps(const __nv_bfloat16* a1, const __nv_bfloat16* a2, int n, int64_t ldt,
+                         CUtensorMap* m1, CUtensorMap* m2);
+cudaError_t oz_make_b_map(const __nv_bfloat16* b, int n, int r, int64_t ldt, CUtensorMap* m);
+// B'(k, j) = scale[k] B(k, j) (scale may be NULL), B column-major with ld ldb.
+cudaError_t launch_oz_b(const double* B, const double* scale, int n, int r, int64_t ldb,
+                        int64_t ldt, __nv_bfloat16* out, int* cexp, const DevScalars* skip,
+                        cudaStream_t st);
+int oz_pick_split(int n, int num_sms);
+cudaError_t launch_oz_gemm(const CUtensorMap& ma, const int* rexp, const CUtensorMap& mb,
+                           const int* cexp, double* C, int64_t ldc, int64_t split_stride, int n,
+                           int ncols, int nsplit, const DevScalars* skip, int* err,
+                           cudaStream_t st);
+
 // TF32 hi/lo split (hi = x with 13 low bits cleared, lo = x - hi).
 cudaError_t launch_tf32_split(const float* src, float* hi, float* lo, int64_t total,
                               cudaStream_t st);

@@ -1,0 +1,488 @@
+// FP64-accurate skinny products on the tensor cores by error-free operand
+// splitting (the splitting scheme of Ozaki, Ogita, Oishi and Rump, 2012):
+// C = op(U_K) B for the FP64-accurate steps of the mixed solve (the
+// right-hand side D_K U_K' B, the true residual's U_K (D_K x̄) and U_K' Ŷ1,
+// and W = U_K x̄; Eq. unaligned-infinite-1 in the eigenbasis of §4.4).
+//
+// Splitting.  Every row i of A (the output row) is scaled by 2^-e_i so that
+// its largest entry is below 1, every column j of B by 2^-f_j likewise, and
+// each scaled value v is cut into S = 7 slices
+//     v = sum_t m_t 2^(-7-8t) + rest,   |m_t| <= 128 integer,  |rest| <= 2^-56,
+// by rounding the remainder to the grid of the slice (m_t = rint(rest 2^(7+8t))).
+// Each slice has at most 8 significant bits, so it is exact in BF16, and
+// the product of two slices, m_t m_u 2^(-14-8(t+u)), is exact in FP32.
+//
+// Products.  C_ij 2^-(e_i+f_j) = sum_{t+u <= 6} (A_t B_u)_ij up to 2^-53 of
+// the row/column scales.  The slice products are grouped by g = t + u: all
+// terms of a group are integer multiples of the group's unit 2^(-14-8g) and
+// bounded by 2^14 units, so a group's sum over a 256-wide k chunk, at most
+// (g+1) 256 2^14 <= 2^24 units for g <= 3, is exact in an FP32 accumulator
+// whatever the order of the additions.  Groups 0..3 (10 products) go to four
+// TMEM accumulators that are read after every chunk and added into
+// double-float registers; groups 4..6 (18 products, at most 2^-32 of the
+// result) share one FP32 accumulator over the whole k range.  The result is
+// FP64-accurate (about 2^-50 of sum_k |A_ik B_kj|, like the double-float
+// product it replaces) at tensor-core speed: the kernel is bound by reading
+// the 7 BF16 slices of the n x n matrix.
+//
+// Layout.  A slices: BF16 [7][mpad][ldt], slice t's row i at row t mpad + i
+// of one K-major tensor map (mpad = n rounded up to 128).  B slices: BF16
+// [7][NP][ldt], slice u's column j at row u NP + j.  Row and column exponents
+// e_i, f_j as int arrays.
+//
+// Block: 10 warps.  Warp 8 (one lane) streams 128-byte k slabs with TMA: per
+// slab the 7 B slices (one ring slot) and the 7 A slices (one stage each);
+// warp 9 (one lane) issues the 28 tcgen05.mma (M = 128, N = NP) per slab and
+// 16 k; warps 0..7 drain: warp w reads TMEM lanes 32 (w % 4).. and columns
+// (w / 4) NP/2.., one output row per thread.  Every wait is bounded (error
+// code, then TMEM is freed and the kernel returns).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "df.cuh"
+#include "launch.h"
+#include "tc_util.cuh"
+
+namespace cphifi {
+
+using namespace tcu;
+
+namespace {
+
+constexpr int kOzS = 7;             // slices per operand
+constexpr int kOzExact = 4;         // groups g = t + u < 4 are exact per chunk
+constexpr int kOzChunkSlabs = 4;    // 4 slabs of 64 k = 256 k per exact chunk
+constexpr int kOzDrainWarps = 8;
+constexpr int kOzThreads = (kOzDrainWarps + 2) * 32;
+constexpr int kOzABytes = 128 * 128;  // one A slice tile: 128 rows x 128 bytes
+constexpr uint32_t kOzTmemCols = 512;  // 5 accumulators in 64-column slots
+
+template <int NP>
+__host__ __device__ constexpr int oz_astages() { return NP <= 48 ? 8 : 6; }
+template <int NP>
+__host__ __device__ constexpr int oz_bbytes() { return kOzS * NP * 128; }
+template <int NP>
+constexpr size_t oz_smem() { return (size_t)oz_astages<NP>() * kOzABytes + 2 * oz_bbytes<NP>() + 1024; }
+
+// Eight consecutive 32-bit TMEM columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7])
+      : "r"(taddr));
+}
+
+}  // namespace
+
+template <int NP>
+__global__ void __launch_bounds__(kOzThreads, 1)
+oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               int mpad, const int* __restrict__ rexp, const int* __restrict__ cexp,
+               double* __restrict__ C, int64_t ldc, int64_t split_stride, int n, int ncols,
+               int kchunk, const DevScalars* skip, int* err) {
+  if (dev_skip(skip)) return;
+  constexpr int AST = oz_astages<NP>();
+  constexpr int BBYTES = oz_bbytes<NP>();
+  constexpr int NH = NP / 2;  // columns per drain thread
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t a_full[AST], a_empty[AST], b_full[2], b_empty[2], ex_full,
+      ex_empty[kOzExact];
+  __shared__ uint32_t tmem_slot;
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* bring = smem + AST * kOzABytes;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * 128;
+  const int kbeg = blockIdx.y * kchunk;
+  const int kend = min(n, kbeg + kchunk);
+  const int nslab = kend > kbeg ? (kend - kbeg + 63) / 64 : 0;
+  const int nch = (nslab + kOzChunkSlabs - 1) / kOzChunkSlabs;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < AST; ++s) {
+      mbar_init(&a_full[s], 1);
+      mbar_init(&a_empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&b_full[s], 1);
+      mbar_init(&b_empty[s], 1);
+    }
+    mbar_init(&ex_full, 1);
+    for (int g = 0; g < kOzExact; ++g) mbar_init(&ex_empty[g], kOzDrainWarps * 32);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(kOzTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == kOzDrainWarps) {
+    if (lane == 0) {  // producer: B slices per slab (2-slot ring), A slices one stage each
+      bool ok = true;
+      for (int c = 0; c < nslab && ok; ++c) {
+        const int k0 = kbeg + c * 64;
+        const int bs = c & 1;
+        if (c >= 2 && !mbar_wait(&b_empty[bs], (uint32_t)((c >> 1) & 1) ^ 1u, err, 1)) break;
+        mbar_expect_tx(&b_full[bs], BBYTES);
+        for (int u = 0; u < kOzS; ++u)
+          tma_load_2d(bring + bs * BBYTES + u * NP * 128, &tmB, k0, u * NP, &b_full[bs]);
+        for (int t = 0; t < kOzS; ++t) {
+          const int idx = c * kOzS + t, s = idx % AST;
+          if (idx >= AST && !mbar_wait(&a_empty[s], (uint32_t)((idx / AST) & 1) ^ 1u, err, 1)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&a_full[s], kOzABytes);
+          tma_load_2d(smem + s * kOzABytes, &tmA, k0, t * mpad + m0, &a_full[s]);
+        }
+      }
+    }
+  } else if (warp == kOzDrainWarps + 1) {
+    if (lane == 0) {  // MMA issuer
+      const uint32_t id = idesc<__nv_bfloat16>(NP);
+      bool ok = true;
+      for (int c = 0; c < nslab && ok; ++c) {
+        const int ch = c / kOzChunkSlabs;
+        const bool first = (c % kOzChunkSlabs) == 0;
+        if (first && ch > 0)  // the exact accumulators of the previous chunk were read
+          for (int g = 0; g < kOzExact && ok; ++g)
+            ok = mbar_wait(&ex_empty[g], (uint32_t)((ch - 1) & 1), err, 8);
+        const int bs = c & 1;
+        if (!ok || !mbar_wait(&b_full[bs], (uint32_t)((c >> 1) & 1), err, 2)) break;
+        const uint8_t* bslab = bring + bs * BBYTES;
+        for (int t = 0; t < kOzS; ++t) {
+          const int idx = c * kOzS + t, s = idx % AST;
+          if (!mbar_wait(&a_full[s], (uint32_t)((idx / AST) & 1), err, 2)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint8_t* a = smem + s * kOzABytes;
+          for (int u = 0; t + u < kOzS; ++u) {
+            const int g = t + u;
+            const uint32_t d = tmem + 64u * (uint32_t)(g < kOzExact ? g : kOzExact);
+            const uint8_t* b = bslab + u * NP * 128;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              // overwrite instead of accumulate: the first term of an exact
+              // group in a chunk (t = 0, u = g), the first inexact term overall
+              const bool fresh = kk == 0 && t == 0 &&
+                                 (g < kOzExact ? first : (c == 0 && g == kOzExact));
+              mma<__nv_bfloat16>(d, sdesc(a + kk * 32), sdesc(b + kk * 32), id, fresh ? 0u : 1u);
+            }
+          }
+          mma_commit(&a_empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&b_empty[bs]);
+        if ((c % kOzChunkSlabs) == kOzChunkSlabs - 1 || c == nslab - 1) mma_commit(&ex_full);
+      }
+    }
+  } else {
+    // drain: exact group sums of every chunk into double-float registers
+    const int quad = warp & 3, half = warp >> 2;
+    const int row = m0 + quad * 32 + lane;
+    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * NH);
+    df acc[NH];
+#pragma unroll
+    for (int c = 0; c < NH; ++c) acc[c] = df{0.f, 0.f};
+    bool ok = true;
+    for (int ch = 0; ch < nch; ++ch) {
+      ok = ok && mbar_wait(&ex_full, (uint32_t)(ch & 1), err, 4);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int g = 0; g < kOzExact; ++g) {
+        uint32_t v[NH];
+#pragma unroll
+        for (int c0 = 0; c0 < NH; c0 += 8)
+          tmem_ld8(tbase + 64u * g + c0, *reinterpret_cast<uint32_t(*)[8]>(&v[c0]));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&ex_empty[g]);
+#pragma unroll
+        for (int c = 0; c < NH; ++c) df_acc_add(acc[c], df{__uint_as_float(v[c]), 0.f});
+      }
+    }
+    if (nslab == 0) {
+      if (row < n)
+        for (int c = 0; c < NH; ++c) {
+          const int j = half * NH + c;
+          if (j < ncols) C[(int64_t)blockIdx.y * split_stride + (int64_t)j * ldc + row] = 0.0;
+        }
+    } else {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t w[NH];
+#pragma unroll
+      for (int c0 = 0; c0 < NH; c0 += 8)
+        tmem_ld8(tbase + 64u * kOzExact + c0, *reinterpret_cast<uint32_t(*)[8]>(&w[c0]));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (ok && row < n) {
+        const int ei = rexp[row];
+        double* Cs = C + (int64_t)blockIdx.y * split_stride;
+#pragma unroll
+        for (int c = 0; c < NH; ++c) {
+          const int j = half * NH + c;
+          if (j < ncols) {
+            const df a = df_norm(acc[c]);
+            const double v = ((double)a.hi + (double)a.lo) + (double)__uint_as_float(w[c]);
+            Cs[(int64_t)j * ldc + row] = ldexp(v, ei + cexp[j]);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kOzTmemCols)
+                 : "memory");
+}
+
+// ------------------------------------------------------------ splitting ---
+
+// Scaled slices of one value: v in (-1, 1) (already scaled by its row or
+// column exponent), m_t = rint(rest 2^(7+8t)), slice t = m_t 2^(-7-8t).
+// Non-finite input: every slice NaN (the product then reports it).
+__device__ __forceinline__ void oz_slices(double v, __nv_bfloat16 (&s)[kOzS]) {
+  if (!isfinite(v)) {
+#pragma unroll
+    for (int t = 0; t < kOzS; ++t) s[t] = __float2bfloat16_rn(__int_as_float(0x7fc00000));
+    return;
+  }
+  double rest = v;
+#pragma unroll
+  for (int t = 0; t < kOzS; ++t) {
+    const int sh = 7 + 8 * t;
+    const double m = rint(ldexp(rest, sh));  // |m| <= 128
+    const double x = ldexp(m, -sh);
+    rest -= x;                               // exact
+    s[t] = __float2bfloat16_rn((float)x);    // exact: at most 8 significant bits
+  }
+}
+
+// Exponent e with max|.| < 2^e (0 for a zero or non-finite maximum).
+__device__ __forceinline__ int oz_exponent(double mx) {
+  if (!(mx > 0.0) || !isfinite(mx)) return 0;
+  int e;
+  frexp(mx, &e);
+  return e;
+}
+
+// Exponents of the row maxima of U_K (column-major n x n): e[i], i < n, for
+// the rows of U_K (A of U_K X), one thread per row (reads coalesced across
+// the threads); e[n + j] for its columns (the rows of U_K', A of U_K' X), one
+// warp per column.
+__global__ void oz_uk_row_exponents_kernel(const double* __restrict__ U, int n, int* e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double mx = 0.0;
+  bool fin = true;
+  for (int k = 0; k < n; ++k) {
+    const double v = U[(int64_t)k * n + i];
+    fin = fin && isfinite(v);
+    mx = fmax(mx, fabs(v));
+  }
+  e[i] = fin ? oz_exponent(mx) : 0;
+}
+
+__global__ void oz_uk_col_exponents_kernel(const double* __restrict__ U, int n, int* e) {
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (j >= n) return;
+  double mx = 0.0;
+  bool fin = true;
+  for (int k = lane; k < n; k += 32) {
+    const double v = U[(int64_t)j * n + k];
+    fin = fin && isfinite(v);
+    mx = fmax(mx, fabs(v));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  fin = __all_sync(0xffffffffu, fin);
+  if (lane == 0) e[n + j] = fin ? oz_exponent(mx) : 0;
+}
+
+// Slices of U_K in one orientation: transpose (A1, row-major U_K: out row i,
+// element k = U(i, k)) or not (A2, row-major U_K': out row j, element k =
+// U(k, j)); 32 x 32 tiles staged in shared memory so that reads and writes
+// are both coalesced.  Slice t of row i is at out[(t mpad + i) ldt + k].
+__global__ void oz_uk_slices_kernel(const double* __restrict__ U, int n, bool transpose,
+                                    const int* __restrict__ rexp, int64_t mpad, int64_t ldt,
+                                    __nv_bfloat16* __restrict__ out) {
+  __shared__ double tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int i = bx + threadIdx.x, j = by + k;
+    tile[k][threadIdx.x] = (i < n && j < n) ? U[(int64_t)j * n + i] : 0.0;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    int orow, ocol;
+    double v;
+    if (transpose) {
+      orow = bx + k;
+      ocol = by + threadIdx.x;
+      v = tile[threadIdx.x][k];
+    } else {
+      orow = by + k;
+      ocol = bx + threadIdx.x;
+      v = tile[k][threadIdx.x];
+    }
+    if (orow < n && ocol < n) {
+      __nv_bfloat16 s[kOzS];
+      oz_slices(ldexp(v, -rexp[orow]), s);
+#pragma unroll
+      for (int t = 0; t < kOzS; ++t) out[((int64_t)t * mpad + orow) * ldt + ocol] = s[t];
+    }
+  }
+}
+
+// B operand of one product: B'(k, j) = scale[k] B(k, j) (scale may be NULL),
+// column exponents f_j and slices, one block per column.  Slice u of column j
+// is at out[(u np + j) ldt + k].
+__global__ void oz_b_slices_kernel(const double* __restrict__ B, const double* __restrict__ scale,
+                                   int n, int64_t ldb, int np, int64_t ldt,
+                                   __nv_bfloat16* __restrict__ out, int* __restrict__ cexp,
+                                   const DevScalars* skip) {
+  if (dev_skip(skip)) return;
+  __shared__ double red[32];
+  __shared__ int fin_all;
+  const int j = blockIdx.x;
+  const double* col = B + (int64_t)j * ldb;
+  double mx = 0.0;
+  bool fin = true;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double v = scale ? scale[k] * col[k] : col[k];
+    fin = fin && isfinite(v);
+    mx = fmax(mx, fabs(v));
+  }
+  if (threadIdx.x == 0) fin_all = 1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __syncthreads();
+  if (!fin) fin_all = 0;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double m2 = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    if (threadIdx.x == 0) red[0] = m2;
+  }
+  __syncthreads();
+  const int f = fin_all ? oz_exponent(red[0]) : 0;
+  if (threadIdx.x == 0) cexp[j] = f;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double v = scale ? scale[k] * col[k] : col[k];
+    __nv_bfloat16 s[kOzS];
+    oz_slices(ldexp(v, -f), s);
+#pragma unroll
+    for (int u = 0; u < kOzS; ++u) out[((int64_t)u * np + j) * ldt + k] = s[u];
+  }
+}
+
+// ------------------------------------------------------------------ host ---
+
+int64_t oz_mpad(int n) { return ((int64_t)n + 127) / 128 * 128; }
+
+size_t oz_uk_bytes(int n, int64_t ldt) {
+  return 2 * (size_t)kOzS * oz_mpad(n) * ldt * sizeof(__nv_bfloat16) + 2 * (size_t)n * sizeof(int);
+}
+
+size_t oz_b_bytes(int r, int64_t ldt) {
+  return (size_t)kOzS * tc_pad_cols(r) * ldt * sizeof(__nv_bfloat16) + 64 * sizeof(int);
+}
+
+cudaError_t launch_oz_uk(const double* U, int n, int64_t ldt, __nv_bfloat16* a1, __nv_bfloat16* a2,
+                         int* e, cudaStream_t st) {
+  const int64_t mpad = oz_mpad(n);
+  const size_t slice_bytes = (size_t)kOzS * mpad * ldt * sizeof(__nv_bfloat16);
+  cudaError_t err;
+  if ((err = cudaMemsetAsync(a1, 0, slice_bytes, st)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(a2, 0, slice_bytes, st)) != cudaSuccess) return err;
+  oz_uk_row_exponents_kernel<<<(n + 255) / 256, 256, 0, st>>>(U, n, e);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  oz_uk_col_exponents_kernel<<<(int)(((int64_t)n * 32 + 255) / 256), 256, 0, st>>>(U, n, e);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  const dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+  oz_uk_slices_kernel<<<grid, block, 0, st>>>(U, n, true, e, mpad, ldt, a1);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  oz_uk_slices_kernel<<<grid, block, 0, st>>>(U, n, false, e + n, mpad, ldt, a2);
+  return cudaGetLastError();
+}
+
+cudaError_t oz_make_maps(const __nv_bfloat16* a1, const __nv_bfloat16* a2, int n, int64_t ldt,
+                         CUtensorMap* m1, CUtensorMap* m2) {
+  const uint64_t rows = (uint64_t)kOzS * oz_mpad(n);
+  cudaError_t e = tc_make_map(m1, a1, true, n, rows, ldt * 2, 128);
+  if (e != cudaSuccess) return e;
+  return tc_make_map(m2, a2, true, n, rows, ldt * 2, 128);
+}
+
+cudaError_t oz_make_b_map(const __nv_bfloat16* b, int n, int r, int64_t ldt, CUtensorMap* m) {
+  const int np = tc_pad_cols(r);
+  return tc_make_map(m, b, true, n, (uint64_t)kOzS * np, ldt * 2, (uint32_t)np);
+}
+
+cudaError_t launch_oz_b(const double* B, const double* scale, int n, int r, int64_t ldb,
+                        int64_t ldt, __nv_bfloat16* out, int* cexp, const DevScalars* skip,
+                        cudaStream_t st) {
+  oz_b_slices_kernel<<<r, 256, 0, st>>>(B, scale, n, ldb, tc_pad_cols(r), ldt, out, cexp, skip);
+  return cudaGetLastError();
+}
+
+int oz_pick_split(int n, int num_sms) {
+  const int mt = (n + 127) / 128;
+  int s = num_sms / mt;  // one wave of one block per SM (the block holds ~215 KB)
+  const int chunks = (n + 255) / 256;
+  if (s > chunks) s = chunks;
+  if (s > 64) s = 64;
+  return s < 1 ? 1 : s;
+}
+
+template <int NP>
+static cudaError_t oz_launch(const CUtensorMap& ma, int mpad, const int* rexp, const CUtensorMap& mb,
+                             const int* cexp, double* C, int64_t ldc, int64_t split_stride, int n,
+                             int ncols, int nsplit, const DevScalars* skip, int* err,
+                             cudaStream_t st) {
+  constexpr size_t smem = oz_smem<NP>();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel<NP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int kchunk = (n + nsplit - 1) / nsplit;
+  kchunk = (kchunk + 255) / 256 * 256;  // whole exact chunks per split
+  const dim3 grid((n + 127) / 128, nsplit);
+  oz_gemm_kernel<NP><<<grid, kOzThreads, smem, st>>>(ma, mb, mpad, rexp, cexp, C, ldc, split_stride,
+                                                     n, ncols, kchunk, skip, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_gemm(const CUtensorMap& ma, const int* rexp, const CUtensorMap& mb,
+                           const int* cexp, double* C, int64_t ldc, int64_t split_stride, int n,
+                           int ncols, int nsplit, const DevScalars* skip, int* err,
+                           cudaStream_t st) {
+  const int mpad = (int)oz_mpad(n);
+  switch (tc_pad_cols(ncols)) {
+    case 16: return oz_launch<16>(ma, mpad, rexp, mb, cexp, C, ldc, split_stride, n, ncols, nsplit, skip, err, st);
+    case 32: return oz_launch<32>(ma, mpad, rexp, mb, cexp, C, ldc, split_stride, n, ncols, nsplit, skip, err, st);
+    case 48: return oz_launch<48>(ma, mpad, rexp, mb, cexp, C, ldc, split_stride, n, ncols, nsplit, skip, err, st);
+    default: return oz_launch<64>(ma, mpad, rexp, mb, cexp, C, ldc, split_stride, n, ncols, nsplit, skip, err, st);
+  }
+}
+
+}  // namespace cphifi

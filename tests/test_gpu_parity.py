@@ -127,6 +127,25 @@ def test_matvec(case):
         assert rel(prob.matvec(X, lam, rho, "mixed_tf32x3"), ref) <= 2e-5
 
 
+@pytest.mark.parametrize("r", [8, 40, 64])
+def test_fp64_accurate_products_several_chunks_and_splits(ctx, pkg, r):
+    # n = 3000: 24 row tiles of 128 (the last one ragged) and the k range split
+    # over several blocks, each more than one 256-wide exact chunk; a narrow
+    # kernel (strongly graded D_K) makes the column scales of the products'
+    # right-hand operand span many binades.  The FP64-accurate operator (both
+    # n x n products and the gather/scatter) must stay at FP64 accuracy.
+    p = synth.planted_problem(7, 3000, (20, 25), 20000, r, bandwidth=0.05, lam=1e-4, rho=1e-6,
+                              shuffle=True)
+    kern, prob = make(ctx, pkg, p)
+    Zh = O.zhat(p.factors, p.oidx)
+    X = np.random.default_rng(13).standard_normal((p.n, p.r))
+    ref = O.matvec(p.K, p.kidx, Zh, 1e-4, 1e-6, X)
+    assert rel(prob.matvec(X, 1e-4, 1e-6, "fp64"), ref) <= 1e-12
+    assert rel(prob.matvec(X, 1e-4, 1e-6, "fp64_emulated"), ref) <= 1e-12
+    prob.close()
+    kern.close()
+
+
 def test_preconditioner(case):
     p, prob = case
     X = np.random.default_rng(13).standard_normal((p.n, p.r))
