@@ -74,12 +74,17 @@ enum { CPHIFI_MEM_HOST = 0, CPHIFI_MEM_DEVICE = 1 };
  *  MIXED_TF32X3  : as MIXED_TF32 with each operand split into two TF32 parts
  *                  (hi + lo) and the product accumulated as hi*hi + hi*lo +
  *                  lo*hi on the tensor cores: near-FP32 accuracy.
- *  FP64_EMULATED : every step FP64-accurate in double-float arithmetic (pairs
- *                  of FP32 numbers, 48-bit significand, error-free TwoSum /
- *                  TwoProd transforms) on the FP32 units.
+ *  FP64_EMULATED : every step FP64-accurate without the FP64 units: the
+ *                  gather-dot/scatter in double-float arithmetic (pairs of
+ *                  FP32 numbers, 48-bit significand, error-free TwoSum /
+ *                  TwoProd transforms), the two n x n products on the tensor
+ *                  cores from 7 BF16 slices of each operand (error-free
+ *                  splitting; the leading slice products are summed exactly),
+ *                  or in double-float arithmetic when the kernel has no
+ *                  slices (no tensor cores, or no room in the HBM budget).
  * In every mode but FP64, the FP64-accurate steps (right-hand side, true
- * residuals, W = U_K Wbar) use the double-float arithmetic: on GB300 its FP32
- * units are ~60x faster than its FP64 units.                                */
+ * residuals, W = U_K Wbar) use this arithmetic: on GB300 the FP32 units and
+ * the tensor cores are far faster than the FP64 units.                      */
 typedef enum cphifi_precision {
   CPHIFI_FP64 = 0,
   CPHIFI_MIXED_FP32 = 1,
@@ -170,7 +175,10 @@ const char* cphifi_status_string(int status);
  *          (FP64 symmetric divide-and-conquer, cuSOLVER dsyevd; the lower
  *          triangle of K is read; n <= 46340).  Tiny negative eigenvalues are
  *          clamped to 0 inside the preconditioner only.
- * The library keeps FP64 and FP32 copies of UK on the device. */
+ * The library keeps FP64 and FP32 copies of UK on the device and, where the
+ * tensor cores are available and the context's HBM budget has room, the
+ * TF32/BF16 operand copies of the tensor-core modes and 7 BF16 slices of UK
+ * and UK' for the FP64-accurate products (about 28 + 28 bytes per entry). */
 int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
                          const double* UK, const double* DK, int mem,
                          cphifi_kernel** out);
