@@ -906,7 +906,7 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
     PCK(tc_make_map(&P->mByh, P->y1h, false, n, r, P->ldt * 4, np));
     PCK(tc_make_map(&P->mByl, P->y1l, false, n, r, P->ldt * 4, np));
     if (kern->oz) {
-      const size_t cnt = (size_t)7 * np * P->ldt;
+      const size_t cnt = (size_t)7 * 64 * P->ldt;  // 7 slices of 64 rows (r padded)
       PCK(dalloc(P, &P->ozb, cnt));
       PCK(cudaMemsetAsync(P->ozb, 0, cnt * sizeof(__nv_bfloat16), st));
       PCK(dalloc(P, &P->ozce, 64));

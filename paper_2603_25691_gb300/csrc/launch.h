@@ -161,7 +161,8 @@ cudaError_t launch_tc_gemm(bool bf16, const CUtensorMap& ma, const CUtensorMap& 
 // each operand (error-free splitting, exact group sums in TMEM).  U_K slices:
 // a1 (rows of U_K), a2 (rows of U_K'), BF16 [7][oz_mpad(n)][ldt] each, with
 // the row exponents e[0..n) (a1) and e[n..2n) (a2).  B slices: BF16
-// [7][tc_pad_cols(r)][ldt] with column exponents cexp[0..r).  C_split gets
+// [7][64][ldt] (r <= 64 rows used, the rest zero) with column exponents
+// cexp[0..r).  C_split gets
 // FP64 partial products over nsplit ranges of k (oz_pick_split).
 int64_t oz_mpad(int n);
 size_t oz_uk_bytes(int n, int64_t ldt);

@@ -17,25 +17,28 @@
 // terms of a group are integer multiples of the group's unit 2^(-14-8g) and
 // bounded by 2^14 units, so a group's sum over a 256-wide k chunk, at most
 // (g+1) 256 2^14 <= 2^24 units for g <= 3, is exact in an FP32 accumulator
-// whatever the order of the additions.  Groups 0..3 (10 products) go to four
-// TMEM accumulators that are read after every chunk and added into
-// double-float registers; groups 4..6 (18 products, at most 2^-32 of the
-// result) share one FP32 accumulator over the whole k range.  The result is
-// FP64-accurate (about 2^-50 of sum_k |A_ik B_kj|, like the double-float
-// product it replaces) at tensor-core speed: the kernel is bound by reading
-// the 7 BF16 slices of the n x n matrix.
+// whatever the order of the additions.  Each group has its own TMEM
+// accumulator, read after every chunk and added into double-float registers;
+// the sums of groups 4..6 (18 products, at most 2^-32 of the result) may
+// round, far below the result's last bit.  The result is FP64-accurate
+// (about 2^-50 of sum_k |A_ik B_kj|, like the double-float product it
+// replaces) at tensor-core speed.
 //
 // Layout.  A slices: BF16 [7][mpad][ldt], slice t's row i at row t mpad + i
 // of one K-major tensor map (mpad = n rounded up to 128).  B slices: BF16
-// [7][NP][ldt], slice u's column j at row u NP + j.  Row and column exponents
-// e_i, f_j as int arrays.
+// [7][64][ldt], slice u's column j at row 64 u + j (rows r..63 zero).  Row
+// and column exponents e_i, f_j as int arrays.
 //
 // Block: 10 warps.  Warp 8 (one lane) streams 128-byte k slabs with TMA: per
-// slab the 7 B slices (one ring slot) and the 7 A slices (one stage each);
-// warp 9 (one lane) issues the 28 tcgen05.mma (M = 128, N = NP) per slab and
-// 16 k; warps 0..7 drain: warp w reads TMEM lanes 32 (w % 4).. and columns
-// (w / 4) NP/2.., one output row per thread.  Every wait is bounded (error
-// code, then TMEM is freed and the kernel returns).
+// slab the 7 B slices (one ring slot, each slice padded to 64 rows) and the 7
+// A slices (one ring stage each); warp 9 (one lane) issues the products: for
+// A_t, the slices B_0..B_{6-t} are contiguous in shared memory, so one
+// tcgen05.mma with N = 64 m covers m <= 4 of them and writes group t + u to
+// the TMEM region of that group (64 columns each, 7 regions): 10 MMAs per
+// 16 k instead of 28.  Warps 0..7 drain every chunk: warp w reads TMEM lanes
+// 32 (w % 4).. and columns (w / 4) NP/2.. of each region, one output row per
+// thread, and adds the 7 group sums into double-float registers.  Every wait
+// is bounded (error code, then TMEM is freed and the kernel returns).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -51,20 +54,16 @@ using namespace tcu;
 
 namespace {
 
-constexpr int kOzS = 7;             // slices per operand
-constexpr int kOzExact = 4;         // groups g = t + u < 4 are exact per chunk
-constexpr int kOzChunkSlabs = 4;    // 4 slabs of 64 k = 256 k per exact chunk
+constexpr int kOzS = 7;               // slices per operand
+constexpr int kOzBRows = 64;          // rows of one B slice (r padded with zero rows)
+constexpr int kOzChunkSlabs = 4;      // 4 slabs of 64 k = 256 k per exact chunk
 constexpr int kOzDrainWarps = 8;
 constexpr int kOzThreads = (kOzDrainWarps + 2) * 32;
 constexpr int kOzABytes = 128 * 128;  // one A slice tile: 128 rows x 128 bytes
-constexpr uint32_t kOzTmemCols = 512;  // 5 accumulators in 64-column slots
-
-template <int NP>
-__host__ __device__ constexpr int oz_astages() { return NP <= 48 ? 8 : 6; }
-template <int NP>
-__host__ __device__ constexpr int oz_bbytes() { return kOzS * NP * 128; }
-template <int NP>
-constexpr size_t oz_smem() { return (size_t)oz_astages<NP>() * kOzABytes + 2 * oz_bbytes<NP>() + 1024; }
+constexpr int kOzAStages = 6;
+constexpr int kOzBBytes = kOzS * kOzBRows * 128;  // the 7 B slices of one slab
+constexpr size_t kOzSmem = (size_t)kOzAStages * kOzABytes + 2 * kOzBBytes + 1024;
+constexpr uint32_t kOzTmemCols = 512;  // 7 group regions of 64 columns
 
 // Eight consecutive 32-bit TMEM columns of this warp's 32 lanes.
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
@@ -73,6 +72,29 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
         "=r"(v[7])
       : "r"(taddr));
+}
+
+// Reads the group regions [G0, G1) (NH columns each, this thread's half),
+// releases them to the MMA issuer through `bar` when `release`, then adds
+// them into acc.
+template <int NH, int G0, int G1>
+__device__ __forceinline__ void oz_drain(uint32_t tbase, df (&acc)[NH], uint64_t* bar,
+                                         bool release) {
+  uint32_t v[G1 - G0][NH];
+#pragma unroll
+  for (int g = G0; g < G1; ++g)
+#pragma unroll
+    for (int c0 = 0; c0 < NH; c0 += 8)
+      tmem_ld8(tbase + 64u * g + c0, *reinterpret_cast<uint32_t(*)[8]>(&v[g - G0][c0]));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  if (release) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    mbar_arrive(bar);
+  }
+#pragma unroll
+  for (int g = 0; g < G1 - G0; ++g)
+#pragma unroll
+    for (int c = 0; c < NH; ++c) df_acc_add(acc[c], df{__uint_as_float(v[g][c]), 0.f});
 }
 
 }  // namespace
@@ -84,15 +106,14 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                double* __restrict__ C, int64_t ldc, int64_t split_stride, int n, int ncols,
                int kchunk, const DevScalars* skip, int* err) {
   if (dev_skip(skip)) return;
-  constexpr int AST = oz_astages<NP>();
-  constexpr int BBYTES = oz_bbytes<NP>();
   constexpr int NH = NP / 2;  // columns per drain thread
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t a_full[AST], a_empty[AST], b_full[2], b_empty[2], ex_full,
-      ex_empty[kOzExact];
+  // ex_lo / ex_hi: the drain has read group regions 0..3 / 4..6 of a chunk
+  __shared__ uint64_t a_full[kOzAStages], a_empty[kOzAStages], b_full[2], b_empty[2], ex_full,
+      ex_lo, ex_hi;
   __shared__ uint32_t tmem_slot;
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* bring = smem + AST * kOzABytes;
+  uint8_t* bring = smem + kOzAStages * kOzABytes;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * 128;
@@ -102,7 +123,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   const int nch = (nslab + kOzChunkSlabs - 1) / kOzChunkSlabs;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < AST; ++s) {
+    for (int s = 0; s < kOzAStages; ++s) {
       mbar_init(&a_full[s], 1);
       mbar_init(&a_empty[s], 1);
     }
@@ -111,7 +132,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       mbar_init(&b_empty[s], 1);
     }
     mbar_init(&ex_full, 1);
-    for (int g = 0; g < kOzExact; ++g) mbar_init(&ex_empty[g], kOzDrainWarps * 32);
+    mbar_init(&ex_lo, kOzDrainWarps * 32);
+    mbar_init(&ex_hi, kOzDrainWarps * 32);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -134,12 +156,14 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int k0 = kbeg + c * 64;
         const int bs = c & 1;
         if (c >= 2 && !mbar_wait(&b_empty[bs], (uint32_t)((c >> 1) & 1) ^ 1u, err, 1)) break;
-        mbar_expect_tx(&b_full[bs], BBYTES);
+        mbar_expect_tx(&b_full[bs], kOzBBytes);
         for (int u = 0; u < kOzS; ++u)
-          tma_load_2d(bring + bs * BBYTES + u * NP * 128, &tmB, k0, u * NP, &b_full[bs]);
+          tma_load_2d(bring + bs * kOzBBytes + u * kOzBRows * 128, &tmB, k0, u * kOzBRows,
+                      &b_full[bs]);
         for (int t = 0; t < kOzS; ++t) {
-          const int idx = c * kOzS + t, s = idx % AST;
-          if (idx >= AST && !mbar_wait(&a_empty[s], (uint32_t)((idx / AST) & 1) ^ 1u, err, 1)) {
+          const int idx = c * kOzS + t, s = idx % kOzAStages;
+          if (idx >= kOzAStages &&
+              !mbar_wait(&a_empty[s], (uint32_t)((idx / kOzAStages) & 1) ^ 1u, err, 1)) {
             ok = false;
             break;
           }
@@ -150,36 +174,41 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
   } else if (warp == kOzDrainWarps + 1) {
     if (lane == 0) {  // MMA issuer
-      const uint32_t id = idesc<__nv_bfloat16>(NP);
+      // descriptors of stage 0 / slot 0; other stages, slices and k offsets
+      // add (byte offset >> 4) to the start-address field
+      const uint64_t da0 = sdesc(smem), db0 = sdesc(bring);
       bool ok = true;
       for (int c = 0; c < nslab && ok; ++c) {
         const int ch = c / kOzChunkSlabs;
         const bool first = (c % kOzChunkSlabs) == 0;
-        if (first && ch > 0)  // the exact accumulators of the previous chunk were read
-          for (int g = 0; g < kOzExact && ok; ++g)
-            ok = mbar_wait(&ex_empty[g], (uint32_t)((ch - 1) & 1), err, 8);
+        if (first && ch > 0)  // the previous chunk's group sums were read
+          ok = mbar_wait(&ex_lo, (uint32_t)((ch - 1) & 1), err, 8) &&
+               mbar_wait(&ex_hi, (uint32_t)((ch - 1) & 1), err, 8);
         const int bs = c & 1;
         if (!ok || !mbar_wait(&b_full[bs], (uint32_t)((c >> 1) & 1), err, 2)) break;
-        const uint8_t* bslab = bring + bs * BBYTES;
+        const uint64_t dbs = db0 + (uint64_t)((bs * kOzBBytes) >> 4);
+#pragma unroll
         for (int t = 0; t < kOzS; ++t) {
-          const int idx = c * kOzS + t, s = idx % AST;
-          if (!mbar_wait(&a_full[s], (uint32_t)((idx / AST) & 1), err, 2)) {
+          const int idx = c * kOzS + t, s = idx % kOzAStages;
+          if (!mbar_wait(&a_full[s], (uint32_t)((idx / kOzAStages) & 1), err, 2)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint8_t* a = smem + s * kOzABytes;
-          for (int u = 0; t + u < kOzS; ++u) {
-            const int g = t + u;
-            const uint32_t d = tmem + 64u * (uint32_t)(g < kOzExact ? g : kOzExact);
-            const uint8_t* b = bslab + u * NP * 128;
+          const uint64_t das = da0 + (uint64_t)((s * kOzABytes) >> 4);
+          // B_u0 .. B_{u0+m-1} in one MMA of N = 64 m into regions t+u0 ..
+#pragma unroll
+          for (int u0 = 0; u0 < kOzS - t; u0 += 4) {
+            const int m = min(4, kOzS - t - u0);
+            const uint32_t id = idesc<__nv_bfloat16>(64 * m);
+            const uint32_t d = tmem + 64u * (uint32_t)(t + u0);
+            const uint64_t db = dbs + (uint64_t)((u0 * kOzBRows * 128) >> 4);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-              // overwrite instead of accumulate: the first term of an exact
-              // group in a chunk (t = 0, u = g), the first inexact term overall
-              const bool fresh = kk == 0 && t == 0 &&
-                                 (g < kOzExact ? first : (c == 0 && g == kOzExact));
-              mma<__nv_bfloat16>(d, sdesc(a + kk * 32), sdesc(b + kk * 32), id, fresh ? 0u : 1u);
+              // the chunk's first products (t = 0) overwrite every region
+              const bool fresh = first && t == 0 && kk == 0;
+              mma<__nv_bfloat16>(d, das + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), id,
+                                 fresh ? 0u : 1u);
             }
           }
           mma_commit(&a_empty[s]);
@@ -190,7 +219,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       }
     }
   } else {
-    // drain: exact group sums of every chunk into double-float registers
+    // drain: the 7 group sums of every chunk into double-float registers
     const int quad = warp & 3, half = warp >> 2;
     const int row = m0 + quad * 32 + lane;
     const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * NH);
@@ -201,43 +230,25 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     for (int ch = 0; ch < nch; ++ch) {
       ok = ok && mbar_wait(&ex_full, (uint32_t)(ch & 1), err, 4);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-      for (int g = 0; g < kOzExact; ++g) {
-        uint32_t v[NH];
-#pragma unroll
-        for (int c0 = 0; c0 < NH; c0 += 8)
-          tmem_ld8(tbase + 64u * g + c0, *reinterpret_cast<uint32_t(*)[8]>(&v[c0]));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        mbar_arrive(&ex_empty[g]);
-#pragma unroll
-        for (int c = 0; c < NH; ++c) df_acc_add(acc[c], df{__uint_as_float(v[c]), 0.f});
+      if constexpr (NH <= 24) {
+        oz_drain<NH, 0, 4>(tbase, acc, &ex_lo, true);
+        oz_drain<NH, 4, 7>(tbase, acc, &ex_hi, true);
+      } else {  // fewer registers in flight
+        oz_drain<NH, 0, 2>(tbase, acc, &ex_lo, false);
+        oz_drain<NH, 2, 4>(tbase, acc, &ex_lo, true);
+        oz_drain<NH, 4, 6>(tbase, acc, &ex_hi, false);
+        oz_drain<NH, 6, 7>(tbase, acc, &ex_hi, true);
       }
     }
-    if (nslab == 0) {
-      if (row < n)
-        for (int c = 0; c < NH; ++c) {
-          const int j = half * NH + c;
-          if (j < ncols) C[(int64_t)blockIdx.y * split_stride + (int64_t)j * ldc + row] = 0.0;
-        }
-    } else {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      uint32_t w[NH];
+    if (row < n && (ok || nslab == 0)) {
+      const int ei = rexp[row];
+      double* Cs = C + (int64_t)blockIdx.y * split_stride;
 #pragma unroll
-      for (int c0 = 0; c0 < NH; c0 += 8)
-        tmem_ld8(tbase + 64u * kOzExact + c0, *reinterpret_cast<uint32_t(*)[8]>(&w[c0]));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (ok && row < n) {
-        const int ei = rexp[row];
-        double* Cs = C + (int64_t)blockIdx.y * split_stride;
-#pragma unroll
-        for (int c = 0; c < NH; ++c) {
-          const int j = half * NH + c;
-          if (j < ncols) {
-            const df a = df_norm(acc[c]);
-            const double v = ((double)a.hi + (double)a.lo) + (double)__uint_as_float(w[c]);
-            Cs[(int64_t)j * ldc + row] = ldexp(v, ei + cexp[j]);
-          }
+      for (int c = 0; c < NH; ++c) {
+        const int j = half * NH + c;
+        if (j < ncols) {
+          const df a = df_norm(acc[c]);
+          Cs[(int64_t)j * ldc + row] = ldexp((double)a.hi + (double)a.lo, ei + cexp[j]);
         }
       }
     }
@@ -252,8 +263,10 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
 // ------------------------------------------------------------ splitting ---
 
-// Scaled slices of one value: v in (-1, 1) (already scaled by its row or
-// column exponent), m_t = rint(rest 2^(7+8t)), slice t = m_t 2^(-7-8t).
+// Scaled slices of one value v in (-1, 1) (already scaled by its row or
+// column exponent), in 64-bit fixed point: M = v 2^62, then for t = 0..6
+// m_t = round(M / 2^(55-8t)) (ties up), M -= m_t 2^(55-8t); slice t =
+// m_t 2^(-7-8t) with |m_t| <= 128, and |v - sum_t slice_t| <= 2^-56.
 // Non-finite input: every slice NaN (the product then reports it).
 __device__ __forceinline__ void oz_slices(double v, __nv_bfloat16 (&s)[kOzS]) {
   if (!isfinite(v)) {
@@ -261,14 +274,13 @@ __device__ __forceinline__ void oz_slices(double v, __nv_bfloat16 (&s)[kOzS]) {
     for (int t = 0; t < kOzS; ++t) s[t] = __float2bfloat16_rn(__int_as_float(0x7fc00000));
     return;
   }
-  double rest = v;
+  long long M = __double2ll_rn(ldexp(v, 62));
 #pragma unroll
   for (int t = 0; t < kOzS; ++t) {
-    const int sh = 7 + 8 * t;
-    const double m = rint(ldexp(rest, sh));  // |m| <= 128
-    const double x = ldexp(m, -sh);
-    rest -= x;                               // exact
-    s[t] = __float2bfloat16_rn((float)x);    // exact: at most 8 significant bits
+    const int sh = 55 - 8 * t;
+    const long long m = (M + (1LL << (sh - 1))) >> sh;
+    M -= m * (1LL << sh);
+    s[t] = __float2bfloat16_rn(ldexpf((float)m, sh - 62));  // exact: |m| <= 128
   }
 }
 
@@ -348,48 +360,69 @@ __global__ void oz_uk_slices_kernel(const double* __restrict__ U, int n, bool tr
   }
 }
 
-// B operand of one product: B'(k, j) = scale[k] B(k, j) (scale may be NULL),
-// column exponents f_j and slices, one block per column.  Slice u of column j
-// is at out[(u np + j) ldt + k].
+// B operand of one product: B'(k, j) = scale[k] B(k, j) (scale may be NULL).
+// Column exponents first: each block reduces the frexp exponents of 1024
+// entries of one column and raises cexp[j] (preset to kOzExpNone) with one
+// atomicMax; a non-finite entry raises it to kOzExpBad.
+constexpr int kOzExpNone = (int)0x80808080;  // the byte pattern of the preset
+constexpr int kOzExpBad = 1 << 20;
+
+__global__ void oz_b_exponents_kernel(const double* __restrict__ B,
+                                      const double* __restrict__ scale, int n, int64_t ldb,
+                                      int* __restrict__ cexp, const DevScalars* skip) {
+  if (dev_skip(skip)) return;
+  __shared__ int red[8];
+  const int j = blockIdx.y;
+  int e = kOzExpNone;
+  for (int u = 0; u < 4; ++u) {
+    const int k = blockIdx.x * 1024 + u * 256 + threadIdx.x;
+    if (k < n) {
+      const double v = scale ? scale[k] * B[(int64_t)j * ldb + k] : B[(int64_t)j * ldb + k];
+      if (!isfinite(v)) {
+        e = kOzExpBad;
+      } else if (v != 0.0) {
+        int ev;
+        frexp(v, &ev);
+        e = max(e, ev);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int m = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, red[w]);
+    if (m != kOzExpNone) atomicMax(&cexp[j], m);
+  }
+}
+
+// Slices of B' (one thread per entry); slice u of column j at
+// out[(u 64 + j) ldt + k].  An all-zero column keeps exponent 0 (zero
+// slices); a non-finite one gets NaN slices.
 __global__ void oz_b_slices_kernel(const double* __restrict__ B, const double* __restrict__ scale,
-                                   int n, int64_t ldb, int np, int64_t ldt,
-                                   __nv_bfloat16* __restrict__ out, int* __restrict__ cexp,
+                                   int n, int64_t ldb, int64_t ldt,
+                                   __nv_bfloat16* __restrict__ out, const int* __restrict__ cexp,
                                    const DevScalars* skip) {
   if (dev_skip(skip)) return;
-  __shared__ double red[32];
-  __shared__ int fin_all;
-  const int j = blockIdx.x;
-  const double* col = B + (int64_t)j * ldb;
-  double mx = 0.0;
-  bool fin = true;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const double v = scale ? scale[k] * col[k] : col[k];
-    fin = fin && isfinite(v);
-    mx = fmax(mx, fabs(v));
-  }
-  if (threadIdx.x == 0) fin_all = 1;
+  const int j = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int f = cexp[j];
+  double v = scale ? scale[k] * B[(int64_t)j * ldb + k] : B[(int64_t)j * ldb + k];
+  if (f >= kOzExpBad) v = __longlong_as_double(0x7ff8000000000000LL);
+  __nv_bfloat16 sl[kOzS];
+  oz_slices(f == kOzExpNone || f >= kOzExpBad ? v : ldexp(v, -f), sl);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  __syncthreads();
-  if (!fin) fin_all = 0;
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double m2 = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
-    if (threadIdx.x == 0) red[0] = m2;
-  }
-  __syncthreads();
-  const int f = fin_all ? oz_exponent(red[0]) : 0;
-  if (threadIdx.x == 0) cexp[j] = f;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const double v = scale ? scale[k] * col[k] : col[k];
-    __nv_bfloat16 s[kOzS];
-    oz_slices(ldexp(v, -f), s);
-#pragma unroll
-    for (int u = 0; u < kOzS; ++u) out[((int64_t)u * np + j) * ldt + k] = s[u];
-  }
+  for (int u = 0; u < kOzS; ++u) out[((int64_t)u * kOzBRows + j) * ldt + k] = sl[u];
+}
+
+// The product's exponent of column j (0 for an all-zero column).
+__global__ void oz_b_fix_exponents_kernel(int* cexp, int r, const DevScalars* skip) {
+  if (dev_skip(skip)) return;
+  const int j = threadIdx.x;
+  if (j < r && (cexp[j] == kOzExpNone || cexp[j] >= kOzExpBad)) cexp[j] = 0;
 }
 
 // ------------------------------------------------------------------ host ---
@@ -401,7 +434,8 @@ size_t oz_uk_bytes(int n, int64_t ldt) {
 }
 
 size_t oz_b_bytes(int r, int64_t ldt) {
-  return (size_t)kOzS * tc_pad_cols(r) * ldt * sizeof(__nv_bfloat16) + 64 * sizeof(int);
+  (void)r;
+  return (size_t)kOzS * kOzBRows * ldt * sizeof(__nv_bfloat16) + 64 * sizeof(int);
 }
 
 cudaError_t launch_oz_uk(const double* U, int n, int64_t ldt, __nv_bfloat16* a1, __nv_bfloat16* a2,
@@ -431,14 +465,22 @@ cudaError_t oz_make_maps(const __nv_bfloat16* a1, const __nv_bfloat16* a2, int n
 }
 
 cudaError_t oz_make_b_map(const __nv_bfloat16* b, int n, int r, int64_t ldt, CUtensorMap* m) {
-  const int np = tc_pad_cols(r);
-  return tc_make_map(m, b, true, n, (uint64_t)kOzS * np, ldt * 2, (uint32_t)np);
+  (void)r;
+  return tc_make_map(m, b, true, n, (uint64_t)kOzS * kOzBRows, ldt * 2, (uint32_t)kOzBRows);
 }
 
 cudaError_t launch_oz_b(const double* B, const double* scale, int n, int r, int64_t ldb,
                         int64_t ldt, __nv_bfloat16* out, int* cexp, const DevScalars* skip,
                         cudaStream_t st) {
-  oz_b_slices_kernel<<<r, 256, 0, st>>>(B, scale, n, ldb, tc_pad_cols(r), ldt, out, cexp, skip);
+  if (r < 1 || r > 64) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(cexp, 0x80, (size_t)r * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  oz_b_exponents_kernel<<<dim3((n + 1023) / 1024, r), 256, 0, st>>>(B, scale, n, ldb, cexp, skip);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  oz_b_slices_kernel<<<dim3((n + 255) / 256, r), 256, 0, st>>>(B, scale, n, ldb, ldt, out, cexp,
+                                                               skip);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  oz_b_fix_exponents_kernel<<<1, 64, 0, st>>>(cexp, r, skip);
   return cudaGetLastError();
 }
 
@@ -456,19 +498,18 @@ static cudaError_t oz_launch(const CUtensorMap& ma, int mpad, const int* rexp, c
                              const int* cexp, double* C, int64_t ldc, int64_t split_stride, int n,
                              int ncols, int nsplit, const DevScalars* skip, int* err,
                              cudaStream_t st) {
-  constexpr size_t smem = oz_smem<NP>();
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel<NP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   int kchunk = (n + nsplit - 1) / nsplit;
   kchunk = (kchunk + 255) / 256 * 256;  // whole exact chunks per split
   const dim3 grid((n + 127) / 128, nsplit);
-  oz_gemm_kernel<NP><<<grid, kOzThreads, smem, st>>>(ma, mb, mpad, rexp, cexp, C, ldc, split_stride,
-                                                     n, ncols, kchunk, skip, err);
+  oz_gemm_kernel<NP><<<grid, kOzThreads, kOzSmem, st>>>(ma, mb, mpad, rexp, cexp, C, ldc,
+                                                        split_stride, n, ncols, kchunk, skip, err);
   return cudaGetLastError();
 }
 
