@@ -18,9 +18,10 @@
 // bounded by 2^14 units, so a group's sum over a 256-wide k chunk, at most
 // (g+1) 256 2^14 <= 2^24 units for g <= 3, is exact in an FP32 accumulator
 // whatever the order of the additions.  Each group has its own TMEM
-// accumulator, read after every chunk and added into double-float registers;
-// the sums of groups 4..6 (18 products, at most 2^-32 of the result) may
-// round, far below the result's last bit.  The result is FP64-accurate
+// accumulator; those of groups 0..3 (10 products) are read after every chunk
+// and added into double-float registers, those of groups 4..6 (18 products,
+// at most 2^-32 of the result) accumulate over the whole k range, their FP32
+// rounding far below the result's last bit.  The result is FP64-accurate
 // (about 2^-50 of sum_k |A_ik B_kj|, like the double-float product it
 // replaces) at tensor-core speed.
 //
@@ -36,9 +37,11 @@
 // tcgen05.mma with N = 64 m covers m <= 4 of them and writes group t + u to
 // the TMEM region of that group (64 columns each, 7 regions): 10 MMAs per
 // 16 k instead of 28.  Warps 0..7 drain every chunk: warp w reads TMEM lanes
-// 32 (w % 4).. and columns (w / 4) NP/2.. of each region, one output row per
-// thread, and adds the 7 group sums into double-float registers.  Every wait
-// is bounded (error code, then TMEM is freed and the kernel returns).
+// 32 (w % 4).. and columns (w / 4) NP/2.. of the regions 0..3, one output row
+// per thread, and adds them into double-float registers (the MMA issuer
+// overwrites them in the next chunk once they are read); the regions 4..6
+// are read once at the end.  Every wait is bounded (error code, then TMEM is
+// freed and the kernel returns).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -108,9 +111,9 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   if (dev_skip(skip)) return;
   constexpr int NH = NP / 2;  // columns per drain thread
   extern __shared__ uint8_t smem_raw[];
-  // ex_lo / ex_hi: the drain has read group regions 0..3 / 4..6 of a chunk
+  // ex_lo: the drain has read the group regions 0..3 of a chunk
   __shared__ uint64_t a_full[kOzAStages], a_empty[kOzAStages], b_full[2], b_empty[2], ex_full,
-      ex_lo, ex_hi;
+      ex_lo;
   __shared__ uint32_t tmem_slot;
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* bring = smem + kOzAStages * kOzABytes;
@@ -133,7 +136,6 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
     mbar_init(&ex_full, 1);
     mbar_init(&ex_lo, kOzDrainWarps * 32);
-    mbar_init(&ex_hi, kOzDrainWarps * 32);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -181,9 +183,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       for (int c = 0; c < nslab && ok; ++c) {
         const int ch = c / kOzChunkSlabs;
         const bool first = (c % kOzChunkSlabs) == 0;
-        if (first && ch > 0)  // the previous chunk's group sums were read
-          ok = mbar_wait(&ex_lo, (uint32_t)((ch - 1) & 1), err, 8) &&
-               mbar_wait(&ex_hi, (uint32_t)((ch - 1) & 1), err, 8);
+        if (first && ch > 0)  // the previous chunk's exact group sums were read
+          ok = mbar_wait(&ex_lo, (uint32_t)((ch - 1) & 1), err, 8);
         const int bs = c & 1;
         if (!ok || !mbar_wait(&b_full[bs], (uint32_t)((c >> 1) & 1), err, 2)) break;
         const uint64_t dbs = db0 + (uint64_t)((bs * kOzBBytes) >> 4);
@@ -205,8 +206,9 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const uint64_t db = dbs + (uint64_t)((u0 * kOzBRows * 128) >> 4);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-              // the chunk's first products (t = 0) overwrite every region
-              const bool fresh = first && t == 0 && kk == 0;
+              // the chunk's first products overwrite regions 0..3 (exact
+              // per chunk); regions 4..6 accumulate over the whole k range
+              const bool fresh = t == 0 && kk == 0 && (u0 == 0 ? first : c == 0);
               mma<__nv_bfloat16>(d, das + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), id,
                                  fresh ? 0u : 1u);
             }
@@ -219,7 +221,9 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       }
     }
   } else {
-    // drain: the 7 group sums of every chunk into double-float registers
+    // drain: the exact group sums of every chunk (regions 0..3), then the
+    // rest (regions 4..6, accumulated over the k range), into double-float
+    // registers
     const int quad = warp & 3, half = warp >> 2;
     const int row = m0 + quad * 32 + lane;
     const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * NH);
@@ -232,14 +236,12 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if constexpr (NH <= 24) {
         oz_drain<NH, 0, 4>(tbase, acc, &ex_lo, true);
-        oz_drain<NH, 4, 7>(tbase, acc, &ex_hi, true);
       } else {  // fewer registers in flight
         oz_drain<NH, 0, 2>(tbase, acc, &ex_lo, false);
         oz_drain<NH, 2, 4>(tbase, acc, &ex_lo, true);
-        oz_drain<NH, 4, 6>(tbase, acc, &ex_hi, false);
-        oz_drain<NH, 6, 7>(tbase, acc, &ex_hi, true);
       }
     }
+    if (nch > 0) oz_drain<NH, 4, 7>(tbase, acc, &ex_lo, false);
     if (row < n && (ok || nslab == 0)) {
       const int ei = rexp[row];
       double* Cs = C + (int64_t)blockIdx.y * split_stride;
