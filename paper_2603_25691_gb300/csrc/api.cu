@@ -64,6 +64,10 @@ struct cphifi_ctx {
   std::vector<std::pair<cudaEvent_t, std::vector<std::pair<void*, size_t>>>> deferred;
   size_t deferred_bytes = 0;
   cudaEvent_t phase[4] = {nullptr, nullptr, nullptr, nullptr};  // solve phase marks
+  // Second stream of the synchronous problem creation: Gram and eig(V) (one
+  // block) overlap the observation passes on the main stream.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // Submitted requests (cphifi_submit): admitted FIFO while a slot (stream)
   // and the HBM budget allow, advanced by cphifi_poll / cphifi_wait.
   uint64_t next_ticket = 1;
@@ -463,7 +467,9 @@ extern "C" int cphifi_ctx_create(cphifi_ctx** out, int device, size_t hbm_budget
             cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) == cudaSuccess &&
             cudaMallocHost(&ctx->h_scalars, sizeof(DevScalars)) == cudaSuccess;
   for (int k = 0; ok && k < 4; ++k) ok = cudaEventCreate(&ctx->phase[k]) == cudaSuccess;
-
+  ok = ok && cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) == cudaSuccess;
   cudaSetDevice(prev);
   if (!ok) {
     delete ctx;
@@ -485,7 +491,12 @@ extern "C" int cphifi_ctx_destroy(cphifi_ctx* ctx) {
   pool_trim(ctx);
   for (auto e : ctx->phase)
     if (e) cudaEventDestroy(e);
-
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side) {
+    cudaStreamSynchronize(ctx->side);
+    cudaStreamDestroy(ctx->side);
+  }
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
   if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
@@ -835,6 +846,7 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
     return p;
   };
   auto bail = [&](int code, const std::string& m) {
+    if (!async) cudaStreamSynchronize(ctx->side);
     cudaStreamSynchronize(st);
     for (auto& t : temps) pool_release(ctx, t.first, t.second);
     free_problem(P);
@@ -945,14 +957,21 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
     PCK(launch_split_rows_df(P->factors[m], sizes[m], r, P->fhl[m], st));
   }
 
-  // ---- Gram V (§3) and eig(V) (Eq. eigV), in order on the problem's stream.
-  // (Run on a second stream to overlap the observation passes, the one-block
-  // eigensolver took registers from one SM, so the Zhat build's single wave of
-  // blocks ran two of them after all the others: the overlap cost 1.2-1.6 ms
-  // more than the 0.7 ms it hid at the bench size.)
-  PCK(launch_gram(P->factors_dev, P->sizes_dev, d_other, r, P->V, st));
-  PCK(launch_jacobi_eig(P->V, r, P->dV, P->UV, 60, P->info, st));
-  PCK(launch_convert<double, float>(P->UV, P->UV32, (int64_t)r * r, st));
+  // ---- Gram V (§3) and eig(V) (Eq. eigV): they need only the factors.  A
+  // synchronous creation runs them on the context's second stream, under the
+  // observation passes below (whose blocks draw their work from a counter, so
+  // the SM that the one-block eigensolver holds only lowers their rate by a
+  // block's share); a submitted request, already on a stream of its own among
+  // others, runs them in order.
+  cudaStream_t gst = async ? st : ctx->side;
+  if (!async) {
+    PCK(cudaEventRecord(ctx->ev_fork, st));
+    PCK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  }
+  PCK(launch_gram(P->factors_dev, P->sizes_dev, d_other, r, P->V, gst));
+  PCK(launch_jacobi_eig(P->V, r, P->dV, P->UV, 60, P->info, gst));
+  PCK(launch_convert<double, float>(P->UV, P->UV32, (int64_t)r * r, gst));
+  if (!async) PCK(cudaEventRecord(ctx->ev_join, ctx->side));
 
   // ---- observations: copy, validate, sort by kernel index
   uint32_t* keys = (uint32_t*)tmp_alloc((size_t)q * sizeof(uint32_t));
@@ -1032,6 +1051,7 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
     PCK(launch_keep_obs(q, d_other, keys, (flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm,
                         oidx_d, vals_d, P->kidx_s, P->oidx_s, P->vals_s, gate, st));
   }
+  if (!async) PCK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
   if (async) {
     cudaEvent_t ev = nullptr;
     PCK(event_get(ctx, &ev));
