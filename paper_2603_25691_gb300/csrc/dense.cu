@@ -99,7 +99,7 @@ gemm_skinny_kernel(const TA* __restrict__ A, int64_t lda, const double* __restri
 constexpr int kF32BM = 256, kF32BK = 16;
 
 template <bool ATRANS, bool SCALEB, int TNMAX>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 gemm_f32_kernel(const float* __restrict__ A, int64_t lda, const double* __restrict__ sk,
                 const float* __restrict__ B, int64_t ldb, float* __restrict__ C, int64_t ldc,
                 int64_t split_stride, int n, int ncols, int kchunk, const DevScalars* skip) {
@@ -107,8 +107,12 @@ gemm_f32_kernel(const float* __restrict__ A, int64_t lda, const double* __restri
   constexpr int BM = kF32BM, BK = kF32BK, TM = BM / 32;
   constexpr int AL = BM * BK / 256;  // A values each thread stages per slab (16)
   constexpr int BL = BK * 64 / 256;  // B values each thread stages per slab (4)
-  __shared__ float As[2][BK][BM + 4];
-  __shared__ float Bs[2][BK][64];
+  // A tile rows: thread ty owns rows 4ty..4ty+3 and 128+4ty..128+4ty+3 (two
+  // 128-bit shared loads per k); B: warp tx's TNMAX columns at [8 tx, 8 tx +
+  // TNMAX) of a 64-float row (two 128-bit broadcast loads per k).
+  static_assert(BM == 256 && TNMAX <= 8, "register tile of 8 rows x 8 columns at most");
+  __shared__ __align__(16) float As[2][BK][BM + 4];
+  __shared__ __align__(16) float Bs[2][BK][64];
   const int tid = threadIdx.x;
   const int ty = tid & 31, tx = tid >> 5;
   const int i0 = blockIdx.x * BM;  // columns tx*TNMAX .. +TNMAX-1 (< 64)
@@ -155,7 +159,8 @@ gemm_f32_kernel(const float* __restrict__ A, int64_t lda, const double* __restri
 #pragma unroll
     for (int u = 0; u < BL; ++u) {
       const int idx = tid + 256 * u;
-      Bs[buf][idx % BK][idx / BK] = rb[u];
+      const int j = idx / BK;
+      if (j < 8 * TNMAX) Bs[buf][idx % BK][(j / TNMAX) * 8 + j % TNMAX] = rb[u];
     }
   };
   if (kbeg < kend) {
@@ -169,15 +174,17 @@ gemm_f32_kernel(const float* __restrict__ A, int64_t lda, const double* __restri
     if (more) fetch(k0 + BK);  // in flight during the multiply below
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      float a[TM], b[TNMAX];
-#pragma unroll
-      for (int m = 0; m < TM; ++m) a[m] = As[buf][kk][ty + 32 * m];
-#pragma unroll
-      for (int c = 0; c < TNMAX; ++c) b[c] = Bs[buf][kk][tx * TNMAX + c];
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][4 * ty]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][128 + 4 * ty]);
+      const float a[TM] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][8 * tx]);
+      float4 b1 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if constexpr (TNMAX > 4) b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][8 * tx + 4]);
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
       for (int m = 0; m < TM; ++m)
 #pragma unroll
-        for (int c = 0; c < TNMAX; ++c) acc[m][c] = fmaf(a[m], b[c], acc[m][c]);
+        for (int c = 0; c < TNMAX; ++c) acc[m][c] = fmaf(a[m], bv[c], acc[m][c]);
     }
     if (more) stash(buf ^ 1);
     __syncthreads();
@@ -186,7 +193,7 @@ gemm_f32_kernel(const float* __restrict__ A, int64_t lda, const double* __restri
   float* Cs = C + (int64_t)blockIdx.y * split_stride;
 #pragma unroll
   for (int m = 0; m < TM; ++m) {
-    const int i = i0 + ty + 32 * m;
+    const int i = i0 + (m < 4 ? 4 * ty + m : 128 + 4 * ty + m - 4);
     if (i >= n) continue;
 #pragma unroll
     for (int c = 0; c < TNMAX; ++c) {
