@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 from dataclasses import dataclass
 
 import numpy as np
@@ -210,6 +211,8 @@ class Context:
         rc = lib().cphifi_ctx_create(ctypes.byref(h), device, hbm_budget_bytes)
         _check(None, rc, "ctx_create")
         self.h = h
+        # kernels and problems created on this context, destroyed before it
+        self._children = weakref.WeakSet()
 
     def set_stream(self, stream) -> None:
         """cphifi_ctx_set_stream: order calls on a torch.cuda.Stream or raw handle."""
@@ -224,7 +227,15 @@ class Context:
         return lib().cphifi_last_error(self.h).decode()
 
     def close(self):
+        """Destroys the problems and kernels still open on this context, then
+        the context (their handles are dead afterwards)."""
         if getattr(self, "h", None):
+            children = list(getattr(self, "_children", ()))
+            for ch in sorted(children, key=lambda c: isinstance(c, Kernel)):
+                try:
+                    ch.close()
+                except CphifiError:
+                    ch.h = None
             lib().cphifi_ctx_destroy(self.h)
             self.h = None
 
@@ -267,6 +278,7 @@ class Kernel:
                                             ctypes.byref(h))
             _check(ctx.h, rc, "kernel_create")
             self.h = h
+            ctx._children.add(self)
             return
         u = _Buf(UK, np.float64, colmajor=True)
         d = _Buf(DK, np.float64)
@@ -277,9 +289,12 @@ class Kernel:
         rc = lib().cphifi_kernel_create(ctx.h, self.n, None, u.ptr, d.ptr, u.mem, ctypes.byref(h))
         _check(ctx.h, rc, "kernel_create")
         self.h = h
+        ctx._children.add(self)
 
     def close(self):
         """cphifi_kernel_destroy (raises while submitted requests still use it)."""
+        if getattr(self, "h", None) and not getattr(self.ctx, "h", None):
+            self.h = None  # the context is gone, and the kernel with it
         if getattr(self, "h", None):
             rc = lib().cphifi_kernel_destroy(self.h)
             _check(self.ctx.h, rc, "kernel_destroy")
@@ -339,12 +354,13 @@ class Problem:
                                          ctypes.byref(h))
         _check(ctx.h, rc, "problem_create")
         self.h = h
+        ctx._children.add(self)
         self.mem = k.mem
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(getattr(self, "ctx", None), "h", None):
             lib().cphifi_problem_destroy(self.h)
-            self.h = None
+        self.h = None
 
     __del__ = close
 

@@ -974,11 +974,12 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
   if (!async) PCK(cudaEventRecord(ctx->ev_join, ctx->side));
 
   // ---- observations: copy, validate, sort by kernel index
-  uint32_t* keys = (uint32_t*)tmp_alloc((size_t)q * sizeof(uint32_t));
+  const bool sorted_in = (flags & CPHIFI_OBS_SORTED) != 0;
+  uint32_t* keys = sorted_in ? nullptr : (uint32_t*)tmp_alloc((size_t)q * sizeof(uint32_t));
   int32_t* oidx_d = nullptr;
   const double* vals_d = nullptr;
   const int32_t* kidx_d = nullptr;
-  if (!keys) return bail(CPHIFI_E_OOM, "temporary allocation failed");
+  if (!sorted_in && !keys) return bail(CPHIFI_E_OOM, "temporary allocation failed");
   if (mem == CPHIFI_MEM_DEVICE) {
     oidx_d = (int32_t*)oidx;
     vals_d = vals;
@@ -994,20 +995,24 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
     vals_d = v;
     kidx_d = k;
   }
-  PCK(launch_validate_obs(kidx_d, oidx_d, vals_d, q, n, d_other, P->sizes_dev, P->err, st));
-  PCK(cudaMemcpyAsync(keys, kidx_d, (size_t)q * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+  // kernel indices here (the sort and the pieces use them); the other
+  // indices and the values are checked by the Zhat build below
+  PCK(launch_validate_kidx(kidx_d, q, n, sorted_in, P->err, st));
+  if (!sorted_in)
+    PCK(cudaMemcpyAsync(keys, kidx_d, (size_t)q * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+  // sorted keys: the validated (non-negative) kernel indices themselves
+  const uint32_t* skeys = sorted_in ? reinterpret_cast<const uint32_t*>(kidx_d) : keys;
   PCK(launch_iota(P->perm, q, st));
   // No host wait from here on: the kernels after the validation are gated on
   // the error word, which a synchronous creation reads once at the end.
   int herr = 0;
   const int* gate = P->err;
-  if (!(flags & CPHIFI_OBS_SORTED) && q > 1) {
+  if (!sorted_in && q > 1) {
     void* rtmp = tmp_alloc(radix_sort_tmp_bytes(q));
     if (!rtmp) return bail(CPHIFI_E_OOM, "temporary allocation failed");
     PCK(radix_sort_pairs(keys, P->perm, q, bits_for(n), rtmp, st));
   }
-  else if (q > 1) PCK(launch_check_sorted(keys, q, P->err, st));
-  PCK(launch_row_ptr(keys, q, n, P->row_ptr, st));
+  PCK(launch_row_ptr(skeys, q, n, P->row_ptr, st));
   // ---- pieces
   {
     void* stmp = tmp_alloc(exclusive_scan_tmp_bytes(n));
@@ -1048,7 +1053,7 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
     PCK(dalloc(P, &P->nfail, 4));
     P->perm_m.assign(d_other, nullptr);
     P->rowp_m.assign(d_other, nullptr);
-    PCK(launch_keep_obs(q, d_other, keys, (flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm,
+    PCK(launch_keep_obs(q, d_other, skeys, (flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm,
                         oidx_d, vals_d, P->kidx_s, P->oidx_s, P->vals_s, gate, st));
   }
   if (!async) PCK(cudaStreamWaitEvent(st, ctx->ev_join, 0));

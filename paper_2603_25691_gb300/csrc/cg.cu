@@ -472,7 +472,9 @@ __global__ void pupdate_kernel(int n, int r, const double* __restrict__ z, doubl
   const int64_t total = (int64_t)n * r;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const double v = z[t] + beta * p[t];
+    // beta = 0 (a restart): p = z without reading p, which a new solve finds
+    // holding whatever its memory held before (0 * NaN would be NaN)
+    const double v = beta != 0.0 ? z[t] + beta * p[t] : z[t];
     p[t] = v;
     const int64_t i = t % n, j = t / n;
     const double sv = scale ? scale[i] * v : v;

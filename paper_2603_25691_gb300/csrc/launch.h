@@ -13,12 +13,11 @@
 namespace cphifi {
 
 // ---------------------------------------------------------------- obs.cu ---
-// Range / finiteness checks of the observation lists; sets *err (int) to a
-// non-zero code on a bad index (1) or a non-finite value (2).
-cudaError_t launch_validate_obs(const int32_t* kidx, const int32_t* oidx,
-                                const double* vals, int64_t q, int n,
-                                int d_other, const int64_t* other_sizes_dev,
-                                int* err, cudaStream_t st);
+// Kernel indices in [0, n) (else bit 1 of *err) and, with `sorted`,
+// non-decreasing (else bit 4).  The Zhat build checks the other modes'
+// indices (bit 1) and the values' finiteness (bit 2).
+cudaError_t launch_validate_kidx(const int32_t* kidx, int64_t q, int n, bool sorted, int* err,
+                                 cudaStream_t st);
 cudaError_t launch_validate_dense(const double* a, int64_t count, int* err,
                                   cudaStream_t st);
 // Stable LSD radix sort of (key, value) pairs by key < 2^key_bits.
@@ -28,8 +27,6 @@ size_t radix_sort_tmp_bytes(int64_t q);
 cudaError_t radix_sort_pairs(uint32_t* keys, int32_t* vals, int64_t q,
                              int key_bits, void* tmp, cudaStream_t st);
 cudaError_t launch_iota(int32_t* v, int64_t q, cudaStream_t st);
-// Sets bit 4 of *err when keys are not non-decreasing.
-cudaError_t launch_check_sorted(const uint32_t* keys, int64_t q, int* err, cudaStream_t st);
 cudaError_t launch_row_ptr(const uint32_t* sorted_keys, int64_t q, int n,
                            int64_t* row_ptr, cudaStream_t st);
 // Pieces: the kernel-index segments cut at multiples of L (each warp of the

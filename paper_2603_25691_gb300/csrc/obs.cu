@@ -10,31 +10,26 @@
 namespace cphifi {
 
 // ----------------------------------------------------------- validation ---
-__global__ void validate_obs_kernel(const int32_t* __restrict__ kidx,
-                                    const int32_t* __restrict__ oidx,
-                                    const double* __restrict__ vals, int64_t q, int n,
-                                    int d_other, const int64_t* __restrict__ sizes,
-                                    int* err) {
+// Kernel indices in [0, n) (bit 1 of *err), and non-decreasing when the
+// caller declared them sorted (bit 4).  The other modes' indices and the
+// values are checked by the Zhat build, which reads them anyway.
+__global__ void validate_kidx_kernel(const int32_t* __restrict__ kidx, int64_t q, int n,
+                                     bool sorted, int* err) {
   int bad = 0;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < q;
        l += (int64_t)gridDim.x * blockDim.x) {
     const int32_t k = kidx[l];
     if (k < 0 || k >= n) bad |= 1;
-    for (int m = 0; m < d_other; ++m) {
-      const int32_t o = oidx[l * d_other + m];
-      if (o < 0 || o >= sizes[m]) bad |= 1;
-    }
-    if (!isfinite(vals[l])) bad |= 2;
+    if (sorted && l + 1 < q && kidx[l + 1] < k) bad |= 4;
   }
   if (bad) atomicOr(err, bad);
 }
 
-cudaError_t launch_validate_obs(const int32_t* kidx, const int32_t* oidx,
-                                const double* vals, int64_t q, int n, int d_other,
-                                const int64_t* sizes_dev, int* err, cudaStream_t st) {
+cudaError_t launch_validate_kidx(const int32_t* kidx, int64_t q, int n, bool sorted, int* err,
+                                 cudaStream_t st) {
   if (q == 0) return cudaSuccess;
   const int blocks = (int)((q + 255) / 256 < 4096 ? (q + 255) / 256 : 4096);
-  validate_obs_kernel<<<blocks, 256, 0, st>>>(kidx, oidx, vals, q, n, d_other, sizes_dev, err);
+  validate_kidx_kernel<<<blocks, 256, 0, st>>>(kidx, q, n, sorted, err);
   return cudaGetLastError();
 }
 
@@ -63,21 +58,6 @@ cudaError_t launch_iota(int32_t* v, int64_t q, cudaStream_t st) {
   if (q == 0) return cudaSuccess;
   const int blocks = (int)((q + 255) / 256 < 4096 ? (q + 255) / 256 : 4096);
   iota_kernel<<<blocks, 256, 0, st>>>(v, q);
-  return cudaGetLastError();
-}
-
-__global__ void check_sorted_kernel(const uint32_t* __restrict__ keys, int64_t q, int* err) {
-  int bad = 0;
-  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l + 1 < q;
-       l += (int64_t)gridDim.x * blockDim.x)
-    if (keys[l] > keys[l + 1]) bad = 4;
-  if (bad) atomicOr(err, bad);
-}
-
-cudaError_t launch_check_sorted(const uint32_t* keys, int64_t q, int* err, cudaStream_t st) {
-  if (q < 2) return cudaSuccess;
-  const int blocks = (int)((q + 255) / 256 < 4096 ? (q + 255) / 256 : 4096);
-  check_sorted_kernel<<<blocks, 256, 0, st>>>(keys, q, err);
   return cudaGetLastError();
 }
 
@@ -505,8 +485,10 @@ zhat_build_kernel(int64_t q, const int32_t* __restrict__ perm, const int32_t* __
     const int64_t l = tile * 32 + lane;
     if (l >= q) continue;
     const int64_t src = perm ? (int64_t)perm[l] : l;
+    const double tv = vals[src];
+    bad |= isfinite(tv) ? 0 : 2;
     if (tdf) {  // the observed value as a double-float pair, in the sorted order
-      const df t = df_from_double(vals[src]);
+      const df t = df_from_double(tv);
       tdf[l] = make_float2(t.hi, t.lo);
     }
     const int32_t* im = oidx + src * d_other;
@@ -561,7 +543,7 @@ zhat_build_kernel(int64_t q, const int32_t* __restrict__ perm, const int32_t* __
       }
     }
   }
-  if (bad) atomicOr(err, 1);
+  if (bad) atomicOr(err, bad);  // 1: other-mode index out of range, 2: non-finite value
   if (wctr && lane == 0) {  // the last warp out resets the counters
     __threadfence();
     if (atomicAdd(&wctr[1], 1u) == (unsigned)nw - 1) {
