@@ -252,6 +252,10 @@ def run_e2e(args, pkg, ctx, kern, p):
           for F in p.factors]
     Wh = pin(np.zeros((r, n))).T
     e2e_steps = max(1, min(3, args.steps))
+    # one untimed call first: the context's memory pool then holds the blocks
+    # a call needs, as it does in a long-running user process
+    pkg.solve(ctx, kern, fh, kh, oh, vh, r, p.lam, p.rho, TOL, 500, precision=args.precision,
+              sorted_obs=True, out=Wh)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_iters = 0
