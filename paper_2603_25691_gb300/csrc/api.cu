@@ -1174,8 +1174,10 @@ struct Launcher {
     ++launches;
     return e;
   }
-  // Double-float product (FP64-accurate on FP32 units): out_part gets the
-  // partial products of op(U_K) diag(scale) B over nsplitdf splits.
+  // FP64-accurate product without the FP64 units: out_part gets the partial
+  // products of op(U_K) diag(scale) B over nsplitdf splits, from the BF16
+  // slices on the tensor cores (oz_gemm.cu) when the kernel has them, else in
+  // double-float arithmetic on the FP32 units.
   cudaError_t gemm_df(bool a_trans, const double* scale, const double* B, double* out_part,
                       const DevScalars* skip, int cat) {
     if (P->ozb) {  // tensor cores, from BF16 slices of both operands
@@ -1249,7 +1251,8 @@ struct Launcher {
     if ((e = gemm64(false, nullptr, P->y164, Cp, skip, cat)) != cudaSuccess) return e;
     return combine<double, double>(mode, Cp, xin, P->bbar, out, s, skip);
   }
-  // The same operator in double-float arithmetic (FP64-accurate, FP32 units).
+  // The same operator FP64-accurate without the FP64 units (double-float
+  // gather/scatter, split-operand or double-float products).
   cudaError_t opdf(int mode, const double* xin, double* out, DevScalars* s,
                    const DevScalars* skip, int cat) {
     double* Cp = (double*)P->cpart;
@@ -1305,7 +1308,8 @@ struct Launcher {
                      const DevScalars* skip, int cat) {
     return emulated ? opdf(mode, xin, out, s, skip, cat) : op64(mode, xin, out, s, skip, cat);
   }
-  // out = D_K U_K' B (emulated: double-float product) with ||out||^2 -> bb
+  // out = D_K U_K' B (emulated: the FP64-accurate product of gemm_df) with
+  // ||out||^2 -> bb
   // when norm is set; the right-hand side and the start transform.
   cudaError_t utb(bool emulated, int mode, const double* B, double* out, DevScalars* s) {
     double* Cp = (double*)P->cpart;
@@ -1315,7 +1319,7 @@ struct Launcher {
     return combine<double, double>(mode, Cp, nullptr, nullptr, out, s, nullptr,
                                    emulated ? P->nsplitdf : P->nsplit64);
   }
-  // out = U_K x (emulated: double-float product).
+  // out = U_K x (emulated: the FP64-accurate product of gemm_df).
   cudaError_t ux(bool emulated, const double* x, double* out, DevScalars* s) {
     double* Cp = (double*)P->cpart;
     cudaError_t e = emulated ? gemm_df(true, nullptr, x, Cp, nullptr, 0)
