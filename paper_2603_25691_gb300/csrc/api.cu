@@ -766,6 +766,51 @@ static void problem_need(const cphifi_ctx* ctx, int n, bool tc, int32_t d_other,
              (size_t)n * r * sizeof(double);
 }
 
+// Zhat and the right-hand side MTTKRP B in one pass (zhat_mttkrp_kernel) over
+// a second decomposition of the sorted observations into ranges of 256
+// (8 tiles), which the warps draw in order: at any time they all write into a
+// narrow window of the Zhat array, as the separate build does with its tile
+// chunks.  The decomposition's arrays come from `alloc` (the caller's
+// temporaries, free once the stream has passed this work).
+template <typename Alloc>
+static cudaError_t zhat_and_rhs(cphifi_problem* P, const int32_t* perm, const int32_t* oidx,
+                                const double* vals, const int* gate, Alloc alloc,
+                                cudaStream_t st) {
+  const int n = P->n;
+  const int64_t q = P->q;
+  if (q == 0) return cudaMemsetAsync(P->Bm, 0, (size_t)n * P->r * sizeof(double), st);
+  const int64_t L2 = 256;
+  const int64_t W2 = (q + L2 - 1) / L2;
+  const int64_t np2 = (int64_t)n + W2 + 1;
+  int32_t* cnt2 = (int32_t*)alloc((size_t)n * sizeof(int32_t));
+  int32_t* first2 = (int32_t*)alloc((size_t)(n + 1) * sizeof(int32_t));
+  int32_t* pseg2 = (int32_t*)alloc((size_t)np2 * sizeof(int32_t));
+  int32_t* pbeg2 = (int32_t*)alloc((size_t)np2 * sizeof(int32_t));
+  int32_t* pend2 = (int32_t*)alloc((size_t)np2 * sizeof(int32_t));
+  int32_t* wfirst2 = (int32_t*)alloc((size_t)(W2 + 1) * sizeof(int32_t));
+  unsigned* ticket2 = (unsigned*)alloc((size_t)n * sizeof(unsigned));
+  double* partial2 = (double*)alloc((size_t)np2 * 64 * sizeof(double));
+  void* stmp2 = alloc(exclusive_scan_tmp_bytes(n));
+  if (!cnt2 || !first2 || !pseg2 || !pbeg2 || !pend2 || !wfirst2 || !ticket2 || !partial2 ||
+      !stmp2)
+    return cudaErrorMemoryAllocation;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ticket2, 0, (size_t)n * sizeof(unsigned), st)) != cudaSuccess ||
+      (e = launch_piece_counts(P->row_ptr, n, L2, cnt2, gate, st)) != cudaSuccess ||
+      (e = exclusive_scan_i32(cnt2, first2, n, stmp2, exclusive_scan_tmp_bytes(n), st)) !=
+          cudaSuccess ||
+      (e = launch_piece_fill(P->row_ptr, n, L2, first2, cnt2, pseg2, pbeg2, pend2, gate, st)) !=
+          cudaSuccess ||
+      (e = launch_warp_first(pbeg2, (int)np2, first2 + n, L2, (int)W2, wfirst2, gate, st)) !=
+          cudaSuccess)
+    return e;
+  const PieceList pl2{pseg2, pbeg2, pend2, first2, cnt2, ticket2, wfirst2, (int)np2, (int)W2,
+                      P->wctr};
+  return launch_zhat_mttkrp_fused(pl2, q, perm, oidx, P->d_other, P->fhl_dev, P->sizes_dev, P->r,
+                                  vals, P->zhi, P->z64, partial2, P->Bm, n, P->err, gate,
+                                  P->ctx->num_sms, st);
+}
+
 // Problem creation on stream `st` (the context's stream for the public call, a
 // pool stream for submitted requests).
 // The device work is queued without host waits: the kernels after the input
@@ -1031,18 +1076,13 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
     PCK(launch_warp_first(P->pbeg, np, P->seg_first + n, L, W, P->warp_first, gate, st));
   }
 
-  // ---- Zhat, then the right-hand side MTTKRP
-  float* tdf_tmp = nullptr;
-  if (P->zhi) {
-    tdf_tmp = (float*)tmp_alloc((size_t)std::max<int64_t>(q, 1) * 2 * sizeof(float));
-    if (!tdf_tmp) return bail(CPHIFI_E_OOM, "temporary allocation failed");
+  // ---- Zhat and the right-hand side MTTKRP
+  {
+    const cudaError_t ez = zhat_and_rhs(P, (flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm,
+                                        oidx_d, vals_d, gate, tmp_alloc, st);
+    if (ez == cudaErrorMemoryAllocation) return bail(CPHIFI_E_OOM, "temporary allocation failed");
+    PCK(ez);
   }
-  PieceList pl{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket,
-               P->warp_first, P->npieces, P->nwarps, P->wctr};
-  PCK(launch_zhat_mttkrp(pl, (flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm, oidx_d, d_other,
-                         P->fhl_dev, P->sizes_dev, r, vals_d, P->zhi, P->zlo,
-                         P->z64, (double*)P->gds_partial, P->Bm, n, P->err, gate,
-                         ctx->num_sms, q, tdf_tmp, st));
   if (flags & CPHIFI_KEEP_OBS) {
     P->keep_obs = true;
     PCK(dalloc(P, &P->kidx_s, (size_t)q));
@@ -1743,19 +1783,21 @@ static int problem_rebuild(cphifi_problem* P) {
   CK(launch_gram(P->factors_dev, P->sizes_dev, d, r, P->V, st));
   CK(launch_jacobi_eig(P->V, r, P->dV, P->UV, 60, P->info, st));
   CK(launch_convert<double, float>(P->UV, P->UV32, (int64_t)r * r, st));
-  const PieceList pl{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket,
-                     P->warp_first, P->npieces, P->nwarps, P->wctr};
-  void* tdf = nullptr;
-  size_t gt = 0;
-  if (P->zhi) CK(pool_alloc(ctx, (size_t)std::max<int64_t>(P->q, 1) * 2 * sizeof(float), &tdf, &gt));
-  const cudaError_t ez = launch_zhat_mttkrp(pl, nullptr, P->oidx_s, d, P->fhl_dev, P->sizes_dev,
-                                            r, P->vals_s, P->zhi, P->zlo, P->z64,
-                                            (double*)P->gds_partial, P->Bm, P->n, P->err, nullptr,
-                                            ctx->num_sms, P->q, (float*)tdf, st);
+  // the same pass as the problem's creation, so a rebuilt problem gives the
+  // bits of one created from the new factors
+  std::vector<std::pair<void*, size_t>> tmps;
+  auto alloc = [&](size_t bytes) -> void* {
+    void* ptr = nullptr;
+    size_t got = 0;
+    if (pool_alloc(ctx, std::max<size_t>(bytes, 1), &ptr, &got) != cudaSuccess) return nullptr;
+    tmps.push_back({ptr, got});
+    return ptr;
+  };
+  const cudaError_t ez = zhat_and_rhs(P, nullptr, P->oidx_s, P->vals_s, nullptr, alloc, st);
   int herr = 0;
   cudaError_t ec = cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, st);
   const cudaError_t es = cudaStreamSynchronize(st);
-  if (tdf) pool_release(ctx, tdf, gt);
+  for (auto& t : tmps) pool_release(ctx, t.first, t.second);
   CK(ez);
   CK(ec);
   CK(es);

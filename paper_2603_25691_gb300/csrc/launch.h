@@ -107,6 +107,17 @@ cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const i
                                int64_t ldb, int* err, const int* gate, int num_sms, int64_t q,
                                float* tdf_tmp, cudaStream_t st);
 
+// Zhat and the MTTKRP in one pass (obs.cu, zhat_mttkrp_kernel) over the
+// pieces of pl (its own decomposition; pl.wctr required).  B is written for
+// every kernel index (zero rows for empty ones); bad other-mode indices set
+// *err bit 1, non-finite values bit 2.  partial: pl.npieces x 64 doubles.
+cudaError_t launch_zhat_mttkrp_fused(const PieceList& pl, int64_t q, const int32_t* perm,
+                                     const int32_t* oidx, int d_other, const float* const* fhl,
+                                     const int64_t* sizes_dev, int r, const double* vals,
+                                     float* zhi, double* z64, double* partial, double* B,
+                                     int64_t ldb, int* err, const int* gate, int num_sms,
+                                     cudaStream_t st);
+
 // -------------------------------------------------------------- dense.cu ---
 // Skinny product C = op(A) diag(s) B for A n x n (op = identity when a_trans
 // is true, transpose otherwise, see dense.cu), B n x ncols column-major; the

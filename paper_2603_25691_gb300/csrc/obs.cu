@@ -1,6 +1,7 @@
 // Observation-side kernels: validation, the stable sort by kernel index, the
 // CSR row pointer, the piece list, Zhat (Eq. zhat, §4.2) and the fused
 // gather-dot/scatter of the matrix-free product (Eqs. vl and yhat1, §4.4.1).
+#include <algorithm>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -810,6 +811,195 @@ cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const i
                                wt);
   return gds_by_rank<GDS_F64>(pl, nullptr, nullptr, z64, r, nullptr, 0, partial, B, ldb, nullptr,
                               st, wt);
+}
+
+// ------------------------------------------ fused Zhat build + MTTKRP ----
+// Zhat and B(i,:) = sum_{i_l = i} t_l Zhat(l,:) (§4, the right-hand side) in
+// one pass: warp w takes the pieces of its range of sorted observations
+// (the gather-dot/scatter decomposition, here with more and shorter ranges),
+// builds each 32-observation tile of a piece column group by column group as
+// the build kernel does (one lane per observation, double-float products of
+// the factor rows, the FP32 pair and/or FP64 stored), and folds t_l Zhat(l,:)
+// into the piece's row sum: the 4 columns of a group are summed over the 32
+// lanes by a reduce-scatter (lanes exchange halves of the group, then
+// butterfly: 12 shuffles, 6 double-float additions per lane), and 4 lanes add
+// the tile's 4 column sums into the warp's row in shared memory.  The rows
+// are written as the gather-dot/scatter writes them (a kernel index split
+// over pieces: partial rows, the last piece adds them in piece order), so B is
+// deterministic, and Zhat is never read back.
+__device__ __forceinline__ df shfl_xor_df(df v, int m) {
+  return df{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
+}
+
+template <bool WHI, bool W64>
+__global__ void __launch_bounds__(256, 4)
+zhat_mttkrp_kernel(PieceList pl, int64_t q, const int32_t* __restrict__ perm,
+                   const int32_t* __restrict__ oidx, int d_other,
+                   const float* const* __restrict__ fhl, const int64_t* __restrict__ sizes, int r,
+                   float* __restrict__ zhi, double* __restrict__ z64,
+                   const double* __restrict__ vals, double* __restrict__ partial,
+                   double* __restrict__ B, int64_t ldb, int* err, const int* gate) {
+  if (gate && *gate) return;  // invalid input found earlier: touch nothing
+  __shared__ df bacc[8][64];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  bool vec = (r % 4 == 0);
+  for (int m = 0; m < d_other; ++m)
+    vec = vec && ((reinterpret_cast<uintptr_t>(fhl[m]) & 31) == 0);
+  // reduce-scatter roles: after it, lanes 8c..8c+7 hold column c of a group
+  const bool up16 = (lane & 16) != 0, up8 = (lane & 8) != 0;
+  const int col = (up16 ? 2 : 0) + (up8 ? 1 : 0);
+  int bad = 0;
+  auto draw = [&]() -> int {
+    unsigned v = 0;
+    if (lane == 0) v = atomicAdd(&pl.wctr[0], 1u);
+    return (int)__shfl_sync(0xffffffffu, v, 0);
+  };
+  for (int w = draw(); w < pl.nwarps; w = draw()) {
+    const int p_end = pl.warp_first[w + 1];
+    for (int p = pl.warp_first[w]; p < p_end; ++p) {
+      const int seg = pl.seg[p];
+      const int64_t b = pl.beg[p], e = pl.end[p];
+      __syncwarp();
+      for (int j = lane; j < 64; j += 32) bacc[wib][j] = df{0.f, 0.f};
+      __syncwarp();
+      for (int64_t tile = b >> 5; e > b && tile <= (e - 1) >> 5; ++tile) {
+        const int64_t l = tile * 32 + lane;
+        const bool act = l >= b && l < e;
+        const int64_t src = act ? (perm ? (int64_t)perm[l] : l) : 0;
+        const double tv = act ? vals[src] : 0.0;
+        bad |= isfinite(tv) ? 0 : 2;
+        const df t = df_from_double(tv);
+        const int32_t* im = oidx + src * d_other;
+        bool ok = act;
+        for (int m = 0; act && m < d_other; ++m) {
+          const int32_t v = __ldg(im + m);
+          ok = ok && v >= 0 && v < sizes[m];
+        }
+        bad |= (act && !ok) ? 1 : 0;
+        const int64_t base = tile * 64 * (int64_t)r + (l & 31);    // hi tile; lo = +32 r
+        const int64_t base64 = tile * 32 * (int64_t)r + (l & 31);  // FP64 copy
+        for (int j0 = 0; j0 < r; j0 += 4) {
+          df z[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) z[u] = df{0.f, 0.f};
+          if (ok) {
+            for (int m = 0; m < d_other; ++m) {
+              const int64_t off = (int64_t)__ldg(im + m) * r + j0;
+              float h[4], lo[4];
+              if (vec) {
+                float v[8];
+                ldg_v8(fhl[m] + 2 * off, v);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  h[u] = v[2 * u];
+                  lo[u] = v[2 * u + 1];
+                }
+              } else {
+                const float2* p2 = reinterpret_cast<const float2*>(fhl[m]) + off;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  const float2 v = j0 + u < r ? __ldg(p2 + u) : make_float2(0.f, 0.f);
+                  h[u] = v.x;
+                  lo[u] = v.y;
+                }
+              }
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const df f{h[u], lo[u]};
+                z[u] = m == 0 ? f : df_mul(z[u], f);
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int j = j0 + u;
+              if (j < r) {
+                if constexpr (WHI) {
+                  __stcs(zhi + base + 32 * (int64_t)j, z[u].hi);
+                  __stcs(zhi + base + 32 * (int64_t)j + 32 * r, z[u].lo);
+                }
+                if constexpr (W64) __stcs(z64 + base64 + 32 * (int64_t)j, df_to_double(z[u]));
+              }
+            }
+          }
+          // t_l Zhat(l, j0..j0+3), summed over the tile's lanes
+          df wv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) wv[u] = ok ? df_mul(t, z[u]) : df{0.f, 0.f};
+          df a0 = up16 ? wv[2] : wv[0], a1 = up16 ? wv[3] : wv[1];
+          df_acc_add(a0, shfl_xor_df(up16 ? wv[0] : wv[2], 16));
+          df_acc_add(a1, shfl_xor_df(up16 ? wv[1] : wv[3], 16));
+          df c = up8 ? a1 : a0;
+          df_acc_add(c, shfl_xor_df(up8 ? a0 : a1, 8));
+          df_acc_add(c, shfl_xor_df(c, 4));
+          df_acc_add(c, shfl_xor_df(c, 2));
+          df_acc_add(c, shfl_xor_df(c, 1));
+          if ((lane & 7) == 0 && j0 + col < r) df_acc_add(bacc[wib][j0 + col], c);
+        }
+      }
+      __syncwarp();
+      // the piece's row: directly into B, or a partial row that the last
+      // piece of the kernel index adds in piece order
+      const int np = pl.seg_count[seg];
+      if (np == 1) {
+        for (int j = lane; j < r; j += 32)
+          B[(int64_t)j * ldb + seg] = df_to_double(df_norm(bacc[wib][j]));
+      } else {
+        for (int j = lane; j < r; j += 32)
+          partial[(int64_t)p * 64 + j] = df_to_double(df_norm(bacc[wib][j]));
+        __threadfence();
+        __syncwarp();
+        unsigned tk = 0;
+        if (lane == 0) tk = atomicAdd(&pl.seg_ticket[seg], 1u);
+        tk = __shfl_sync(0xffffffffu, tk, 0);
+        if (tk == (unsigned)(np - 1)) {
+          __threadfence();
+          const int f = pl.seg_first[seg];
+          for (int j = lane; j < r; j += 32) {
+            double sacc = 0.0;
+            for (int k = 0; k < np; ++k) sacc += __ldcg(&partial[(int64_t)(f + k) * 64 + j]);
+            B[(int64_t)j * ldb + seg] = sacc;
+          }
+          if (lane == 0) pl.seg_ticket[seg] = 0u;
+        }
+      }
+    }
+  }
+  if (bad) atomicOr(err, bad);  // 1: other-mode index out of range, 2: non-finite value
+  if (lane == 0) {  // the last warp out resets the counters
+    __threadfence();
+    if (atomicAdd(&pl.wctr[1], 1u) == (unsigned)nwarps - 1) {
+      pl.wctr[0] = 0u;
+      pl.wctr[1] = 0u;
+      __threadfence();
+    }
+  }
+}
+
+cudaError_t launch_zhat_mttkrp_fused(const PieceList& pl, int64_t q, const int32_t* perm,
+                                     const int32_t* oidx, int d_other, const float* const* fhl,
+                                     const int64_t* sizes_dev, int r, const double* vals,
+                                     float* zhi, double* z64, double* partial, double* B,
+                                     int64_t ldb, int* err, const int* gate, int num_sms,
+                                     cudaStream_t st) {
+  if (q == 0 || pl.npieces == 0 || pl.nwarps == 0) return cudaSuccess;
+  if (d_other < 1 || d_other > 16 || r < 1 || r > 64 || (!zhi && !z64) || !pl.wctr)
+    return cudaErrorInvalidValue;
+  // one resident wave (4 blocks of 8 warps per SM); the warps draw the ranges
+  const int blocks = (int)std::min<int64_t>((pl.nwarps + 7) / 8, (int64_t)num_sms * 4);
+  if (zhi && z64)
+    zhat_mttkrp_kernel<true, true><<<blocks, 256, 0, st>>>(pl, q, perm, oidx, d_other, fhl,
+                                                           sizes_dev, r, zhi, z64, vals, partial,
+                                                           B, ldb, err, gate);
+  else if (zhi)
+    zhat_mttkrp_kernel<true, false><<<blocks, 256, 0, st>>>(pl, q, perm, oidx, d_other, fhl,
+                                                            sizes_dev, r, zhi, z64, vals, partial,
+                                                            B, ldb, err, gate);
+  else
+    zhat_mttkrp_kernel<false, true><<<blocks, 256, 0, st>>>(pl, q, perm, oidx, d_other, fhl,
+                                                            sizes_dev, r, zhi, z64, vals, partial,
+                                                            B, ldb, err, gate);
+  return cudaGetLastError();
 }
 
 // Elementwise conversions between the FP64 Zhat and its interleaved FP32 pair.
