@@ -92,25 +92,15 @@ cudaError_t launch_gds_f64(const PieceList& pl, const double* z64, int r, const 
 cudaError_t launch_gds_df(const PieceList& pl, const float* zhi, const float* zlo, int r,
                           const double* Xh, int64_t xld, double* partial, double* Y,
                           int64_t yld, const DevScalars* skip, cudaStream_t st);
-// Zhat (Eq. zhat) in sorted order, computed in double-float from the factors'
-// interleaved hi/lo rows (fhl[m], see launch_split_rows_df) and written as
-// hi/lo FP32 pairs and/or FP64 (zhi/zlo or z64 may be NULL, not both); then
-// the MTTKRP B(i,:) = sum_{i_l = i} t_l Zhat(l,:) (B column-major, ld ldb,
-// FP64-accurate) as the weights mode of the gather-dot/scatter.  perm = NULL:
-// input already sorted.  Bad indices set *err bit 1 (the MTTKRP then skips).
-// tdf_tmp: 2 q floats of scratch (the values as double-float pairs in the
-// sorted order) when zhi is set; unused otherwise.
-cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const int32_t* oidx,
-                               int d_other, const float* const* fhl,
-                               const int64_t* sizes_dev, int r, const double* vals,
-                               float* zhi, float* zlo, double* z64, double* partial, double* B,
-                               int64_t ldb, int* err, const int* gate, int num_sms, int64_t q,
-                               float* tdf_tmp, cudaStream_t st);
-
-// Zhat and the MTTKRP in one pass (obs.cu, zhat_mttkrp_kernel) over the
-// pieces of pl (its own decomposition; pl.wctr required).  B is written for
-// every kernel index (zero rows for empty ones); bad other-mode indices set
-// *err bit 1, non-finite values bit 2.  partial: pl.npieces x 64 doubles.
+// Zhat (Eq. zhat) in sorted order, computed in double-float from the
+// factors' interleaved hi/lo rows (fhl[m], see launch_split_rows_df) and
+// written as hi/lo FP32 pairs (zhi, tiles [hi | lo]) and/or FP64 (z64), and
+// in the same pass the MTTKRP B(i,:) = sum_{i_l = i} t_l Zhat(l,:) (B
+// column-major, ld ldb, FP64-accurate), over the pieces of pl (its own
+// decomposition; pl.wctr required).  perm = NULL: input already sorted.  B is
+// written for every kernel index (zero rows for empty ones); bad other-mode
+// indices set *err bit 1, non-finite values bit 2.  partial: pl.npieces x 64
+// doubles.
 cudaError_t launch_zhat_mttkrp_fused(const PieceList& pl, int64_t q, const int32_t* perm,
                                      const int32_t* oidx, int d_other, const float* const* fhl,
                                      const int64_t* sizes_dev, int r, const double* vals,

@@ -358,15 +358,16 @@ cudaError_t launch_warp_first(const int32_t* pbeg, int npieces, const int32_t* n
 
 // -------------------------------------------------------------- Zhat ------
 // Zhat(s, j) = prod_m A_m(oidx[perm[s], m], j) for the s-th observation in the
-// sorted order (Eq. zhat), computed in FP64 and stored as an unevaluated sum of
-// two FP32 numbers hi + lo (hi = fl32(z), lo = fl32(z - hi); |z - hi - lo| <=
-// 2^-48 |z|): hi alone is the FP32 operator's Zhat, hi + lo the FP64 one.
-// Storage is in tiles of 32 observations (zidx in launch.h), so the 32 x r
-// values a warp round reads form one contiguous block.
+// sorted order (Eq. zhat), computed in double-float arithmetic and stored as an
+// unevaluated sum of two FP32 numbers hi + lo (|z - hi - lo| <= 2^-48 |z|):
+// hi alone is the FP32 operator's Zhat, hi + lo the FP64 one (and/or the FP64
+// value itself).  Storage is in tiles of 32 observations (zidx in launch.h),
+// so the 32 x r values a warp round reads form one contiguous block.
 //
-// The same pass forms the sparse MTTKRP B(i,:) = sum_{i_l = i} t_l Zhat(l,:)
-// (§4, the right-hand side) in FP64, with the piece/warp decomposition and
-// deterministic combine of the gather-dot/scatter below.
+// The pass that builds Zhat also forms the sparse MTTKRP B(i,:) =
+// sum_{i_l = i} t_l Zhat(l,:) (§4, the right-hand side), FP64-accurate, with
+// the piece decomposition and deterministic combine of the gather-dot/scatter
+// below (zhat_mttkrp_kernel).
 
 // Cross-lane helpers for LPO lanes per observation: lane = sub * OPW + o with
 // OPW = 32 / LPO observations per warp round; the lane owns the CPL = RP/LPO
@@ -441,120 +442,6 @@ __device__ __forceinline__ void ldg_v8(const float* p, float (&v)[8]) {
       : "l"(p));
 }
 
-// Resident 256-thread blocks per SM of the Zhat build (a register budget of
-// 40 per thread: with 32 the compiler spills to local memory, which shares the
-// L1 data path that the factor-row gathers saturate).
-constexpr int kBuildBlocksPerSM = 6;
-
-// One lane per observation, tiles of 32 sorted observations in chunks of 8
-// tiles that the warps draw from a counter (grid-stride when no counter is
-// given): every column of a Zhat tile is written by one coalesced
-// 128-byte store per array.  Each lane walks the columns in groups of 4
-// (16-byte factor-row loads) and forms the double-float product over the
-// other modes.  No per-lane state survives a tile, so registers stay few and
-// the launch fills the SMs (the gathers from L2 need many warps in flight).
-// W64: also store Zhat in FP64 (a template flag, so the FP64 conversions are
-// not executed, even speculatively, when only the FP32 pair is stored).
-template <bool W64>
-__global__ void __launch_bounds__(256, kBuildBlocksPerSM)
-zhat_build_kernel(int64_t q, const int32_t* __restrict__ perm, const int32_t* __restrict__ oidx,
-                  int d_other, const float* const* __restrict__ fhl,
-                  const int64_t* __restrict__ sizes, int r,
-                  float* __restrict__ zhi, float* __restrict__ zlo, double* __restrict__ z64,
-                  const double* __restrict__ vals, float2* __restrict__ tdf, int* err,
-                  const int* gate, unsigned* wctr) {
-  if (gate && *gate) return;  // invalid input found earlier: touch nothing
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t ntiles = (q + 31) >> 5;
-  // 32-byte aligned groups of 4 (hi, lo) pairs: one 256-bit load each
-  bool vec = (r % 4 == 0);
-  for (int m = 0; m < d_other; ++m)
-    vec = vec && ((reinterpret_cast<uintptr_t>(fhl[m]) & 31) == 0);
-  int bad = 0;
-  // tiles in chunks of 8, drawn from the counter (dynamic) or taken grid-stride
-  constexpr int64_t kChunk = 8;
-  auto draw = [&]() -> int64_t {
-    unsigned v = 0;
-    if (lane == 0) v = atomicAdd(&wctr[0], 1u);
-    return (int64_t)__shfl_sync(0xffffffffu, v, 0) * kChunk;
-  };
-  for (int64_t t0 = wctr ? draw() : gw * kChunk; t0 < ntiles;
-       t0 = wctr ? draw() : t0 + nw * kChunk)
-  for (int64_t tile = t0; tile < min(t0 + kChunk, ntiles); ++tile) {
-    const int64_t l = tile * 32 + lane;
-    if (l >= q) continue;
-    const int64_t src = perm ? (int64_t)perm[l] : l;
-    const double tv = vals[src];
-    bad |= isfinite(tv) ? 0 : 2;
-    if (tdf) {  // the observed value as a double-float pair, in the sorted order
-      const df t = df_from_double(tv);
-      tdf[l] = make_float2(t.hi, t.lo);
-    }
-    const int32_t* im = oidx + src * d_other;
-    bool ok = true;
-    for (int m = 0; m < d_other; ++m) {
-      const int32_t v = __ldg(im + m);
-      ok = ok && v >= 0 && v < sizes[m];
-    }
-    bad |= ok ? 0 : 1;
-    const int64_t base = tile * 64 * (int64_t)r + lane;     // hi tile; lo = +32 r
-    const int64_t base64 = tile * 32 * (int64_t)r + lane;   // FP64 copy
-    for (int j0 = 0; j0 < r; j0 += 4) {
-      df z[4];
-      for (int m = 0; m < d_other; ++m) {
-        const int64_t off = (ok ? (int64_t)__ldg(im + m) : 0) * r + j0;
-        float h[4], lo[4];
-        if (vec) {  // columns j0..j0+3 as (hi, lo) pairs: one 32-byte sector
-          float v[8];
-          ldg_v8(fhl[m] + 2 * off, v);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            h[u] = v[2 * u];
-            lo[u] = v[2 * u + 1];
-          }
-        } else {
-          const float2* p2 = reinterpret_cast<const float2*>(fhl[m]) + off;
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const bool in = j0 + u < r;
-            const float2 v = in ? __ldg(p2 + u) : make_float2(0.f, 0.f);
-            h[u] = v.x;
-            lo[u] = v.y;
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const df f{ok ? h[u] : 0.f, ok ? lo[u] : 0.f};
-          z[u] = m == 0 ? f : df_mul(z[u], f);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = j0 + u;
-        if (j < r) {
-          if (zhi) {
-            const int64_t zi = base + 32 * (int64_t)j;
-            __stcs(zhi + zi, z[u].hi);
-            __stcs(zhi + zi + 32 * r, z[u].lo);
-          }
-          if constexpr (W64) __stcs(z64 + base64 + 32 * (int64_t)j, df_to_double(z[u]));
-        }
-      }
-    }
-  }
-  if (bad) atomicOr(err, bad);  // 1: other-mode index out of range, 2: non-finite value
-  if (wctr && lane == 0) {  // the last warp out resets the counters
-    __threadfence();
-    if (atomicAdd(&wctr[1], 1u) == (unsigned)nw - 1) {
-      wctr[0] = 0u;
-      wctr[1] = 0u;
-      __threadfence();
-    }
-  }
-}
-
 // ------------------------------------------------ gather-dot / scatter ----
 // Warp w owns the pieces [warp_first[w], warp_first[w+1]), i.e. the sorted
 // observations [w L, (w+1) L).  Per piece (one kernel index i), each
@@ -593,9 +480,11 @@ __device__ __forceinline__ float acc_out(float a) { return a; }
 __device__ __forceinline__ double acc_out(double a) { return a; }
 __device__ __forceinline__ double acc_out(df a) { return df_to_double(df_norm(a)); }
 
-// WTS (weights mode, the sparse MTTKRP B = T Z of §4): xbar_l is the given
-// weight t_l (wts[wperm[l]], or wts[l] without a permutation) instead of the
-// dot product, so Y(i,:) = sum_{i_l = i} t_l Zhat(l,:).
+// WTS (weights mode): xbar_l is a given weight t_l (wts[wperm[l]], or wts[l]
+// without a permutation) instead of the dot product, so Y(i,:) =
+// sum_{i_l = i} t_l Zhat(l,:), a sparse MTTKRP over a stored Zhat.  (The
+// right-hand side of a problem comes from zhat_mttkrp_kernel, which needs no
+// stored Zhat.)
 template <int MODE, int RP, int LPO, bool WTS>
 __global__ void __launch_bounds__(256, 2) gds_kernel(PieceList pl, const float* __restrict__ zhi,
                                                   const float* __restrict__ zlo,
@@ -772,45 +661,6 @@ static cudaError_t gds_by_rank(const PieceList& pl, const float* zhi, const floa
   if (r <= 48) return gds_dispatch<MODE, 48, wide ? 4 : 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
   if (r <= 64) return gds_dispatch<MODE, 64, wide ? 4 : 2>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
   return cudaErrorInvalidValue;
-}
-
-// Zhat, then the sparse MTTKRP B = T Z as the weights mode of the
-// gather-dot/scatter (double-float from hi + lo, or FP64 from z64).
-cudaError_t launch_zhat_mttkrp(const PieceList& pl, const int32_t* perm, const int32_t* oidx,
-                               int d_other, const float* const* fhl,
-                               const int64_t* sizes_dev, int r, const double* vals, float* zhi,
-                               float* zlo, double* z64, double* partial, double* B, int64_t ldb,
-                               int* err, const int* gate, int num_sms, int64_t q, float* tdf_tmp,
-                               cudaStream_t st) {
-  if (q == 0 || pl.npieces == 0 || pl.nwarps == 0) return cudaSuccess;
-  float2* tdf = zhi ? reinterpret_cast<float2*>(tdf_tmp) : nullptr;
-  if (zhi && !tdf) return cudaErrorInvalidValue;
-  if (d_other < 1 || d_other > 16 || r < 1 || r > 64 || (!zhi && !z64) || (zhi && !zlo))
-    return cudaErrorInvalidValue;
-  const int64_t tiles = (q + 31) / 32;
-  int64_t blocks = (tiles + 7) / 8;
-  const int64_t cap = (int64_t)num_sms * kBuildBlocksPerSM;  // one resident wave
-  if (blocks > cap) blocks = cap;
-  if (z64)
-    zhat_build_kernel<true><<<(int)blocks, 256, 0, st>>>(q, perm, oidx, d_other, fhl,
-                                                         sizes_dev, r, zhi, zlo, z64, vals, tdf,
-                                                         err, gate, pl.wctr);
-  else
-    zhat_build_kernel<false><<<(int)blocks, 256, 0, st>>>(q, perm, oidx, d_other, fhl,
-                                                          sizes_dev, r, zhi, zlo, z64, vals, tdf,
-                                                          err, gate, pl.wctr);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  GdsWeights wt;
-  wt.wts = vals;
-  wt.wperm = perm;
-  wt.wdf = tdf;
-  wt.gate = err;  // no MTTKRP over invalid indices (the build flags them)
-  if (zhi)
-    return gds_by_rank<GDS_DF>(pl, zhi, zlo, nullptr, r, nullptr, 0, partial, B, ldb, nullptr, st,
-                               wt);
-  return gds_by_rank<GDS_F64>(pl, nullptr, nullptr, z64, r, nullptr, 0, partial, B, ldb, nullptr,
-                              st, wt);
 }
 
 // ------------------------------------------ fused Zhat build + MTTKRP ----
