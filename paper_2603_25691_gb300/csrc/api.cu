@@ -681,11 +681,21 @@ extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
     const size_t oz_bytes = oz_uk_bytes((int)n, ldt);
     if (!ctx->budget || ctx->in_use + bytes + tc_bytes + oz_bytes <= ctx->budget) {
       const size_t sb = (size_t)oz_mpad((int)n) * ldt * 7 * sizeof(__nv_bfloat16);
-      if (cudaMalloc(&kern->oz1, sb) == cudaSuccess && cudaMalloc(&kern->oz2, sb) == cudaSuccess &&
-          cudaMalloc(&kern->oze, 2 * (size_t)n * sizeof(int)) == cudaSuccess &&
-          launch_oz_uk(kern->UK64, (int)n, ldt, kern->oz1, kern->oz2, kern->oze, st) == cudaSuccess &&
-          oz_make_maps(kern->oz1, kern->oz2, (int)n, ldt, &kern->mOz1, &kern->mOz2) == cudaSuccess &&
-          cudaStreamSynchronize(st) == cudaSuccess) {
+      const bool got = cudaMalloc(&kern->oz1, sb) == cudaSuccess &&
+                       cudaMalloc(&kern->oz2, sb) == cudaSuccess &&
+                       cudaMalloc(&kern->oze, 2 * (size_t)n * sizeof(int)) == cudaSuccess;
+      if (!got) {  // no room on the device: the double-float products serve instead
+        cudaGetLastError();
+        for (void** a : {(void**)&kern->oz1, (void**)&kern->oz2, (void**)&kern->oze})
+          if (*a) {
+            cudaFree(*a);
+            *a = nullptr;
+          }
+      } else if (launch_oz_uk(kern->UK64, (int)n, ldt, kern->oz1, kern->oz2, kern->oze, st) ==
+                     cudaSuccess &&
+                 oz_make_maps(kern->oz1, kern->oz2, (int)n, ldt, &kern->mOz1, &kern->mOz2) ==
+                     cudaSuccess &&
+                 cudaStreamSynchronize(st) == cudaSuccess) {
         kern->oz = true;
         tc_bytes += oz_bytes;
       } else {
