@@ -542,19 +542,4 @@ template cudaError_t launch_convert<double, float>(const double*, float*, int64_
 template cudaError_t launch_convert<float, double>(const float*, double*, int64_t, cudaStream_t);
 template cudaError_t launch_convert<double, double>(const double*, double*, int64_t, cudaStream_t);
 
-__global__ void scale_rows_kernel(const double* __restrict__ dK, const double* __restrict__ X,
-                                  double* __restrict__ Y, int n, int r) {
-  const int64_t total = (int64_t)n * r;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x)
-    Y[t] = dK[t % n] * X[t];
-}
-
-cudaError_t launch_scale_rows(const double* dK, const double* X, double* Y, int n, int r,
-                              cudaStream_t st) {
-  const int blocks = vec_blocks((int64_t)n * r);
-  scale_rows_kernel<<<blocks, 256, 0, st>>>(dK, X, Y, n, r);
-  return cudaGetLastError();
-}
-
 }  // namespace cphifi

@@ -495,23 +495,6 @@ cudaError_t launch_split_rows_df(const double* X, int64_t rows, int cols, float*
   return cudaGetLastError();
 }
 
-// out = hi + lo in FP64.
-__global__ void join_df_kernel(const float* __restrict__ hi, const float* __restrict__ lo,
-                               int64_t total, double* __restrict__ out) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x)
-    out[t] = (double)hi[t] + (double)lo[t];
-}
-
-cudaError_t launch_join_df(const float* hi, const float* lo, int64_t total, double* out,
-                           cudaStream_t st) {
-  if (total == 0) return cudaSuccess;
-  int64_t b = (total + 255) / 256;
-  if (b > 4096) b = 4096;
-  join_df_kernel<<<(int)b, 256, 0, st>>>(hi, lo, total, out);
-  return cudaGetLastError();
-}
-
 template cudaError_t launch_gemm_skinny<double, double>(const double*, int64_t, bool, const double*,
                                                         const double*, int64_t, double*, int64_t,
                                                         int64_t, int, int, int, const DevScalars*,

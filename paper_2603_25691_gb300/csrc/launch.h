@@ -133,9 +133,6 @@ int gemm_df_pick_split(int n, int num_sms);
 // holds 4 consecutive elements of a row, hi and lo together).
 cudaError_t launch_split_rows_df(const double* X, int64_t rows, int cols, float* hl,
                                  cudaStream_t st);
-// out[t] = hi[t] + lo[t] in FP64.
-cudaError_t launch_join_df(const float* hi, const float* lo, int64_t total, double* out,
-                           cudaStream_t st);
 // hi + lo = scale[t % rows] * X[t] (scale may be NULL), t < total.
 cudaError_t launch_split_df(const double* X, const double* scale, int64_t rows, int64_t total,
                             float* hi, float* lo, cudaStream_t st);
@@ -244,8 +241,6 @@ cudaError_t launch_precond_only(int n, int r, const double* X, double* Y,
                                 const double* UV, const double* D, cudaStream_t st);
 template <typename TS, typename TD>
 cudaError_t launch_convert(const TS* src, TD* dst, int64_t count, cudaStream_t st);
-cudaError_t launch_scale_rows(const double* dK, const double* X, double* Y,
-                              int n, int r, cudaStream_t st);
 
 // ---------------------------------------------------------------- als.cu ---
 // The alternating fit (§2).  keep_obs: kidx_s = sorted keys, and the
