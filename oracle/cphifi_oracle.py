@@ -29,6 +29,12 @@ Parity status of each function (what pins it in ``tests/test_oracle_*.py``):
   aligned closed form of Eq. W-decoupled (§3.2); NumPy least squares on the
   stacked least-squares form; a scalar closed form.
 * matvec: dense system matrix; the one-step form below Eq. vl (§4.4.1).
+* segment_grams, yhat1_from_grams, matvec_grams: the diagonal blocks of H in
+  F'F = (I (x) K) H (I (x) K) assembled from the literal F; yhat1_from_grams
+  against scatter_rows(gather_dot(..)) on tiny inputs.
+* relative_residual: ||A d|| / ||b|| for W = W* + d with A and b assembled
+  from the literal F (a wrong W must give a large residual), with the
+  observations split into chunks that do not divide q.
 * gram: explicit Khatri-Rao Z'Z.
 * precond_apply: M^{-1}(M x) = x with M assembled from Eq. precon.
 * pcg / cg: convergence to solve_direct; one iteration in the aligned case.
@@ -43,7 +49,8 @@ __all__ = [
     "system_matrix_from_F", "system_matrix_blocks", "solve_direct",
     "kernel_times", "gather_dot", "scatter_rows", "matvec",
     "precond_setup", "precond_apply", "pcg", "cg", "relative_residual",
-    "fitted_values", "vec", "unvec", "density",
+    "fitted_values", "vec", "unvec", "density", "segment_grams", "yhat1_from_grams",
+    "matvec_grams", "fitted_error_sq_grams",
 ]
 
 
@@ -202,6 +209,50 @@ def matvec(K, kidx, Zh, lam: float, rho: float, X, chunk: int = 1 << 21):
         xb = gather_dot(Xh, kidx[s:e], Zc)
         Y1 += scatter_rows(n, kidx[s:e], xb, Zc)
     return K @ Y1 + lam * Xh + rho * X
+
+
+def segment_grams(n: int, kidx, Zh, C=None) -> np.ndarray:
+    """The per-index Gram blocks behind Eq. yhat1 (§4.4.1).  Row i of Yhat1
+    only collects observations with i_l = i, and each adds
+    (Xhat(i,:).Zhat(l,:)) Zhat(l,:) = (Zhat(l,:)' Zhat(l,:)) Xhat(i,:)', so
+    Yhat1(i,:)' = C_i Xhat(i,:)' with C_i = sum over l with i_l = i of
+    Zhat(l,:)' Zhat(l,:) (r x r).  These are the diagonal blocks of H in
+    F'F = (I (x) K) H (I (x) K) (see system_matrix_blocks).  Returns an
+    (n, r, r) array; with C given, the observations are added into it (so a
+    long list can be visited in chunks)."""
+    r = Zh.shape[1]
+    if C is None:
+        C = np.zeros((n, r, r))
+    kidx = np.asarray(kidx)
+    order = np.argsort(kidx, kind="stable")
+    ks = kidx[order]
+    bounds = np.searchsorted(ks, np.arange(n + 1))
+    for i in np.unique(ks):
+        rows = np.asarray(Zh[order[bounds[i]:bounds[i + 1]]], dtype=np.float64)
+        C[i] += rows.T @ rows
+    return C
+
+
+def yhat1_from_grams(C, Xh) -> np.ndarray:
+    """Eq. yhat1 through the per-index Gram blocks: Yhat1(i,:) = C_i Xhat(i,:)'
+    (segment_grams)."""
+    return np.einsum("ijk,ik->ij", C, np.asarray(Xh, dtype=np.float64))
+
+
+def matvec_grams(K, C, lam: float, rho: float, X) -> np.ndarray:
+    """The product of §4.4.1 with the gather-dot/scatter replaced by the
+    per-index Gram blocks: y = K Yhat1 + lam Xhat + rho X, Xhat = K X,
+    Yhat1(i,:) = C_i Xhat(i,:)'."""
+    K = np.asarray(K, dtype=np.float64)
+    Xh = kernel_times(K, X)
+    return K @ yhat1_from_grams(C, Xh) + lam * Xh + rho * np.asarray(X, dtype=np.float64)
+
+
+def fitted_error_sq_grams(K, C, E) -> float:
+    """||F vec(E)||^2 = vec(E)' F'F vec(E) = sum_i (K E)(i,:) C_i (K E)(i,:)'
+    (F'F = (I (x) K) H (I (x) K) with the blocks C_i of H)."""
+    KE = kernel_times(K, E)
+    return float(np.einsum("ij,ij->", KE, yhat1_from_grams(C, KE)))
 
 
 def fitted_values(K, W, kidx, Zh) -> np.ndarray:

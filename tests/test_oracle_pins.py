@@ -313,6 +313,95 @@ def test_relative_residual_of_direct_solution_is_tiny():
     assert O.relative_residual(K, factors, kidx, oidx, vals, lam, rho, W) < 1e-12
 
 
+@pytest.mark.parametrize("chunk", [4, 5, 1 << 21])
+def test_relative_residual_of_a_wrong_W(chunk):
+    """For W = W* + d the residual is A vec(d) (A W* = b), so the oracle must
+    report ||A vec(d)|| / ||b|| with A and b assembled from the literal F
+    (b = F't, §2 and §4.1).  q = 15 is not a multiple of the chunk sizes 4 and
+    5, so the chunked sums over observations are covered too."""
+    K, factors, kidx, oidx, vals, lam, rho = tiny_problem(q=15, r=2, seed=6)
+    n, r = K.shape[0], 2
+    F = literal_F(K, factors, kidx, oidx)
+    A = F.T @ F + lam * np.kron(np.eye(r), K) + rho * np.eye(n * r)
+    b = F.T @ vals
+    Ws = O.solve_direct(K, factors, kidx, oidx, vals, lam, rho)
+    rng = np.random.default_rng(7)
+    for scale in (1.0, 1e-3, 1e-7):
+        d = scale * rng.standard_normal((n, r))
+        want = np.linalg.norm(A @ O.vec(d)) / np.linalg.norm(b)
+        got = O.relative_residual(K, factors, kidx, oidx, vals, lam, rho, Ws + d, chunk=chunk)
+        assert want > 1e-9
+        np.testing.assert_allclose(got, want, rtol=1e-6)
+    # the zero start has residual exactly 1
+    z = O.relative_residual(K, factors, kidx, oidx, vals, lam, rho, np.zeros((n, r)),
+                            chunk=chunk)
+    np.testing.assert_allclose(z, 1.0, rtol=1e-13)
+
+
+def test_relative_residual_catches_a_dropped_ridge(monkeypatch):
+    """A residual routine that dropped the rho term would call a wrong W
+    converged; the pin above must catch it (mistake planted in the oracle)."""
+    K, factors, kidx, oidx, vals, lam, rho = tiny_problem(q=15, r=2, seed=6, rho=0.5)
+    n, r = K.shape[0], 2
+    F = literal_F(K, factors, kidx, oidx)
+    A = F.T @ F + lam * np.kron(np.eye(r), K) + rho * np.eye(n * r)
+    b = F.T @ vals
+    d = np.random.default_rng(8).standard_normal((n, r))
+    W = O.solve_direct(K, factors, kidx, oidx, vals, lam, rho) + d
+    want = np.linalg.norm(A @ O.vec(d)) / np.linalg.norm(b)
+    good = OC.matvec
+    monkeypatch.setattr(OC, "matvec", lambda KK, kk, Z, la, rh, X, ch=1 << 21:
+                        good(KK, kk, Z, la, 0.0, X, ch))
+    bad = OC.relative_residual(K, factors, kidx, oidx, vals, lam, rho, W, chunk=4)
+    assert abs(bad - want) > 1e-3 * want
+
+
+# ---------------------------------------------------- per-index Gram blocks
+def test_segment_grams_are_the_blocks_of_FtF():
+    """F'F = (I (x) K) H (I (x) K) with H block diagonal over kernel indices,
+    block i = C_i (Appendix A.2 mixed-product rule); F from the literal
+    selection-matrix form S'(Z (x) K).  K is positive definite here, so the
+    blocks are recovered uniquely."""
+    K, factors, kidx, oidx, vals, lam, rho = tiny_problem(n=5, q=23, r=3, seed=9,
+                                                          other=(3, 4), sigma=0.3)
+    n, r = K.shape[0], 3
+    F = literal_F(K, factors, kidx, oidx)
+    IKinv = np.kron(np.eye(r), np.linalg.inv(K))
+    H = (IKinv @ (F.T @ F) @ IKinv).reshape(r, n, r, n)
+    C = O.segment_grams(n, kidx, O.zhat(factors, oidx))
+    for i in range(n):
+        np.testing.assert_allclose(C[i], H[:, i, :, i], rtol=1e-8, atol=1e-8)
+        for i2 in range(n):
+            if i2 != i:
+                assert np.abs(H[:, i, :, i2]).max() <= 1e-8
+    # chunks of the observation list add up to the same blocks
+    Zh = O.zhat(factors, oidx)
+    C2 = O.segment_grams(n, kidx[:10], Zh[:10])
+    O.segment_grams(n, kidx[10:], Zh[10:], C2)
+    np.testing.assert_allclose(C2, C, rtol=1e-14, atol=1e-14)
+
+
+def test_gram_form_of_the_product():
+    """Yhat1(i,:) = C_i Xhat(i,:)' equals the gather-dot/scatter of Eqs. vl and
+    yhat1, the Gram-form operator equals the dense literal system, and
+    ||F vec(E)||^2 from the blocks equals the literal one."""
+    K, factors, kidx, oidx, vals, lam, rho = tiny_problem(n=6, q=21, r=3, seed=10)
+    n, r = K.shape[0], 3
+    Zh = O.zhat(factors, oidx)
+    C = O.segment_grams(n, kidx, Zh)
+    X = np.random.default_rng(11).standard_normal((n, r))
+    Xh = O.kernel_times(K, X)
+    np.testing.assert_allclose(O.yhat1_from_grams(C, Xh),
+                               O.scatter_rows(n, kidx, O.gather_dot(Xh, kidx, Zh), Zh),
+                               rtol=1e-12, atol=1e-13)
+    F = literal_F(K, factors, kidx, oidx)
+    A = F.T @ F + lam * np.kron(np.eye(r), K) + rho * np.eye(n * r)
+    np.testing.assert_allclose(O.vec(O.matvec_grams(K, C, lam, rho, X)), A @ O.vec(X),
+                               rtol=1e-12, atol=1e-12)
+    fe = F @ O.vec(X)
+    np.testing.assert_allclose(O.fitted_error_sq_grams(K, C, X), fe @ fe, rtol=1e-12)
+
+
 # ----------------------------------------------------------- planted mistakes
 def test_pins_catch_planted_mistakes(monkeypatch):
     """A dropped term or a transposed operand planted in the oracle must make
