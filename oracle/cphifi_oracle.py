@@ -261,12 +261,13 @@ def fitted_values(K, W, kidx, Zh) -> np.ndarray:
 
 
 # -------------------------------------------------------------- §4.4.2 ----
-def precond_setup(K, V, gamma: float, lam: float, rho: float):
+def precond_setup(K, V, gamma: float, lam: float, rho: float, eigK=None):
     """Eigendecompositions (Eqs. eigK, eigV) and the n x r matrix D with
     D(i,j) = 1 / (gamma D_V(j) D_K(i)^2 + lam D_K(i) + rho) (Eq. fx and the
     definition of d above it).  Negative round-off eigenvalues of the PSD
-    matrices are clamped to zero inside D only."""
-    dK, UK = np.linalg.eigh(np.asarray(K, dtype=np.float64))
+    matrices are clamped to zero inside D only.  eigK = (D_K, U_K) from
+    numpy.linalg.eigh(K) may be passed when it is already at hand."""
+    dK, UK = eigK if eigK is not None else np.linalg.eigh(np.asarray(K, dtype=np.float64))
     dV, UV = np.linalg.eigh(np.asarray(V, dtype=np.float64))
     dK = np.maximum(dK, 0.0)
     dV = np.maximum(dV, 0.0)

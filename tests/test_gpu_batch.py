@@ -14,6 +14,7 @@ import pytest
 
 import oracle as O
 import synth
+from kcache import eigh_cached
 
 # every test here drives host-side request loops: bound each one
 pytestmark = [pytest.mark.gpu, pytest.mark.timeout(300)]
@@ -141,7 +142,7 @@ def test_budget_admission(pkg):
             W, st = r_.wait()
             np.testing.assert_array_equal(W, ref)
         big = synth.planted_problem(40, 300, (200, 200), 2_000_000, 32, bandwidth=0.1)
-        dK, UK = np.linalg.eigh(big.K)
+        dK, UK = eigh_cached(big.K)
         kb = ctx.kernel_create(big.n, UK, dK)
         rq = pkg.submit(ctx, kb, big.factors, big.kidx, big.oidx, big.vals, big.r, 1e-4, 1e-6,
                         1e-8, precision="mixed_fp32")
