@@ -67,16 +67,21 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch", type=int, default=256,
                     help="uneven subproblems in the batched run (0: skip)")
-    ap.add_argument("--serve-rates", default="200,1000",
+    ap.add_argument("--serve-rates", default="50,100,200,500,1000,2000",
                     help="Poisson arrival rates (req/s) of the serving run ('' : skip)")
+    ap.add_argument("--serve-fp64-rates", default="50,200",
+                    help="rates at which the FP64 one-at-a-time path is also served")
     ap.add_argument("--slots", type=int, default=16, help="requests running at once")
-    ap.add_argument("--als-ranks", default="20",
+    ap.add_argument("--als-ranks", default="10,20,40",
                     help="ranks of the alternating-fit run (n=2000, 200x300, q=6e6; '' : skip)")
     ap.add_argument("--als-sweeps", type=int, default=20)
     ap.add_argument("--no-paper-shapes", action="store_true",
                     help="skip the runs on the paper's vortex / Miranda shapes")
-    ap.add_argument("--serve-requests", type=int, default=300,
-                    help="requests per serving rate (at most ~2 s of arrivals)")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests per serving rate (at most --serve-seconds of arrivals)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--tol2", type=float, default=1e-8,
+                    help="second tolerance of the single-solve workload (0: skip)")
     return ap.parse_args()
 
 
@@ -113,6 +118,7 @@ def config_dict(args, p, world):
     """The workload description shared by both arms' JSON lines."""
     return {"workload": args.workload, "n": p.n, "other_sizes": p.other_sizes, "q": p.q,
             "r": p.r, "lambda": p.lam, "rho": p.rho, "tol": TOL, "precision": args.precision,
+            "values": "fp32", "indices": "int32, sorted by kernel index",
             "parallelism": f"replicas x{world}", "l2": "inputs larger than L2"}
 
 
@@ -247,7 +253,7 @@ def run_e2e(args, pkg, ctx, kern, p):
     import torch
     n, r, q = p.n, p.r, p.q
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-    kh, oh, vh = pin(p.kidx), pin(p.oidx.ravel()), pin(p.vals)
+    kh, oh, vh = pin(p.kidx), pin(p.oidx.ravel()), pin(p.vals.astype(np.float32))
     fh = [pin(np.asfortranarray(F).ravel(order="F")).reshape(F.shape[1], F.shape[0]).T
           for F in p.factors]
     Wh = pin(np.zeros((r, n))).T
@@ -265,7 +271,7 @@ def run_e2e(args, pkg, ctx, kern, p):
         e2e_iters += st["iterations"]
     torch.cuda.synchronize()
     te2e = time.perf_counter() - t0
-    h2d = q * 4 + q * 4 * p.oidx.shape[1] + q * 8 + sum(F.size * 8 for F in p.factors)
+    h2d = q * 4 + q * 4 * p.oidx.shape[1] + q * 4 + sum(F.size * 8 for F in p.factors)
     return {"value": q * e2e_iters / te2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(n * r * 8), "solves_per_s": e2e_steps / te2e}
 
@@ -370,21 +376,37 @@ def run_batch(args, pkg, ctx, dev, seed):
     return out
 
 
+def _pcts(lat):
+    lat = sorted(lat)
+    if not lat:
+        return {"p50_ms": None, "p99_ms": None, "max_ms": None, "count": 0}
+    pct = lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))]
+    return {"p50_ms": pct(0.5), "p99_ms": pct(0.99), "max_ms": lat[-1], "count": len(lat)}
+
+
 def run_serve(args, pkg, ctx, dev, seed, big_kern, big_p):
     """Poisson arrivals of subproblems sized as the batch (plus 5% large ones,
     n = 8000, q = 2e7, r = 40); each is submitted at its arrival time and its
-    latency runs from the arrival to the poll that sees it complete."""
+    latency runs from the arrival to the poll that sees it complete.  At the
+    rates of --serve-fp64-rates the same arrivals are also served by the plain
+    FP64 path one request at a time (cphifi_solve in arrival order)."""
     import torch
     import synth
     rates = [float(x) for x in args.serve_rates.split(",") if x]
+    rates64 = {float(x) for x in args.serve_fp64_rates.split(",") if x}
     pool = BatchInputs(pkg, ctx, dev, synth.batch_specs(seed + 7, 64))
     big = BatchInputs.upload(big_p, big_kern, dev) if big_p is not None else None
     rng = np.random.default_rng(seed)
     out = []
     for it in pool.items[:8]:
         submit_item(pkg, ctx, it, args.precision).wait()
+    if big is not None:  # the large shape once alone: its latency on an idle GPU
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        submit_item(pkg, ctx, big, args.precision).wait()
+        big_alone_ms = 1e3 * (time.perf_counter() - t0)
     for rate in rates:
-        nreq = int(min(args.serve_requests, max(20, 2.0 * rate)))
+        nreq = int(min(args.serve_requests, max(20, args.serve_seconds * rate)))
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
         which = [big if (big is not None and rng.uniform() < 0.05) else
                  pool.items[int(rng.integers(len(pool.items)))] for _ in range(nreq)]
@@ -407,17 +429,36 @@ def run_serve(args, pkg, ctx, dev, seed, big_kern, big_p):
             now = time.perf_counter() - t0
             for t in done:
                 done_t[tick[t][0]] = now
-        sts = [rq.wait()[1] for _, rq in tick.values()]
-        lat = sorted(1e3 * (done_t[i] - arrivals[i]) for i in range(nreq))
-        pct = lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))]
+        sts = {i: rq.wait()[1] for i, rq in tick.values()}
+        lat = [1e3 * (done_t[i] - arrivals[i]) for i in range(nreq)]
+        is_big = [it is big for it in which]
         span = max(done_t.values()) - arrivals[0]
-        out.append({"rate_req_s": rate, "requests": nreq,
-                    "large": int(sum(1 for it in which if it is big)),
-                    "solves_per_s": nreq / span, "p50_ms": pct(0.5), "p99_ms": pct(0.99),
-                    "max_ms": lat[-1],
-                    "converged": sum(1 for st in sts if st["status"] == 0)})
+        row = {"rate_req_s": rate, "requests": nreq, "large": int(sum(is_big)),
+               "solves_per_s": nreq / span, **_pcts(lat),
+               "small": _pcts([x for x, b in zip(lat, is_big) if not b]),
+               "large_lat": _pcts([x for x, b in zip(lat, is_big) if b]),
+               "mean_queue_ms": float(np.mean([sts[i]["queue_ms"] for i in range(nreq)])),
+               "converged": sum(1 for st in sts.values() if st["status"] == 0)}
+        if rate in rates64:
+            # the plain FP64 GPU path, one request at a time in arrival order
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lat64 = []
+            for i, it in enumerate(which):
+                now = time.perf_counter() - t0
+                if arrivals[i] > now:
+                    time.sleep(arrivals[i] - now)
+                pp = it["p"]
+                pkg.solve(ctx, it["kern"], it["f"], it["k"], it["o"], it["v"], pp.r, pp.lam,
+                          pp.rho, TOL, max_iter=MAX_ITER_BATCH, precision="fp64",
+                          sorted_obs=True, out=outs[i])
+                lat64.append(1e3 * (time.perf_counter() - t0 - arrivals[i]))
+            span64 = time.perf_counter() - t0 - arrivals[0]
+            row["fp64_one_at_a_time"] = {"solves_per_s": nreq / span64, **_pcts(lat64)}
+        out.append(row)
     pool.close()
-    return out
+    return {"rates": out, "large_alone_ms": big_alone_ms if big is not None else None,
+            "slots": args.slots}
 
 
 # Stand-ins for the paper's unaligned experiments (§5.2): mode sizes of the
@@ -520,7 +561,7 @@ def main():
     dev = torch.device("cuda", local)
     kidx_d = torch.from_numpy(p.kidx).to(dev)
     oidx_d = torch.from_numpy(np.ascontiguousarray(p.oidx).ravel()).to(dev)
-    vals_d = torch.from_numpy(p.vals).to(dev)
+    vals_d = torch.from_numpy(p.vals.astype(np.float32)).to(dev)  # the workload's FP32 values
     fac_d = [torch.from_numpy(np.asfortranarray(F).ravel(order="F")).to(dev) for F in p.factors]
     W_d = torch.empty(n * r, dtype=torch.float64, device=dev)
 
@@ -613,6 +654,33 @@ def main():
                        "rel_residual": sts[-1]["rel_residual"], "status": sts[-1]["status"],
                        "gemm_avg_ms": gm / max(1, gl)}
 
+    # ---- the same workload at the second tolerance (C3: errors at 1e-6 and 1e-8)
+    tol2 = None
+    if args.tol2 > 0:
+        def step2(precision):
+            prob = pkg.Problem(ctx, kern, fac_d, kidx_d, oidx_d, vals_d, r, sorted_obs=True,
+                               lowp=precision != "fp64")
+            W, st = prob.solve(p.lam, p.rho, args.tol2, max_iter=500, precision=precision,
+                               profile=True, out=W_d, raise_on_error=False)
+            prob.close()
+            return st
+        tol2 = {}
+        for prec in dict.fromkeys([args.precision, "mixed_tf32x3"]):
+            step2(prec)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sts = [step2(prec) for _ in range(2)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 2
+            it2 = sum(x["iterations"] for x in sts) / 2
+            tol2[prec] = {"tol": args.tol2, "solves_per_s": 1e3 / ms, "iterations": it2,
+                          "value": q * it2 / (sum(x["iter_ms"] for x in sts) / 2 / 1e3),
+                          "true_residuals": sts[-1]["true_residuals"],
+                          "rel_residual": sts[-1]["rel_residual"], "status": sts[-1]["status"]}
+
     # ---- end to end through the public API with host buffers (pinned)
     e2e = None
     if not args.no_e2e:
@@ -688,6 +756,7 @@ def main():
                          "avg_launch_ms": gds_ms / max(1, gds_exec)},
             "fp64_path": fp64,
             "precision_sweep": sweep,
+            "second_tolerance": tol2,
             "mixed_vs_fp64_solves": (solves_per_s / fp64["solves_per_s"]) if fp64 else None,
             "batched": batched, "serving": serving, "als": als_runs, "paper_shapes": paper,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary(),

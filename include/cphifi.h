@@ -103,6 +103,10 @@ typedef enum cphifi_precision {
 #define CPHIFI_KEEP_OBS 0x8u    /* keep the observation lists on the device in
                                    sorted order: needed by the alternating-fit
                                    calls (set_factors, update_factor, fit) */
+#define CPHIFI_VALS_F32 0x10u   /* the observed values are FP32 (float), not
+                                   FP64 (double): half the bytes to copy; they
+                                   are widened to FP64 on the device, and the
+                                   solve is then exact for those values    */
 
 typedef struct cphifi_params {
   double lambda;      /* RKHS regularisation, >= 0 (§2)                       */
@@ -197,8 +201,10 @@ int cphifi_kernel_destroy(cphifi_kernel* kern);
  * oidx        : q x d_other other-mode indices, row-major (observation l's
  *               indices are oidx[l*d_other .. l*d_other + d_other - 1]),
  *               index m in [0, n_m).
- * vals        : q observed values t_l.
- * flags       : CPHIFI_OBS_SORTED and/or CPHIFI_NEED_LOWP.
+ * vals        : q observed values t_l: double, or float with
+ *               CPHIFI_VALS_F32.
+ * flags       : CPHIFI_OBS_SORTED, CPHIFI_NEED_FP64 / CPHIFI_NEED_LOWP,
+ *               CPHIFI_KEEP_OBS, CPHIFI_VALS_F32.
  * Builds on the device: the stable sort by kernel index, Zhat (Eq. zhat) in
  * the sorted order, the Gram V = Hadamard of A_m'A_m (§3), eig(V)
  * (Eq. eigV), the density gamma = q/(nM) and the preconditioner diagonal D
@@ -208,7 +214,7 @@ int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern,
                           int32_t d_other, const int64_t* other_sizes,
                           const double* const* factors, int32_t r, int64_t q,
                           const int32_t* kidx, const int32_t* oidx,
-                          const double* vals, uint32_t flags, int mem,
+                          const void* vals, uint32_t flags, int mem,
                           cphifi_problem** out);
 int cphifi_problem_destroy(cphifi_problem* prob);
 /* Device bytes the problem holds. */
@@ -228,7 +234,7 @@ int cphifi_problem_solve(cphifi_problem* prob, const cphifi_params* params,
 int cphifi_solve(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
                  const int64_t* other_sizes, const double* const* factors,
                  int32_t r, int64_t q, const int32_t* kidx,
-                 const int32_t* oidx, const double* vals, uint32_t flags,
+                 const int32_t* oidx, const void* vals, uint32_t flags,
                  const cphifi_params* params, const double* W0, double* W_out,
                  int mem, cphifi_stats* stats);
 
@@ -238,8 +244,14 @@ int cphifi_solve(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
  * submitted request holds the arguments of cphifi_solve.  It is admitted --
  * its problem created on a stream of its own, its PCG started -- as soon as
  * fewer than `max_active` requests run and its device footprint fits the
- * context's HBM budget next to the running ones; requests are admitted in
- * submission order.  Admitted requests advance concurrently on their own
+ * context's HBM budget next to the running ones.  Pending requests are
+ * considered oldest first, but one that cannot start yet is passed over by
+ * smaller ones behind it: a request whose footprint (problem plus creation
+ * temporaries) exceeds 1 GiB is "large", and large requests hold at most a
+ * quarter of the slots (at least one), so a burst of large requests, or one
+ * waiting for memory, does not hold up the small ones.  A request pending
+ * for more than 50 ms is overtaken by nobody: from it on, admission is in
+ * submission order until it starts.  Admitted requests advance concurrently on their own
  * streams: each PCG chunk (k_replace iterations and the true-residual check
  * of §4.4 mixed mode) is replayed from a CUDA graph captured on first use,
  * and the host only looks at a request between chunks.
@@ -271,7 +283,7 @@ int cphifi_ctx_set_slots(cphifi_ctx* ctx, int max_active);
 int cphifi_submit(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
                   const int64_t* other_sizes, const double* const* factors,
                   int32_t r, int64_t q, const int32_t* kidx,
-                  const int32_t* oidx, const double* vals, uint32_t flags,
+                  const int32_t* oidx, const void* vals, uint32_t flags,
                   const cphifi_params* params, const double* W0, double* W_out,
                   int mem, cphifi_ticket* ticket);
 int cphifi_poll(cphifi_ctx* ctx, int32_t* n_active, int32_t* n_pending,
@@ -352,7 +364,7 @@ int cphifi_problem_fit(cphifi_problem* prob, const double* W, int mem, double* r
                        double* t2);
 int cphifi_als(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
                const int64_t* other_sizes, double* const* factors_io, int32_t r,
-               int64_t q, const int32_t* kidx, const int32_t* oidx, const double* vals,
+               int64_t q, const int32_t* kidx, const int32_t* oidx, const void* vals,
                uint32_t flags, const cphifi_params* params, int32_t sweeps, double als_tol,
                int32_t warm, double* W_io, double* err_out, int32_t* sweeps_done, int mem,
                cphifi_stats* stats);
@@ -360,20 +372,22 @@ int cphifi_als(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
 /* ---- allocation-free entry point -----------------------------------------
  * cphifi_gds_noalloc: the gather-dot/scatter product of the solver, FP64,
  * without allocating device memory.  There is no counterpart in the paper:
- * it exists for callers that cannot call cudaMalloc (for example code inside
- * a CUDA-graph capture that must not record allocations, a real-time host
- * loop that may not take the allocator's locks or its implicit
- * synchronisation, or a runtime that owns all device memory).  The caller
- * passes inputs and outputs; the working memory comes from a fixed array of
- * about 10.7 MB compiled into the library, which every GPU that loads the
- * library keeps until the process exits.
+ * it exists for callers that cannot call cudaMalloc (for example a real-time
+ * host loop that may not take the allocator's locks or wait for its implicit
+ * device synchronisation, or a runtime that owns all device memory and lets
+ * no library take more).  The caller passes inputs and outputs; the working
+ * memory comes from a fixed array of about 10.7 MB compiled into the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.
  *   n, r     : kernel-mode size in [1, 16384] and rank in [1, 64]; larger
  *              sizes return CPHIFI_E_INVALID_ARG with *err_msg naming the limit.
  *   q        : number of observations, in [0, 2^31).
  *   row_ptr  : device, n+1 int64: observations of kernel index i occupy
- *              sorted positions [row_ptr[i], row_ptr[i+1]); row_ptr[0] = 0,
- *              non-decreasing, row_ptr[n] = q (not checked: a bad CSR gives
- *              undefined results).
+ *              sorted positions [row_ptr[i], row_ptr[i+1]).  It must be a CSR
+ *              of q entries: row_ptr[0] = 0, non-decreasing, row_ptr[n] = q.
+ *              This is checked on the device: otherwise no memory but Y1 is
+ *              written and Y1 is filled with NaN (the call itself has already
+ *              returned CPHIFI_OK, since the check runs on the stream).
  *   zhat     : device FP64, Zhat in that sorted order, column-major q x r with
  *              leading dimension ldz >= q.
  *   Xhat     : device FP64 n x r column-major (leading dimension n).
@@ -383,11 +397,12 @@ int cphifi_als(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
  *   err_msg  : optional; set to a static string describing the outcome.
  * Runs on the calling thread's current device and returns once the work is
  * queued (asynchronous: synchronise `stream` before reading Y1).  The first
- * call on a device looks up the device address of the scratch array; make
- * that first call before any stream capture.  Every call on a device shares
- * the scratch array, so calls that overlap on the GPU (other streams or host
- * threads) race: serialise them on one stream.  Returns CPHIFI_OK,
- * CPHIFI_E_INVALID_ARG or CPHIFI_E_DEVICE. */
+ * call on a device looks up the device address of the scratch array (a
+ * failed lookup is retried by the next call); make that first call before
+ * any stream capture.  Every call on a device shares the scratch array, and
+ * each call clears what must start at zero, so calls that overlap on the GPU
+ * (other streams or host threads) race: serialise them on one stream.
+ * Returns CPHIFI_OK, CPHIFI_E_INVALID_ARG or CPHIFI_E_DEVICE. */
 int cphifi_gds_noalloc(int32_t n, int32_t r, int64_t q, const int64_t* row_ptr,
                        const double* zhat, int64_t ldz, const double* Xhat,
                        double* Y1, void* stream, const char** err_msg);

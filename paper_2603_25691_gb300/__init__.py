@@ -49,6 +49,7 @@ PRECISIONS = {"fp64": FP64, "mixed_fp32": MIXED_FP32, "mixed_tf32": MIXED_TF32,
               "mixed_tf32x3": MIXED_TF32X3}
 NEED_FP64 = 0x2
 KEEP_OBS = 0x8
+VALS_F32 = 0x10
 
 
 class Params(ctypes.Structure):
@@ -174,7 +175,8 @@ class _Buf:
     def __init__(self, x, dtype, shape_check=None, colmajor=False):
         if _is_torch(x):
             import torch
-            want = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+            want = {np.float64: torch.float64, np.float32: torch.float32,
+                    np.int32: torch.int32}[dtype]
             if not x.is_cuda:
                 x = x.numpy()
             else:
@@ -315,13 +317,23 @@ def _factor_bufs(factors, r):
     return bufs, sizes
 
 
+def _vals_f32(vals) -> bool:
+    """FP32 observation values (numpy or torch float32) go to the library as
+    they are, with the CPHIFI_VALS_F32 flag; anything else as FP64."""
+    return str(getattr(vals, "dtype", "")) in ("float32", "torch.float32")
+
+
 def _obs_bufs(kidx, oidx, vals):
     k = _Buf(kidx, np.int32)
     o = _Buf(oidx, np.int32)
-    v = _Buf(vals, np.float64)
+    v = _Buf(vals, np.float32 if _vals_f32(vals) else np.float64)
     if not (k.mem == o.mem == v.mem):
         raise ValueError("observation lists must live in the same memory kind")
     return k, o, v
+
+
+def _vals_flag(vals) -> int:
+    return VALS_F32 if _vals_f32(vals) else 0
 
 
 class Problem:
@@ -343,7 +355,8 @@ class Problem:
         self.sizes = sizes
         sizes_arr = (ctypes.c_int64 * len(sizes))(*sizes)
         fptrs = (ctypes.c_void_p * len(fb))(*[b.ptr for b in fb])
-        flags = (OBS_SORTED if sorted_obs else 0) | (KEEP_OBS if keep_obs else 0)
+        flags = (OBS_SORTED if sorted_obs else 0) | (KEEP_OBS if keep_obs else 0) | \
+            _vals_flag(vals)
         if lowp is True:
             flags |= NEED_LOWP
         elif lowp is False:
@@ -493,7 +506,7 @@ def solve(ctx: Context, kernel: Kernel, factors, kidx, oidx, vals, r: int, lam: 
     w0 = _Buf(W0, np.float64, colmajor=True) if W0 is not None else None
     sizes_arr = (ctypes.c_int64 * len(sizes))(*sizes)
     fptrs = (ctypes.c_void_p * len(fb))(*[b.ptr for b in fb])
-    flags = OBS_SORTED if sorted_obs else 0
+    flags = (OBS_SORTED if sorted_obs else 0) | _vals_flag(vals)
     rc = lib().cphifi_solve(ctx.h, kernel.h, len(fb), sizes_arr, fptrs, int(r), k.numel, k.ptr,
                             o.ptr, v.ptr, flags, ctypes.byref(prm), w0.ptr if w0 else None,
                             wb.ptr, k.mem, ctypes.byref(st))
@@ -521,7 +534,8 @@ def als(ctx: Context, kernel: Kernel, factors, kidx, oidx, vals, r: int, lam: fl
     done = ctypes.c_int32()
     st = Stats()
     rc = lib().cphifi_als(ctx.h, kernel.h, len(facs), sizes_arr, fptrs, int(r), k.numel, k.ptr,
-                          o.ptr, v.ptr, OBS_SORTED if sorted_obs else 0, ctypes.byref(prm),
+                          o.ptr, v.ptr, (OBS_SORTED if sorted_obs else 0) | _vals_flag(vals),
+                          ctypes.byref(prm),
                           int(sweeps), float(als_tol), 1 if W0 is not None else 0,
                           W.ctypes.data, errs.ctypes.data, ctypes.byref(done), MEM_HOST,
                           ctypes.byref(st))
@@ -570,7 +584,7 @@ def submit(ctx: Context, kernel: Kernel, factors, kidx, oidx, vals, r: int, lam:
     w0 = _Buf(W0, np.float64, colmajor=True) if W0 is not None else None
     sizes_arr = (ctypes.c_int64 * len(sizes))(*sizes)
     fptrs = (ctypes.c_void_p * len(fb))(*[b.ptr for b in fb])
-    flags = OBS_SORTED if sorted_obs else 0
+    flags = (OBS_SORTED if sorted_obs else 0) | _vals_flag(vals)
     t = ctypes.c_uint64()
     rc = lib().cphifi_submit(ctx.h, kernel.h, len(fb), sizes_arr, fptrs, int(r), k.numel, k.ptr,
                              o.ptr, v.ptr, flags, ctypes.byref(prm), w0.ptr if w0 else None,
@@ -581,13 +595,29 @@ def submit(ctx: Context, kernel: Kernel, factors, kidx, oidx, vals, r: int, lam:
 
 
 def gds_noalloc(n: int, r: int, q: int, row_ptr, zhat, ldz: int, Xhat, Y1, stream=None):
-    """cphifi_gds_noalloc on device tensors (int64 row_ptr, FP64 zhat/Xhat/Y1,
-    column-major).  Queues the work on `stream` (a torch.cuda.Stream, a raw
-    handle or None) and returns without waiting.  Raises CphifiError on a
-    rejected size or a CUDA failure."""
+    """cphifi_gds_noalloc on device tensors (int64 row_ptr of n + 1 entries,
+    FP64 zhat with at least ldz * r entries, FP64 Xhat and Y1 with at least
+    n * r entries, all column-major).  Queues the work on `stream` (a
+    torch.cuda.Stream, a raw handle or None) and returns without waiting.
+    Raises ValueError on a wrong dtype or size, CphifiError on a size beyond
+    the entry point's limit or a CUDA failure."""
+    import torch
     for t in (row_ptr, zhat, Xhat, Y1):
         if not (_is_torch(t) and t.is_cuda and t.is_contiguous()):
             raise ValueError("gds_noalloc takes contiguous CUDA tensors")
+    if row_ptr.dtype != torch.int64:
+        raise ValueError("row_ptr must be int64")
+    for name, t in (("zhat", zhat), ("Xhat", Xhat), ("Y1", Y1)):
+        if t.dtype != torch.float64:
+            raise ValueError(f"{name} must be float64")
+    if int(ldz) < int(q):
+        raise ValueError("ldz must be >= q")
+    if row_ptr.numel() != int(n) + 1:
+        raise ValueError("row_ptr must hold n + 1 entries")
+    if int(q) > 0 and zhat.numel() < int(ldz) * int(r):
+        raise ValueError("zhat must hold ldz * r entries")
+    if Xhat.numel() < int(n) * int(r) or Y1.numel() < int(n) * int(r):
+        raise ValueError("Xhat and Y1 must hold n * r entries")
     handle = getattr(stream, "cuda_stream", stream) if stream is not None else None
     msg = ctypes.c_char_p()
     rc = lib().cphifi_gds_noalloc(int(n), int(r), int(q), row_ptr.data_ptr(), zhat.data_ptr(),

@@ -834,7 +834,7 @@ static cudaError_t zhat_and_rhs(cphifi_problem* P, const int32_t* perm, const in
 static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
                              const int64_t* other_sizes, const double* const* factors, int32_t r,
                              int64_t q, const int32_t* kidx, const int32_t* oidx,
-                             const double* vals, uint32_t flags, int mem, cudaStream_t st,
+                             const void* vals, uint32_t flags, int mem, cudaStream_t st,
                              bool async, cphifi_problem** out) {
   if (!ctx || !out) return CPHIFI_E_INVALID_ARG;
   *out = nullptr;
@@ -1034,21 +1034,31 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
   int32_t* oidx_d = nullptr;
   const double* vals_d = nullptr;
   const int32_t* kidx_d = nullptr;
+  const bool vals32 = (flags & CPHIFI_VALS_F32) != 0;
+  const size_t vbytes = (size_t)q * (vals32 ? sizeof(float) : sizeof(double));
   if (!sorted_in && !keys) return bail(CPHIFI_E_OOM, "temporary allocation failed");
+  const void* vsrc = vals;  // the values on the device, in the caller's type
   if (mem == CPHIFI_MEM_DEVICE) {
     oidx_d = (int32_t*)oidx;
-    vals_d = vals;
     kidx_d = kidx;
   } else {
     oidx_d = (int32_t*)tmp_alloc((size_t)q * d_other * sizeof(int32_t));
-    double* v = (double*)tmp_alloc((size_t)q * sizeof(double));
+    void* v = tmp_alloc(vbytes);
     int32_t* k = (int32_t*)tmp_alloc((size_t)q * sizeof(int32_t));
     if (!oidx_d || !v || !k) return bail(CPHIFI_E_OOM, "temporary allocation failed");
     PCK(upload(oidx_d, oidx, (size_t)q * d_other * sizeof(int32_t), mem, st));
-    PCK(upload(v, vals, (size_t)q * sizeof(double), mem, st));
+    PCK(upload(v, vals, vbytes, mem, st));
     PCK(upload(k, kidx, (size_t)q * sizeof(int32_t), mem, st));
-    vals_d = v;
+    vsrc = v;
     kidx_d = k;
+  }
+  if (vals32 && q > 0) {  // FP32 values are widened to FP64 once, on the device
+    double* v64 = (double*)tmp_alloc((size_t)q * sizeof(double));
+    if (!v64) return bail(CPHIFI_E_OOM, "temporary allocation failed");
+    PCK(launch_convert<float, double>((const float*)vsrc, v64, q, st));
+    vals_d = v64;
+  } else {
+    vals_d = (const double*)vsrc;
   }
   // kernel indices here (the sort and the pieces use them); the other
   // indices and the values are checked by the Zhat build below
@@ -1131,7 +1141,7 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
 extern "C" int cphifi_problem_create(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
                                      const int64_t* other_sizes, const double* const* factors,
                                      int32_t r, int64_t q, const int32_t* kidx,
-                                     const int32_t* oidx, const double* vals, uint32_t flags,
+                                     const int32_t* oidx, const void* vals, uint32_t flags,
                                      int mem, cphifi_problem** out) {
   if (!ctx) return CPHIFI_E_INVALID_ARG;
   return problem_create_on(ctx, kern, d_other, other_sizes, factors, r, q, kidx, oidx, vals,
@@ -1947,7 +1957,7 @@ extern "C" int cphifi_problem_solve(cphifi_problem* P, const cphifi_params* prm,
 extern "C" int cphifi_solve(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
                             const int64_t* other_sizes, const double* const* factors, int32_t r,
                             int64_t q, const int32_t* kidx, const int32_t* oidx,
-                            const double* vals, uint32_t flags, const cphifi_params* params,
+                            const void* vals, uint32_t flags, const cphifi_params* params,
                             const double* W0, double* W_out, int mem, cphifi_stats* stats) {
   if (!ctx) return CPHIFI_E_INVALID_ARG;
   int rc = check_params(ctx, params);
@@ -1968,6 +1978,13 @@ extern "C" int cphifi_solve(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t 
 }
 
 // ------------------------------------------------ submitted requests -----
+// Admission classes: a request whose device footprint exceeds
+// kLargeRequestBytes is large; large requests hold at most a quarter of the
+// slots (at least one).  A pending request older than kAdmitAgeMs is no
+// longer overtaken by newer ones.
+constexpr size_t kLargeRequestBytes = size_t(1) << 30;
+constexpr double kAdmitAgeMs = 50.0;
+
 struct Request {
   uint64_t id = 0;
   const cphifi_kernel* kern = nullptr;
@@ -1978,13 +1995,14 @@ struct Request {
   int64_t q = 0;
   const int32_t* kidx = nullptr;
   const int32_t* oidx = nullptr;
-  const double* vals = nullptr;
+  const void* vals = nullptr;
   uint32_t flags = 0;
   cphifi_params prm{};
   const double* W0 = nullptr;
   double* W_out = nullptr;
   int mem = 0;
   size_t need = 0;
+  bool large = false;  // footprint above kLargeRequestBytes (admission class)
   enum { PENDING, ACTIVE, DONE } state = PENDING;
   cphifi_problem* P = nullptr;
   std::unique_ptr<SolveRun> run;
@@ -2050,22 +2068,43 @@ bool progress(cphifi_ctx* ctx) {
       ++k;
     }
   }
-  while (!ctx->pending.empty() && (int)ctx->active.size() < ctx->max_active) {
-    Request* R = ctx->pending.front();
+  // Size-aware admission: pending requests are considered oldest first, and
+  // one that cannot start yet (its footprint does not fit the budget next to
+  // the running ones, or it is large and the slots large requests may hold
+  // are taken) is passed over by the smaller ones behind it, so that a large
+  // request waiting for memory does not hold up the small ones.  A request
+  // that has waited longer than kAdmitAgeMs is passed over by nobody: from it
+  // on, admission is in submission order until it starts.
+  const auto now = std::chrono::steady_clock::now();
+  int large_active = 0;
+  for (const Request* A : ctx->active) large_active += A->large ? 1 : 0;
+  const int max_large = std::max(1, ctx->max_active / 4);
+  size_t cand = 0;
+  while (cand < ctx->pending.size() && (int)ctx->active.size() < ctx->max_active) {
+    Request* R = ctx->pending[cand];
     deferred_collect(ctx, false);
+    const bool aged =
+        std::chrono::duration<double, std::milli>(now - R->t_submit).count() > kAdmitAgeMs;
     if (ctx->budget && ctx->in_use + ctx->deferred_bytes + R->need > ctx->budget) {
       if (ctx->active.empty() && !ctx->deferred.empty()) {
         deferred_collect(ctx, true);  // empties the list: runs once per request
         continue;
       }
       if (ctx->active.empty()) {  // cannot fit even alone
-        ctx->pending.pop_front();
+        ctx->pending.erase(ctx->pending.begin() + cand);
         R->error = "request footprint exceeds the HBM budget";
         request_finish(ctx, R, CPHIFI_E_ADMISSION);
         moved = true;
         continue;
       }
-      break;  // wait for memory to free up
+      if (aged) break;  // wait for memory to free up; nothing newer goes first
+      ++cand;
+      continue;
+    }
+    if (R->large && large_active >= max_large) {
+      if (aged) break;
+      ++cand;
+      continue;
     }
     int slot = -1;
     for (int k = 0; k < (int)ctx->slot_busy.size(); ++k)
@@ -2077,7 +2116,8 @@ bool progress(cphifi_ctx* ctx) {
       ctx->slot_busy.push_back(false);
       slot = (int)ctx->slot_stream.size() - 1;
     }
-    ctx->pending.pop_front();
+    ctx->pending.erase(ctx->pending.begin() + cand);
+    large_active += R->large ? 1 : 0;
     moved = true;
     R->t_admit = std::chrono::steady_clock::now();
     ctx->slot_busy[slot] = true;
@@ -2138,7 +2178,7 @@ extern "C" int cphifi_ctx_set_slots(cphifi_ctx* ctx, int max_active) {
 extern "C" int cphifi_submit(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
                              const int64_t* other_sizes, const double* const* factors, int32_t r,
                              int64_t q, const int32_t* kidx, const int32_t* oidx,
-                             const double* vals, uint32_t flags, const cphifi_params* params,
+                             const void* vals, uint32_t flags, const cphifi_params* params,
                              const double* W0, double* W_out, int mem, cphifi_ticket* ticket) {
   if (!ctx || !ticket) return CPHIFI_E_INVALID_ARG;
   *ticket = 0;
@@ -2178,6 +2218,7 @@ extern "C" int cphifi_submit(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
     size_t need = 0, tmp = 0;
     problem_need(ctx, kern->n, kern->tc, d_other, R->sizes, r, q, R->flags, &need, &tmp);
     R->need = need + tmp;
+    R->large = R->need > kLargeRequestBytes;
   }
   if (cudaEventCreateWithFlags(&R->ev_submit, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventRecord(R->ev_submit, ctx->stream) != cudaSuccess) {
@@ -2378,7 +2419,7 @@ extern "C" int cphifi_problem_fit(cphifi_problem* P, const double* W, int mem, d
 
 extern "C" int cphifi_als(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
                           const int64_t* other_sizes, double* const* factors_io, int32_t r,
-                          int64_t q, const int32_t* kidx, const int32_t* oidx, const double* vals,
+                          int64_t q, const int32_t* kidx, const int32_t* oidx, const void* vals,
                           uint32_t flags, const cphifi_params* params, int32_t sweeps,
                           double als_tol, int32_t warm, double* W_io, double* err_out,
                           int32_t* sweeps_done, int mem, cphifi_stats* stats) {

@@ -3,15 +3,14 @@
 // same computation as cphifi_problem_gds in FP64, for callers that must not
 // allocate device memory.
 //
-// Who needs this: code that runs where cudaMalloc is not an option, e.g.
-// inside a CUDA-graph capture that must not contain allocation nodes, a host
-// thread driving a real-time loop that may not hit the allocator's locks or
-// its implicit device synchronisation, or an embedding runtime that owns all
-// device memory itself and forbids libraries from taking more.  Such a caller
-// passes its own inputs and outputs; the working memory this computation
-// needs (the piece list, the per-piece partial rows, the per-index tickets)
-// comes from one fixed array compiled into this library instead of from the
-// allocator.
+// Who needs this: code that runs where cudaMalloc is not an option, e.g. a
+// host thread driving a real-time loop that may not take the allocator's
+// locks or wait for its implicit device synchronisation, or an embedding
+// runtime that owns all device memory itself and forbids libraries from
+// taking more.  Such a caller passes its own inputs and outputs; the working
+// memory this computation needs (the piece list, the per-piece partial rows,
+// the per-index tickets, an error word) comes from one fixed array compiled
+// into this library instead of from the allocator.
 //
 // The array is `g_noalloc_scratch` below: kNoallocScratchBytes bytes of
 // device memory in every GPU that loads the library, held until the process
@@ -37,7 +36,8 @@ constexpr int64_t kNoallocMaxPieces = (int64_t)kNoallocMaxN + kNoallocMaxWarps +
 
 // Byte offsets of the pieces of the scratch array (each 256-byte aligned).
 constexpr size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
-constexpr size_t kOffCount = 0;
+constexpr size_t kOffErr = 0;  // error word: nonzero = row_ptr is not a CSR of q
+constexpr size_t kOffCount = kOffErr + 256;
 constexpr size_t kOffFirst = kOffCount + al(sizeof(int32_t) * kNoallocMaxN);
 constexpr size_t kOffTicket = kOffFirst + al(sizeof(int32_t) * (kNoallocMaxN + 1));
 constexpr size_t kOffSeg = kOffTicket + al(sizeof(unsigned) * kNoallocMaxN);
@@ -54,15 +54,33 @@ constexpr size_t kNoallocScratchBytes =
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
+// The caller's row_ptr must be a CSR of q observations: row_ptr[0] = 0,
+// non-decreasing, row_ptr[n] = q.  Anything else sets *err, and every later
+// kernel of the call then returns without touching memory (a bad row_ptr
+// would otherwise index past the piece arrays and past Zhat); the last kernel
+// fills Y1 with NaN so that the caller sees the failure.
+__global__ void noalloc_check_csr_kernel(const int64_t* __restrict__ row_ptr, int n, int64_t q,
+                                         int* err) {
+  int bad = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) {
+    const int64_t v = row_ptr[i];
+    if (i == 0 && v != 0) bad = 1;
+    if (i == n && v != q) bad = 1;
+    if (i < n && row_ptr[i + 1] < v) bad = 1;
+  }
+  if (bad) atomicOr(err, 1);
+}
+
 // warp_first for the no-allocation path: like launch_warp_first, but the
-// number of pieces is read on the device (seg_first[n]) so the host never
-// waits for it.
+// number of pieces is read on the device (seg_first[n], clamped to the
+// scratch array's piece capacity) so the host never waits for it.
 __global__ void noalloc_warp_first_kernel(const int32_t* __restrict__ pbeg,
                                           const int32_t* __restrict__ seg_first, int n,
-                                          int64_t L, int W, int32_t* warp_first) {
+                                          int64_t L, int W, int32_t* warp_first,
+                                          const int* gate) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w > W) return;
-  const int npieces = seg_first[n];
+  if (w > W || *gate) return;
+  const int npieces = (int)min((int64_t)seg_first[n], kNoallocMaxPieces);
   if (w == W) { warp_first[W] = npieces; return; }
   const int64_t v = (int64_t)w * L;
   int lo = 0, hi = npieces;
@@ -73,14 +91,23 @@ __global__ void noalloc_warp_first_kernel(const int32_t* __restrict__ pbeg,
   warp_first[w] = lo;
 }
 
+// Y1 = NaN when the CSR check failed.
+__global__ void noalloc_flag_output_kernel(const int* gate, int64_t count, double* Y) {
+  if (!*gate) return;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
+       t += (int64_t)gridDim.x * blockDim.x)
+    Y[t] = __longlong_as_double(0x7ff8000000000000LL);
+}
+
 // The gather-dot/scatter of gds_kernel (Eqs. vl and yhat1), FP64, reading Zhat
 // in the caller's plain column-major layout (Zhat(l, j) at j*ldz + l).
 template <int RP>
 __global__ void __launch_bounds__(256)
 noalloc_gds_kernel(PieceList pl, const double* __restrict__ Z, int64_t ldz, int r,
                    const double* __restrict__ Xh, int64_t ldx, double* __restrict__ partial,
-                   double* __restrict__ Y, int64_t ldy) {
+                   double* __restrict__ Y, int64_t ldy, const int* gate) {
   __shared__ double xs[8][RP];
+  if (*gate) return;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -141,27 +168,36 @@ noalloc_gds_kernel(PieceList pl, const double* __restrict__ Z, int64_t ldz, int 
 namespace {
 
 struct DeviceSlot {
-  std::once_flag once;
-  cudaError_t err = cudaSuccess;
+  bool ready = false;
   unsigned char* base = nullptr;
   int num_sms = 0;
 };
 constexpr int kMaxDevices = 64;
 DeviceSlot g_slots[kMaxDevices];
+std::mutex g_slots_mu;
 
-// Once per device, with that device current: the device address of the
-// scratch array (the host-side name g_noalloc_scratch is only a stand-in) and
-// the SM count.
-DeviceSlot* device_slot(int dev) {
+// The device address of the scratch array (the host-side name
+// g_noalloc_scratch is only a stand-in for it) and the SM count, looked up
+// with the device current on its first successful call and kept from then
+// on.  A failed lookup is not cached: the next call tries again.
+cudaError_t device_slot(int dev, DeviceSlot* out) {
+  std::lock_guard<std::mutex> lock(g_slots_mu);
   DeviceSlot* s = &g_slots[dev];
-  std::call_once(s->once, [s, dev]() {
+  if (!s->ready) {
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    s->err = e;
+    int sms = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+    }
     s->base = (unsigned char*)ptr;
-  });
-  return s;
+    s->num_sms = sms;
+    s->ready = true;
+  }
+  *out = *s;
+  return cudaSuccess;
 }
 
 int reject(const char** msg, const char* text) {
@@ -192,13 +228,14 @@ extern "C" int cphifi_gds_noalloc(int32_t n, int32_t r, int64_t q, const int64_t
     if (err_msg) *err_msg = "cphifi_gds_noalloc: no usable current CUDA device";
     return CPHIFI_E_DEVICE;
   }
-  DeviceSlot* slot = device_slot(dev);
-  if (slot->err != cudaSuccess || !slot->base) {
+  DeviceSlot slot;
+  if (device_slot(dev, &slot) != cudaSuccess) {
     if (err_msg) *err_msg = "cphifi_gds_noalloc: cudaGetSymbolAddress of the scratch array failed";
     return CPHIFI_E_DEVICE;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  unsigned char* base = slot->base;
+  unsigned char* base = slot.base;
+  int* gate = (int*)(base + kOffErr);
   int32_t* seg_count = (int32_t*)(base + kOffCount);
   int32_t* seg_first = (int32_t*)(base + kOffFirst);
   unsigned* seg_ticket = (unsigned*)(base + kOffTicket);
@@ -210,23 +247,29 @@ extern "C" int cphifi_gds_noalloc(int32_t n, int32_t r, int64_t q, const int64_t
   double* partial = (double*)(base + kOffPartial);
 
   int64_t W64 = (q + 63) / 64;
-  const int64_t wcap = std::min<int64_t>((int64_t)slot->num_sms * 16, kNoallocMaxWarps);
+  const int64_t wcap = std::min<int64_t>((int64_t)slot.num_sms * 16, kNoallocMaxWarps);
   if (W64 > wcap) W64 = wcap;
   if (W64 < 1) W64 = 1;
   const int W = (int)W64;
   const int64_t L = std::max<int64_t>(1, (q + W - 1) / W);
 
   cudaError_t e = cudaSuccess;
-  // The tickets must start at zero; the last piece of an index resets its own,
-  // but a call that was cut short could leave stale counts behind.
+  // The error word and the tickets must start at zero: the array keeps what
+  // the last call left (the last piece of an index resets its own ticket, but
+  // a call cut short by a failed check leaves stale counts behind).
+  e = cudaMemsetAsync(base, 0, kOffCount, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(seg_ticket, 0, sizeof(unsigned) * n, st);
-  if (e == cudaSuccess) e = launch_piece_counts(row_ptr, n, L, seg_count, nullptr, st);
+  if (e == cudaSuccess) {
+    noalloc_check_csr_kernel<<<(n + 1 + 255) / 256, 256, 0, st>>>(row_ptr, n, q, gate);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = launch_piece_counts(row_ptr, n, L, seg_count, gate, st);
   if (e == cudaSuccess) e = exclusive_scan_i32(seg_count, seg_first, n, scan_tmp, kScanBytes, st);
   if (e == cudaSuccess)
-    e = launch_piece_fill(row_ptr, n, L, seg_first, seg_count, pseg, pbeg, pend, nullptr, st);
+    e = launch_piece_fill(row_ptr, n, L, seg_first, seg_count, pseg, pbeg, pend, gate, st);
   if (e == cudaSuccess) {
     noalloc_warp_first_kernel<<<(W + 1 + 255) / 256, 256, 0, st>>>(pbeg, seg_first, n, L, W,
-                                                                  warp_first);
+                                                                  warp_first, gate);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
@@ -234,13 +277,23 @@ extern "C" int cphifi_gds_noalloc(int32_t n, int32_t r, int64_t q, const int64_t
                  (int)kNoallocMaxPieces, W};
     const int blocks = (W + 7) / 8;
     if (r <= 8)
-      noalloc_gds_kernel<8><<<blocks, 256, 0, st>>>(pl, zhat, ldz, r, Xhat, n, partial, Y1, n);
+      noalloc_gds_kernel<8><<<blocks, 256, 0, st>>>(pl, zhat, ldz, r, Xhat, n, partial, Y1, n,
+                                                    gate);
     else if (r <= 16)
-      noalloc_gds_kernel<16><<<blocks, 256, 0, st>>>(pl, zhat, ldz, r, Xhat, n, partial, Y1, n);
+      noalloc_gds_kernel<16><<<blocks, 256, 0, st>>>(pl, zhat, ldz, r, Xhat, n, partial, Y1, n,
+                                                     gate);
     else if (r <= 32)
-      noalloc_gds_kernel<32><<<blocks, 256, 0, st>>>(pl, zhat, ldz, r, Xhat, n, partial, Y1, n);
+      noalloc_gds_kernel<32><<<blocks, 256, 0, st>>>(pl, zhat, ldz, r, Xhat, n, partial, Y1, n,
+                                                     gate);
     else
-      noalloc_gds_kernel<64><<<blocks, 256, 0, st>>>(pl, zhat, ldz, r, Xhat, n, partial, Y1, n);
+      noalloc_gds_kernel<64><<<blocks, 256, 0, st>>>(pl, zhat, ldz, r, Xhat, n, partial, Y1, n,
+                                                     gate);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    const int64_t count = (int64_t)n * r;
+    const int blocks = (int)std::min<int64_t>((count + 255) / 256, 1024);
+    noalloc_flag_output_kernel<<<blocks, 256, 0, st>>>(gate, count, Y1);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {
