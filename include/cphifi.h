@@ -117,7 +117,18 @@ typedef struct cphifi_params {
   int32_t k_replace;  /* mixed: FP64 true-residual check every k (>= 1)      */
   int32_t check_every;/* FP64: iterations between host convergence polls (>=1)*/
   int32_t profile;    /* 1: time every n x n product and gather-dot/scatter  */
-  int32_t reserved;
+  int32_t gram;       /* how the product forms Yhat1 (Eq. yhat1), 0, 1 or 2:
+                         0: every product streams Zhat (Eqs. vl, yhat1);
+                         1: the PCG iterations apply the per-index Gram
+                            blocks C_i = sum_{i_l = i} Zhat(l,:)'Zhat(l,:)
+                            instead (Yhat1(i,:) = C_i Xhat(i,:)', n r^2 values
+                            read per product instead of q r), built once per
+                            problem on first use -- FP32 for the mixed modes,
+                            FP64-accurate otherwise -- and kept until the
+                            factors change; the FP64-accurate checks of the
+                            mixed modes still stream Zhat;
+                         2: as 1, and the FP64-accurate checks (true
+                            residuals) also apply FP64-accurate blocks.      */
 } cphifi_params;
 
 typedef struct cphifi_stats {
@@ -176,9 +187,11 @@ const char* cphifi_status_string(int status);
  * UK, DK : K = UK diag(DK) UK' with UK orthogonal (n x n, column-major,
  *          column j = eigenvector j) and DK the n eigenvalues.  Pass both, or
  *          neither: then the library computes them from K on the device
- *          (FP64 symmetric divide-and-conquer, cuSOLVER dsyevd; the lower
- *          triangle of K is read; n <= 46340).  Tiny negative eigenvalues are
- *          clamped to 0 inside the preconditioner only.
+ *          (FP64 cyclic two-sided Jacobi with a parallel ordering, this
+ *          library's own kernels; the lower triangle of K is read;
+ *          n <= 4096, larger n gives CPHIFI_E_UNSUPPORTED: pass UK and DK).
+ *          Tiny negative eigenvalues are clamped to 0 inside the
+ *          preconditioner only.
  * The library keeps FP64 and FP32 copies of UK on the device and, where the
  * tensor cores are available and the context's HBM budget has room, the
  * TF32/BF16 operand copies of the tensor-core modes and 7 BF16 slices of UK
@@ -189,6 +202,11 @@ int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
 /* Fails with CPHIFI_E_INVALID_ARG while a submitted request that uses the
  * kernel has not completed. */
 int cphifi_kernel_destroy(cphifi_kernel* kern);
+/* The eigendecomposition the kernel handle holds (Eq. eigK): UK (n x n,
+ * column-major, column j = eigenvector j) and DK (n eigenvalues; ascending
+ * when the library computed them), FP64, copied to memory kind `mem`.
+ * Either output may be NULL. */
+int cphifi_kernel_eig(const cphifi_kernel* kern, double* UK, double* DK, int mem);
 
 /* ---- one subproblem (§4: everything that depends on the observations) ---
  * d_other     : number of other (finite) modes, >= 1.
@@ -304,9 +322,20 @@ int cphifi_problem_matvec(cphifi_problem* prob, int precision, double lambda,
                           double rho, const double* X, double* Y, int mem);
 /* Y1 = Yhat1 of Eqs. vl and yhat1 for a given Xhat (n x r):
  * xbar_l = Xhat(i_l,:).Zhat(l,:), Yhat1(i,:) = sum_{i_l = i} xbar_l Zhat(l,:),
- * in FP64 or (precision != FP64) FP32 arithmetic. */
+ * in FP64, double-float (FP64_EMULATED) or (mixed modes) FP32 arithmetic.
+ * With precision | CPHIFI_GRAM_FORM (here and in cphifi_problem_matvec) the
+ * product applies the per-index Gram blocks instead (see cphifi_params.gram):
+ * FP32 blocks for the mixed modes, FP64-accurate ones otherwise. */
+#define CPHIFI_GRAM_FORM 0x100
 int cphifi_problem_gds(cphifi_problem* prob, int precision, const double* Xhat,
                        double* Y1, int mem);
+/* The per-index Gram blocks C_i = sum over l with i_l = i of
+ * Zhat(l,:)'Zhat(l,:) (the r x r diagonal blocks of H in
+ * F'F = (I (x) K) H (I (x) K), §4.4.1), as the solver holds them: FP32 (mixed
+ * modes, returned widened to FP64) or FP64-accurate (FP64, FP64_EMULATED).
+ * C: n r^2 doubles, C[(i r + j) r + k] = C_i(j, k), in memory kind mem.
+ * Builds the blocks if the problem has none yet. */
+int cphifi_problem_grams(cphifi_problem* prob, int precision, double* C, int mem);
 /* Y = M^{-1} X for the preconditioner of Eq. precon, applied as Eq. fx. */
 int cphifi_problem_precond(cphifi_problem* prob, double lambda, double rho,
                            const double* X, double* Y, int mem);

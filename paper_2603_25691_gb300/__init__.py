@@ -56,7 +56,7 @@ class Params(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("rho", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("k_replace", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("gram", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -95,6 +95,7 @@ _SIG = {
     "cphifi_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cphifi_kernel_create": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, ctypes.c_int, _PP]),
     "cphifi_kernel_destroy": (ctypes.c_int, [_P]),
+    "cphifi_kernel_eig": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "cphifi_problem_create": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32,
                                              ctypes.c_int64, _P, _P, _P, ctypes.c_uint32,
                                              ctypes.c_int, _PP]),
@@ -113,6 +114,7 @@ _SIG = {
     "cphifi_problem_precond": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, _P,
                                               ctypes.c_int]),
     "cphifi_problem_gram": (ctypes.c_int, [_P, _P, _P, _P]),
+    "cphifi_problem_grams": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
     "cphifi_problem_order": (ctypes.c_int, [_P, _P, _P]),
     "cphifi_ctx_set_slots": (ctypes.c_int, [_P, ctypes.c_int]),
     "cphifi_problem_set_factors": (ctypes.c_int, [_P, _P, ctypes.c_int]),
@@ -293,6 +295,14 @@ class Kernel:
         self.h = h
         ctx._children.add(self)
 
+    def eig(self):
+        """cphifi_kernel_eig: (D_K, U_K) held by the handle, as host arrays."""
+        U = np.empty((self.n, self.n), order="F")
+        d = np.empty(self.n)
+        _check(self.ctx.h, lib().cphifi_kernel_eig(self.h, U.ctypes.data, d.ctypes.data,
+                                                   MEM_HOST), "kernel_eig")
+        return d, U
+
     def close(self):
         """cphifi_kernel_destroy (raises while submitted requests still use it)."""
         if getattr(self, "h", None) and not getattr(self.ctx, "h", None):
@@ -389,9 +399,11 @@ class Problem:
 
     def solve(self, lam: float, rho: float, tol: float, max_iter: int = 1000,
               precision: str | int = "fp64", k_replace: int = 10, check_every: int = 8,
-              profile: bool = False, W0=None, out=None, raise_on_error: bool = True):
+              profile: bool = False, W0=None, out=None, raise_on_error: bool = True,
+              gram: int = 0):
         """cphifi_problem_solve.  Returns (W, stats dict)."""
-        prm = make_params(lam, rho, tol, max_iter, precision, k_replace, check_every, profile)
+        prm = make_params(lam, rho, tol, max_iter, precision, k_replace, check_every, profile,
+                          gram)
         st = Stats()
         W = out if out is not None else self._out(False)
         wb = _Buf(W, np.float64, colmajor=True) if not _is_torch(W) else _Buf(W, np.float64)
@@ -433,6 +445,13 @@ class Problem:
         _check(self.ctx.h, lib().cphifi_problem_precond(self.h, lam, rho, x.ptr, Y.ctypes.data,
                                                         MEM_HOST), "problem_precond")
         return Y
+
+    def grams(self, precision: str | int = "fp64"):
+        """cphifi_problem_grams: the per-index Gram blocks, an (n, r, r) array."""
+        C = np.empty((self.n, self.r, self.r))
+        _check(self.ctx.h, lib().cphifi_problem_grams(self.h, _prec(precision), C.ctypes.data,
+                                                      MEM_HOST), "problem_grams")
+        return C
 
     def gram(self):
         """cphifi_problem_gram: (V, DV, UV) computed on the device."""
@@ -478,23 +497,31 @@ class Problem:
         return perm, rp
 
 
+GRAM_FORM = 0x100
+
+
 def _prec(p) -> int:
-    return PRECISIONS[p] if isinstance(p, str) else int(p)
+    """Precision name or code; a '+gram' suffix adds CPHIFI_GRAM_FORM (step
+    calls: the product from the per-index Gram blocks)."""
+    if isinstance(p, str):
+        base, _, form = p.partition("+")
+        return PRECISIONS[base] | (GRAM_FORM if form == "gram" else 0)
+    return int(p)
 
 
 def make_params(lam, rho, tol, max_iter=1000, precision="fp64", k_replace=10, check_every=8,
-                profile=False) -> Params:
+                profile=False, gram=0) -> Params:
     return Params(float(lam), float(rho), float(tol), int(max_iter), _prec(precision),
-                  int(k_replace), int(check_every), 1 if profile else 0, 0)
+                  int(k_replace), int(check_every), 1 if profile else 0, int(gram))
 
 
 def solve(ctx: Context, kernel: Kernel, factors, kidx, oidx, vals, r: int, lam: float, rho: float,
           tol: float, max_iter: int = 1000, precision="fp64", sorted_obs=False, k_replace=10,
-          check_every=8, profile=False, W0=None, out=None):
+          check_every=8, profile=False, W0=None, out=None, gram=0):
     """cphifi_solve: one-shot create + solve + destroy.  Returns (W, stats)."""
     fb, sizes = _factor_bufs(factors, r)
     k, o, v = _obs_bufs(kidx, oidx, vals)
-    prm = make_params(lam, rho, tol, max_iter, precision, k_replace, check_every, profile)
+    prm = make_params(lam, rho, tol, max_iter, precision, k_replace, check_every, profile, gram)
     st = Stats()
     n = kernel.n
     if out is None:
@@ -569,11 +596,11 @@ class Request:
 
 def submit(ctx: Context, kernel: Kernel, factors, kidx, oidx, vals, r: int, lam: float,
            rho: float, tol: float, max_iter: int = 1000, precision="fp64", sorted_obs=False,
-           k_replace=10, check_every=8, W0=None, out=None) -> Request:
+           k_replace=10, check_every=8, W0=None, out=None, gram=0) -> Request:
     """cphifi_submit: queue one solve; returns a Request whose wait() gives (W, stats)."""
     fb, sizes = _factor_bufs(factors, r)
     k, o, v = _obs_bufs(kidx, oidx, vals)
-    prm = make_params(lam, rho, tol, max_iter, precision, k_replace, check_every, False)
+    prm = make_params(lam, rho, tol, max_iter, precision, k_replace, check_every, False, gram)
     n = kernel.n
     if out is None:
         out = np.empty((n, r), order="F") if k.mem == MEM_HOST else None

@@ -64,7 +64,7 @@ def build(verbose: bool = False, extra=(), force: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
-        run([cc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart", "-lcusolver"])
+        run([cc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"])
     return LIB
 
 

@@ -13,7 +13,6 @@
 // rounded U_K stays symmetric positive definite because U_K appears on both
 // sides.  W = U_K Wbar at the end.
 #include <cuda_runtime.h>
-#include <cusolverDn.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -38,7 +37,6 @@ static void requests_clear(cphifi_ctx* ctx);
 
 struct cphifi_ctx {
   int device = 0;
-  cusolverDnHandle_t solver = nullptr;  // device eig(K), created on first use
   int num_sms = 1;
   cudaStream_t stream = nullptr;
   cudaStream_t user_stream = nullptr;
@@ -186,6 +184,18 @@ struct cphifi_problem {
   double* fit2 = nullptr;  // 2 doubles
   int* nfail = nullptr;
   bool stale = false;
+  // Per-index Gram blocks C_i (gram.cu), n x r x r each, built on first use
+  // and kept until the factors change: FP32 (the mixed operator) and
+  // FP64-accurate (the FP64 operators and checks); the piece decomposition of
+  // their build (L_g observations per piece) and its partial blocks.
+  float* C32 = nullptr;
+  double* C64 = nullptr;
+  bool c32_ok = false, c64_ok = false;
+  int32_t *gseg = nullptr, *gbeg = nullptr, *gend = nullptr, *gfirst = nullptr,
+          *gcount = nullptr;
+  unsigned* gticket = nullptr;
+  double* gpart = nullptr;
+  int gnp = 0;
 };
 
 // ------------------------------------------------------------ helpers -----
@@ -487,7 +497,6 @@ extern "C" int cphifi_ctx_destroy(cphifi_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   requests_clear(ctx);
   deferred_collect(ctx, true);
-  if (ctx->solver) cusolverDnDestroy(ctx->solver);
   pool_trim(ctx);
   for (auto e : ctx->phase)
     if (e) cudaEventDestroy(e);
@@ -522,56 +531,6 @@ extern "C" const char* cphifi_last_error(const cphifi_ctx* ctx) {
 }
 
 // ------------------------------------------------------------ kernel ------
-// Symmetric eigendecomposition A = U diag(w) U' in FP64 on the device (the
-// one-time eig(K) of Eq. eigK): cuSOLVER's divide-and-conquer dsyevd on the
-// context's stream, A (n x n column-major, lower triangle read) overwritten
-// by U, eigenvalues ascending into w.  Synchronous.
-static int sym_eig_device(cphifi_ctx* ctx, int n, double* A, double* w, cudaStream_t st,
-                          std::string* why) {
-  if (!ctx->solver) {
-    if (cusolverDnCreate(&ctx->solver) != CUSOLVER_STATUS_SUCCESS) {
-      ctx->solver = nullptr;
-      *why = "cusolverDnCreate failed";
-      return CPHIFI_E_DEVICE;
-    }
-  }
-  if (cusolverDnSetStream(ctx->solver, st) != CUSOLVER_STATUS_SUCCESS) {
-    *why = "cusolverDnSetStream failed";
-    return CPHIFI_E_DEVICE;
-  }
-  int lwork = 0;
-  if (cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
-                                  A, n, w, &lwork) != CUSOLVER_STATUS_SUCCESS) {
-    *why = "cusolverDnDsyevd_bufferSize failed";
-    return CPHIFI_E_DEVICE;
-  }
-  double* work = nullptr;
-  int* info = nullptr;
-  if (cudaMalloc(&work, (size_t)std::max(lwork, 1) * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&info, sizeof(int)) != cudaSuccess) {
-    if (work) cudaFree(work);
-    *why = "workspace allocation for the eigensolver failed";
-    return CPHIFI_E_OOM;
-  }
-  int hinfo = 0;
-  const cusolverStatus_t cs = cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR,
-                                               CUBLAS_FILL_MODE_LOWER, n, A, n, w, work, lwork,
-                                               info);
-  const cudaError_t e1 = cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st);
-  const cudaError_t e2 = cudaStreamSynchronize(st);
-  cudaFree(work);
-  cudaFree(info);
-  if (cs != CUSOLVER_STATUS_SUCCESS || e1 != cudaSuccess || e2 != cudaSuccess) {
-    *why = "cusolverDnDsyevd failed";
-    return CPHIFI_E_DEVICE;
-  }
-  if (hinfo != 0) {
-    *why = "the eigensolver did not converge (info " + std::to_string(hinfo) + ")";
-    return CPHIFI_E_INVALID_ARG;
-  }
-  return CPHIFI_OK;
-}
-
 extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
                                     const double* UK, const double* DK, int mem,
                                     cphifi_kernel** out) {
@@ -583,8 +542,10 @@ extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
     return fail(ctx, CPHIFI_E_INVALID_ARG, "either K or its eigendecomposition (UK, DK) is needed");
   if (!device_eig && (!UK || !DK))
     return fail(ctx, CPHIFI_E_INVALID_ARG, "UK and DK are passed together");
-  if (device_eig && n > 46340)
-    return fail(ctx, CPHIFI_E_UNSUPPORTED, "n too large for the device eigensolver");
+  if (device_eig && n > kSymEigMaxN)
+    return fail(ctx, CPHIFI_E_UNSUPPORTED,
+                "n too large for the device eigensolver (n <= " + std::to_string(kSymEigMaxN) +
+                    "): pass UK and DK");
   if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
   const size_t nn = (size_t)n * n;
@@ -626,7 +587,7 @@ extern "C" int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
       return cleanup(CPHIFI_E_DEVICE, "uploading K failed");
     if (herr) return cleanup(CPHIFI_E_INVALID_ARG, "non-finite entry in K");
     std::string why;
-    const int rc = sym_eig_device(ctx, (int)n, kern->UK64, kern->dK, st, &why);
+    const int rc = sym_eig_jacobi(kern->UK64, (int)n, kern->dK, st, &why);
     if (rc != CPHIFI_OK) return cleanup(rc, why);
   }
   if ((!device_eig && (upload(kern->UK64, UK, nn * sizeof(double), mem, st) != cudaSuccess ||
@@ -733,6 +694,19 @@ extern "C" int cphifi_kernel_destroy(cphifi_kernel* kern) {
   ctx->in_use -= std::min(ctx->in_use, kern->bytes);
   cudaSetDevice(prev);
   delete kern;
+  return CPHIFI_OK;
+}
+
+extern "C" int cphifi_kernel_eig(const cphifi_kernel* kern, double* UK, double* DK, int mem) {
+  if (!kern) return CPHIFI_E_INVALID_ARG;
+  cphifi_ctx* ctx = kern->ctx;
+  if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
+  Enter guard(ctx);
+  const size_t n = (size_t)kern->n;
+  if (UK) CK(download(UK, kern->UK64, n * n * sizeof(double), mem, ctx->stream));
+  if (DK) CK(download(DK, kern->dK, n * sizeof(double), mem, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   return CPHIFI_OK;
 }
 
@@ -1179,6 +1153,10 @@ struct Launcher {
   cudaStream_t st;
   Timer* tm;
   int64_t launches = 0;
+  // 0: every product streams Zhat; 1: the iteration operator (CM_APPLY)
+  // applies the per-index Gram blocks instead; 2: the checks as well.
+  int gram = 0;
+  bool gram_for(int mode) const { return gram == 2 || (gram == 1 && mode == CM_APPLY); }
 
   PieceList pieces() const {
     return PieceList{P->pseg, P->pbeg, P->pend, P->seg_first, P->seg_count, P->seg_ticket,
@@ -1299,6 +1277,25 @@ struct Launcher {
     return e;
   }
 
+  // Yhat1 from the per-index Gram blocks (Eq. yhat1 with the sum over the
+  // observations done once): FP32 blocks, or the FP64-accurate ones.
+  cudaError_t gram32(const float* Xh, float* Y, const DevScalars* skip, int cat,
+                     int64_t yld = 0) {
+    cudaEvent_t b = (cat && tm) ? tm->begin() : nullptr;
+    cudaError_t e = launch_gram_apply_f32(P->C32, P->n, P->r, Xh, P->n, Y, yld ? yld : P->n,
+                                          skip, st);
+    if (cat && tm) tm->end(b, cat == 1 ? tm->gds : tm->gds64);
+    ++launches;
+    return e;
+  }
+  cudaError_t gram64(const double* Xh, double* Y, const DevScalars* skip, int cat) {
+    cudaEvent_t b = (cat && tm) ? tm->begin() : nullptr;
+    cudaError_t e = launch_gram_apply_f64(P->C64, P->n, P->r, Xh, P->n, Y, P->n, skip, st);
+    if (cat && tm) tm->end(b, cat == 1 ? tm->gds : tm->gds64);
+    ++launches;
+    return e;
+  }
+
   // FP64 operator in the eigenbasis: out = Abar xin (mode CM_APPLY) or the
   // true residual res = bbar - Abar xin (mode CM_RESID).
   cudaError_t op64(int mode, const double* xin, double* out, DevScalars* s,
@@ -1307,7 +1304,9 @@ struct Launcher {
     cudaError_t e;
     if ((e = gemm64(true, P->kern->dK, xin, Cp, skip, cat)) != cudaSuccess) return e;
     if ((e = combine<double, double>(CM_STORE, Cp, nullptr, nullptr, P->xh64, s, skip)) != cudaSuccess) return e;
-    if ((e = gds64(P->xh64, P->y164, skip, cat)) != cudaSuccess) return e;
+    if ((e = (gram_for(mode) && P->c64_ok) ? gram64(P->xh64, P->y164, skip, cat)
+                                           : gds64(P->xh64, P->y164, skip, cat)) != cudaSuccess)
+      return e;
     if ((e = gemm64(false, nullptr, P->y164, Cp, skip, cat)) != cudaSuccess) return e;
     return combine<double, double>(mode, Cp, xin, P->bbar, out, s, skip);
   }
@@ -1320,7 +1319,9 @@ struct Launcher {
     cudaError_t e;
     if ((e = gemm_df(true, P->kern->dK, xin, Cp, skip, cat)) != cudaSuccess) return e;
     if ((e = combine<double, double>(CM_STORE, Cp, nullptr, nullptr, P->xh64, s, skip, ns)) != cudaSuccess) return e;
-    if ((e = gdsdf(P->xh64, P->y164, skip, cat)) != cudaSuccess) return e;
+    if ((e = (gram_for(mode) && P->c64_ok) ? gram64(P->xh64, P->y164, skip, cat)
+                                           : gdsdf(P->xh64, P->y164, skip, cat)) != cudaSuccess)
+      return e;
     if ((e = gemm_df(false, nullptr, P->y164, Cp, skip, cat)) != cudaSuccess) return e;
     return combine<double, double>(mode, Cp, xin, P->bbar, out, s, skip, ns);
   }
@@ -1346,7 +1347,9 @@ struct Launcher {
     // Yhat1 with leading dimension ldt (the product operand), dense for the
     // BF16 conversion that feeds the BF16 product
     const int64_t yld = bf ? P->n : P->ldt;
-    if ((e = gds32(P->xh32, P->y132, skip, 1, yld)) != cudaSuccess) return e;
+    if ((e = (gram >= 1 && P->c32_ok) ? gram32(P->xh32, P->y132, skip, 1, yld)
+                                      : gds32(P->xh32, P->y132, skip, 1, yld)) != cudaSuccess)
+      return e;
     if (bf) {
       ++launches;
       if ((e = launch_scale_to<float, __nv_bfloat16>(P->y132, nullptr, P->n, (int64_t)P->n * P->r,
@@ -1470,6 +1473,7 @@ int check_params(cphifi_ctx* ctx, const cphifi_params* prm) {
   if (prm->max_iter < 0) return fail(ctx, CPHIFI_E_INVALID_ARG, "max_iter must be >= 0");
   if (prm->precision < CPHIFI_FP64 || prm->precision > CPHIFI_MIXED_TF32X3)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
+  if (prm->gram < 0 || prm->gram > 2) return fail(ctx, CPHIFI_E_INVALID_ARG, "gram must be 0, 1 or 2");
   return CPHIFI_OK;
 }
 
@@ -1496,6 +1500,66 @@ int ensure_fp64(cphifi_problem* P) {
     return fail(ctx, CPHIFI_E_ADMISSION, "FP64 operator data exceeds the HBM budget");
   CK(dalloc(P, &P->z64, elems));
   CK(launch_zhat_join(P->zhi, P->q, P->r, P->z64, P->st));
+  return CPHIFI_OK;
+}
+
+// The per-index Gram blocks (FP32 and/or FP64-accurate) on the problem's
+// stream, built once and kept.  The FP32 blocks come from Zhat's hi parts;
+// the FP64-accurate ones from the hi/lo pair, or from the FP64 copy when the
+// problem has only that.
+int ensure_grams(cphifi_problem* P, bool want32, bool want64) {
+  cphifi_ctx* ctx = P->ctx;
+  if ((!want32 || P->c32_ok) && (!want64 || P->c64_ok)) return CPHIFI_OK;
+  if (want32 || !P->z64) {
+    const int rc = ensure_lowp(P);
+    if (rc != CPHIFI_OK) return rc;
+  }
+  const int n = P->n, r = P->r;
+  const int64_t q = P->q;
+  const size_t rr = (size_t)r * r;
+  cudaStream_t st = P->st;
+  const int64_t Lg = std::max<int64_t>(1024, (q + 8 * ctx->num_sms - 1) / (8 * ctx->num_sms));
+  if (!P->gseg) {
+    const int64_t gnp = (int64_t)n + (q + Lg - 1) / Lg + 1;
+    const size_t extra = (size_t)gnp * (3 * sizeof(int32_t) + rr * sizeof(double)) +
+                         (size_t)n * (3 * sizeof(int32_t)) + 64 +
+                         exclusive_scan_tmp_bytes(n);
+    if (ctx->budget && ctx->in_use + extra > ctx->budget)
+      return fail(ctx, CPHIFI_E_ADMISSION, "Gram blocks exceed the HBM budget");
+    P->gnp = (int)gnp;
+    int64_t* scan_tmp = nullptr;
+    CK(dalloc(P, &P->gseg, (size_t)gnp));
+    CK(dalloc(P, &P->gbeg, (size_t)gnp));
+    CK(dalloc(P, &P->gend, (size_t)gnp));
+    CK(dalloc(P, &P->gfirst, (size_t)n + 1));
+    CK(dalloc(P, &P->gcount, (size_t)n));
+    CK(dalloc(P, &P->gticket, (size_t)n));
+    CK(dalloc(P, &P->gpart, (size_t)gnp * rr));
+    CK(dalloc(P, &scan_tmp, exclusive_scan_tmp_bytes(n) / sizeof(int64_t) + 1));
+    CK(cudaMemsetAsync(P->gticket, 0, (size_t)n * sizeof(unsigned), st));
+    CK(launch_piece_counts(P->row_ptr, n, Lg, P->gcount, nullptr, st));
+    CK(exclusive_scan_i32(P->gcount, P->gfirst, n, scan_tmp, exclusive_scan_tmp_bytes(n), st));
+    CK(launch_piece_fill(P->row_ptr, n, Lg, P->gfirst, P->gcount, P->gseg, P->gbeg, P->gend,
+                         nullptr, st));
+  }
+  const PieceList pl{P->gseg, P->gbeg, P->gend, P->gfirst, P->gcount, P->gticket, nullptr,
+                     P->gnp, 0, nullptr};
+  const int grid = std::max(1, std::min(P->gnp, ctx->num_sms * 8));
+  if (want32 && !P->c32_ok) {
+    if (ctx->budget && ctx->in_use + (size_t)n * rr * sizeof(float) > ctx->budget)
+      return fail(ctx, CPHIFI_E_ADMISSION, "Gram blocks exceed the HBM budget");
+    if (!P->C32) CK(dalloc(P, &P->C32, (size_t)n * rr));
+    CK(launch_gram_build_f32(pl, P->gfirst + n, grid, P->zhi, r, (float*)P->gpart, P->C32, st));
+    P->c32_ok = true;
+  }
+  if (want64 && !P->c64_ok) {
+    if (ctx->budget && ctx->in_use + (size_t)n * rr * sizeof(double) > ctx->budget)
+      return fail(ctx, CPHIFI_E_ADMISSION, "Gram blocks exceed the HBM budget");
+    if (!P->C64) CK(dalloc(P, &P->C64, (size_t)n * rr));
+    CK(launch_gram_build_df(pl, P->gfirst + n, grid, P->zhi, P->zhi ? nullptr : P->z64, r,
+                            P->gpart, P->C64, st));
+    P->c64_ok = true;
+  }
   return CPHIFI_OK;
 }
 
@@ -1536,7 +1600,9 @@ struct SolveRun {
       : P(p), prm(pr), W0(w0), W_out(wout), mem(m), prec(pr.precision),
         mixed(is_lowp(pr.precision)), emul(pr.precision != CPHIFI_FP64), st(p->st),
         tm(p->st, pr.profile != 0), L{p, p->st, &tm},
-        use_graphs(graphs_ok && pr.profile == 0) {}
+        use_graphs(graphs_ok && pr.profile == 0) {
+    L.gram = pr.gram;
+  }
   ~SolveRun() {
     for (auto& g : graphs) cudaGraphExecDestroy(g.second);
   }
@@ -1583,6 +1649,14 @@ struct SolveRun {
     h.max_iter = prm.max_iter;
     h.mode = mixed ? 1 : 0;
     SR_CK(cudaEventRecord(P->ev[0], st));
+    if (prm.gram) {  // the Gram blocks this solve uses (built once per problem)
+      const int rc = ensure_grams(P, mixed, !mixed || prm.gram == 2);
+      if (rc != CPHIFI_OK) {
+        status = rc;
+        stage = DONE;
+        return rc;
+      }
+    }
     SR_CK(cudaMemcpyAsync(P->s, &h, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
     if (P->tc_err) SR_CK(cudaMemsetAsync(P->tc_err, 0, sizeof(int), st));
     SR_CK(launch_build_D(P->kern->dK, P->dV, n, r, P->gamma, prm.lambda, prm.rho, P->D64, P->D32, st));
@@ -1795,6 +1869,7 @@ static int problem_rebuild(cphifi_problem* P) {
   cphifi_ctx* ctx = P->ctx;
   cudaStream_t st = P->st;
   const int r = P->r, d = P->d_other;
+  P->c32_ok = P->c64_ok = false;  // the Gram blocks follow Zhat
   CK(cudaMemsetAsync(P->err, 0, sizeof(int), st));
   for (int m = 0; m < d; ++m) {
     CK(launch_validate_dense(P->factors[m], P->sizes[m] * r, P->err, st));
@@ -2304,6 +2379,8 @@ extern "C" int cphifi_problem_matvec(cphifi_problem* P, int precision, double la
                                      const double* X, double* Y, int mem) {
   if (!P || !X || !Y) return CPHIFI_E_INVALID_ARG;
   cphifi_ctx* ctx = P->ctx;
+  const bool gram = (precision & CPHIFI_GRAM_FORM) != 0;
+  precision &= ~CPHIFI_GRAM_FORM;
   if (precision < CPHIFI_FP64 || precision > CPHIFI_MIXED_TF32X3)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
   if (is_tc(precision) && !P->kern->tc)
@@ -2311,9 +2388,12 @@ extern "C" int cphifi_problem_matvec(cphifi_problem* P, int precision, double la
   Enter guard(ctx);
   int rc;
   if ((rc = precision == CPHIFI_FP64 ? ensure_fp64(P) : ensure_lowp(P)) != CPHIFI_OK) return rc;
+  if (gram && (rc = ensure_grams(P, is_lowp(precision), !is_lowp(precision))) != CPHIFI_OK)
+    return rc;
   cudaStream_t st = P->st;
   const size_t nr = (size_t)P->n * P->r;
   Launcher L{P, st, nullptr};
+  L.gram = gram ? 2 : 0;
   DevScalars h{};
   h.lam = lambda;
   h.rho = rho;
@@ -2343,16 +2423,26 @@ extern "C" int cphifi_problem_gds(cphifi_problem* P, int precision, const double
                                   int mem) {
   if (!P || !Xhat || !Y1) return CPHIFI_E_INVALID_ARG;
   cphifi_ctx* ctx = P->ctx;
+  const bool gram = (precision & CPHIFI_GRAM_FORM) != 0;
+  precision &= ~CPHIFI_GRAM_FORM;
   if (precision < CPHIFI_FP64 || precision > CPHIFI_MIXED_TF32X3)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
   Enter guard(ctx);
   int rc;
   if ((rc = precision == CPHIFI_FP64 ? ensure_fp64(P) : ensure_lowp(P)) != CPHIFI_OK) return rc;
+  if (gram && (rc = ensure_grams(P, is_lowp(precision), !is_lowp(precision))) != CPHIFI_OK)
+    return rc;
   cudaStream_t st = P->st;
   const size_t nr = (size_t)P->n * P->r;
   Launcher L{P, st, nullptr};
   CK(upload(P->xh64, Xhat, nr * sizeof(double), mem, st));
-  if (precision == CPHIFI_FP64) {
+  if (gram && !is_lowp(precision)) {
+    CK(L.gram64(P->xh64, P->y164, nullptr, 0));
+  } else if (gram) {
+    CK(launch_convert<double, float>(P->xh64, P->xh32, (int64_t)nr, st));
+    CK(L.gram32(P->xh32, P->y132, nullptr, 0));
+    CK(launch_convert<float, double>(P->y132, P->y164, (int64_t)nr, st));
+  } else if (precision == CPHIFI_FP64) {
     CK(L.gds64(P->xh64, P->y164, nullptr, 0));
   } else if (precision == CPHIFI_FP64_EMULATED) {
     CK(L.gdsdf(P->xh64, P->y164, nullptr, 0));
@@ -2362,6 +2452,34 @@ extern "C" int cphifi_problem_gds(cphifi_problem* P, int precision, const double
     CK(launch_convert<float, double>(P->y132, P->y164, (int64_t)nr, st));
   }
   CK(download(Y1, P->y164, nr * sizeof(double), mem, st));
+  CK(cudaStreamSynchronize(st));
+  return CPHIFI_OK;
+}
+
+extern "C" int cphifi_problem_grams(cphifi_problem* P, int precision, double* C, int mem) {
+  if (!P || !C) return CPHIFI_E_INVALID_ARG;
+  cphifi_ctx* ctx = P->ctx;
+  if (precision < CPHIFI_FP64 || precision > CPHIFI_MIXED_TF32X3)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
+  if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
+  Enter guard(ctx);
+  const bool lowp = is_lowp(precision);
+  int rc;
+  if ((rc = precision == CPHIFI_FP64 ? ensure_fp64(P) : ensure_lowp(P)) != CPHIFI_OK) return rc;
+  if ((rc = ensure_grams(P, lowp, !lowp)) != CPHIFI_OK) return rc;
+  cudaStream_t st = P->st;
+  const size_t cnt = (size_t)P->n * P->r * P->r;
+  if (!lowp) {
+    CK(download(C, P->C64, cnt * sizeof(double), mem, st));
+  } else if (mem == CPHIFI_MEM_DEVICE) {
+    CK(launch_convert<float, double>(P->C32, C, (int64_t)cnt, st));
+  } else {
+    std::vector<float> h(cnt);
+    CK(cudaMemcpyAsync(h.data(), P->C32, cnt * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (size_t t = 0; t < cnt; ++t) C[t] = (double)h[t];
+  }
   CK(cudaStreamSynchronize(st));
   return CPHIFI_OK;
 }

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "common.cuh"
 
 namespace cphifi {
@@ -241,6 +243,36 @@ cudaError_t launch_precond_only(int n, int r, const double* X, double* Y,
                                 const double* UV, const double* D, cudaStream_t st);
 template <typename TS, typename TD>
 cudaError_t launch_convert(const TS* src, TD* dst, int64_t count, cudaStream_t st);
+
+// --------------------------------------------------------------- gram.cu ---
+// Per-index Gram blocks C_i = sum_{i_l = i} Zhat(l,:)'Zhat(l,:) (n blocks of
+// r x r, row-major, symmetric) over the pieces of pl (a decomposition of the
+// sorted observations; the exact piece count at np_dev, the capacity in
+// pl.npieces; partial: capacity x r^2 values): FP32 from Zhat's hi parts, or
+// FP64-accurate (double-float) from the hi/lo pair zhi or, when zhi is NULL,
+// the FP64 copy z64.  And Yhat1(i,:) = C_i Xhat(i,:)' for all i.
+cudaError_t launch_gram_build_f32(const PieceList& pl, const int32_t* np_dev, int grid,
+                                  const float* zhi, int r, float* partial, float* C,
+                                  cudaStream_t st);
+cudaError_t launch_gram_build_df(const PieceList& pl, const int32_t* np_dev, int grid,
+                                 const float* zhi, const double* z64, int r, double* partial,
+                                 double* C, cudaStream_t st);
+cudaError_t launch_gram_apply_f32(const float* C, int n, int r, const float* Xh, int64_t xld,
+                                  float* Y, int64_t yld, const DevScalars* skip,
+                                  cudaStream_t st);
+cudaError_t launch_gram_apply_f64(const double* C, int n, int r, const double* Xh, int64_t xld,
+                                  double* Y, int64_t yld, const DevScalars* skip,
+                                  cudaStream_t st);
+
+// ---------------------------------------------------------------- eig.cu ---
+// FP64 symmetric eigendecomposition by parallel two-sided Jacobi (Eq. eigK):
+// A (n x n, column-major; the lower triangle is read) is overwritten by the
+// eigenvectors in the order of the eigenvalues w (ascending).  Synchronous on
+// st; returns a cphifi_status, with the reason in *why on failure.
+constexpr int kSymEigMaxN = 4096;
+constexpr int kSymEigMaxSweeps = 60;
+int sym_eig_jacobi(double* A, int n, double* w, cudaStream_t st, std::string* why);
+int sym_eig_max_n();
 
 // ---------------------------------------------------------------- als.cu ---
 // The alternating fit (§2).  keep_obs: kidx_s = sorted keys, and the
