@@ -66,6 +66,9 @@ struct cphifi_ctx {
   // block) overlap the observation passes on the main stream.
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // Streams that only ever capture (the bodies of the device-side iteration
+  // loop's conditional nodes), created on first use.
+  cudaStream_t cap[2] = {nullptr, nullptr};
   // Submitted requests (cphifi_submit): admitted FIFO while a slot (stream)
   // and the HBM budget allow, advanced by cphifi_poll / cphifi_wait.
   uint64_t next_ticket = 1;
@@ -508,6 +511,8 @@ extern "C" int cphifi_ctx_destroy(cphifi_ctx* ctx) {
   }
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+  for (auto c : ctx->cap)
+    if (c) cudaStreamDestroy(c);
   if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
   for (auto e : ctx->events_free) cudaEventDestroy(e);
   for (auto p : ctx->pinned_slabs) cudaFreeHost(p);
@@ -711,6 +716,17 @@ extern "C" int cphifi_kernel_eig(const cphifi_kernel* kern, double* UK, double* 
 }
 
 // ----------------------------------------------------------- problem ------
+// Warps of the gather-dot/scatter decomposition: at most two resident 8-warp
+// blocks per SM, and enough that no warp walks more than about 8 pieces
+// (every kernel index, even an empty one, is a piece: with n > q most pieces
+// are empty, and a warp takes its pieces one after another) while keeping at
+// least 64 observations per warp when there are few indices.
+static int64_t gds_warps(int num_sms, int64_t n, int64_t q) {
+  const int64_t by_obs = (q + 63) / 64, by_pieces = (q + n + 7) / 8;
+  return std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms * 16,
+                                                std::max(by_obs, std::min(by_pieces, q))));
+}
+
 static size_t problem_footprint(int64_t n, int64_t q, int r, int d_other,
                                 const std::vector<int64_t>& sizes, bool lowp, int nsplit,
                                 int64_t npieces_max) {
@@ -733,7 +749,7 @@ static size_t problem_footprint(int64_t n, int64_t q, int r, int d_other,
 static void problem_need(const cphifi_ctx* ctx, int n, bool tc, int32_t d_other,
                          const std::vector<int64_t>& sizes, int32_t r, int64_t q, uint32_t flags,
                          size_t* need, size_t* tmp) {
-  const int64_t W = std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 16, (q + 63) / 64));
+  const int64_t W = gds_warps(ctx->num_sms, n, q);
   const int64_t npieces_max = (int64_t)n + W + 1;
   const int nsplit = std::max(
       std::max(gemm_pick_split<double, double>(n, ctx->num_sms), gemm_pick_split<float, float>(n, ctx->num_sms)),
@@ -763,8 +779,13 @@ static cudaError_t zhat_and_rhs(cphifi_problem* P, const int32_t* perm, const in
   const int n = P->n;
   const int64_t q = P->q;
   if (q == 0) return cudaMemsetAsync(P->Bm, 0, (size_t)n * P->r * sizeof(double), st);
-  const int64_t L2 = 256;
-  const int64_t W2 = (q + L2 - 1) / L2;
+  // ranges of 256 observations; more (and shorter) ranges when the kernel
+  // indices outnumber the observations, so that no warp walks long runs of
+  // empty pieces (as in gds_warps)
+  const int64_t W2 = std::max<int64_t>(
+      (q + 255) / 256,
+      std::min<int64_t>(std::min<int64_t>((q + n + 7) / 8, q), (int64_t)P->ctx->num_sms * 16));
+  const int64_t L2 = (q + W2 - 1) / W2;
   const int64_t np2 = (int64_t)n + W2 + 1;
   int32_t* cnt2 = (int32_t*)alloc((size_t)n * sizeof(int32_t));
   int32_t* first2 = (int32_t*)alloc((size_t)(n + 1) * sizeof(int32_t));
@@ -829,9 +850,8 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
   }
   const int n = kern->n;
   Enter guard(ctx);
-  // Gather-dot/scatter decomposition: W warps (two resident 8-warp blocks per
-  // SM at most, and no fewer than 64 observations per warp), L = ceil(q / W).
-  const int64_t W64 = std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 16, (q + 63) / 64));
+  // Gather-dot/scatter decomposition: W warps, L = ceil(q / W) observations each.
+  const int64_t W64 = gds_warps(ctx->num_sms, n, q);
   const int W = (int)W64;
   const int64_t L = std::max<int64_t>(1, (q + W - 1) / W);
   const int64_t npieces_max = (int64_t)n + W + 1;
@@ -1594,6 +1614,16 @@ struct SolveRun {
   bool use_graphs;
   std::vector<std::pair<int, cudaGraphExec_t>> graphs;
   std::vector<int64_t> graph_launches;  // kernels captured in each graph
+  // Mixed modes with graphs: the whole iteration loop as one graph (a WHILE
+  // node over cycles of k iterations + the FP64-accurate true residual + the
+  // decide kernel, and an IF node over the adopt-and-restart step), so the
+  // host looks at the solve only when the loop has ended.  Kernels per cycle
+  // and per restart, and the device counters when the loop was launched, for
+  // the launch count.
+  cudaGraphExec_t loop_exec = nullptr;
+  int64_t loop_cycle_launches = 0, loop_restart_launches = 0;
+  int loop_cycles0 = 0, loop_restarts0 = 0;
+  bool loop_pending = false;
 
   SolveRun(cphifi_problem* p, const cphifi_params& pr, const double* w0, double* wout, int m,
            bool graphs_ok)
@@ -1605,6 +1635,7 @@ struct SolveRun {
   }
   ~SolveRun() {
     for (auto& g : graphs) cudaGraphExecDestroy(g.second);
+    if (loop_exec) cudaGraphExecDestroy(loop_exec);
   }
   SolveRun(const SolveRun&) = delete;
   SolveRun& operator=(const SolveRun&) = delete;
@@ -1679,9 +1710,98 @@ struct SolveRun {
     return mark();
   }
 
+  // The loop graph of the mixed modes (see loop_exec), built on first use.
+  int build_loop(int m) {
+    cphifi_ctx* c = ctx();
+    for (auto& cs : c->cap)
+      if (!cs) SR_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    SR_CK(cudaGraphCreate(&g, 0));
+    cudaError_t e = cudaSuccess;
+    cudaGraphConditionalHandle hl = 0, hr = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hl, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hr, g, 0, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams wp{};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hl;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wn = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &wp);
+    const int64_t before = L.launches;
+    const cudaStream_t saved = L.st;
+    bool capturing = false, capturing2 = false;
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(c->cap[0], wp.conditional.phGraph_out[0], nullptr,
+                                        nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      capturing = true;
+      L.st = c->cap[0];
+      for (int k = 0; k < m && e == cudaSuccess; ++k) e = L.iteration(prec);
+      if (e == cudaSuccess) e = L.true_residual_check(prec);
+      if (e == cudaSuccess) e = launch_loop_decide(P->s, hl, hr, prm.max_iter + 2, c->cap[0]);
+      ++L.launches;
+    }
+    loop_cycle_launches = L.launches - before;
+    // the adopt-and-restart step under an IF node after the decide kernel
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t body = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaGraphNodeParams ip{};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hr;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t in = nullptr;
+    if (e == cudaSuccess)
+      e = cudaStreamGetCaptureInfo(c->cap[0], &cst, nullptr, &body, &deps, nullptr, &ndeps);
+    if (e == cudaSuccess) e = cudaGraphAddNode(&in, body, deps, nullptr, ndeps, &ip);
+    if (e == cudaSuccess)
+      e = cudaStreamUpdateCaptureDependencies(c->cap[0], &in, nullptr, 1,
+                                              cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(c->cap[1], ip.conditional.phGraph_out[0], nullptr,
+                                        nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    const int64_t before2 = L.launches;
+    if (e == cudaSuccess) {
+      capturing2 = true;
+      L.st = c->cap[1];
+      e = L.adopt_restart(prec);
+    }
+    loop_restart_launches = L.launches - before2;
+    cudaGraph_t done_g = nullptr;
+    const cudaError_t e2 = capturing2 ? cudaStreamEndCapture(c->cap[1], &done_g) : cudaSuccess;
+    const cudaError_t e1 = capturing ? cudaStreamEndCapture(c->cap[0], &done_g) : cudaSuccess;
+    L.st = saved;
+    L.launches = before;
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = e1;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&loop_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      loop_exec = nullptr;
+      return err(e, "building the iteration loop graph");
+    }
+    return CPHIFI_OK;
+  }
+
+  int queue_loop() {
+    if (!loop_exec) {
+      const int rc = build_loop(std::max(1, prm.k_replace));
+      if (rc != CPHIFI_OK) return rc;
+    }
+    loop_cycles0 = P->hs->cycles;
+    loop_restarts0 = P->hs->restarts;
+    loop_pending = true;
+    SR_CK(cudaGraphLaunch(loop_exec, st));
+    return CPHIFI_OK;
+  }
+
   // m PCG iterations (plus, in the mixed modes, the FP64-accurate true
   // residual and restart that close every cycle).
   int queue_chunk(int m) {
+    if (use_graphs && mixed) return queue_loop();
     if (!use_graphs) {
       for (int k = 0; k < m; ++k) SR_CK(L.iteration(prec));
       if (mixed) SR_CK(L.true_residual_check(prec));
@@ -1750,6 +1870,11 @@ struct SolveRun {
         stage = CHUNK;
         return next_chunk();
       case CHUNK:
+        if (loop_pending) {  // kernels the device-side loop ran
+          loop_pending = false;
+          L.launches += (int64_t)(hs->cycles - loop_cycles0) * loop_cycle_launches +
+                        (int64_t)(hs->restarts - loop_restarts0) * loop_restart_launches;
+        }
         if (hs->status) return finish_loop();
         if (mixed) {
           if (hs->done) { converged = true; return finish_loop(); }

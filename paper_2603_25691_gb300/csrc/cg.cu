@@ -326,6 +326,41 @@ cudaError_t launch_adopt_residual(const double* tres, double* res, int64_t count
   return cudaGetLastError();
 }
 
+// The decision that closes one cycle of the mixed solve's device-side loop
+// (k iterations, then the FP64-accurate true residual into the check buffer):
+// stop when the solve is done (the true residual met the tolerance) or broke
+// down; otherwise restart from the true residual when the recurrence has
+// stopped (it met the tolerance, or max_iter) or has drifted below the true
+// residual by more than a factor 2, unless no iterations are left (then stop:
+// the host forms the last residual); and stop after max_cycles cycles.  The
+// two graph conditions it sets drive the WHILE node of the loop and the IF
+// node of the restart.
+__global__ void loop_decide_kernel(DevScalars* s, cudaGraphConditionalHandle h_loop,
+                                   cudaGraphConditionalHandle h_restart, int max_cycles) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  s->cycles += 1;
+  unsigned go = 1, restart = 0;
+  const bool left = s->max_iter - s->iter > 0;
+  if (s->status || s->done) {
+    go = 0;
+  } else if (s->inner_done || s->rr < 0.25 * s->true_rr) {
+    if (left) restart = 1; else go = 0;
+  } else if (!left) {
+    go = 0;
+  }
+  if (s->cycles >= max_cycles) go = 0;
+  if (!go) restart = 0;
+  cudaGraphSetConditional(h_restart, restart);
+  cudaGraphSetConditional(h_loop, go);
+}
+
+cudaError_t launch_loop_decide(DevScalars* s, cudaGraphConditionalHandle h_loop,
+                               cudaGraphConditionalHandle h_restart, int max_cycles,
+                               cudaStream_t st) {
+  loop_decide_kernel<<<1, 32, 0, st>>>(s, h_loop, h_restart, max_cycles);
+  return cudaGetLastError();
+}
+
 template <typename TC, typename TO>
 cudaError_t launch_combine(int mode, const TC* C, int64_t split_stride, int nsplit, int n, int r,
                            const double* dK, const double* V, const double* Bv, TO* out,
@@ -351,14 +386,14 @@ template cudaError_t launch_combine<float, double>(int, const float*, int64_t, i
                                                    cudaStream_t);
 
 // --------------------------------- update + preconditioner (Eq. fx) --------
-// A block walks tiles of 64 kernel-eigenbasis rows.  UP_ITER first applies
+// A block walks tiles of kUpRows kernel-eigenbasis rows.  UP_ITER first applies
 // x += alpha p, r -= alpha y (FP64).  Then, per row i,
 // z(i,:) = ((r(i,:) U_V) .* D(i,:)) U_V' as two small products through
 // shared memory in arithmetic TP, and the last block turns (r, z) and ||r||^2
 // into beta and the convergence flags.
-constexpr int kUpRows = 64;
-
-template <typename TP>
+// Tiles of 64 rows; 16 when the rows would otherwise occupy fewer blocks
+// than there are SMs (small n: more blocks share the r x r products).
+template <typename TP, int kUpRows>
 __global__ void __launch_bounds__(256)
 update_precond_kernel(int mode, int n, int r, double* __restrict__ x, double* __restrict__ rres,
                       const double* __restrict__ p, const double* __restrict__ y,
@@ -436,16 +471,22 @@ cudaError_t launch_update_precond(int mode, int n, int r, double* x, double* rre
                                   const double* p, const double* y, double* z, const TP* UV,
                                   const TP* D, DevScalars* s, RedScratch red, cudaStream_t st) {
   if (r < 1 || r > kMaxRank) return cudaErrorInvalidValue;
-  int blocks = (n + kUpRows - 1) / kUpRows;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const bool narrow = (n + 63) / 64 < sms;
+  const int rows = narrow ? 16 : 64;
+  int blocks = (n + rows - 1) / rows;
   if (blocks > kRedMaxBlocks) blocks = kRedMaxBlocks;
   if (blocks < 1) blocks = 1;
-  const size_t smem = (size_t)(r * r + 2 * kUpRows * (r + 1)) * sizeof(TP);
+  const size_t smem = (size_t)(r * r + 2 * rows * (r + 1)) * sizeof(TP);
+  auto kern = narrow ? update_precond_kernel<TP, 16> : update_precond_kernel<TP, 64>;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(update_precond_kernel<TP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
   }
-  update_precond_kernel<TP><<<blocks, 256, smem, st>>>(mode, n, r, x, rres, p, y, z, UV, D, s, red);
+  kern<<<blocks, 256, smem, st>>>(mode, n, r, x, rres, p, y, z, UV, D, s, red);
   return cudaGetLastError();
 }
 
