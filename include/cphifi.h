@@ -157,6 +157,7 @@ typedef struct cphifi_stats {
                                 and restarts), i.e. the iteration phase        */
   double final_ms;           /* CUDA-event time: W = U_K Wbar and its copy    */
   double queue_ms;           /* submitted requests: wait for admission (host) */
+  double graph_build_ms;     /* host time spent building this solve's CUDA graphs */
 } cphifi_stats;
 
 typedef struct cphifi_ctx cphifi_ctx;
@@ -298,6 +299,27 @@ int cphifi_solve(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
  * Destroying the context releases requests that were never waited for. */
 typedef uint64_t cphifi_ticket;
 int cphifi_ctx_set_slots(cphifi_ctx* ctx, int max_active);
+
+/* ---- launch shapes per problem size (set by an autotuner) -----------------
+ * A problem of kernel size n, q observations and rank r belongs to the bucket
+ * (floor(log2 n), floor(log2 max(q, 1)), r).  cphifi_ctx_set_tuning stores
+ * the launch shapes for one bucket (t = NULL removes the entry); problems
+ * created afterwards in that bucket -- by problem_create, solve, submit or
+ * als -- use them instead of the built-in heuristics.  A field of 0 keeps the
+ * heuristic value; the others are clamped to what each kernel supports.
+ * Shapes change the order of floating-point sums (results stay within the
+ * arithmetic's bounds) but never the results' determinism: a given context
+ * and problem always give the same bits.  No counterpart in the paper. */
+typedef struct cphifi_tuning {
+  int32_t gds_warps_per_sm; /* gather-dot/scatter warps per SM, at most (16) */
+  int32_t split32;          /* k-range splits of the FP32 n x n products    */
+  int32_t split_tc;         /* ... of the tensor-core (TF32/BF16) products  */
+  int32_t split_wide;       /* ... of the FP64-accurate products            */
+  int32_t split64;          /* ... of the FP64 products                     */
+  int32_t reserved[3];
+} cphifi_tuning;
+int cphifi_ctx_set_tuning(cphifi_ctx* ctx, int32_t n_log2, int32_t q_log2, int32_t r,
+                          const cphifi_tuning* t);
 int cphifi_submit(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
                   const int64_t* other_sizes, const double* const* factors,
                   int32_t r, int64_t q, const int32_t* kidx,

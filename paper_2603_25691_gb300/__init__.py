@@ -70,10 +70,17 @@ class Stats(ctypes.Structure):
                 ("gemm64_launches", ctypes.c_int32), ("gemm64_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("setup_launches", ctypes.c_int64),
                 ("rhs_ms", ctypes.c_double), ("iter_ms", ctypes.c_double),
-                ("final_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
+                ("final_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("graph_build_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("gds_warps_per_sm", ctypes.c_int32), ("split32", ctypes.c_int32),
+                ("split_tc", ctypes.c_int32), ("split_wide", ctypes.c_int32),
+                ("split64", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class CphifiError(RuntimeError):
@@ -117,6 +124,8 @@ _SIG = {
     "cphifi_problem_grams": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
     "cphifi_problem_order": (ctypes.c_int, [_P, _P, _P]),
     "cphifi_ctx_set_slots": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cphifi_ctx_set_tuning": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.POINTER(Tuning)]),
     "cphifi_problem_set_factors": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "cphifi_problem_update_factor": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int]),
     "cphifi_problem_fit": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -244,6 +253,18 @@ class Context:
             self.h = None
 
     __del__ = close
+
+    def set_tuning(self, bucket, shapes) -> None:
+        """cphifi_ctx_set_tuning: launch shapes (a dict with the fields of
+        Tuning, missing ones 0 = heuristic; None removes the entry) for the
+        size bucket (floor(log2 n), floor(log2 q), r), see size_bucket()."""
+        n_log2, q_log2, r = (int(x) for x in bucket)
+        if shapes is None:
+            rc = lib().cphifi_ctx_set_tuning(self.h, n_log2, q_log2, r, None)
+        else:
+            t = Tuning(*[int(shapes.get(f, 0)) for f, _ in Tuning._fields_[:5]])
+            rc = lib().cphifi_ctx_set_tuning(self.h, n_log2, q_log2, r, ctypes.byref(t))
+        _check(self.h, rc, "ctx_set_tuning")
 
     def set_slots(self, max_active: int) -> None:
         """cphifi_ctx_set_slots: how many submitted requests run at once."""
@@ -498,6 +519,11 @@ class Problem:
 
 
 GRAM_FORM = 0x100
+
+
+def size_bucket(n: int, q: int, r: int):
+    """The tuning bucket of a problem: (floor(log2 n), floor(log2 max(q, 1)), r)."""
+    return (int(n).bit_length() - 1, max(int(q), 1).bit_length() - 1, int(r))
 
 
 def _prec(p) -> int:

@@ -23,6 +23,7 @@
 #include <map>
 #include <memory>
 #include <thread>
+#include <tuple>
 #include <string>
 #include <utility>
 #include <vector>
@@ -66,9 +67,10 @@ struct cphifi_ctx {
   // block) overlap the observation passes on the main stream.
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  // Streams that only ever capture (the bodies of the device-side iteration
-  // loop's conditional nodes), created on first use.
-  cudaStream_t cap[2] = {nullptr, nullptr};
+  // Launch shapes per problem-size bucket (floor(log2 n), floor(log2 q), r),
+  // set by cphifi_ctx_set_tuning (the autotuner); absent buckets use the
+  // built-in heuristics.
+  std::map<std::tuple<int, int, int>, cphifi_tuning> tuning;
   // Submitted requests (cphifi_submit): admitted FIFO while a slot (stream)
   // and the HBM budget allow, advanced by cphifi_poll / cphifi_wait.
   uint64_t next_ticket = 1;
@@ -511,8 +513,6 @@ extern "C" int cphifi_ctx_destroy(cphifi_ctx* ctx) {
   }
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
-  for (auto c : ctx->cap)
-    if (c) cudaStreamDestroy(c);
   if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
   for (auto e : ctx->events_free) cudaEventDestroy(e);
   for (auto p : ctx->pinned_slabs) cudaFreeHost(p);
@@ -721,10 +721,46 @@ extern "C" int cphifi_kernel_eig(const cphifi_kernel* kern, double* UK, double* 
 // (every kernel index, even an empty one, is a piece: with n > q most pieces
 // are empty, and a warp takes its pieces one after another) while keeping at
 // least 64 observations per warp when there are few indices.
-static int64_t gds_warps(int num_sms, int64_t n, int64_t q) {
+static int64_t gds_warps(int num_sms, int64_t n, int64_t q, int warps_per_sm = 16) {
   const int64_t by_obs = (q + 63) / 64, by_pieces = (q + n + 7) / 8;
-  return std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms * 16,
+  return std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms * warps_per_sm,
                                                 std::max(by_obs, std::min(by_pieces, q))));
+}
+
+static int floor_log2(int64_t v) {
+  int b = 0;
+  while (v > 1) {
+    v >>= 1;
+    ++b;
+  }
+  return b;
+}
+
+// Launch shapes of a problem: the gather-dot/scatter's warps and the k-range
+// splits of the n x n products, from the context's tuning table when it has
+// an entry for the problem's bucket, else from the heuristics.  Tuned splits
+// are clamped to what each product kernel supports.
+struct Shapes {
+  int64_t W;
+  int s64, s32, sdf, stc;
+};
+static Shapes problem_shapes(const cphifi_ctx* ctx, const cphifi_kernel* kern, int n, int64_t q,
+                             int r) {
+  cphifi_tuning t{};
+  auto it = ctx->tuning.find(std::make_tuple(floor_log2(n), floor_log2(std::max<int64_t>(q, 1)), r));
+  if (it != ctx->tuning.end()) t = it->second;
+  const int sms = ctx->num_sms;
+  auto pick = [](int tuned, int dflt, int cap) {
+    return tuned > 0 ? std::max(1, std::min(tuned, cap)) : dflt;
+  };
+  Shapes sh;
+  sh.W = gds_warps(sms, n, q, t.gds_warps_per_sm > 0 ? t.gds_warps_per_sm : 16);
+  sh.s64 = pick(t.split64, gemm_pick_split<double, double>(n, sms), std::min(32, (n + 31) / 32));
+  sh.s32 = pick(t.split32, gemm_pick_split<float, float>(n, sms), std::min(32, (n + 31) / 32));
+  sh.sdf = kern->oz ? pick(t.split_wide, oz_pick_split(n, sms), std::min(64, (n + 255) / 256))
+                    : pick(t.split_wide, gemm_df_pick_split(n, sms), std::min(32, (n + 15) / 16));
+  sh.stc = kern->tc ? pick(t.split_tc, tc_pick_split(n, sms), std::min(64, (n + 31) / 32)) : 1;
+  return sh;
 }
 
 static size_t problem_footprint(int64_t n, int64_t q, int r, int d_other,
@@ -746,14 +782,14 @@ static size_t problem_footprint(int64_t n, int64_t q, int r, int d_other,
 
 // Device bytes a problem holds (`need`) and the temporaries of its creation
 // (`tmp`), for admission against the context's HBM budget.
-static void problem_need(const cphifi_ctx* ctx, int n, bool tc, int32_t d_other,
+static void problem_need(const cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t d_other,
                          const std::vector<int64_t>& sizes, int32_t r, int64_t q, uint32_t flags,
                          size_t* need, size_t* tmp) {
-  const int64_t W = gds_warps(ctx->num_sms, n, q);
-  const int64_t npieces_max = (int64_t)n + W + 1;
-  const int nsplit = std::max(
-      std::max(gemm_pick_split<double, double>(n, ctx->num_sms), gemm_pick_split<float, float>(n, ctx->num_sms)),
-      std::max(gemm_df_pick_split(n, ctx->num_sms), tc ? tc_pick_split(n, ctx->num_sms) : 1));
+  const int n = kern->n;
+  const bool tc = kern->tc;
+  const Shapes sh = problem_shapes(ctx, kern, n, q, r);
+  const int64_t npieces_max = (int64_t)n + sh.W + 1;
+  const int nsplit = std::max(std::max(sh.s64, sh.s32), std::max(sh.sdf, sh.stc));
   const bool need64 = (flags & CPHIFI_NEED_FP64) || !(flags & CPHIFI_NEED_LOWP);
   const bool lowp = (flags & CPHIFI_NEED_LOWP) || !(flags & CPHIFI_NEED_FP64);
   *need = problem_footprint(n, q, r, d_other, sizes, lowp, nsplit, npieces_max) +
@@ -851,21 +887,22 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
   const int n = kern->n;
   Enter guard(ctx);
   // Gather-dot/scatter decomposition: W warps, L = ceil(q / W) observations each.
-  const int64_t W64 = gds_warps(ctx->num_sms, n, q);
+  const Shapes shapes = problem_shapes(ctx, kern, n, q, r);
+  const int64_t W64 = shapes.W;
   const int W = (int)W64;
   const int64_t L = std::max<int64_t>(1, (q + W - 1) / W);
   const int64_t npieces_max = (int64_t)n + W + 1;
-  const int nsplit64 = gemm_pick_split<double, double>(n, ctx->num_sms);
-  const int nsplit32 = gemm_pick_split<float, float>(n, ctx->num_sms);
-  const int nsplitdf = kern->oz ? oz_pick_split(n, ctx->num_sms) : gemm_df_pick_split(n, ctx->num_sms);
-  const int nsplittc = kern->tc ? tc_pick_split(n, ctx->num_sms) : 1;
+  const int nsplit64 = shapes.s64;
+  const int nsplit32 = shapes.s32;
+  const int nsplitdf = shapes.sdf;
+  const int nsplittc = shapes.stc;
   const int nsplit = std::max(std::max(nsplit64, nsplit32), std::max(nsplitdf, nsplittc));
   // Operator data: FP64 Zhat for the FP64 operator, hi/lo FP32 pairs for the
   // mixed modes; neither flag set means both.
   const bool need64 = (flags & CPHIFI_NEED_FP64) || !(flags & CPHIFI_NEED_LOWP);
   const bool lowp = (flags & CPHIFI_NEED_LOWP) || !(flags & CPHIFI_NEED_FP64);
   size_t need = 0, tmp_need = 0;
-  problem_need(ctx, n, kern->tc, d_other, sizes, r, q, flags, &need, &tmp_need);
+  problem_need(ctx, kern, d_other, sizes, r, q, flags, &need, &tmp_need);
   if (ctx->budget && ctx->in_use + need + tmp_need > ctx->budget)
     return fail(ctx, CPHIFI_E_ADMISSION, "problem footprint exceeds the HBM budget");
   auto t0 = std::chrono::steady_clock::now();
@@ -1614,16 +1651,7 @@ struct SolveRun {
   bool use_graphs;
   std::vector<std::pair<int, cudaGraphExec_t>> graphs;
   std::vector<int64_t> graph_launches;  // kernels captured in each graph
-  // Mixed modes with graphs: the whole iteration loop as one graph (a WHILE
-  // node over cycles of k iterations + the FP64-accurate true residual + the
-  // decide kernel, and an IF node over the adopt-and-restart step), so the
-  // host looks at the solve only when the loop has ended.  Kernels per cycle
-  // and per restart, and the device counters when the loop was launched, for
-  // the launch count.
-  cudaGraphExec_t loop_exec = nullptr;
-  int64_t loop_cycle_launches = 0, loop_restart_launches = 0;
-  int loop_cycles0 = 0, loop_restarts0 = 0;
-  bool loop_pending = false;
+  double chunk_build_ms = 0.0;  // host time of building the chunk graphs
 
   SolveRun(cphifi_problem* p, const cphifi_params& pr, const double* w0, double* wout, int m,
            bool graphs_ok)
@@ -1635,7 +1663,6 @@ struct SolveRun {
   }
   ~SolveRun() {
     for (auto& g : graphs) cudaGraphExecDestroy(g.second);
-    if (loop_exec) cudaGraphExecDestroy(loop_exec);
   }
   SolveRun(const SolveRun&) = delete;
   SolveRun& operator=(const SolveRun&) = delete;
@@ -1710,98 +1737,9 @@ struct SolveRun {
     return mark();
   }
 
-  // The loop graph of the mixed modes (see loop_exec), built on first use.
-  int build_loop(int m) {
-    cphifi_ctx* c = ctx();
-    for (auto& cs : c->cap)
-      if (!cs) SR_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t g = nullptr;
-    SR_CK(cudaGraphCreate(&g, 0));
-    cudaError_t e = cudaSuccess;
-    cudaGraphConditionalHandle hl = 0, hr = 0;
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hl, g, 1, cudaGraphCondAssignDefault);
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hr, g, 0, cudaGraphCondAssignDefault);
-    cudaGraphNodeParams wp{};
-    wp.type = cudaGraphNodeTypeConditional;
-    wp.conditional.handle = hl;
-    wp.conditional.type = cudaGraphCondTypeWhile;
-    wp.conditional.size = 1;
-    cudaGraphNode_t wn = nullptr;
-    if (e == cudaSuccess) e = cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &wp);
-    const int64_t before = L.launches;
-    const cudaStream_t saved = L.st;
-    bool capturing = false, capturing2 = false;
-    if (e == cudaSuccess)
-      e = cudaStreamBeginCaptureToGraph(c->cap[0], wp.conditional.phGraph_out[0], nullptr,
-                                        nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      capturing = true;
-      L.st = c->cap[0];
-      for (int k = 0; k < m && e == cudaSuccess; ++k) e = L.iteration(prec);
-      if (e == cudaSuccess) e = L.true_residual_check(prec);
-      if (e == cudaSuccess) e = launch_loop_decide(P->s, hl, hr, prm.max_iter + 2, c->cap[0]);
-      ++L.launches;
-    }
-    loop_cycle_launches = L.launches - before;
-    // the adopt-and-restart step under an IF node after the decide kernel
-    cudaStreamCaptureStatus cst;
-    cudaGraph_t body = nullptr;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t ndeps = 0;
-    cudaGraphNodeParams ip{};
-    ip.type = cudaGraphNodeTypeConditional;
-    ip.conditional.handle = hr;
-    ip.conditional.type = cudaGraphCondTypeIf;
-    ip.conditional.size = 1;
-    cudaGraphNode_t in = nullptr;
-    if (e == cudaSuccess)
-      e = cudaStreamGetCaptureInfo(c->cap[0], &cst, nullptr, &body, &deps, nullptr, &ndeps);
-    if (e == cudaSuccess) e = cudaGraphAddNode(&in, body, deps, nullptr, ndeps, &ip);
-    if (e == cudaSuccess)
-      e = cudaStreamUpdateCaptureDependencies(c->cap[0], &in, nullptr, 1,
-                                              cudaStreamSetCaptureDependencies);
-    if (e == cudaSuccess)
-      e = cudaStreamBeginCaptureToGraph(c->cap[1], ip.conditional.phGraph_out[0], nullptr,
-                                        nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    const int64_t before2 = L.launches;
-    if (e == cudaSuccess) {
-      capturing2 = true;
-      L.st = c->cap[1];
-      e = L.adopt_restart(prec);
-    }
-    loop_restart_launches = L.launches - before2;
-    cudaGraph_t done_g = nullptr;
-    const cudaError_t e2 = capturing2 ? cudaStreamEndCapture(c->cap[1], &done_g) : cudaSuccess;
-    const cudaError_t e1 = capturing ? cudaStreamEndCapture(c->cap[0], &done_g) : cudaSuccess;
-    L.st = saved;
-    L.launches = before;
-    if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = e1;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&loop_exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-      loop_exec = nullptr;
-      return err(e, "building the iteration loop graph");
-    }
-    return CPHIFI_OK;
-  }
-
-  int queue_loop() {
-    if (!loop_exec) {
-      const int rc = build_loop(std::max(1, prm.k_replace));
-      if (rc != CPHIFI_OK) return rc;
-    }
-    loop_cycles0 = P->hs->cycles;
-    loop_restarts0 = P->hs->restarts;
-    loop_pending = true;
-    SR_CK(cudaGraphLaunch(loop_exec, st));
-    return CPHIFI_OK;
-  }
-
   // m PCG iterations (plus, in the mixed modes, the FP64-accurate true
   // residual and restart that close every cycle).
   int queue_chunk(int m) {
-    if (use_graphs && mixed) return queue_loop();
     if (!use_graphs) {
       for (int k = 0; k < m; ++k) SR_CK(L.iteration(prec));
       if (mixed) SR_CK(L.true_residual_check(prec));
@@ -1812,6 +1750,7 @@ struct SolveRun {
     for (size_t k = 0; k < graphs.size(); ++k)
       if (graphs[k].first == m) { ex = graphs[k].second; nl = graph_launches[k]; }
     if (!ex) {
+      const auto tb = std::chrono::steady_clock::now();
       cudaGraph_t g = nullptr;
       const int64_t before = L.launches;
       SR_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -1828,6 +1767,8 @@ struct SolveRun {
       SR_CK(e);
       graphs.push_back({m, ex});
       graph_launches.push_back(nl);
+      chunk_build_ms += std::chrono::duration<double, std::milli>(
+                            std::chrono::steady_clock::now() - tb).count();
     }
     SR_CK(cudaGraphLaunch(ex, st));
     L.launches += nl;
@@ -1870,11 +1811,6 @@ struct SolveRun {
         stage = CHUNK;
         return next_chunk();
       case CHUNK:
-        if (loop_pending) {  // kernels the device-side loop ran
-          loop_pending = false;
-          L.launches += (int64_t)(hs->cycles - loop_cycles0) * loop_cycle_launches +
-                        (int64_t)(hs->restarts - loop_restarts0) * loop_restart_launches;
-        }
         if (hs->status) return finish_loop();
         if (mixed) {
           if (hs->done) { converged = true; return finish_loop(); }
@@ -1965,6 +1901,7 @@ struct SolveRun {
     stats->rel_residual_recurrence = hs->bb > 0 ? std::sqrt(hs->rr) / bn : 0.0;
     stats->solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     stats->kernel_launches = L.launches;
+    stats->graph_build_ms = chunk_build_ms;
     stats->setup_launches = P->create_launches;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, P->ev[0], P->ev[1]) == cudaSuccess) stats->rhs_ms = ms;
@@ -2369,6 +2306,22 @@ static void requests_clear(cphifi_ctx* ctx) {
   ctx->slot_busy.clear();
 }
 
+extern "C" int cphifi_ctx_set_tuning(cphifi_ctx* ctx, int32_t n_log2, int32_t q_log2, int32_t r,
+                                     const cphifi_tuning* t) {
+  if (!ctx) return CPHIFI_E_INVALID_ARG;
+  if (n_log2 < 0 || n_log2 > 30 || q_log2 < 0 || q_log2 > 31 || r < 1 || r > kMaxRank)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "tuning bucket out of range");
+  const auto key = std::make_tuple((int)n_log2, (int)q_log2, (int)r);
+  if (!t) {
+    ctx->tuning.erase(key);
+    return CPHIFI_OK;
+  }
+  for (int v : {t->gds_warps_per_sm, t->split32, t->split_tc, t->split_wide, t->split64})
+    if (v < 0 || v > 64) return fail(ctx, CPHIFI_E_INVALID_ARG, "tuning value out of [0, 64]");
+  ctx->tuning[key] = *t;
+  return CPHIFI_OK;
+}
+
 extern "C" int cphifi_ctx_set_slots(cphifi_ctx* ctx, int max_active) {
   if (!ctx || max_active < 1 || max_active > 1024) return CPHIFI_E_INVALID_ARG;
   ctx->max_active = max_active;
@@ -2416,7 +2369,7 @@ extern "C" int cphifi_submit(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
   R->t_submit = R->t_admit = R->t_created = std::chrono::steady_clock::now();
   {
     size_t need = 0, tmp = 0;
-    problem_need(ctx, kern->n, kern->tc, d_other, R->sizes, r, q, R->flags, &need, &tmp);
+    problem_need(ctx, kern, d_other, R->sizes, r, q, R->flags, &need, &tmp);
     R->need = need + tmp;
     R->large = R->need > kLargeRequestBytes;
   }

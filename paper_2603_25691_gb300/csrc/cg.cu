@@ -326,41 +326,6 @@ cudaError_t launch_adopt_residual(const double* tres, double* res, int64_t count
   return cudaGetLastError();
 }
 
-// The decision that closes one cycle of the mixed solve's device-side loop
-// (k iterations, then the FP64-accurate true residual into the check buffer):
-// stop when the solve is done (the true residual met the tolerance) or broke
-// down; otherwise restart from the true residual when the recurrence has
-// stopped (it met the tolerance, or max_iter) or has drifted below the true
-// residual by more than a factor 2, unless no iterations are left (then stop:
-// the host forms the last residual); and stop after max_cycles cycles.  The
-// two graph conditions it sets drive the WHILE node of the loop and the IF
-// node of the restart.
-__global__ void loop_decide_kernel(DevScalars* s, cudaGraphConditionalHandle h_loop,
-                                   cudaGraphConditionalHandle h_restart, int max_cycles) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  s->cycles += 1;
-  unsigned go = 1, restart = 0;
-  const bool left = s->max_iter - s->iter > 0;
-  if (s->status || s->done) {
-    go = 0;
-  } else if (s->inner_done || s->rr < 0.25 * s->true_rr) {
-    if (left) restart = 1; else go = 0;
-  } else if (!left) {
-    go = 0;
-  }
-  if (s->cycles >= max_cycles) go = 0;
-  if (!go) restart = 0;
-  cudaGraphSetConditional(h_restart, restart);
-  cudaGraphSetConditional(h_loop, go);
-}
-
-cudaError_t launch_loop_decide(DevScalars* s, cudaGraphConditionalHandle h_loop,
-                               cudaGraphConditionalHandle h_restart, int max_cycles,
-                               cudaStream_t st) {
-  loop_decide_kernel<<<1, 32, 0, st>>>(s, h_loop, h_restart, max_cycles);
-  return cudaGetLastError();
-}
-
 template <typename TC, typename TO>
 cudaError_t launch_combine(int mode, const TC* C, int64_t split_stride, int nsplit, int n, int r,
                            const double* dK, const double* V, const double* Bv, TO* out,

@@ -40,7 +40,6 @@ struct DevScalars {
   int true_evals;
   int restarts;
   int mode;         // 0: FP64 (stop on the recurrence); 1: mixed (stop on true residual)
-  int cycles;       // cycles of the device-side iteration loop run so far
 };
 
 struct RedScratch {

@@ -213,11 +213,6 @@ enum CombineMode {
   CM_TRUE = 5     // as CM_RESID into a separate buffer: sets true_rr and the
                   // convergence flag, leaves the recurrence (rr, inner_done) alone
 };
-// One thread: the end-of-cycle decision of the mixed solve's device-side
-// loop (see cg.cu); sets the loop's WHILE and the restart's IF conditions.
-cudaError_t launch_loop_decide(DevScalars* s, cudaGraphConditionalHandle h_loop,
-                               cudaGraphConditionalHandle h_restart, int max_cycles,
-                               cudaStream_t st);
 // res = tres, rr = true_rr, inner_done = 0: the true residual of CM_TRUE
 // replaces the recurrence residual (before a restart).
 cudaError_t launch_adopt_residual(const double* tres, double* res, int64_t count, DevScalars* s,
