@@ -261,8 +261,18 @@ combine_kernel(int mode, const TC* __restrict__ C, int64_t split_stride, int nsp
   double acc[1] = {0.0};
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
+    // the split partials in order; loaded eight at a time so that their
+    // latencies overlap (the sum is the same, term by term)
     double c = 0.0;
-    for (int k = 0; k < nsplit; ++k) c += (double)C[k * split_stride + t];
+    int k = 0;
+    for (; k + 8 <= nsplit; k += 8) {
+      TC v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = C[(k + u) * split_stride + t];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) c += (double)v[u];
+    }
+    for (; k < nsplit; ++k) c += (double)C[k * split_stride + t];
     const int i = (int)(t % n);
     double o;
     if (mode == CM_STORE) {
