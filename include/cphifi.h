@@ -203,6 +203,26 @@ int cphifi_kernel_create(cphifi_ctx* ctx, int64_t n, const double* K,
 /* Fails with CPHIFI_E_INVALID_ARG while a submitted request that uses the
  * kernel has not completed. */
 int cphifi_kernel_destroy(cphifi_kernel* kern);
+/* ---- kernel matrices from design points (§2: k(x_i, x_j) on the kernel
+ * mode's points) --------------------------------------------------------------
+ * cphifi_kernel_create_points: the kernel handle of K(i, j) = k(x_i, x_j)
+ * for n points x (row-major n x dim, memory kind mem), built on the device
+ * in FP64 and decomposed there (as cphifi_kernel_create with K alone, so
+ * n <= 4096).  kind: CPHIFI_KERNEL_GAUSSIAN, k = exp(-|x - y|^2 / (2 s^2)),
+ * or CPHIFI_KERNEL_MATERN32, k = (1 + sqrt(3) d / s) exp(-sqrt(3) d / s),
+ * d = |x - y|; s = bandwidth > 0.  The handle keeps the points: products
+ * with K (cphifi_kernel_apply, and the alternating fit's A_k = K W) then
+ * generate K's entries instead of reading a stored matrix.
+ * cphifi_kernel_apply: Y = K X for X, Y n x r (column-major, r <= 64, memory
+ * kind mem).  With points, K's tiles are generated on the fly: precision
+ * CPHIFI_FP64 in FP64, CPHIFI_MIXED_FP32 in FP32 with the hardware
+ * exponential (about 1e-6 relative); without points, Y = U_K (D_K o (U_K' X))
+ * in FP64 from the stored eigendecomposition. */
+enum cphifi_kernel_kind { CPHIFI_KERNEL_GAUSSIAN = 0, CPHIFI_KERNEL_MATERN32 = 1 };
+int cphifi_kernel_create_points(cphifi_ctx* ctx, int64_t n, int32_t dim, const double* x,
+                                int32_t kind, double bandwidth, int mem, cphifi_kernel** out);
+int cphifi_kernel_apply(const cphifi_kernel* kern, int32_t precision, int32_t r,
+                        const double* X, double* Y, int mem);
 /* The eigendecomposition the kernel handle holds (Eq. eigK): UK (n x n,
  * column-major, column j = eigenvector j) and DK (n eigenvalues; ascending
  * when the library computed them), FP64, copied to memory kind `mem`.

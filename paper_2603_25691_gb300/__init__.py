@@ -103,6 +103,11 @@ _SIG = {
     "cphifi_kernel_create": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, ctypes.c_int, _PP]),
     "cphifi_kernel_destroy": (ctypes.c_int, [_P]),
     "cphifi_kernel_eig": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "cphifi_kernel_create_points": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P,
+                                                   ctypes.c_int32, ctypes.c_double, ctypes.c_int,
+                                                   _PP]),
+    "cphifi_kernel_apply": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P,
+                                           ctypes.c_int]),
     "cphifi_problem_create": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32,
                                              ctypes.c_int64, _P, _P, _P, ctypes.c_uint32,
                                              ctypes.c_int, _PP]),
@@ -284,6 +289,11 @@ class Context:
     def kernel_create(self, n: int, UK, DK, K=None) -> "Kernel":
         return Kernel(self, n, UK, DK, K)
 
+    def kernel_from_points(self, x, kind: str = "gaussian", bandwidth: float = 0.1) -> "Kernel":
+        """cphifi_kernel_create_points: K(i, j) = k(x_i, x_j) for the points x
+        (n values, or an n x dim array), kind "gaussian" or "matern32"."""
+        return Kernel.from_points(self, x, kind, bandwidth)
+
 
 class Kernel:
     """cphifi_kernel_create: the kernel matrix's eigendecomposition (Eq. eigK)."""
@@ -315,6 +325,33 @@ class Kernel:
         _check(ctx.h, rc, "kernel_create")
         self.h = h
         ctx._children.add(self)
+
+    @classmethod
+    def from_points(cls, ctx: Context, x, kind: str = "gaussian", bandwidth: float = 0.1):
+        pts = np.asarray(x, dtype=np.float64)
+        if pts.ndim == 1:
+            pts = pts[:, None]
+        pts = np.ascontiguousarray(pts)
+        self = cls.__new__(cls)
+        self.ctx, self.n = ctx, int(pts.shape[0])
+        h = ctypes.c_void_p()
+        kinds = {"gaussian": 0, "matern32": 1}
+        rc = lib().cphifi_kernel_create_points(ctx.h, self.n, int(pts.shape[1]), pts.ctypes.data,
+                                               kinds[kind], float(bandwidth), MEM_HOST,
+                                               ctypes.byref(h))
+        _check(ctx.h, rc, "kernel_create_points")
+        self.h = h
+        ctx._children.add(self)
+        return self
+
+    def apply(self, X, precision: str = "fp64"):
+        """cphifi_kernel_apply: K X for an (n, r) host array."""
+        X = np.asfortranarray(np.asarray(X, dtype=np.float64))
+        Y = np.empty_like(X, order="F")
+        _check(self.ctx.h, lib().cphifi_kernel_apply(self.h, _prec(precision), int(X.shape[1]),
+                                                     X.ctypes.data, Y.ctypes.data, MEM_HOST),
+               "kernel_apply")
+        return Y
 
     def eig(self):
         """cphifi_kernel_eig: (D_K, U_K) held by the handle, as host arrays."""

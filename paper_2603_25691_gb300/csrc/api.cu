@@ -105,6 +105,11 @@ struct cphifi_kernel {
   CUtensorMap mOz1, mOz2;
   double* dK = nullptr;    // n
   size_t bytes = 0;
+  // design points (kernels created from points): K's entries are generated
+  // from them in the products with K
+  double* pts = nullptr;   // n x dim, row-major
+  int dim = 0, kind = 0;
+  double bandwidth = 0.0;
 };
 
 struct cphifi_problem {
@@ -696,10 +701,131 @@ extern "C" int cphifi_kernel_destroy(cphifi_kernel* kern) {
                   (void*)kern->A1h, (void*)kern->A1l, (void*)kern->A2h, (void*)kern->A2l,
                   (void*)kern->oz1, (void*)kern->oz2, (void*)kern->oze})
     if (a) cudaFree(a);
+  if (kern->pts) cudaFree(kern->pts);
   ctx->in_use -= std::min(ctx->in_use, kern->bytes);
   cudaSetDevice(prev);
   delete kern;
   return CPHIFI_OK;
+}
+
+extern "C" int cphifi_kernel_create_points(cphifi_ctx* ctx, int64_t n, int32_t dim,
+                                           const double* x, int32_t kind, double bandwidth,
+                                           int mem, cphifi_kernel** out) {
+  if (!ctx || !out || !x) return CPHIFI_E_INVALID_ARG;
+  *out = nullptr;
+  if (n < 1 || n > kSymEigMaxN)
+    return fail(ctx, n < 1 ? CPHIFI_E_INVALID_ARG : CPHIFI_E_UNSUPPORTED,
+                "n must be in [1, " + std::to_string(kSymEigMaxN) + "] (device eigensolver)");
+  if (dim < 1 || dim > 64) return fail(ctx, CPHIFI_E_INVALID_ARG, "dim must be in [1, 64]");
+  if (kind != CPHIFI_KERNEL_GAUSSIAN && kind != CPHIFI_KERNEL_MATERN32)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown kernel kind");
+  if (!(bandwidth > 0.0) || !std::isfinite(bandwidth))
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "bandwidth must be finite and > 0");
+  if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
+  const size_t npts = (size_t)n * dim;
+  if (ctx->budget && ctx->in_use + (size_t)n * n * sizeof(double) + npts * sizeof(double) >
+                         ctx->budget)
+    return fail(ctx, CPHIFI_E_ADMISSION, "kernel matrix exceeds the HBM budget");
+  Enter guard(ctx);
+  cudaStream_t st = ctx->stream;
+  double* pts = nullptr;
+  double* K = nullptr;
+  int* err = nullptr;
+  int herr = 0;
+  auto bail = [&](int code, const std::string& m) {
+    cudaStreamSynchronize(st);
+    if (pts) cudaFree(pts);
+    if (K) cudaFree(K);
+    if (err) cudaFree(err);
+    return fail(ctx, code, m);
+  };
+  if (cudaMalloc(&pts, npts * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&K, (size_t)n * n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&err, sizeof(int)) != cudaSuccess)
+    return bail(CPHIFI_E_OOM, "cudaMalloc failed for the points or K");
+  if (upload(pts, x, npts * sizeof(double), mem, st) != cudaSuccess ||
+      cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess ||
+      launch_validate_dense(pts, (int64_t)npts, err, st) != cudaSuccess ||
+      cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return bail(CPHIFI_E_DEVICE, "uploading the points failed");
+  if (herr) return bail(CPHIFI_E_INVALID_ARG, "non-finite point coordinate");
+  if (launch_kpoints_build(pts, (int)n, dim, kind, bandwidth, K, st) != cudaSuccess)
+    return bail(CPHIFI_E_DEVICE, "building K from the points failed");
+  cphifi_kernel* kern = nullptr;
+  const int rc = cphifi_kernel_create(ctx, n, K, nullptr, nullptr, CPHIFI_MEM_DEVICE, &kern);
+  cudaFree(K);
+  K = nullptr;
+  cudaFree(err);
+  err = nullptr;
+  if (rc != CPHIFI_OK) {
+    cudaFree(pts);
+    return rc;
+  }
+  kern->pts = pts;
+  kern->dim = dim;
+  kern->kind = kind;
+  kern->bandwidth = bandwidth;
+  kern->bytes += npts * sizeof(double);
+  ctx->in_use += npts * sizeof(double);
+  *out = kern;
+  return CPHIFI_OK;
+}
+
+extern "C" int cphifi_kernel_apply(const cphifi_kernel* kern, int32_t precision, int32_t r,
+                                   const double* X, double* Y, int mem) {
+  if (!kern || !X || !Y) return CPHIFI_E_INVALID_ARG;
+  cphifi_ctx* ctx = kern->ctx;
+  if (r < 1 || r > kMaxRank) return fail(ctx, CPHIFI_E_INVALID_ARG, "r must be in [1, 64]");
+  if (precision != CPHIFI_FP64 && precision != CPHIFI_MIXED_FP32)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "precision must be FP64 or MIXED_FP32");
+  if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
+  Enter guard(ctx);
+  cudaStream_t st = ctx->stream;
+  const int n = kern->n;
+  const size_t nr = (size_t)n * r;
+  double *Xd = nullptr, *Yd = nullptr, *T = nullptr;
+  auto done = [&](int code, const char* m) {
+    cudaStreamSynchronize(st);
+    if (mem != CPHIFI_MEM_DEVICE) {
+      if (Xd) cudaFree(Xd);
+      if (Yd) cudaFree(Yd);
+    }
+    if (T) cudaFree(T);
+    return code == CPHIFI_OK ? code : fail(ctx, code, m);
+  };
+  if (mem == CPHIFI_MEM_DEVICE) {
+    Xd = const_cast<double*>(X);
+    Yd = Y;
+  } else if (cudaMalloc(&Xd, nr * sizeof(double)) != cudaSuccess ||
+             cudaMalloc(&Yd, nr * sizeof(double)) != cudaSuccess ||
+             cudaMemcpyAsync(Xd, X, nr * sizeof(double), cudaMemcpyHostToDevice, st) !=
+                 cudaSuccess) {
+    return done(CPHIFI_E_OOM, "staging X and Y failed");
+  }
+  cudaError_t e;
+  if (kern->pts) {
+    e = launch_kpoints_apply(precision == CPHIFI_FP64, kern->pts, n, kern->dim, kern->kind,
+                             kern->bandwidth, r, Xd, Yd, st);
+  } else {  // Y = U_K (D_K o (U_K' X)), FP64
+    e = cudaMalloc(&T, nr * sizeof(double));
+    if (e == cudaSuccess)
+      e = launch_gemm_skinny<double, double>(kern->UK64, n, false, nullptr, Xd, n, T, n,
+                                             (int64_t)nr, n, r, 1, nullptr, st);
+    if (e == cudaSuccess)
+      e = launch_gemm_skinny<double, double>(kern->UK64, n, true, kern->dK, T, n, Yd, n,
+                                             (int64_t)nr, n, r, 1, nullptr, st);
+  }
+  if (e == cudaSuccess && mem != CPHIFI_MEM_DEVICE)
+    e = cudaMemcpyAsync(Y, Yd, nr * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return done(CPHIFI_E_DEVICE, "kernel_apply failed");
+  }
+  return done(CPHIFI_OK, "");
 }
 
 extern "C" int cphifi_kernel_eig(const cphifi_kernel* kern, double* UK, double* DK, int mem) {
@@ -1966,6 +2092,10 @@ static int problem_rebuild(cphifi_problem* P) {
 // A_k = K W = U_K (D_K o (U_K' W)) in FP64 into P->Ak; W is a device n x r
 // array (column-major).
 static cudaError_t kernel_factor(cphifi_problem* P, const double* Wd) {
+  const cphifi_kernel* K = P->kern;
+  if (K->pts)  // K generated from the points, FP64
+    return launch_kpoints_apply(true, K->pts, P->n, K->dim, K->kind, K->bandwidth, P->r, Wd,
+                                P->Ak, P->st);
   Launcher L{P, P->st, nullptr};
   double* Cp = (double*)P->cpart;
   cudaError_t e = L.gemm64(false, nullptr, Wd, Cp, nullptr, 0);

@@ -264,6 +264,17 @@ cudaError_t launch_gram_apply_f64(const double* C, int n, int r, const double* X
                                   double* Y, int64_t yld, const DevScalars* skip,
                                   cudaStream_t st);
 
+// ------------------------------------------------------------ kpoints.cu ---
+// K(i, j) = k(x_i, x_j) from n points (row-major n x dim) for the Gaussian or
+// Matern-3/2 kernel (cphifi_kernel_kind) with the given bandwidth: the whole
+// K (FP64), or Y = K X (X, Y n x r column-major) with K's tiles generated on
+// the fly in FP64 or FP32.
+cudaError_t launch_kpoints_build(const double* pts, int n, int dim, int kind, double bandwidth,
+                                 double* K, cudaStream_t st);
+cudaError_t launch_kpoints_apply(bool fp64, const double* pts, int n, int dim, int kind,
+                                 double bandwidth, int r, const double* X, double* Y,
+                                 cudaStream_t st);
+
 // ---------------------------------------------------------------- eig.cu ---
 // FP64 symmetric eigendecomposition by parallel two-sided Jacobi (Eq. eigK):
 // A (n x n, column-major; the lower triangle is read) is overwritten by the
