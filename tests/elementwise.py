@@ -10,7 +10,14 @@ kernel index with no observations) must come back exactly zero.  Unlike a
 norm-wise check, a large error confined to a short row (an index with one or
 two observations) cannot hide under the norm of the long rows.
 """
+import json
+import os
+
 import numpy as np
+
+# With CPHIFI_PARITY_LOG set, every check appends {what, tol, worst err/bound}
+# to that file (one JSON object per line): the margins behind the tolerances.
+_LOG = os.environ.get("CPHIFI_PARITY_LOG")
 
 
 def check_rows(a, b, tol, what=""):
@@ -30,4 +37,9 @@ def check_rows(a, b, tol, what=""):
         raise AssertionError(f"{what}: {int(bad.sum())} elements out of bound (tol {tol}); "
                              f"first at ({i}, {j}): got {a[i, j]!r}, want {b[i, j]!r}, "
                              f"row max {rowmax[i, 0]!r}; worst err/bound {ratio:.3g}")
-    return float(np.max(err / np.maximum(np.abs(b) + rowmax, 1e-300))) if b.size else 0.0
+    worst = float(np.max(err / np.maximum(np.abs(b) + rowmax, 1e-300))) if b.size else 0.0
+    if _LOG:
+        with open(_LOG, "a") as fh:
+            fh.write(json.dumps({"what": what, "tol": tol, "worst_rel": worst,
+                                 "margin": (tol / worst) if worst > 0 else None}) + "\n")
+    return worst
