@@ -10,7 +10,9 @@
 // of Zhat: at q / n = 6250 observations per index and r = 40 that is 1.6k
 // instead of 250k values per index.
 //
-// gram_build_kernel: a segmented SYRK over the sorted observations.  The
+// gram_build_f32_tiled_kernel (FP32 blocks, r <= 48) is described where it is
+// defined.  gram_build_kernel (FP64-accurate blocks; FP32 for 48 < r <= 64):
+// a segmented SYRK over the sorted observations.  The
 // observations are cut into pieces (one kernel index, at most L of its
 // observations); a block takes a piece, stages each 32-observation tile of
 // Zhat in shared memory (observation-major) and accumulates its tile of the
@@ -30,6 +32,8 @@
 // symmetric) coalesced for k = 0..r-1.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "df.cuh"
 #include "launch.h"
@@ -203,6 +207,139 @@ __global__ void __launch_bounds__(256) gram_apply_kernel(const TC* __restrict__ 
   }
 }
 
+// The FP32 blocks as a register-tiled segmented SYRK.  A block takes a piece;
+// its 8 warps take the piece's 32-observation tiles in turn (warp w: tiles w,
+// w + 8, ...), each staging its own tile in its own region of shared memory
+// (observation-major rows, coalesced loads; only __syncwarp, so a warp
+// waiting for its loads does not hold up the others).  Within a warp, lane
+// u < U = G (G + 1) / 2 (G = RP / 8) owns the 8 x 8 tile (ti, tj), ti <= tj,
+// of the upper triangle: per observation 2 + 2 128-bit shared loads feed 64
+// multiply-adds.  At the end of the piece the 8 warps' partial blocks are
+// added in warp order through shared memory.
+template <int RP>
+__global__ void __launch_bounds__(256, 2) gram_build_f32_tiled_kernel(PieceList pl,
+                                                                      const int32_t* np_dev,
+                                                                      const float* __restrict__ zhi,
+                                                                      int r, float* partial,
+                                                                      float* C) {
+  // staged row pitch: 4 padding floats after every 32 columns, so that the
+  // 8-float column groups a phase of 8 lanes loads fall in distinct banks
+  constexpr int G = RP / 8, U = G * (G + 1) / 2, LD = RP + 4 * (RP / 32) + 8;
+  static_assert(U <= 32, "one warp holds the upper triangle's 8 x 8 tiles");
+  extern __shared__ __align__(16) float gsm[];  // 8 x 32 x LD staged values, then 8 x RP x RP
+  __shared__ int s_last;
+  const int npieces = min(pl.npieces, *np_dev);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // lane -> upper-triangle tile (ti, tj)
+  int ti = 0, tj = 0;
+  {
+    int u = lane, row = 0;
+    while (row < G && u >= G - row) { u -= G - row; ++row; }
+    ti = row;
+    tj = row + u;
+  }
+  const bool act = lane < U;
+  const int xo = ti * 8 + 4 * (ti >> 2), yo = tj * 8 + 4 * (tj >> 2);
+  const int64_t rr = (int64_t)r * r;
+  const int64_t ts = 64 * (int64_t)r;  // tile stride of the FP32 pair
+  float* zt = gsm + warp * 32 * LD;
+  for (int p = blockIdx.x; p < npieces; p += gridDim.x) {
+    const int seg = pl.seg[p];
+    const int b = pl.beg[p], e = pl.end[p];
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[a][c] = 0.f;
+    for (int t0 = (b & ~31) + 32 * warp; t0 < e; t0 += 256) {
+      // stage observations t0 .. t0 + 31 (lane = observation), zero outside
+      // [b, e) and j >= r
+      const int64_t g = (int64_t)t0 + lane;
+      const bool in = g >= b && g < e;
+      const float* src = zhi + (g >> 5) * ts + (g & 31);
+      __syncwarp();
+#pragma unroll 4
+      for (int j = 0; j < RP; ++j) {
+        const float v = (in && j < r) ? __ldcs(src + 32 * (int64_t)j) : 0.f;
+        zt[lane * LD + j + 4 * (j >> 5)] = v;
+      }
+      __syncwarp();
+      if (act) {
+#pragma unroll 2
+        for (int l = 0; l < 32; ++l) {
+          const float4 x0 = *reinterpret_cast<const float4*>(zt + l * LD + xo);
+          const float4 x1 = *reinterpret_cast<const float4*>(zt + l * LD + xo + 4);
+          const float4 y0 = *reinterpret_cast<const float4*>(zt + l * LD + yo);
+          const float4 y1 = *reinterpret_cast<const float4*>(zt + l * LD + yo + 4);
+          const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+          const float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+#pragma unroll
+          for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[a][c] = fmaf(xv[a], yv[c], acc[a][c]);
+        }
+      }
+    }
+    // the 8 warps' partial blocks, added in warp order
+    __syncthreads();
+    float* red = gsm;  // 8 x RP x RP
+    if (act) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          red[(warp * RP + ti * 8 + a) * RP + tj * 8 + c] = acc[a][c];
+    }
+    __syncthreads();
+    const int np = pl.seg_count[seg];
+    float* dst = np == 1 ? C + (int64_t)seg * rr : partial + (int64_t)p * rr;
+    for (int t = tid; t < RP * RP; t += 256) {
+      const int j = t / RP, k = t % RP;
+      if (j < r && k < r && (j >> 3) <= (k >> 3)) {
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) v += red[(w * RP + j) * RP + k];
+        // within a diagonal 8 x 8 tile both (j, k) and (k, j) were accumulated;
+        // the upper one is written to both places
+        if (j <= k) {
+          dst[(int64_t)j * r + k] = v;
+          dst[(int64_t)k * r + j] = v;
+        }
+      }
+    }
+    __syncthreads();  // red is read before the next piece stages over it
+    if (np > 1) {
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) s_last = atomicAdd(&pl.seg_ticket[seg], 1u) == (unsigned)(np - 1);
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        const int f = pl.seg_first[seg];
+        for (int64_t t = tid; t < rr; t += 256) {
+          float sum = 0.f;
+          for (int k = 0; k < np; ++k) sum += __ldcg(&partial[(int64_t)(f + k) * rr + t]);
+          C[(int64_t)seg * rr + t] = sum;
+        }
+        if (tid == 0) pl.seg_ticket[seg] = 0u;
+      }
+    }
+  }
+}
+
+template <int RP>
+cudaError_t build_f32_tiled(const PieceList& pl, const int32_t* np_dev, int grid,
+                            const float* zhi, int r, float* partial, float* C, cudaStream_t st) {
+  const size_t smem = (size_t)std::max(8 * 32 * (RP + 4 * (RP / 32) + 8), 8 * RP * RP) *
+                      sizeof(float);
+  const cudaError_t e = cudaFuncSetAttribute(gram_build_f32_tiled_kernel<RP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+  if (e != cudaSuccess) return e;
+  gram_build_f32_tiled_kernel<RP><<<grid, 256, smem, st>>>(pl, np_dev, zhi, r, partial, C);
+  return cudaGetLastError();
+}
+
 template <int MODE>
 cudaError_t build_by_rank(const PieceList& pl, const int32_t* np_dev, int grid, const float* zhi,
                           const double* z64, int r, typename GbTypes<MODE>::Out* partial,
@@ -226,6 +363,9 @@ cudaError_t launch_gram_build_f32(const PieceList& pl, const int32_t* np_dev, in
                                   const float* zhi, int r, float* partial, float* C,
                                   cudaStream_t st) {
   if (pl.npieces == 0) return cudaSuccess;
+  if (r <= 16) return build_f32_tiled<16>(pl, np_dev, grid, zhi, r, partial, C, st);
+  if (r <= 32) return build_f32_tiled<32>(pl, np_dev, grid, zhi, r, partial, C, st);
+  if (r <= 48) return build_f32_tiled<48>(pl, np_dev, grid, zhi, r, partial, C, st);
   return build_by_rank<GB_F32>(pl, np_dev, grid, zhi, nullptr, r, partial, C, nullptr, st);
 }
 
