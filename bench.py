@@ -269,15 +269,19 @@ def run_e2e(args, pkg, ctx, kern, p):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_iters = 0
+    host_setup_ms, host_solve_ms = [], []
     for _ in range(e2e_steps):
         Wo, st = pkg.solve(ctx, kern, fh, kh, oh, vh, r, p.lam, p.rho, TOL, 500,
                            precision=args.precision, sorted_obs=True, out=Wh)
         e2e_iters += st["iterations"]
+        host_setup_ms.append(st["setup_ms"])
+        host_solve_ms.append(st["solve_ms"])
     torch.cuda.synchronize()
     te2e = time.perf_counter() - t0
     h2d = q * 4 + q * 4 * p.oidx.shape[1] + q * 4 + sum(F.size * 8 for F in p.factors)
     return {"value": q * e2e_iters / te2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(n * r * 8), "solves_per_s": e2e_steps / te2e}
+            "d2h_bytes_per_step": int(n * r * 8), "solves_per_s": e2e_steps / te2e,
+            "host_create_ms": host_setup_ms, "host_solve_ms": host_solve_ms}
 
 
 class BatchInputs:

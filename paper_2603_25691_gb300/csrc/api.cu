@@ -67,6 +67,8 @@ struct cphifi_ctx {
   // block) overlap the observation passes on the main stream.
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // Host-to-device stream of the chunked observation upload (§ zhat_and_rhs).
+  cudaStream_t copy = nullptr;
   // Launch shapes per problem-size bucket (floor(log2 n), floor(log2 q), r),
   // set by cphifi_ctx_set_tuning (the autotuner); absent buckets use the
   // built-in heuristics.
@@ -488,6 +490,7 @@ extern "C" int cphifi_ctx_create(cphifi_ctx** out, int device, size_t hbm_budget
             cudaMallocHost(&ctx->h_scalars, sizeof(DevScalars)) == cudaSuccess;
   for (int k = 0; ok && k < 4; ++k) ok = cudaEventCreate(&ctx->phase[k]) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking) == cudaSuccess &&
        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) == cudaSuccess;
   cudaSetDevice(prev);
@@ -515,6 +518,10 @@ extern "C" int cphifi_ctx_destroy(cphifi_ctx* ctx) {
   if (ctx->side) {
     cudaStreamSynchronize(ctx->side);
     cudaStreamDestroy(ctx->side);
+  }
+  if (ctx->copy) {
+    cudaStreamSynchronize(ctx->copy);
+    cudaStreamDestroy(ctx->copy);
   }
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
@@ -842,6 +849,11 @@ extern "C" int cphifi_kernel_eig(const cphifi_kernel* kern, double* UK, double* 
 }
 
 // ----------------------------------------------------------- problem ------
+// The chunked upload of host observations (problem_create_on): sorted lists
+// of at least kPipelineMinQ observations, in kUploadChunks chunks.
+constexpr int64_t kPipelineMinQ = int64_t(1) << 20;
+constexpr int kUploadChunks = 8;
+
 // Warps of the gather-dot/scatter decomposition: at most two resident 8-warp
 // blocks per SM, and enough that no warp walks more than about 8 pieces
 // (every kernel index, even an empty one, is a piece: with n > q most pieces
@@ -934,20 +946,38 @@ static void problem_need(const cphifi_ctx* ctx, const cphifi_kernel* kern, int32
 // narrow window of the Zhat array, as the separate build does with its tile
 // chunks.  The decomposition's arrays come from `alloc` (the caller's
 // temporaries, free once the stream has passed this work).
+// The Zhat pass's decomposition: W2 ranges of L2 observations, 256 each; more
+// (and shorter) ranges when the kernel indices outnumber the observations,
+// so that no warp walks long runs of empty pieces (as in gds_warps).
+static void zhat_ranges(int num_sms, int64_t n, int64_t q, int64_t* W2, int64_t* L2) {
+  *W2 = std::max<int64_t>(
+      (q + 255) / 256, std::min<int64_t>(std::min<int64_t>((q + n + 7) / 8, q), (int64_t)num_sms * 16));
+  *L2 = (q + *W2 - 1) / *W2;
+}
+
+// Chunks of a pipelined upload: chunk c covers the ranges [c W2 / K, (c+1) W2 /
+// K), i.e. the observations [w0 L2, min(q, w1 L2)) -- pieces never cross a
+// range boundary, so a chunk's ranges read only that chunk's observations.
+static void zhat_chunk(int64_t W2, int64_t L2, int64_t q, int K, int c, int64_t* w0, int64_t* w1,
+                       int64_t* o0, int64_t* o1) {
+  *w0 = c * W2 / K;
+  *w1 = (c + 1) * W2 / K;
+  *o0 = std::min<int64_t>(q, *w0 * L2);
+  *o1 = std::min<int64_t>(q, *w1 * L2);
+}
+
+// With `chunk_ready` (K events), the pass runs as K launches, launch c after
+// event c (the upload of its chunk of other-mode indices and values).
 template <typename Alloc>
 static cudaError_t zhat_and_rhs(cphifi_problem* P, const int32_t* perm, const int32_t* oidx,
                                 const double* vals, const int* gate, Alloc alloc,
-                                cudaStream_t st) {
+                                cudaStream_t st,
+                                const std::vector<cudaEvent_t>* chunk_ready = nullptr) {
   const int n = P->n;
   const int64_t q = P->q;
   if (q == 0) return cudaMemsetAsync(P->Bm, 0, (size_t)n * P->r * sizeof(double), st);
-  // ranges of 256 observations; more (and shorter) ranges when the kernel
-  // indices outnumber the observations, so that no warp walks long runs of
-  // empty pieces (as in gds_warps)
-  const int64_t W2 = std::max<int64_t>(
-      (q + 255) / 256,
-      std::min<int64_t>(std::min<int64_t>((q + n + 7) / 8, q), (int64_t)P->ctx->num_sms * 16));
-  const int64_t L2 = (q + W2 - 1) / W2;
+  int64_t W2 = 0, L2 = 0;
+  zhat_ranges(P->ctx->num_sms, n, q, &W2, &L2);
   const int64_t np2 = (int64_t)n + W2 + 1;
   int32_t* cnt2 = (int32_t*)alloc((size_t)n * sizeof(int32_t));
   int32_t* first2 = (int32_t*)alloc((size_t)(n + 1) * sizeof(int32_t));
@@ -973,9 +1003,22 @@ static cudaError_t zhat_and_rhs(cphifi_problem* P, const int32_t* perm, const in
     return e;
   const PieceList pl2{pseg2, pbeg2, pend2, first2, cnt2, ticket2, wfirst2, (int)np2, (int)W2,
                       P->wctr};
-  return launch_zhat_mttkrp_fused(pl2, q, perm, oidx, P->d_other, P->fhl_dev, P->sizes_dev, P->r,
-                                  vals, P->zhi, P->z64, partial2, P->Bm, n, P->err, gate,
-                                  P->ctx->num_sms, st);
+  if (!chunk_ready)
+    return launch_zhat_mttkrp_fused(pl2, q, perm, oidx, P->d_other, P->fhl_dev, P->sizes_dev,
+                                    P->r, vals, P->zhi, P->z64, partial2, P->Bm, n, P->err, gate,
+                                    P->ctx->num_sms, st);
+  const int K = (int)chunk_ready->size();
+  for (int c = 0; c < K; ++c) {
+    int64_t w0, w1, o0, o1;
+    zhat_chunk(W2, L2, q, K, c, &w0, &w1, &o0, &o1);
+    if ((e = cudaStreamWaitEvent(st, (*chunk_ready)[c], 0)) != cudaSuccess ||
+        (e = launch_zhat_mttkrp_fused(pl2, q, perm, oidx, P->d_other, P->fhl_dev, P->sizes_dev,
+                                      P->r, vals, P->zhi, P->z64, partial2, P->Bm, n, P->err,
+                                      gate, P->ctx->num_sms, st, (int)w0, (int)w1)) !=
+            cudaSuccess)
+      return e;
+  }
+  return cudaSuccess;
 }
 
 // Problem creation on stream `st` (the context's stream for the public call, a
@@ -1057,9 +1100,15 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
     temps.push_back({p, got});
     return p;
   };
+  std::vector<cudaEvent_t>* chunk_events = nullptr;  // set below when the upload is chunked
   auto bail = [&](int code, const std::string& m) {
-    if (!async) cudaStreamSynchronize(ctx->side);
+    if (!async) {
+      cudaStreamSynchronize(ctx->side);
+      cudaStreamSynchronize(ctx->copy);
+    }
     cudaStreamSynchronize(st);
+    if (chunk_events)
+      for (auto e : *chunk_events) ctx->events_free.push_back(e);
     for (auto& t : temps) pool_release(ctx, t.first, t.second);
     free_problem(P);
     delete P;
@@ -1195,6 +1244,14 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
   const size_t vbytes = (size_t)q * (vals32 ? sizeof(float) : sizeof(double));
   if (!sorted_in && !keys) return bail(CPHIFI_E_OOM, "temporary allocation failed");
   const void* vsrc = vals;  // the values on the device, in the caller's type
+  // Host inputs of a large sorted problem, synchronous creation: the kernel
+  // indices go first (the row pointer and the pieces need them); the other
+  // indices and the values follow in kUploadChunks chunks on the copy stream,
+  // and the Zhat pass runs chunk by chunk behind them (the host link, ~210
+  // GB/s, then overlaps the pass instead of preceding it).
+  const bool pipelined = mem == CPHIFI_MEM_HOST && sorted_in && !async && q >= kPipelineMinQ;
+  std::vector<cudaEvent_t> chunk_ready;
+  chunk_events = &chunk_ready;
   if (mem == CPHIFI_MEM_DEVICE) {
     oidx_d = (int32_t*)oidx;
     kidx_d = kidx;
@@ -1203,19 +1260,46 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
     void* v = tmp_alloc(vbytes);
     int32_t* k = (int32_t*)tmp_alloc((size_t)q * sizeof(int32_t));
     if (!oidx_d || !v || !k) return bail(CPHIFI_E_OOM, "temporary allocation failed");
-    PCK(upload(oidx_d, oidx, (size_t)q * d_other * sizeof(int32_t), mem, st));
-    PCK(upload(v, vals, vbytes, mem, st));
     PCK(upload(k, kidx, (size_t)q * sizeof(int32_t), mem, st));
+    if (!pipelined) {
+      PCK(upload(oidx_d, oidx, (size_t)q * d_other * sizeof(int32_t), mem, st));
+      PCK(upload(v, vals, vbytes, mem, st));
+    }
     vsrc = v;
     kidx_d = k;
   }
+  double* v64 = nullptr;
   if (vals32 && q > 0) {  // FP32 values are widened to FP64 once, on the device
-    double* v64 = (double*)tmp_alloc((size_t)q * sizeof(double));
+    v64 = (double*)tmp_alloc((size_t)q * sizeof(double));
     if (!v64) return bail(CPHIFI_E_OOM, "temporary allocation failed");
-    PCK(launch_convert<float, double>((const float*)vsrc, v64, q, st));
+    if (!pipelined) PCK(launch_convert<float, double>((const float*)vsrc, v64, q, st));
     vals_d = v64;
   } else {
     vals_d = (const double*)vsrc;
+  }
+  if (pipelined) {
+    int64_t W2 = 0, L2 = 0;
+    zhat_ranges(ctx->num_sms, n, q, &W2, &L2);
+    cudaStream_t cs = ctx->copy;
+    PCK(cudaEventRecord(ctx->ev_in, st));  // after the caller's work on its stream
+    PCK(cudaStreamWaitEvent(cs, ctx->ev_in, 0));
+    const size_t es = vals32 ? sizeof(float) : sizeof(double);
+    for (int c = 0; c < kUploadChunks; ++c) {
+      int64_t w0, w1, o0, o1;
+      zhat_chunk(W2, L2, q, kUploadChunks, c, &w0, &w1, &o0, &o1);
+      cudaEvent_t ev = nullptr;
+      PCK(event_get(ctx, &ev));
+      chunk_ready.push_back(ev);
+      if (o1 > o0) {
+        PCK(upload(oidx_d + o0 * d_other, oidx + o0 * d_other,
+                   (size_t)(o1 - o0) * d_other * sizeof(int32_t), mem, cs));
+        PCK(upload((char*)vsrc + o0 * es, (const char*)vals + o0 * es, (size_t)(o1 - o0) * es,
+                   mem, cs));
+        if (vals32)
+          PCK(launch_convert<float, double>((const float*)vsrc + o0, v64 + o0, o1 - o0, cs));
+      }
+      PCK(cudaEventRecord(ev, cs));
+    }
   }
   // kernel indices here (the sort and the pieces use them); the other
   // indices and the values are checked by the Zhat build below
@@ -1256,7 +1340,8 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
   // ---- Zhat and the right-hand side MTTKRP
   {
     const cudaError_t ez = zhat_and_rhs(P, (flags & CPHIFI_OBS_SORTED) ? nullptr : P->perm,
-                                        oidx_d, vals_d, gate, tmp_alloc, st);
+                                        oidx_d, vals_d, gate, tmp_alloc, st,
+                                        pipelined ? &chunk_ready : nullptr);
     if (ez == cudaErrorMemoryAllocation) return bail(CPHIFI_E_OOM, "temporary allocation failed");
     PCK(ez);
   }
@@ -1284,6 +1369,8 @@ static int problem_create_on(cphifi_ctx* ctx, const cphifi_kernel* kern, int32_t
   } else {
     PCK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     PCK(cudaStreamSynchronize(st));
+    for (auto e : chunk_ready) ctx->events_free.push_back(e);
+    chunk_ready.clear();
     if (herr) return bail(CPHIFI_E_INVALID_ARG, input_error_text(herr));
     // the temporaries are free to reuse only after the work (synchronized above)
     for (auto& t : temps) pool_release(ctx, t.first, t.second);

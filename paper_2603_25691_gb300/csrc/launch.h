@@ -102,13 +102,14 @@ cudaError_t launch_gds_df(const PieceList& pl, const float* zhi, const float* zl
 // decomposition; pl.wctr required).  perm = NULL: input already sorted.  B is
 // written for every kernel index (zero rows for empty ones); bad other-mode
 // indices set *err bit 1, non-finite values bit 2.  partial: pl.npieces x 64
-// doubles.
+// doubles.  [w_begin, w_end) restricts a launch to those virtual warps (-1:
+// all), so that the pass can follow a chunked upload of the observations.
 cudaError_t launch_zhat_mttkrp_fused(const PieceList& pl, int64_t q, const int32_t* perm,
                                      const int32_t* oidx, int d_other, const float* const* fhl,
                                      const int64_t* sizes_dev, int r, const double* vals,
                                      float* zhi, double* z64, double* partial, double* B,
                                      int64_t ldb, int* err, const int* gate, int num_sms,
-                                     cudaStream_t st);
+                                     cudaStream_t st, int w_begin = 0, int w_end = -1);
 
 // -------------------------------------------------------------- dense.cu ---
 // Skinny product C = op(A) diag(s) B for A n x n (op = identity when a_trans

@@ -688,7 +688,8 @@ zhat_mttkrp_kernel(PieceList pl, int64_t q, const int32_t* __restrict__ perm,
                    const float* const* __restrict__ fhl, const int64_t* __restrict__ sizes, int r,
                    float* __restrict__ zhi, double* __restrict__ z64,
                    const double* __restrict__ vals, double* __restrict__ partial,
-                   double* __restrict__ B, int64_t ldb, int* err, const int* gate) {
+                   double* __restrict__ B, int64_t ldb, int* err, const int* gate, int w_begin,
+                   int w_end) {
   if (gate && *gate) return;  // invalid input found earlier: touch nothing
   __shared__ df bacc[8][64];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -705,7 +706,8 @@ zhat_mttkrp_kernel(PieceList pl, int64_t q, const int32_t* __restrict__ perm,
     if (lane == 0) v = atomicAdd(&pl.wctr[0], 1u);
     return (int)__shfl_sync(0xffffffffu, v, 0);
   };
-  for (int w = draw(); w < pl.nwarps; w = draw()) {
+  // this launch's virtual warps: [w_begin, w_end) of the decomposition
+  for (int w = w_begin + draw(); w < w_end; w = w_begin + draw()) {
     const int p_end = pl.warp_first[w + 1];
     for (int p = pl.warp_first[w]; p < p_end; ++p) {
       const int seg = pl.seg[p];
@@ -831,24 +833,26 @@ cudaError_t launch_zhat_mttkrp_fused(const PieceList& pl, int64_t q, const int32
                                      const int64_t* sizes_dev, int r, const double* vals,
                                      float* zhi, double* z64, double* partial, double* B,
                                      int64_t ldb, int* err, const int* gate, int num_sms,
-                                     cudaStream_t st) {
-  if (q == 0 || pl.npieces == 0 || pl.nwarps == 0) return cudaSuccess;
-  if (d_other < 1 || d_other > 16 || r < 1 || r > 64 || (!zhi && !z64) || !pl.wctr)
+                                     cudaStream_t st, int w_begin, int w_end) {
+  if (w_end < 0) w_end = pl.nwarps;
+  if (q == 0 || pl.npieces == 0 || pl.nwarps == 0 || w_end <= w_begin) return cudaSuccess;
+  if (d_other < 1 || d_other > 16 || r < 1 || r > 64 || (!zhi && !z64) || !pl.wctr ||
+      w_begin < 0 || w_end > pl.nwarps)
     return cudaErrorInvalidValue;
   // one resident wave (4 blocks of 8 warps per SM); the warps draw the ranges
-  const int blocks = (int)std::min<int64_t>((pl.nwarps + 7) / 8, (int64_t)num_sms * 4);
+  const int blocks = (int)std::min<int64_t>((w_end - w_begin + 7) / 8, (int64_t)num_sms * 4);
   if (zhi && z64)
     zhat_mttkrp_kernel<true, true><<<blocks, 256, 0, st>>>(pl, q, perm, oidx, d_other, fhl,
                                                            sizes_dev, r, zhi, z64, vals, partial,
-                                                           B, ldb, err, gate);
+                                                           B, ldb, err, gate, w_begin, w_end);
   else if (zhi)
     zhat_mttkrp_kernel<true, false><<<blocks, 256, 0, st>>>(pl, q, perm, oidx, d_other, fhl,
                                                             sizes_dev, r, zhi, z64, vals, partial,
-                                                            B, ldb, err, gate);
+                                                            B, ldb, err, gate, w_begin, w_end);
   else
     zhat_mttkrp_kernel<false, true><<<blocks, 256, 0, st>>>(pl, q, perm, oidx, d_other, fhl,
                                                             sizes_dev, r, zhi, z64, vals, partial,
-                                                            B, ldb, err, gate);
+                                                            B, ldb, err, gate, w_begin, w_end);
   return cudaGetLastError();
 }
 

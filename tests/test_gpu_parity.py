@@ -281,6 +281,36 @@ def test_fp32_values_equal_the_same_values_in_fp64(ctx, pkg):
     kern.close()
 
 
+@pytest.mark.parametrize("vals32", [False, True])
+def test_chunked_host_upload_equals_device_inputs(ctx, pkg, vals32):
+    # Sorted host inputs with q >= 2^20 are uploaded in chunks that the Zhat
+    # pass follows; the pass does the same arithmetic per piece, so the solve
+    # must give the same bits as from device-resident inputs.
+    import torch
+    p = synth.planted_problem(17, 600, (60, 70), 1_500_000, 16, bandwidth=0.1, lam=1e-4,
+                              rho=1e-6)
+    vals = p.vals.astype(np.float32) if vals32 else p.vals
+    dK, UK = eigh_cached(p.K)
+    kern = ctx.kernel_create(p.n, UK, dK)
+    dev = torch.device("cuda", 0)
+    fac = [torch.from_numpy(np.asfortranarray(F).ravel(order="F")).to(dev) for F in p.factors]
+    outs = []
+    for inputs in ("host", "device"):
+        if inputs == "host":
+            args = (p.factors, p.kidx, p.oidx, vals)
+        else:
+            args = (fac, torch.from_numpy(p.kidx).to(dev),
+                    torch.from_numpy(np.ascontiguousarray(p.oidx).ravel()).to(dev),
+                    torch.from_numpy(vals).to(dev))
+        out = torch.empty(p.n * p.r, dtype=torch.float64, device=dev)
+        W, st = pkg.solve(ctx, kern, *args, p.r, p.lam, p.rho, 1e-8, 500,
+                          precision="mixed_fp32", sorted_obs=True, out=out)
+        outs.append((out.cpu().numpy(), st["iterations"]))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
+    kern.close()
+
+
 def test_deterministic(ctx, pkg):
     p = synth.planted_problem(9, 70, (15, 16), 8000, 12, bandwidth=0.1, lam=1e-4, rho=1e-6)
     kern, prob = make(ctx, pkg, p)
