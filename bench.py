@@ -356,13 +356,42 @@ def _timed_batch(pkg, ctx, items, precision):
             "iterations": int(sum(st["iterations"] for st in stats))}
 
 
+def _timed_persistent(pkg, ctx, items):
+    """cphifi_solve_batch over every item: the problems created on the
+    library's streams, then one persistent launch for all solves.  Host clock
+    around the call (it returns with the results written)."""
+    import torch
+    probs = [dict(kernel=it["kern"], factors=it["f"], kidx=it["k"], oidx=it["o"], vals=it["v"],
+                  r=it["r"], sorted_obs=True, out=it["W"]) for it in items]
+    p0 = items[0]["p"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, stats, info = pkg.solve_batch(ctx, probs, p0.lam, p0.rho, TOL, max_iter=MAX_ITER_BATCH)
+    elapsed = time.perf_counter() - t0
+    lat = sorted(st["iter_ms"] for st in stats)  # launch start -> each solve's completion
+    pct = lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))]
+    obs_iter = sum(it["q"] * st["iterations"] for it, st in zip(items, stats))
+    launches = sum(st["setup_launches"] for st in stats) + 1
+    return {"elapsed_ms": 1e3 * elapsed, "solves_per_s": len(items) / elapsed,
+            "obs_iter_per_s": obs_iter / elapsed,
+            "converged": sum(1 for st in stats if st["status"] == 0),
+            "max_rel_residual": max(st["rel_residual"] for st in stats),
+            "kernel_ms": info["kernel_ms"], "create_ms": info["create_ms"],
+            "solves_per_s_kernel": len(items) / (1e-3 * info["kernel_ms"]),
+            "completion_in_launch_ms": {"p50": pct(0.5), "p99": pct(0.99), "max": lat[-1]},
+            "tiles": info["tiles"], "blocks": info["blocks"], "timed_out": info["timed_out"],
+            "gpu_launches": int(launches), "launches_per_solve": launches / len(items),
+            "iterations": int(sum(st["iterations"] for st in stats))}
+
+
 def run_batch(args, pkg, ctx, dev, seed):
-    """All subproblems submitted at once; every request's PCG runs on its own
-    stream, its iteration loop on the device (one graph per solve with a
-    conditional WHILE node), as slots and HBM free up.  Timed on the host
-    clock from the first submit to the last completion, with the device idle
-    on both sides; then again after the autotuner has chosen the launch
-    shapes of the batch's size buckets (untimed)."""
+    """All subproblems at once, two ways.  (1) Submitted: every request's PCG
+    runs on its own stream, each chunk of iterations replayed from a CUDA
+    graph, as slots and HBM free up; timed on the host clock from the first
+    submit to the last completion, with the device idle on both sides, then
+    again after the autotuner has chosen the launch shapes of the batch's
+    size buckets (untimed).  (2) Persistent: cphifi_solve_batch, every solve
+    in one kernel launch (best of two calls)."""
     import torch
     import synth
     B = BatchInputs(pkg, ctx, dev, synth.batch_specs(seed, args.batch))
@@ -385,6 +414,11 @@ def run_batch(args, pkg, ctx, dev, seed):
             submit_item(pkg, ctx, it, args.precision).wait()
         tuned = _timed_batch(pkg, ctx, items, args.precision)
         tuned.update({"buckets_tuned": nb, "tuning_s": tune_s})
+    persistent = None
+    for _ in range(2):
+        run = _timed_persistent(pkg, ctx, items)
+        if persistent is None or run["elapsed_ms"] < persistent["elapsed_ms"]:
+            persistent = run
     # The plain FP64 GPU path, one subproblem at a time, same inputs and tolerance.
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -398,10 +432,12 @@ def run_batch(args, pkg, ctx, dev, seed):
     torch.cuda.synchronize()
     t64 = time.perf_counter() - t1
     best = tuned if tuned and tuned["elapsed_ms"] < untuned["elapsed_ms"] else untuned
+    if persistent["converged"] == len(items) and persistent["elapsed_ms"] < best["elapsed_ms"]:
+        best = persistent
     out = {"workload": f"c4_batch_{len(items)}_uneven", "precision": args.precision, "tol": TOL,
            "requests": len(items), "sum_q": int(sum(it["q"] for it in items)),
            "n_grid": list(synth.BATCH_N_GRID), "kernels": len(B.kerns), **untuned,
-           "autotuned": tuned,
+           "autotuned": tuned, "persistent": persistent,
            "fp64_one_at_a_time": {"solves_per_s": len(items) / t64, "elapsed_ms": 1e3 * t64,
                                   "iterations": it64},
            "speedup_vs_fp64_one_at_a_time": t64 / (best["elapsed_ms"] / 1e3),

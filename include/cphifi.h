@@ -351,6 +351,62 @@ int cphifi_poll(cphifi_ctx* ctx, int32_t* n_active, int32_t* n_pending,
 int cphifi_wait(cphifi_ctx* ctx, cphifi_ticket ticket, int64_t timeout_us,
                 cphifi_stats* stats);
 
+/* ---- many solves in one persistent launch ---------------------------------
+ * cphifi_solve_batch solves `count` independent kernel-mode subproblems
+ * (§4.4), each given as cphifi_solve's arguments, with the mixed-precision
+ * PCG (params->precision must be CPHIFI_MIXED_FP32, params->gram 0; zero
+ * start; one params for all items).  The problems are created first, on
+ * streams of the context, without host waits (as cphifi_submit does); then
+ * ONE kernel launch runs every solve.  In it each solve is a chain of phases
+ * (set-up, right-hand side, restart, the five phases of a PCG iteration, the
+ * four of the FP64-accurate true residual every k_replace iterations, the
+ * final W = U_K Wbar), each phase a set of tiles; the blocks claim tiles
+ * from a device work list (of the solves with an unclaimed tile, the one
+ * that has run the most iterations, the one with the least work per
+ * iteration among equals), and the block that finishes the last tile of a
+ * phase takes that solve's decisions (step sizes, convergence, restart) on
+ * the device and runs a tile of the next phase itself.  A solve's result is
+ * the same, bit for bit, whatever else is in the batch.  The kernel's only
+ * wait is that of its idle blocks; it ends with CPHIFI_E_TIMEOUT for the
+ * unfinished solves if no tile finished anywhere for 4 seconds.
+ * items[k].W_out is n_k x r_k, column-major, in memory kind `mem` (the
+ * other pointers as in cphifi_solve, memory kind `mem` too); count <= 65535.
+ * stats: NULL or
+ * `count` entries; solve_ms is the persistent launch's device time and
+ * setup_ms the host time of all creations (the same in every entry), iter_ms
+ * the device time from the launch's start to this solve's completion.
+ * info (may be NULL) describes the launch.  Returns CPHIFI_OK when every
+ * solve converged, else the status of the first item (in the order given)
+ * that did not; argument and creation errors return before any launch and
+ * name the item in cphifi_last_error.  No counterpart in the paper. */
+typedef struct cphifi_batch_item {
+  const cphifi_kernel* kern;
+  int32_t d_other;
+  int32_t r;
+  const int64_t* other_sizes;
+  const double* const* factors;
+  int64_t q;
+  const int32_t* kidx;
+  const int32_t* oidx;
+  const void* vals;
+  uint32_t flags;     /* as in cphifi_problem_create                          */
+  uint32_t reserved;
+  double* W_out;
+} cphifi_batch_item;
+
+typedef struct cphifi_batch_info {
+  double create_ms;   /* host time of queueing every problem's creation      */
+  double kernel_ms;   /* device time of the persistent launch                */
+  double total_ms;    /* the whole call                                       */
+  int64_t tiles;      /* tiles the launch ran                                 */
+  int32_t blocks;     /* blocks of the persistent launch                      */
+  int32_t timed_out;  /* 1: the launch's bounded wait expired                 */
+} cphifi_batch_info;
+
+int cphifi_solve_batch(cphifi_ctx* ctx, int32_t count, const cphifi_batch_item* items,
+                       const cphifi_params* params, int mem, cphifi_stats* stats,
+                       cphifi_batch_info* info);
+
 /* ---- the steps of the path, one call each (for checking each step) ------
  * All n x r arrays are column-major in memory kind `mem`. */
 

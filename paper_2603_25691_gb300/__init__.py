@@ -83,6 +83,23 @@ class Tuning(ctypes.Structure):
                 ("split64", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("kern", ctypes.c_void_p), ("d_other", ctypes.c_int32), ("r", ctypes.c_int32),
+                ("other_sizes", ctypes.c_void_p), ("factors", ctypes.c_void_p),
+                ("q", ctypes.c_int64), ("kidx", ctypes.c_void_p), ("oidx", ctypes.c_void_p),
+                ("vals", ctypes.c_void_p), ("flags", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("W_out", ctypes.c_void_p)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("create_ms", ctypes.c_double), ("kernel_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double), ("tiles", ctypes.c_int64),
+                ("blocks", ctypes.c_int32), ("timed_out", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class CphifiError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"cphifi status {status}: {msg}")
@@ -149,6 +166,9 @@ _SIG = {
                                    ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32,
                                    ctypes.POINTER(ctypes.c_int32)]),
     "cphifi_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(Stats)]),
+    "cphifi_solve_batch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(BatchItem),
+                                          ctypes.POINTER(Params), ctypes.c_int,
+                                          ctypes.POINTER(Stats), ctypes.POINTER(BatchInfo)]),
     "cphifi_gds_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P,
                                           ctypes.c_int64, _P, _P, _P,
                                           ctypes.POINTER(ctypes.c_char_p)]),
@@ -682,6 +702,60 @@ def submit(ctx: Context, kernel: Kernel, factors, kidx, oidx, vals, r: int, lam:
     _check(ctx.h, rc, "submit")
     # the request keeps its buffers and the kernel handle alive until wait()
     return Request(ctx, t.value, (kernel, fb, k, o, v, wb, w0, sizes_arr, fptrs, prm), wb.obj)
+
+
+def solve_batch(ctx: Context, problems, lam: float, rho: float, tol: float, max_iter: int = 1000,
+                k_replace=10, precision="mixed_fp32"):
+    """cphifi_solve_batch: many mixed-FP32 solves in one persistent launch.
+
+    problems: a list of dicts with keys kernel, factors, kidx, oidx, vals, r
+    and optionally sorted_obs and out (W's storage); all host arrays, or all
+    device tensors.
+    Returns (list of W, list of stats dicts, launch info dict); a solve that
+    did not converge has its status in its stats."""
+    prm = make_params(lam, rho, tol, max_iter, precision, k_replace, 8, False, 0)
+    items = (BatchItem * len(problems))()
+    keep, outs = [], []
+    mem = None
+    for k, pb in enumerate(problems):
+        r = int(pb["r"])
+        fb, sizes = _factor_bufs(pb["factors"], r)
+        kb, ob, vb = _obs_bufs(pb["kidx"], pb["oidx"], pb["vals"])
+        if mem is None:
+            mem = kb.mem
+        elif kb.mem != mem:
+            raise ValueError("every problem of a batch must use the same memory kind")
+        n = pb["kernel"].n
+        out = pb.get("out")
+        if out is None and mem == MEM_HOST:
+            out = np.empty((n, r), order="F")
+        elif out is None:
+            import torch
+            out = torch.empty(n * r, dtype=torch.float64, device="cuda")
+        wb = _Buf(out, np.float64, colmajor=not _is_torch(out))
+        sizes_arr = (ctypes.c_int64 * len(sizes))(*sizes)
+        fptrs = (ctypes.c_void_p * len(fb))(*[b.ptr for b in fb])
+        flags = (OBS_SORTED if pb.get("sorted_obs") else 0) | _vals_flag(pb["vals"])
+        it = items[k]
+        it.kern = pb["kernel"].h
+        it.d_other = len(fb)
+        it.r = r
+        it.other_sizes = ctypes.cast(sizes_arr, ctypes.c_void_p)
+        it.factors = ctypes.cast(fptrs, ctypes.c_void_p)
+        it.q = kb.numel
+        it.kidx, it.oidx, it.vals = kb.ptr, ob.ptr, vb.ptr
+        it.flags = flags
+        it.W_out = wb.ptr
+        keep.append((fb, kb, ob, vb, wb, sizes_arr, fptrs))
+        outs.append(wb.obj)
+    stats = (Stats * max(1, len(problems)))()
+    info = BatchInfo()
+    rc = lib().cphifi_solve_batch(ctx.h, len(problems), items, ctypes.byref(prm),
+                                  MEM_HOST if mem is None else mem, stats, ctypes.byref(info))
+    if rc != OK and info.blocks == 0:  # nothing launched: an argument or creation error
+        _check(ctx.h, rc, "solve_batch")
+    del keep
+    return outs, [stats[k].as_dict() for k in range(len(problems))], info.as_dict()
 
 
 def gds_noalloc(n: int, r: int, q: int, row_ptr, zhat, ldz: int, Xhat, Y1, stream=None):

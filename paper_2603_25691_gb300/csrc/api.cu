@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <numeric>
 #include <deque>
 #include <map>
 #include <memory>
@@ -83,6 +84,10 @@ struct cphifi_ctx {
   std::vector<Request*> active;
   std::map<uint64_t, Request*> requests;
   std::vector<uint64_t> done_unreported;  // completed, not yet listed by poll
+  // Streams of the batch call's problem creations (created on first use) and
+  // the events timing its persistent launch.
+  std::vector<cudaStream_t> batch_streams;
+  cudaEvent_t batch_ev[2] = {nullptr, nullptr};
 };
 
 struct cphifi_kernel {
@@ -523,6 +528,12 @@ extern "C" int cphifi_ctx_destroy(cphifi_ctx* ctx) {
     cudaStreamSynchronize(ctx->copy);
     cudaStreamDestroy(ctx->copy);
   }
+  for (auto bs : ctx->batch_streams) {
+    cudaStreamSynchronize(bs);
+    cudaStreamDestroy(bs);
+  }
+  for (auto e : ctx->batch_ev)
+    if (e) cudaEventDestroy(e);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
   if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
@@ -2647,6 +2658,279 @@ extern "C" int cphifi_wait(cphifi_ctx* ctx, cphifi_ticket ticket, int64_t timeou
   ctx->requests.erase(it);
   delete R;
   return status;
+}
+
+// ------------------------------------------- one persistent launch -------
+// cphifi_solve_batch: every problem created without host waits on the
+// context's batch streams, then one launch of the persistent kernel
+// (batch.cu) over all solves.  The descriptors are ordered by the work of one
+// PCG iteration (2 n^2 r for the two products, 2 q r for the gather-dot/
+// scatter), smallest first: idle blocks serve the first request with a free
+// tile, so the short phases of small requests (whose chains are as long as
+// the large ones' and often longer) never queue behind the many tiles of a
+// large request, and the large requests take the blocks left over.
+constexpr int kBatchStreams = 16;
+constexpr long long kBatchTimeoutNs = 4000000000ll;  // no tile finished anywhere for 4 s
+
+// k-range splits of a batch request's products: chunks of about 64 (FP32)
+// and 32 (double-float) columns of U_K (a few k slabs per tile: the tiles
+// are bound by the latency of their loads, and short ones run side by
+// side), at most 64 splits, or the tuning table's splits.
+static void batch_splits(const cphifi_ctx* ctx, int n, int64_t q, int r, BatchReq* d) {
+  cphifi_tuning t{};
+  auto it = ctx->tuning.find(std::make_tuple(floor_log2(n), floor_log2(std::max<int64_t>(q, 1)), r));
+  if (it != ctx->tuning.end()) t = it->second;
+  auto chunk = [n](int tuned, int target, int cap, int align) {
+    int s = tuned > 0 ? tuned : (n + target - 1) / target;
+    s = std::max(1, std::min(s, cap));
+    int kc = (n + s - 1) / s;
+    kc = (kc + align - 1) / align * align;
+    return kc;
+  };
+  d->kc32 = chunk(t.split32, 64, 32, 16);
+  d->s32 = (n + d->kc32 - 1) / d->kc32;
+  d->kcdf = chunk(t.split_wide, 32, 32, 16);
+  d->sdf = (n + d->kcdf - 1) / d->kcdf;
+}
+
+extern "C" int cphifi_solve_batch(cphifi_ctx* ctx, int32_t count, const cphifi_batch_item* items,
+                                  const cphifi_params* prm, int mem, cphifi_stats* stats,
+                                  cphifi_batch_info* info) {
+  if (!ctx) return CPHIFI_E_INVALID_ARG;
+  if (count < 0 || count > 65535 || (count > 0 && !items))
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "batch: count not in [0, 65535] or null items");
+  int rc = check_params(ctx, prm);
+  if (rc != CPHIFI_OK) return rc;
+  if (prm->precision != CPHIFI_MIXED_FP32)
+    return fail(ctx, CPHIFI_E_UNSUPPORTED, "batch: the persistent launch runs mixed FP32 solves");
+  if (prm->gram != 0)
+    return fail(ctx, CPHIFI_E_UNSUPPORTED, "batch: the persistent launch streams Zhat (gram 0)");
+  if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");
+  if (info) memset(info, 0, sizeof(*info));
+  if (count == 0) return CPHIFI_OK;
+  for (int k = 0; k < count; ++k)
+    if (!items[k].W_out)
+      return fail(ctx, CPHIFI_E_INVALID_ARG, "batch item " + std::to_string(k) + ": null W_out");
+  Enter guard(ctx);
+  const auto t0 = std::chrono::steady_clock::now();
+  while ((int)ctx->batch_streams.size() < std::min(count, kBatchStreams)) {
+    cudaStream_t bs = nullptr;
+    CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+    ctx->batch_streams.push_back(bs);
+  }
+  for (auto& e : ctx->batch_ev)
+    if (!e) CK(cudaEventCreate(&e));
+  const int nstreams = (int)ctx->batch_streams.size();
+  std::vector<cphifi_problem*> P(count, nullptr);
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  auto cleanup = [&]() {
+    for (auto* p : P)
+      if (p) cphifi_problem_destroy(p);
+    if (ws) {
+      cudaStreamSynchronize(ctx->stream);
+      pool_release(ctx, ws, ws_bytes);
+      ctx->in_use -= ws_bytes;
+    }
+  };
+  // 1. the problems, on the batch streams, in order after the caller's work
+  CK(cudaEventRecord(ctx->ev_in, ctx->stream));
+  for (auto bs : ctx->batch_streams) CK(cudaStreamWaitEvent(bs, ctx->ev_in, 0));
+  for (int k = 0; k < count; ++k) {
+    const cphifi_batch_item& it = items[k];
+    rc = problem_create_on(ctx, it.kern, it.d_other, it.other_sizes, it.factors, it.r, it.q,
+                           it.kidx, it.oidx, it.vals, it.flags | CPHIFI_NEED_LOWP, mem,
+                           ctx->batch_streams[k % nstreams], /*async=*/true, &P[k]);
+    if (rc == CPHIFI_OK) rc = solve_prepare(P[k], prm, it.W_out, mem);
+    if (rc != CPHIFI_OK) {
+      const std::string why = ctx->last_error;
+      cleanup();
+      return fail(ctx, rc, "batch item " + std::to_string(k) + ": " + why);
+    }
+  }
+  const double create_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  // 2. descriptors in descending order of one iteration's work
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  auto work = [&](int k) {
+    const double n = P[k]->n, r = P[k]->r;
+    return 2.0 * n * n * r + 2.0 * (double)P[k]->q * r;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) < work(b); });
+  std::vector<BatchReq> reqs(count);
+  std::vector<size_t> cp_off(count), red_off(count), p2_off(count);
+  size_t bytes = 0;
+  auto take = [&bytes](size_t b) {
+    const size_t o = bytes;
+    bytes += (b + 255) / 256 * 256;
+    return o;
+  };
+  const size_t off_reqs = take(sizeof(BatchReq) * count);
+  const size_t off_state = take(sizeof(BatchState) * count);
+  const size_t off_scal = take(sizeof(DevScalars) * count);
+  const size_t off_ctl = take(sizeof(BatchCtl));
+  for (int j = 0; j < count; ++j) {
+    cphifi_problem* p = P[order[j]];
+    BatchReq& d = reqs[j];
+    d.n = p->n;
+    d.r = p->r;
+    batch_splits(ctx, p->n, p->q, p->r, &d);
+    const size_t nr = (size_t)p->n * p->r;
+    cp_off[j] = take(std::max((size_t)d.s32 * sizeof(float), (size_t)d.sdf * sizeof(double)) * nr);
+    p2_off[j] = take(sizeof(double) * nr);
+    red_off[j] = take(2 * sizeof(double) * (size_t)((p->n + kBatchRows - 1) / kBatchRows));
+  }
+  {
+    size_t got = 0;
+    CK(pool_alloc(ctx, bytes, &ws, &got));
+    ws_bytes = got;
+    ctx->in_use += got;
+  }
+  char* wb = static_cast<char*>(ws);
+  std::vector<BatchState> st0(count);
+  std::vector<DevScalars> sc0(count);
+  for (int j = 0; j < count; ++j) {
+    const int k = order[j];
+    cphifi_problem* p = P[k];
+    BatchReq& d = reqs[j];
+    d.max_iter = prm->max_iter;
+    d.k_replace = std::max(1, prm->k_replace);
+    d.tol2 = prm->tol * prm->tol;
+    d.lam = prm->lambda;
+    d.rho = prm->rho;
+    d.gamma = p->gamma;
+    d.UKhi = p->kern->UK32;
+    d.UKlo = p->kern->UKlo;
+    d.dK = p->kern->dK;
+    d.dV = p->dV;
+    d.UV32 = p->UV32;
+    d.pl = PieceList{p->pseg, p->pbeg, p->pend, p->seg_first, p->seg_count, p->seg_ticket,
+                     p->warp_first, p->npieces, p->nwarps, nullptr};
+    d.zhi = p->zhi;
+    d.Bm = p->Bm;
+    d.err = p->err;
+    d.x = p->x;
+    d.res = p->res;
+    d.p[0] = p->p;
+    d.p[1] = reinterpret_cast<double*>(wb + p2_off[j]);
+    d.z = p->z;
+    d.y = p->y;
+    d.bbar = p->bbar;
+    d.tres = p->tres;
+    d.D64 = p->D64;
+    d.y164 = p->y164;
+    d.D32 = p->D32;
+    d.y132 = p->y132;
+    d.cp32 = reinterpret_cast<float*>(wb + cp_off[j]);  // the FP32 and double-float
+    d.cpd = reinterpret_cast<double*>(wb + cp_off[j]);  // partials are never live together
+    d.gds_partial = p->gds_partial;
+    d.red = reinterpret_cast<double*>(wb + red_off[j]);
+    d.s = reinterpret_cast<DevScalars*>(wb + off_scal) + j;
+    d.W = mem == CPHIFI_MEM_DEVICE ? items[k].W_out : p->tmp64;
+    st0[j].claim = batch_first_claim(d);
+    DevScalars& h = sc0[j];
+    memset(&h, 0, sizeof(h));
+    h.tol2 = d.tol2;
+    h.lam = d.lam;
+    h.rho = d.rho;
+    h.max_iter = d.max_iter;
+    h.mode = 1;
+  }
+  BatchCtl ctl0{};
+  // 3. inputs of the launch, after every creation; the launch
+  for (int k = 0; k < nstreams; ++k) {
+    cudaEvent_t e = nullptr;
+    CK(event_get(ctx, &e));
+    CK(cudaEventRecord(e, ctx->batch_streams[k]));
+    CK(cudaStreamWaitEvent(ctx->stream, e, 0));
+    ctx->events_free.push_back(e);
+  }
+  CK(cudaMemcpyAsync(wb + off_reqs, reqs.data(), sizeof(BatchReq) * count,
+                     cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(wb + off_state, st0.data(), sizeof(BatchState) * count,
+                     cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(wb + off_scal, sc0.data(), sizeof(DevScalars) * count,
+                     cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(wb + off_ctl, &ctl0, sizeof(BatchCtl), cudaMemcpyHostToDevice, ctx->stream));
+  const int blocks = batch_blocks(ctx->num_sms);
+  if (blocks < 1) {
+    cleanup();
+    return fail(ctx, CPHIFI_E_DEVICE, "batch: the persistent kernel does not fit an SM");
+  }
+  CK(cudaEventRecord(ctx->batch_ev[0], ctx->stream));
+  CK(launch_batch(reinterpret_cast<const BatchReq*>(wb + off_reqs),
+                  reinterpret_cast<BatchState*>(wb + off_state),
+                  reinterpret_cast<BatchCtl*>(wb + off_ctl), count, kBatchTimeoutNs, blocks,
+                  ctx->stream));
+  CK(cudaEventRecord(ctx->batch_ev[1], ctx->stream));
+  // 4. results: W (host memory: from each problem's staging array), scalars
+  if (mem != CPHIFI_MEM_DEVICE)
+    for (int j = 0; j < count; ++j) {
+      const int k = order[j];
+      CK(download(items[k].W_out, reqs[j].W, (size_t)reqs[j].n * reqs[j].r * sizeof(double), mem,
+                  ctx->stream));
+    }
+  std::vector<DevScalars> sc(count);
+  std::vector<BatchState> stf(count);
+  BatchCtl ctl{};
+  CK(cudaMemcpyAsync(sc.data(), wb + off_scal, sizeof(DevScalars) * count, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(stf.data(), wb + off_state, sizeof(BatchState) * count,
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctl, wb + off_ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  float kms = 0.f;
+  cudaEventElapsedTime(&kms, ctx->batch_ev[0], ctx->batch_ev[1]);
+  // 5. statuses and statistics, in the caller's order
+  int first_bad = CPHIFI_OK;
+  std::string bad_msg;
+  for (int j = 0; j < count; ++j) {
+    const int k = order[j];
+    const DevScalars& h = sc[j];
+    int status = CPHIFI_OK;
+    if (stf[j].fail) status = CPHIFI_E_INVALID_ARG;
+    else if (stf[j].phase != kBatchPhaseDone) status = CPHIFI_E_TIMEOUT;
+    else if (h.status) status = h.status;
+    else if (!h.done) status = CPHIFI_E_NOT_CONVERGED;
+    if (stats) {
+      cphifi_stats& o = stats[k];
+      memset(&o, 0, sizeof(o));
+      o.status = status;
+      o.iterations = h.iter;
+      o.true_residuals = h.true_evals;
+      o.restarts = h.restarts;
+      const double bn = std::sqrt(h.bb);
+      o.rel_residual = h.bb > 0 ? std::sqrt(h.true_evals ? h.true_rr : h.rr) / bn : 0.0;
+      o.rel_residual_recurrence = h.bb > 0 ? std::sqrt(h.rr) / bn : 0.0;
+      o.setup_ms = create_ms;
+      o.solve_ms = kms;
+      o.iter_ms = stf[j].t_done > 0 && ctl.t_start > 0 ? 1e-6 * (double)(stf[j].t_done - ctl.t_start)
+                                                       : kms;
+      o.kernel_launches = 1;
+      o.setup_launches = P[k]->create_launches;
+    }
+    if (status != CPHIFI_OK && first_bad == CPHIFI_OK) {
+      first_bad = status;
+      bad_msg = "batch item " + std::to_string(k) + ": " +
+                (status == CPHIFI_E_INVALID_ARG ? std::string("invalid observations or factors")
+                                                : std::string(cphifi_status_string(status)));
+    }
+  }
+  if (info) {
+    info->create_ms = create_ms;
+    info->kernel_ms = kms;
+    info->tiles = ctl.progress;
+    info->blocks = blocks;
+    info->timed_out = ctl.err;
+  }
+  cleanup();
+  if (info)
+    info->total_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (first_bad != CPHIFI_OK) ctx->last_error = bad_msg;
+  return first_bad;
 }
 
 // ------------------------------------------------- step-by-step calls -----

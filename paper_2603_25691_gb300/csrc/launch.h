@@ -310,4 +310,71 @@ cudaError_t launch_fit(int64_t q, int d_other, int r, int n, const int32_t* kidx
                        const double* const* factors, const int64_t* sizes, RedScratch red,
                        double* out, int num_sms, cudaStream_t st);
 
+// -------------------------------------------------------------- batch.cu ---
+// Many mixed-FP32 PCG solves in one persistent launch.  Each request is a
+// chain of phases (set-up, right-hand side, restart, the six phases of an
+// iteration, the four of the FP64-accurate true residual, the final
+// W = U_K x); a phase is a set of independent tiles.  Blocks claim tiles
+// from the requests' claim words (requests in the order given, the first
+// with an unclaimed tile first); the block that finishes the last tile of a
+// phase reduces the phase's partial sums in tile order, takes the decisions
+// of the PCG (step sizes, convergence, restart) and opens the next phase.
+// No tile ever waits for another, so blocks need not be co-resident; an idle
+// block polls, and every block leaves when all requests are done, or when no
+// tile finished anywhere for `timeout_ns` (error 1 in BatchCtl::err).
+constexpr int kBatchRows = 32;    // rows of a vector tile
+constexpr int kBatchBM = 128;     // rows of an FP32 product tile
+constexpr int kBatchBMdf = 64;    // rows of a double-float product tile
+constexpr int kBatchPhaseDone = 15;  // BatchState::phase of a finished request
+struct BatchReq {
+  int n = 0, r = 0;
+  int s32 = 1, sdf = 1;           // k-range splits of the FP32 / double-float products
+  int kc32 = 0, kcdf = 0;         // their k chunks
+  int max_iter = 0, k_replace = 10;
+  double tol2 = 0.0, lam = 0.0, rho = 0.0, gamma = 0.0;
+  const float* UKhi = nullptr;    // U_K = UKhi + UKlo (n x n column-major)
+  const float* UKlo = nullptr;
+  const double* dK = nullptr;     // eigenvalues of K
+  const double* dV = nullptr;     // eigenvalues of V
+  const float* UV32 = nullptr;    // eigenvectors of V (r x r)
+  PieceList pl{};                 // gather-dot/scatter decomposition (static shares)
+  const float* zhi = nullptr;     // Zhat hi/lo tiles
+  const double* Bm = nullptr;     // sparse MTTKRP B (n x r)
+  const int* err = nullptr;       // input error word of the problem's creation
+  double *x = nullptr, *res = nullptr, *z = nullptr, *y = nullptr, *bbar = nullptr,
+         *tres = nullptr, *D64 = nullptr, *y164 = nullptr;
+  double* p[2] = {nullptr, nullptr};  // the direction, alternating between two buffers
+  float *D32 = nullptr, *y132 = nullptr;
+  float* cp32 = nullptr;          // s32 x n x r split partials
+  double* cpd = nullptr;          // sdf x n x r split partials
+  void* gds_partial = nullptr;    // npieces x 64 values
+  double* red = nullptr;          // 2 per vector tile
+  DevScalars* s = nullptr;
+  double* W = nullptr;            // n x r result (column-major)
+};
+struct alignas(64) BatchState {
+  unsigned long long claim = 0;   // open phase, its tiles, tiles claimed (batch.cu)
+  unsigned done = 0;              // tiles of the open phase finished
+  int phase = 0;
+  int chunk = 0;                  // iterations since the last true residual
+  int adopt = 0;                  // the next restart starts from the true residual
+  int par = 0;                    // p[par] is the current direction
+  int iters = 0;                  // PCG iterations so far (the claim priority)
+  int fail = 0;                   // input error found at set-up
+  long long t_done = 0;           // global timer (ns) when the request finished
+};
+struct BatchCtl {
+  unsigned completed = 0;         // requests finished
+  unsigned progress = 0;          // tiles finished, all requests
+  int abort = 0;
+  int err = 0;                    // 1: no tile finished within timeout_ns
+  long long t_start = 0;          // global timer (ns) when the first block started
+};
+// First claim word of a request (its set-up phase).
+unsigned long long batch_first_claim(const BatchReq& q);
+// Blocks of the persistent launch on this device, and the launch itself.
+int batch_blocks(int num_sms);
+cudaError_t launch_batch(const BatchReq* reqs, BatchState* st, BatchCtl* ctl, int nreq,
+                         long long timeout_ns, int blocks, cudaStream_t stream);
+
 }  // namespace cphifi

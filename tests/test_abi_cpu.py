@@ -59,7 +59,9 @@ def test_struct_layouts_match_the_header(tmp_path):
     import ctypes
 
     import paper_2603_25691_gb300 as pkg
-    fields = {"cphifi_params": pkg.Params, "cphifi_stats": pkg.Stats}
+    fields = {"cphifi_params": pkg.Params, "cphifi_stats": pkg.Stats,
+              "cphifi_tuning": pkg.Tuning, "cphifi_batch_item": pkg.BatchItem,
+              "cphifi_batch_info": pkg.BatchInfo}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cphifi.h"',
              "int main(void) {"]
     for cname, py in fields.items():
