@@ -2862,6 +2862,7 @@ extern "C" int cphifi_solve_batch(cphifi_ctx* ctx, int32_t count, const cphifi_b
   CK(cudaEventRecord(ctx->batch_ev[0], ctx->stream));
   CK(launch_batch(reinterpret_cast<const BatchReq*>(wb + off_reqs),
                   reinterpret_cast<BatchState*>(wb + off_state),
+                  reinterpret_cast<const DevScalars*>(wb + off_scal),
                   reinterpret_cast<BatchCtl*>(wb + off_ctl), count, kBatchTimeoutNs, blocks,
                   ctx->stream));
   CK(cudaEventRecord(ctx->batch_ev[1], ctx->stream));

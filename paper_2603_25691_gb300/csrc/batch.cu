@@ -125,6 +125,17 @@ __device__ __forceinline__ long long global_ns() {
   return t;
 }
 
+// The claiming block's copy (shared memory) of what a tile and the phase's
+// decisions read: the request's descriptor, its scalars and its state.  The
+// scalars and the state change only in the decisions that close a phase, so
+// the copy taken at a claim holds for the whole phase; the block that takes
+// the decisions updates its copy as it writes them back.
+struct BatchLocal {
+  BatchReq q;
+  DevScalars s;
+  int chunk, adopt, par, iters;
+};
+
 // ---------------------------------------------------------- vector tiles --
 // Rows [32 t, 32 t + 32) of the n x r arrays, all r columns; 256 threads
 // walk the 32 r elements (32 consecutive rows of one column per warp: one
@@ -135,8 +146,8 @@ constexpr int kVecPerThread = kBatchRows * kMaxRank / kThreads;  // 8
 // adopting restart, or after x += alpha p, r -= alpha y) and
 // z = ((r U_V) .* D) U_V' (Eq. fx in the eigenbasis, FP32 as in the mixed
 // solve), with (r, z) and ||r||^2.
-__device__ __forceinline__ void precond_tile(int ph, const BatchReq& q, int aux, int tile,
-                                             float* sm, double (&acc)[2]) {
+__device__ __forceinline__ void precond_tile(int ph, const BatchReq& q, const DevScalars& ss,
+                                             int aux, int tile, float* sm, double (&acc)[2]) {
   const int adopt = aux & 1;
   const double* pc = q.p[(aux >> 1) & 1];  // the current direction
   const int n = q.n, r = q.r, ld = r + 1;
@@ -146,7 +157,7 @@ __device__ __forceinline__ void precond_tile(int ph, const BatchReq& q, int aux,
   const int i0 = tile * kBatchRows;
   const int rows = min(kBatchRows, n - i0);
   for (int t = threadIdx.x; t < r * r; t += kThreads) uv[t] = q.UV32[t];
-  const double alpha = ph == BP_UPDATE ? __ldcg(&q.s->alpha) : 0.0;
+  const double alpha = ph == BP_UPDATE ? ss.alpha : 0.0;
   double rv[kVecPerThread];
 #pragma unroll
   for (int u = 0; u < kVecPerThread; ++u) {
@@ -194,15 +205,15 @@ __device__ __forceinline__ void precond_tile(int ph, const BatchReq& q, int aux,
   }
 }
 
-__device__ __noinline__ void vec_tile(int ph, const BatchReq& q, int aux, int tile,
-                                      unsigned char* smem, double* sred) {
+__device__ __noinline__ void vec_tile(int ph, const BatchReq& q, const DevScalars& ss, int aux,
+                                      int tile, unsigned char* smem, double* sred) {
   const int n = q.n, r = q.r;
   const int64_t nr = (int64_t)n * r;
   const int i0 = tile * kBatchRows;
   const int rows = min(kBatchRows, n - i0);
   double acc[2] = {0.0, 0.0};
   if (ph == BP_RESTART || ph == BP_UPDATE) {
-    precond_tile(ph, q, aux, tile, reinterpret_cast<float*>(smem), acc);
+    precond_tile(ph, q, ss, aux, tile, reinterpret_cast<float*>(smem), acc);
   } else {
     const double* pc = q.p[(aux >> 1) & 1];
     for (int e = threadIdx.x; e < kBatchRows * r; e += kThreads) {
@@ -279,7 +290,8 @@ __device__ __noinline__ void vec_tile(int ph, const BatchReq& q, int aux, int ti
 // restart, beta = 0) as it stages B; the tiles of the first row block store
 // it (each k in exactly one of them) into the other p buffer.
 template <bool ATRANS, int TN>
-__device__ __noinline__ void prod32_tile(const BatchReq& q, int aux, int tile, float* sm) {
+__device__ __noinline__ void prod32_tile(const BatchReq& q, const DevScalars& ss, int aux, int tile,
+                                         float* sm) {
   constexpr int BM = kBatchBM, BK = kBK32, TM = 4, LDA = BM + 4;
   constexpr int AL = BM * BK / kThreads, BL = BK * 64 / kThreads;
   const int n = q.n, r = q.r;
@@ -291,7 +303,7 @@ __device__ __noinline__ void prod32_tile(const BatchReq& q, int aux, int tile, f
   const int par = (aux >> 1) & 1;
   double* pnew = q.p[par];
   const double* pold = q.p[par ^ 1];
-  const double beta = ATRANS ? __ldcg(&q.s->beta) : 0.0;
+  const double beta = ATRANS ? ss.beta : 0.0;
   const bool store_p = ATRANS && i0 == 0;
   float* As = sm;                      // [2][BK][LDA]
   float* Bs = sm + 2 * BK * LDA;       // [2][BK][64]
@@ -497,11 +509,12 @@ __device__ __noinline__ void proddf_tile(const BatchReq& q, int tile, const doub
 }
 
 template <bool ATRANS>
-__device__ void prod32_by_rank(const BatchReq& q, int aux, int tile, float* sm) {
-  if (q.r <= 8) prod32_tile<ATRANS, 1>(q, aux, tile, sm);
-  else if (q.r <= 16) prod32_tile<ATRANS, 2>(q, aux, tile, sm);
-  else if (q.r <= 32) prod32_tile<ATRANS, 4>(q, aux, tile, sm);
-  else prod32_tile<ATRANS, 8>(q, aux, tile, sm);
+__device__ void prod32_by_rank(const BatchReq& q, const DevScalars& ss, int aux, int tile,
+                               float* sm) {
+  if (q.r <= 8) prod32_tile<ATRANS, 1>(q, ss, aux, tile, sm);
+  else if (q.r <= 16) prod32_tile<ATRANS, 2>(q, ss, aux, tile, sm);
+  else if (q.r <= 32) prod32_tile<ATRANS, 4>(q, ss, aux, tile, sm);
+  else prod32_tile<ATRANS, 8>(q, ss, aux, tile, sm);
 }
 
 template <bool ATRANS>
@@ -562,8 +575,9 @@ __device__ void gdsdf_by_rank(const BatchReq& q, int tile, unsigned char* smem) 
 // FP64-accurate true residual decides convergence, and a restart from it
 // when the cycle ended or the recurrence drifted below a quarter of it.
 // Returns the next phase in thread 0 (other threads: BP_DONE).
-__device__ __noinline__ int decide(const BatchReq& q, BatchState* S, int ph, int ntiles,
+__device__ __noinline__ int decide(BatchLocal& L, BatchState* S, int ph, int ntiles,
                                    double* sred) {
+  const BatchReq& q = L.q;
   const bool sums = ph == BP_RHS_COMB || ph == BP_RESTART || ph == BP_COMB2 ||
                     ph == BP_UPDATE || ph == BP_TR_COMB;
   double tot[2] = {0.0, 0.0};
@@ -575,13 +589,13 @@ __device__ __noinline__ int decide(const BatchReq& q, BatchState* S, int ph, int
     block_sum<2>(tot, sred);
   }
   if (threadIdx.x != 0) return BP_DONE;
-  volatile DevScalars* s = q.s;
-  volatile BatchState* vs = S;
+  DevScalars* s = &L.s;
+  BatchLocal* vs = &L;
   int next = BP_DONE;
   switch (ph) {
     case BP_SETUP:
       if (*(volatile const int*)q.err != 0) {
-        vs->fail = 1;
+        *(volatile int*)&S->fail = 1;
         next = BP_DONE;
       } else {
         next = BP_RHS_PROD;
@@ -701,54 +715,102 @@ __device__ __noinline__ int decide(const BatchReq& q, BatchState* S, int ph, int
       break;
   }
   if (next == BP_PROD1) vs->par = vs->par ^ 1;  // the new direction goes to the other buffer
-  vs->phase = next;
+  // write the decisions back (no wait: the fence before the next phase is
+  // published orders them)
+  volatile DevScalars* gs = q.s;
+  gs->rz = s->rz;
+  gs->pAp = s->pAp;
+  gs->alpha = s->alpha;
+  gs->beta = s->beta;
+  gs->rr = s->rr;
+  gs->bb = s->bb;
+  gs->true_rr = s->true_rr;
+  gs->iter = s->iter;
+  gs->inner_done = s->inner_done;
+  gs->done = s->done;
+  gs->status = s->status;
+  gs->true_evals = s->true_evals;
+  gs->restarts = s->restarts;
+  volatile BatchState* gst = S;
+  gst->chunk = vs->chunk;
+  gst->adopt = vs->adopt;
+  gst->par = vs->par;
+  gst->iters = vs->iters;
+  gst->phase = next;
   return next;
 }
 
 // Thread 0: publishes the next phase of a request (its claim word with no
 // tile claimed), or its completion.
-__device__ void open_phase(const BatchReq& q, BatchState* S, BatchCtl* ctl, int next) {
-  volatile BatchState* vs = S;
-  atomicExch(&S->done, 0u);
+// With `take`, the caller keeps the first tile of the new phase (the claim
+// word is published with one tile claimed).
+__device__ void open_phase(const BatchLocal& L, BatchState* S, BatchCtl* ctl, int next,
+                           bool take) {
+  *(volatile unsigned*)&S->done = 0u;
   __threadfence();
-  atomicExch(&S->claim, claim_word(phase_tiles(q, next), next, vs->adopt | (vs->par << 1)));
+  const int nt = phase_tiles(L.q, next);
+  atomicExch(&S->claim, claim_word(nt, next, L.adopt | (L.par << 1)) + (take && nt > 0 ? 1 : 0));
   if (next == BP_DONE) {
-    vs->t_done = global_ns();
+    *(volatile long long*)&S->t_done = global_ns();
     __threadfence();
     atomicAdd(&ctl->completed, 1u);
   }
 }
 
 // ---------------------------------------------------------------- kernel --
-__device__ void run_tile(const BatchReq& q, int ph, int aux, int tile, unsigned char* smem,
+__device__ void run_tile(const BatchLocal& L, int ph, int aux, int tile, unsigned char* smem,
                          double* sred) {
+  const BatchReq& q = L.q;
   float* smf = reinterpret_cast<float*>(smem);
   switch (ph) {
     case BP_RHS_PROD: proddf_by_rank<false>(q, tile, q.Bm, false, smf); break;
-    case BP_PROD1: prod32_by_rank<true>(q, aux, tile, smf); break;
+    case BP_PROD1: prod32_by_rank<true>(q, L.s, aux, tile, smf); break;
     case BP_GDS: gds32_by_rank(q, tile, smem); break;
-    case BP_PROD2: prod32_by_rank<false>(q, aux, tile, smf); break;
+    case BP_PROD2: prod32_by_rank<false>(q, L.s, aux, tile, smf); break;
     case BP_TR_PROD1: proddf_by_rank<true>(q, tile, q.x, true, smf); break;
     case BP_TR_GDS: gdsdf_by_rank(q, tile, smem); break;
     case BP_TR_PROD2: proddf_by_rank<false>(q, tile, q.y164, false, smf); break;
     case BP_FINAL_PROD: proddf_by_rank<true>(q, tile, q.x, false, smf); break;
-    default: vec_tile(ph, q, aux, tile, smem, sred); break;
+    default: vec_tile(ph, q, L.s, aux, tile, smem, sred); break;
   }
 }
 
+// The block's copy of request jr: the descriptor (unless already held), the
+// scalars and the state, in one round of independent loads.
+__device__ __forceinline__ void load_local(const BatchReq* __restrict__ reqs, const BatchState* st,
+                                           const DevScalars* scal, int jr, bool have_q,
+                                           BatchLocal& L) {
+  constexpr int kQW = sizeof(BatchReq) / 4, kSW = sizeof(DevScalars) / 8;
+  static_assert(sizeof(BatchReq) % 4 == 0 && sizeof(DevScalars) % 8 == 0, "word copies");
+  static_assert(kQW <= 128 && kSW <= 32, "one load per thread");
+  const int t = threadIdx.x;
+  if (!have_q && t < kQW)
+    reinterpret_cast<unsigned*>(&L.q)[t] = __ldg(reinterpret_cast<const unsigned*>(reqs + jr) + t);
+  if (t >= 128 && t < 128 + kSW)
+    reinterpret_cast<unsigned long long*>(&L.s)[t - 128] =
+        __ldcg(reinterpret_cast<const unsigned long long*>(scal + jr) + (t - 128));
+  if (t == 160) L.chunk = __ldcg(&st[jr].chunk);
+  if (t == 161) L.adopt = __ldcg(&st[jr].adopt);
+  if (t == 162) L.par = __ldcg(&st[jr].par);
+  if (t == 163) L.iters = __ldcg(&st[jr].iters);
+}
+
 __global__ void __launch_bounds__(kThreads, 2)
-batch_kernel(const BatchReq* __restrict__ reqs, BatchState* st, BatchCtl* ctl, int nreq,
-             long long timeout_ns) {
+batch_kernel(const BatchReq* __restrict__ reqs, BatchState* st, const DevScalars* scal,
+             BatchCtl* ctl, int nreq, long long timeout_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double sred[64];
   __shared__ int s_min[kThreads / 32];
-  __shared__ int s_req, s_tile, s_ntiles, s_phase, s_aux, s_exit, s_fin;
+  __shared__ int s_req, s_tile, s_ntiles, s_phase, s_aux, s_exit, s_fin, s_held;
+  __shared__ __align__(16) BatchLocal L;
   unsigned seen = 0xffffffffu;
   long long t_last = global_ns();
   unsigned backoff = 32;
-  if (threadIdx.x == 0)
+  if (threadIdx.x == 0) {
+    s_held = -1;
     atomicCAS(reinterpret_cast<unsigned long long*>(&ctl->t_start), 0ull,
               (unsigned long long)t_last);
+  }
   for (;;) {
     // the request with an unclaimed tile that has run the most iterations
     // (a long chain so far is likely to stay long), the first in the given
@@ -808,38 +870,13 @@ batch_kernel(const BatchReq* __restrict__ reqs, BatchState* st, BatchCtl* ctl, i
       continue;
     }
     backoff = 32;
-    const BatchReq& q = reqs[jr];
-    run_tile(q, s_phase, s_aux, s_tile, smem, sred);
+    load_local(reqs, st, scal, jr, s_held == jr, L);
     __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(&ctl->progress, 1u);
-      const unsigned d = atomicAdd(&st[jr].done, 1u);
-      s_fin = d == (unsigned)s_ntiles - 1u;
-      if (s_fin) __threadfence();
-    }
-    __syncthreads();
-    if (!s_fin) continue;
-    // the block that closed the phase opens the next one and takes its first
-    // tile itself: the request's chain goes on without waiting for a poll
-    const int nx = decide(q, &st[jr], s_phase, s_ntiles, sred);
-    if (threadIdx.x == 0) {
-      open_phase(q, &st[jr], ctl, nx);
-      s_req = -1;
-      if (nx != BP_DONE) {
-        const unsigned long long old = atomicAdd(&st[jr].claim, 1ull);
-        if ((int)claim_count(old) < claim_tiles(old)) {
-          s_req = jr;
-          s_tile = (int)claim_count(old);
-          s_ntiles = claim_tiles(old);
-          s_phase = claim_phase(old);
-          s_aux = claim_aux(old);
-        }
-      }
-    }
-    __syncthreads();
-    while (s_req == jr) {  // ... and runs it, and the next ones it closes
-      run_tile(q, s_phase, s_aux, s_tile, smem, sred);
+    if (threadIdx.x == 0) s_held = jr;
+    // this tile, and while this block closes phases, the first tile of each
+    // next phase (the request's chain goes on without waiting for a poll)
+    for (;;) {
+      run_tile(L, s_phase, s_aux, s_tile, smem, sred);
       __syncthreads();
       if (threadIdx.x == 0) {
         __threadfence();
@@ -850,22 +887,18 @@ batch_kernel(const BatchReq* __restrict__ reqs, BatchState* st, BatchCtl* ctl, i
       }
       __syncthreads();
       if (!s_fin) break;
-      const int nx2 = decide(q, &st[jr], s_phase, s_ntiles, sred);
+      const int nx = decide(L, &st[jr], s_phase, s_ntiles, sred);
       if (threadIdx.x == 0) {
-        open_phase(q, &st[jr], ctl, nx2);
-        s_req = -1;
-        if (nx2 != BP_DONE) {
-          const unsigned long long old = atomicAdd(&st[jr].claim, 1ull);
-          if ((int)claim_count(old) < claim_tiles(old)) {
-            s_req = jr;
-            s_tile = (int)claim_count(old);
-            s_ntiles = claim_tiles(old);
-            s_phase = claim_phase(old);
-            s_aux = claim_aux(old);
-          }
-        }
+        const int nt = phase_tiles(L.q, nx);
+        open_phase(L, &st[jr], ctl, nx, true);
+        s_fin = nx != BP_DONE && nt > 0;
+        s_tile = 0;
+        s_ntiles = nt;
+        s_phase = nx;
+        s_aux = L.adopt | (L.par << 1);
       }
       __syncthreads();
+      if (!s_fin) break;
     }
   }
 }
@@ -897,14 +930,15 @@ int batch_blocks(int num_sms) {
   return occ < 1 ? 0 : occ * num_sms;
 }
 
-cudaError_t launch_batch(const BatchReq* reqs, BatchState* st, BatchCtl* ctl, int nreq,
-                         long long timeout_ns, int blocks, cudaStream_t stream) {
+cudaError_t launch_batch(const BatchReq* reqs, BatchState* st, const DevScalars* scal,
+                         BatchCtl* ctl, int nreq, long long timeout_ns, int blocks,
+                         cudaStream_t stream) {
   if (nreq <= 0) return cudaSuccess;
   if (blocks < 1) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kBatchSmem);
   if (e != cudaSuccess) return e;
-  batch_kernel<<<blocks, kThreads, kBatchSmem, stream>>>(reqs, st, ctl, nreq, timeout_ns);
+  batch_kernel<<<blocks, kThreads, kBatchSmem, stream>>>(reqs, st, scal, ctl, nreq, timeout_ns);
   return cudaGetLastError();
 }
 

@@ -374,7 +374,8 @@ struct BatchCtl {
 unsigned long long batch_first_claim(const BatchReq& q);
 // Blocks of the persistent launch on this device, and the launch itself.
 int batch_blocks(int num_sms);
-cudaError_t launch_batch(const BatchReq* reqs, BatchState* st, BatchCtl* ctl, int nreq,
-                         long long timeout_ns, int blocks, cudaStream_t stream);
+cudaError_t launch_batch(const BatchReq* reqs, BatchState* st, const DevScalars* scal,
+                         BatchCtl* ctl, int nreq, long long timeout_ns, int blocks,
+                         cudaStream_t stream);  // scal: reqs[j].s == scal + j
 
 }  // namespace cphifi
