@@ -825,8 +825,11 @@ extern "C" int cphifi_kernel_apply(const cphifi_kernel* kern, int32_t precision,
   }
   cudaError_t e;
   if (kern->pts) {
-    e = launch_kpoints_apply(precision == CPHIFI_FP64, kern->pts, n, kern->dim, kern->kind,
-                             kern->bandwidth, r, Xd, Yd, st);
+    const int ns = kpoints_pick_split(n, ctx->num_sms);
+    e = ns > 1 ? cudaMalloc(&T, (size_t)ns * nr * sizeof(double)) : cudaSuccess;
+    if (e == cudaSuccess)
+      e = launch_kpoints_apply(precision == CPHIFI_FP64, kern->pts, n, kern->dim, kern->kind,
+                               kern->bandwidth, r, Xd, Yd, ns, T, st);
   } else {  // Y = U_K (D_K o (U_K' X)), FP64
     e = cudaMalloc(&T, nr * sizeof(double));
     if (e == cudaSuccess)
@@ -2191,9 +2194,12 @@ static int problem_rebuild(cphifi_problem* P) {
 // array (column-major).
 static cudaError_t kernel_factor(cphifi_problem* P, const double* Wd) {
   const cphifi_kernel* K = P->kern;
-  if (K->pts)  // K generated from the points, FP64
+  if (K->pts) {  // K generated from the points, FP64; partials in cpart
+    const int cap = std::max(std::max(P->nsplit64, P->nsplit32), std::max(P->nsplitdf, P->nsplittc));
+    const int ns = std::min(kpoints_pick_split(P->n, P->ctx->num_sms), cap);
     return launch_kpoints_apply(true, K->pts, P->n, K->dim, K->kind, K->bandwidth, P->r, Wd,
-                                P->Ak, P->st);
+                                P->Ak, ns, (double*)P->cpart, P->st);
+  }
   Launcher L{P, P->st, nullptr};
   double* Cp = (double*)P->cpart;
   cudaError_t e = L.gemm64(false, nullptr, Wd, Cp, nullptr, 0);

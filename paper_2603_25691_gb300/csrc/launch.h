@@ -272,9 +272,13 @@ cudaError_t launch_gram_apply_f64(const double* C, int n, int r, const double* X
 // the fly in FP64 or FP32.
 cudaError_t launch_kpoints_build(const double* pts, int n, int dim, int kind, double bandwidth,
                                  double* K, cudaStream_t st);
+// nsplit > 1: the column range of K split over nsplit blocks per row block,
+// their partial products in `part` (nsplit x n x r doubles), added in split
+// order into Y.  kpoints_pick_split: the split that fills the GPU.
+int kpoints_pick_split(int n, int num_sms);
 cudaError_t launch_kpoints_apply(bool fp64, const double* pts, int n, int dim, int kind,
                                  double bandwidth, int r, const double* X, double* Y,
-                                 cudaStream_t st);
+                                 int nsplit, double* part, cudaStream_t st);
 
 // ---------------------------------------------------------------- eig.cu ---
 // FP64 symmetric eigendecomposition by parallel two-sided Jacobi (Eq. eigK):

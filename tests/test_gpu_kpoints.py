@@ -45,8 +45,11 @@ def _euclid_kernel(P, kind, s):
     return (1 + u) * np.exp(-u)
 
 
+# n = 1500: the column range of K split over 10 blocks per row block (the
+# last split shorter), partial products added in split order
 @pytest.mark.parametrize("kind,n,dim,s", [("gaussian", 300, 1, 0.1), ("matern32", 257, 1, 0.1),
-                                          ("gaussian", 200, 2, 0.3), ("matern32", 1, 1, 0.5)])
+                                          ("gaussian", 200, 2, 0.3), ("matern32", 1, 1, 0.5),
+                                          ("matern32", 1500, 1, 0.1)])
 def test_kernel_from_points(ctx, pkg, kind, n, dim, s):
     if dim == 1:
         x = synth.grid_points(n)
