@@ -494,7 +494,7 @@ __device__ __forceinline__ df shfl_xor_df(df v, int m) {
 }
 
 template <bool WHI, bool W64>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, 3)
 zhat_mttkrp_kernel(PieceList pl, int64_t q, const int32_t* __restrict__ perm,
                    const int32_t* __restrict__ oidx, int d_other,
                    const float* const* __restrict__ fhl, const int64_t* __restrict__ sizes, int r,
@@ -543,37 +543,10 @@ zhat_mttkrp_kernel(PieceList pl, int64_t q, const int32_t* __restrict__ perm,
         bad |= (act && !ok) ? 1 : 0;
         const int64_t base = tile * 64 * (int64_t)r + (l & 31);    // hi tile; lo = +32 r
         const int64_t base64 = tile * 32 * (int64_t)r + (l & 31);  // FP64 copy
-        for (int j0 = 0; j0 < r; j0 += 4) {
-          df z[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) z[u] = df{0.f, 0.f};
+        // the 4 columns j0..j0+3 of Zhat(l, :): stored, then t_l Zhat(l, j0..j0+3)
+        // summed over the tile's lanes into the piece's row
+        auto emit = [&](int j0, df (&z)[4]) {
           if (ok) {
-            for (int m = 0; m < d_other; ++m) {
-              const int64_t off = (int64_t)__ldg(im + m) * r + j0;
-              float h[4], lo[4];
-              if (vec) {
-                float v[8];
-                ldg_v8(fhl[m] + 2 * off, v);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  h[u] = v[2 * u];
-                  lo[u] = v[2 * u + 1];
-                }
-              } else {
-                const float2* p2 = reinterpret_cast<const float2*>(fhl[m]) + off;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  const float2 v = j0 + u < r ? __ldg(p2 + u) : make_float2(0.f, 0.f);
-                  h[u] = v.x;
-                  lo[u] = v.y;
-                }
-              }
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const df f{h[u], lo[u]};
-                z[u] = m == 0 ? f : df_mul(z[u], f);
-              }
-            }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int j = j0 + u;
@@ -586,7 +559,6 @@ zhat_mttkrp_kernel(PieceList pl, int64_t q, const int32_t* __restrict__ perm,
               }
             }
           }
-          // t_l Zhat(l, j0..j0+3), summed over the tile's lanes
           df wv[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) wv[u] = ok ? df_mul(t, z[u]) : df{0.f, 0.f};
@@ -599,6 +571,75 @@ zhat_mttkrp_kernel(PieceList pl, int64_t q, const int32_t* __restrict__ perm,
           df_acc_add(c, shfl_xor_df(c, 2));
           df_acc_add(c, shfl_xor_df(c, 1));
           if ((lane & 7) == 0 && j0 + col < r) df_acc_add(bacc[wib][j0 + col], c);
+        };
+        if (vec && d_other == 2) {
+          // two other modes (the common case): the next column group's factor
+          // values are fetched while this group is multiplied, stored and
+          // reduced, so a lane has two gathers in flight instead of one
+          const float* f0 = fhl[0] + 2 * (int64_t)(ok ? __ldg(im) : 0) * r;
+          const float* f1 = fhl[1] + 2 * (int64_t)(ok ? __ldg(im + 1) : 0) * r;
+          float c0[8], c1[8], n0[8], n1[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) c0[u] = c1[u] = 0.f;
+          if (ok) {
+            ldg_v8(f0, c0);
+            ldg_v8(f1, c1);
+          }
+          for (int j0 = 0; j0 < r; j0 += 4) {
+            const bool more = ok && j0 + 4 < r;
+            if (more) {
+              ldg_v8(f0 + 2 * (j0 + 4), n0);
+              ldg_v8(f1 + 2 * (j0 + 4), n1);
+            }
+            df z[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              z[u] = ok ? df_mul(df{c0[2 * u], c0[2 * u + 1]}, df{c1[2 * u], c1[2 * u + 1]})
+                        : df{0.f, 0.f};
+            emit(j0, z);
+            if (more) {
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                c0[u] = n0[u];
+                c1[u] = n1[u];
+              }
+            }
+          }
+        } else {
+          for (int j0 = 0; j0 < r; j0 += 4) {
+            df z[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) z[u] = df{0.f, 0.f};
+            if (ok) {
+              for (int m = 0; m < d_other; ++m) {
+                const int64_t off = (int64_t)__ldg(im + m) * r + j0;
+                float h[4], lo[4];
+                if (vec) {
+                  float v[8];
+                  ldg_v8(fhl[m] + 2 * off, v);
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) {
+                    h[u] = v[2 * u];
+                    lo[u] = v[2 * u + 1];
+                  }
+                } else {
+                  const float2* p2 = reinterpret_cast<const float2*>(fhl[m]) + off;
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) {
+                    const float2 v = j0 + u < r ? __ldg(p2 + u) : make_float2(0.f, 0.f);
+                    h[u] = v.x;
+                    lo[u] = v.y;
+                  }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  const df f{h[u], lo[u]};
+                  z[u] = m == 0 ? f : df_mul(z[u], f);
+                }
+              }
+            }
+            emit(j0, z);
+          }
         }
       }
       __syncwarp();
