@@ -140,6 +140,10 @@ __device__ __forceinline__ void gds_warp_range(
   for (int p = pl.warp_first[w]; p < p_end; ++p) {
     const int seg = pl.seg[p];
     const int b = pl.beg[p], e = pl.end[p];
+    if (b == e) {  // an index without observations (its own single piece): a zero row
+      for (int j = lane; j < r; j += 32) Y[(int64_t)j * yld + seg] = IO(0);
+      continue;
+    }
     if constexpr (!WTS) {
       __syncwarp();
       for (int j = lane; j < RP; j += 32) {
