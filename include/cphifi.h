@@ -368,7 +368,8 @@ int cphifi_wait(cphifi_ctx* ctx, cphifi_ticket ticket, int64_t timeout_us,
  * the device and runs a tile of the next phase itself.  A solve's result is
  * the same, bit for bit, whatever else is in the batch.  The kernel's only
  * wait is that of its idle blocks; it ends with CPHIFI_E_TIMEOUT for the
- * unfinished solves if no tile finished anywhere for 4 seconds.
+ * unfinished solves if no tile finished anywhere for the context's batch
+ * wait (4 seconds unless cphifi_ctx_set_batch_wait changed it).
  * items[k].W_out is n_k x r_k, column-major, in memory kind `mem` (the
  * other pointers as in cphifi_solve, memory kind `mem` too); count <= 65535.
  * stats: NULL or
@@ -390,7 +391,12 @@ typedef struct cphifi_batch_item {
   const int32_t* oidx;
   const void* vals;
   uint32_t flags;     /* as in cphifi_problem_create                          */
-  uint32_t reserved;
+  /* 0 in normal use.  1 holds the item back: it is created, but no block
+   * ever claims a tile of it, so the launch can end only by its bounded
+   * wait; the item reports CPHIFI_E_TIMEOUT (its W_out is left undefined),
+   * the others their own results, and info->timed_out is 1.  This is how
+   * the wait's expiry is exercised without any device fault.               */
+  uint32_t hold;
   double* W_out;
 } cphifi_batch_item;
 
@@ -406,6 +412,13 @@ typedef struct cphifi_batch_info {
 int cphifi_solve_batch(cphifi_ctx* ctx, int32_t count, const cphifi_batch_item* items,
                        const cphifi_params* params, int mem, cphifi_stats* stats,
                        cphifi_batch_info* info);
+
+/* cphifi_ctx_set_batch_wait: the bound of the persistent launch's idle wait,
+ * in milliseconds (1 .. 600000; 4000 when never set).  The launch gives up,
+ * and reports CPHIFI_E_TIMEOUT for every unfinished solve, once no tile has
+ * finished anywhere for that long.  Returns CPHIFI_E_INVALID_ARG outside the
+ * range. */
+int cphifi_ctx_set_batch_wait(cphifi_ctx* ctx, int32_t ms);
 
 /* ---- the steps of the path, one call each (for checking each step) ------
  * All n x r arrays are column-major in memory kind `mem`. */

@@ -88,7 +88,7 @@ class BatchItem(ctypes.Structure):
                 ("other_sizes", ctypes.c_void_p), ("factors", ctypes.c_void_p),
                 ("q", ctypes.c_int64), ("kidx", ctypes.c_void_p), ("oidx", ctypes.c_void_p),
                 ("vals", ctypes.c_void_p), ("flags", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("W_out", ctypes.c_void_p)]
+                ("hold", ctypes.c_uint32), ("W_out", ctypes.c_void_p)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -146,6 +146,7 @@ _SIG = {
     "cphifi_problem_grams": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
     "cphifi_problem_order": (ctypes.c_int, [_P, _P, _P]),
     "cphifi_ctx_set_slots": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cphifi_ctx_set_batch_wait": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cphifi_ctx_set_tuning": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                              ctypes.POINTER(Tuning)]),
     "cphifi_problem_set_factors": (ctypes.c_int, [_P, _P, ctypes.c_int]),
@@ -294,6 +295,10 @@ class Context:
     def set_slots(self, max_active: int) -> None:
         """cphifi_ctx_set_slots: how many submitted requests run at once."""
         _check(self.h, lib().cphifi_ctx_set_slots(self.h, int(max_active)), "ctx_set_slots")
+
+    def set_batch_wait(self, ms: int) -> None:
+        """cphifi_ctx_set_batch_wait: the persistent launch's idle-wait bound."""
+        _check(self.h, lib().cphifi_ctx_set_batch_wait(self.h, int(ms)), "ctx_set_batch_wait")
 
     def poll(self, done_cap: int = 0):
         """cphifi_poll: advance all submitted requests.  Returns (active,
@@ -709,8 +714,9 @@ def solve_batch(ctx: Context, problems, lam: float, rho: float, tol: float, max_
     """cphifi_solve_batch: many mixed-FP32 solves in one persistent launch.
 
     problems: a list of dicts with keys kernel, factors, kidx, oidx, vals, r
-    and optionally sorted_obs and out (W's storage); all host arrays, or all
-    device tensors.
+    and optionally sorted_obs, out (W's storage) and hold (True: the item is
+    never started, so the launch ends by its bounded wait); all host arrays,
+    or all device tensors.
     Returns (list of W, list of stats dicts, launch info dict); a solve that
     did not converge has its status in its stats."""
     prm = make_params(lam, rho, tol, max_iter, precision, k_replace, 8, False, 0)
@@ -745,6 +751,7 @@ def solve_batch(ctx: Context, problems, lam: float, rho: float, tol: float, max_
         it.q = kb.numel
         it.kidx, it.oidx, it.vals = kb.ptr, ob.ptr, vb.ptr
         it.flags = flags
+        it.hold = 1 if pb.get("hold") else 0
         it.W_out = wb.ptr
         keep.append((fb, kb, ob, vb, wb, sizes_arr, fptrs))
         outs.append(wb.obj)

@@ -88,6 +88,8 @@ struct cphifi_ctx {
   // the events timing its persistent launch.
   std::vector<cudaStream_t> batch_streams;
   cudaEvent_t batch_ev[2] = {nullptr, nullptr};
+  // bound of the persistent launch's idle wait: no tile finished anywhere
+  long long batch_wait_ns = 4000000000ll;
 };
 
 struct cphifi_kernel {
@@ -2676,7 +2678,14 @@ extern "C" int cphifi_wait(cphifi_ctx* ctx, cphifi_ticket ticket, int64_t timeou
 // the large ones' and often longer) never queue behind the many tiles of a
 // large request, and the large requests take the blocks left over.
 constexpr int kBatchStreams = 16;
-constexpr long long kBatchTimeoutNs = 4000000000ll;  // no tile finished anywhere for 4 s
+
+extern "C" int cphifi_ctx_set_batch_wait(cphifi_ctx* ctx, int32_t ms) {
+  if (!ctx) return CPHIFI_E_INVALID_ARG;
+  if (ms < 1 || ms > 600000)
+    return fail(ctx, CPHIFI_E_INVALID_ARG, "batch wait not in [1, 600000] ms");
+  ctx->batch_wait_ns = 1000000ll * ms;
+  return CPHIFI_OK;
+}
 
 // k-range splits of a batch request's products: chunks of about 64 (FP32)
 // and 32 (double-float) columns of U_K (a few k slabs per tile: the tiles
@@ -2835,7 +2844,8 @@ extern "C" int cphifi_solve_batch(cphifi_ctx* ctx, int32_t count, const cphifi_b
     d.red = reinterpret_cast<double*>(wb + red_off[j]);
     d.s = reinterpret_cast<DevScalars*>(wb + off_scal) + j;
     d.W = mem == CPHIFI_MEM_DEVICE ? items[k].W_out : p->tmp64;
-    st0[j].claim = batch_first_claim(d);
+    // a held item: zero tiles in its first phase, so no block ever claims it
+    st0[j].claim = items[k].hold ? 0ull : batch_first_claim(d);
     DevScalars& h = sc0[j];
     memset(&h, 0, sizeof(h));
     h.tol2 = d.tol2;
@@ -2869,7 +2879,7 @@ extern "C" int cphifi_solve_batch(cphifi_ctx* ctx, int32_t count, const cphifi_b
   CK(launch_batch(reinterpret_cast<const BatchReq*>(wb + off_reqs),
                   reinterpret_cast<BatchState*>(wb + off_state),
                   reinterpret_cast<const DevScalars*>(wb + off_scal),
-                  reinterpret_cast<BatchCtl*>(wb + off_ctl), count, kBatchTimeoutNs, blocks,
+                  reinterpret_cast<BatchCtl*>(wb + off_ctl), count, ctx->batch_wait_ns, blocks,
                   ctx->stream));
   CK(cudaEventRecord(ctx->batch_ev[1], ctx->stream));
   // 4. results: W (host memory: from each problem's staging array), scalars

@@ -174,3 +174,33 @@ def test_unsupported_and_bad_arguments(pkg, env):
     assert e.value.status == pkg.E_INVALID_ARG
     Ws, stats, info = pkg.solve_batch(ctx, [], LAM, RHO, TOL)
     assert Ws == [] and stats == []
+
+
+def test_bounded_wait_expires_for_a_held_item(pkg, env):
+    # A held item is created but never started, so the launch can end only by
+    # its bounded idle wait: the held item reports a timeout, the others their
+    # own results, bit for bit, and the context stays usable.
+    ctx, probs, kerns = env
+    items = _items(probs[:2], kerns[:2])
+    Wref, _, _ = pkg.solve_batch(ctx, items, LAM, RHO, TOL, max_iter=4000)
+    for bad in (0, 600001, -5):
+        with pytest.raises(pkg.CphifiError) as e:
+            ctx.set_batch_wait(bad)
+        assert e.value.status == pkg.E_INVALID_ARG
+    ctx.set_batch_wait(100)
+    try:
+        held = dict(items[1], hold=True)
+        Ws, stats, info = pkg.solve_batch(ctx, [items[0], held], LAM, RHO, TOL, max_iter=4000)
+        assert info["timed_out"] == 1
+        assert stats[0]["status"] == pkg.OK
+        np.testing.assert_array_equal(Ws[0], Wref[0])
+        assert stats[1]["status"] == pkg.E_TIMEOUT and stats[1]["iterations"] == 0
+        # the launch waited about the bound, not the 4 s default
+        assert 100.0 <= info["kernel_ms"] < 2000.0, info
+    finally:
+        ctx.set_batch_wait(4000)
+    Ws, stats, info = pkg.solve_batch(ctx, items, LAM, RHO, TOL, max_iter=4000)
+    assert info["timed_out"] == 0
+    for k in (0, 1):
+        assert stats[k]["status"] == pkg.OK
+        np.testing.assert_array_equal(Ws[k], Wref[k])
