@@ -451,10 +451,13 @@ static cudaError_t gds_dispatch(const PieceList& pl, const float* zhi, const flo
 }
 
 // Lanes per observation keep the per-lane registers (RP/LPO values of the
-// row and of the accumulator) within budget.  The FP32 pass has a 40-column
-// instance (at r = 40, n = 8000, q = 5e7: 1.37 ms per pass against 1.48 ms
-// with 48 columns); the double-float pass ran slower with 40 columns (5.5
-// against 4.5 ms), so the wide modes keep 48.
+// row and of the accumulator) within budget.  At n = 8000, q = 5e7, r = 40:
+// the FP32 pass takes 1.37 ms with its 40-column instance against 1.48 ms
+// with 48 columns; the FP64 pass also has one (the FP64 solve 8.4 -> 8.8
+// solves/s).  The double-float pass keeps 48 columns: with 40 (4 lanes per
+// observation) it ran 2.96 against 3.32 ms alone but 4.6 against 3.9 ms as
+// the true residual inside a solve, and 8 lanes per observation took 4.1 ms
+// alone.
 template <int MODE>
 static cudaError_t gds_by_rank(const PieceList& pl, const float* zhi, const float* zlo,
                                const double* z64, int r, const typename GdsTypes<MODE>::IO* Xh,
@@ -467,8 +470,8 @@ static cudaError_t gds_by_rank(const PieceList& pl, const float* zhi, const floa
   if (r <= 8) return gds_dispatch<MODE, 8, 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
   if (r <= 16) return gds_dispatch<MODE, 16, 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
   if (r <= 32) return gds_dispatch<MODE, 32, wide ? 2 : 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
-  if constexpr (!wide) {
-    if (r <= 40) return gds_dispatch<MODE, 40, 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
+  if constexpr (MODE != GDS_DF) {
+    if (r <= 40) return gds_dispatch<MODE, 40, wide ? 4 : 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
   }
   if (r <= 48) return gds_dispatch<MODE, 48, wide ? 4 : 1>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
   if (r <= 64) return gds_dispatch<MODE, 64, wide ? 4 : 2>(pl, zhi, zlo, z64, r, Xh, xld, partial, Y, yld, skip, st, wt);
