@@ -241,11 +241,74 @@ cudaError_t launch_build_D(const double* dK, const double* dV, int n, int r, dou
 // also forms (p, Ap) and, in its last block, alpha = rz / pAp; CM_RESID and
 // CM_TRUE form ||b - A x||^2 and, in their last block, decide convergence on
 // the FP64 true residual (CM_RESID also makes it the recurrence residual).
+//
+// The partials are dead once summed, and each element is read by one thread
+// only: every warp drops from L2, without write-back, the 128-byte lines of
+// partials that lie wholly inside what it has read (discard.global.L2).  Left
+// dirty, those lines (tens to hundreds of MB) are written back while the next
+// observation pass streams Zhat, and slow it: a 400 MB dirty buffer in L2
+// made a double-float pass at n = 8000, q = 5e7 take 5.5 ms instead of 3.3.
+
+// Drops the lines of the split partials C[k stride + b0, k stride + e0)
+// (k < ns) that lie wholly inside that range; called by the whole warp after
+// it has read those elements.
+template <typename TC>
+__device__ __forceinline__ void discard_partials(const TC* C, int64_t stride, int ns, int64_t b0,
+                                                 int64_t e0) {
+  for (int k = threadIdx.x & 31; k < ns; k += 32) {
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(C + k * stride + b0);
+    const uintptr_t hi = reinterpret_cast<uintptr_t>(C + k * stride + e0);
+    for (uintptr_t a = (lo + 127) & ~uintptr_t(127); a + 128 <= hi; a += 128)
+      asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
+  }
+}
+
 static int vec_blocks(int64_t total) {
   int64_t b = (total + 255) / 256;
   if (b > kRedMaxBlocks) b = kRedMaxBlocks;
   if (b < 1) b = 1;
   return (int)b;
+}
+
+// One output element t of the epilogue (acc: this thread's share of the
+// reduction of its mode).
+template <typename TC, typename TO>
+__device__ __forceinline__ void combine_elem(int mode, const TC* __restrict__ C,
+                                             int64_t split_stride, int nsplit, int n, int64_t t,
+                                             const double* __restrict__ dK,
+                                             const double* __restrict__ V,
+                                             const double* __restrict__ Bv, TO* __restrict__ out,
+                                             double lam, double rho, double (&acc)[1]) {
+  // the split partials in order; loaded eight at a time so that their
+  // latencies overlap (the sum is the same, term by term)
+  double c = 0.0;
+  int k = 0;
+  for (; k + 8 <= nsplit; k += 8) {
+    TC v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = C[(k + u) * split_stride + t];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) c += (double)v[u];
+  }
+  for (; k < nsplit; ++k) c += (double)C[k * split_stride + t];
+  const int i = (int)(t % n);
+  double o;
+  if (mode == CM_STORE) {
+    o = c;
+  } else if (mode == CM_DK || mode == CM_DK_NORM) {
+    o = dK[i] * c;
+    acc[0] += o * o;
+  } else {
+    const double y = dK[i] * c + (lam * dK[i] + rho) * V[t];
+    if (mode == CM_APPLY) {
+      o = y;
+      acc[0] += V[t] * y;
+    } else {
+      o = Bv[t] - y;
+      acc[0] += o * o;
+    }
+  }
+  out[t] = (TO)o;
 }
 
 template <typename TC, typename TO>
@@ -259,38 +322,15 @@ combine_kernel(int mode, const TC* __restrict__ C, int64_t split_stride, int nsp
   double lam = 0.0, rho = 0.0;
   if (s) { lam = s->lam; rho = s->rho; }
   double acc[1] = {0.0};
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    // the split partials in order; loaded eight at a time so that their
-    // latencies overlap (the sum is the same, term by term)
-    double c = 0.0;
-    int k = 0;
-    for (; k + 8 <= nsplit; k += 8) {
-      TC v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = C[(k + u) * split_stride + t];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) c += (double)v[u];
-    }
-    for (; k < nsplit; ++k) c += (double)C[k * split_stride + t];
-    const int i = (int)(t % n);
-    double o;
-    if (mode == CM_STORE) {
-      o = c;
-    } else if (mode == CM_DK || mode == CM_DK_NORM) {
-      o = dK[i] * c;
-      acc[0] += o * o;
-    } else {
-      const double y = dK[i] * c + (lam * dK[i] + rho) * V[t];
-      if (mode == CM_APPLY) {
-        o = y;
-        acc[0] += V[t] * y;
-      } else {
-        o = Bv[t] - y;
-        acc[0] += o * o;
-      }
-    }
-    out[t] = (TO)o;
+  // warp-uniform loop (blockDim is a multiple of 32): lane l takes t = t0 + l
+  const int lane = threadIdx.x & 31;
+  for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane; t0 < total;
+       t0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = t0 + lane;
+    if (t < total)
+      combine_elem<TC, TO>(mode, C, split_stride, nsplit, n, t, dK, V, Bv, out, lam, rho, acc);
+    __syncwarp();
+    discard_partials(C, split_stride, nsplit, t0, t0 + 32 < total ? t0 + 32 : total);
   }
   if (mode == CM_APPLY || mode == CM_RESID || mode == CM_TRUE || mode == CM_DK_NORM) {
     double tot[1];

@@ -218,6 +218,8 @@ enum CombineMode {
 // replaces the recurrence residual (before a restart).
 cudaError_t launch_adopt_residual(const double* tres, double* res, int64_t count, DevScalars* s,
                                   cudaStream_t st);
+// C (nsplit partials of n x r, split_stride apart) is consumed: its contents
+// are undefined afterwards (the lines are dropped from L2 without write-back).
 template <typename TC, typename TO>
 cudaError_t launch_combine(int mode, const TC* C, int64_t split_stride, int nsplit,
                            int n, int r, const double* dK, const double* V,
