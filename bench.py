@@ -57,8 +57,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--precision", default="mixed_fp32")
-    ap.add_argument("--sweep", default="mixed_tf32x3,mixed_tf32,mixed_bf16,fp64_emulated",
+    ap.add_argument("--precision", default="mixed_bf16x3",
+                    help="operator arithmetic of the single-solve workload")
+    ap.add_argument("--batch-precision", default="mixed_fp32",
+                    help="operator arithmetic of the batched and served subproblems (n <= 2000 "
+                         "but for the large served requests; the persistent launch is FP32)")
+    ap.add_argument("--sweep",
+                    default="mixed_fp32,mixed_bf16x3,mixed_tf32x3,mixed_tf32,mixed_bf16,"
+                            "fp64_emulated",
                     help="other operator arithmetics timed on the same data (2 steps each)")
     ap.add_argument("--q", type=int, default=0, help="override q (smaller runs)")
     ap.add_argument("--n", type=int, default=0, help="override n (smaller runs)")
@@ -401,8 +407,8 @@ def run_batch(args, pkg, ctx, dev, seed):
     B = BatchInputs(pkg, ctx, dev, synth.batch_specs(seed, args.batch))
     items = B.items
     for it in items[:16]:  # warm-up: module loads, pools, pinned slots
-        submit_item(pkg, ctx, it, args.precision).wait()
-    untuned = _timed_batch(pkg, ctx, items, args.precision)
+        submit_item(pkg, ctx, it, args.batch_precision).wait()
+    untuned = _timed_batch(pkg, ctx, items, args.batch_precision)
     tuned = None
     if args.autotune:
         from paper_2603_25691_gb300 import autotune
@@ -411,12 +417,12 @@ def run_batch(args, pkg, ctx, dev, seed):
         insts = [(it["kern"], dict(factors=it["f"], kidx=it["k"], oidx=it["o"], vals=it["v"],
                                    r=it["r"], lam=it["p"].lam, rho=it["p"].rho, sorted=True))
                  for it in items]
-        nb = cache.tune_instances(ctx, insts, args.precision, iters=6, reps=1)
+        nb = cache.tune_instances(ctx, insts, args.batch_precision, iters=6, reps=1)
         tune_s = time.perf_counter() - t0
-        cache.apply(ctx, args.precision)
+        cache.apply(ctx, args.batch_precision)
         for it in items[:16]:
-            submit_item(pkg, ctx, it, args.precision).wait()
-        tuned = _timed_batch(pkg, ctx, items, args.precision)
+            submit_item(pkg, ctx, it, args.batch_precision).wait()
+        tuned = _timed_batch(pkg, ctx, items, args.batch_precision)
         tuned.update({"buckets_tuned": nb, "tuning_s": tune_s})
     persistent = None
     for _ in range(2):
@@ -438,7 +444,8 @@ def run_batch(args, pkg, ctx, dev, seed):
     best = tuned if tuned and tuned["elapsed_ms"] < untuned["elapsed_ms"] else untuned
     if persistent["converged"] == len(items) and persistent["elapsed_ms"] < best["elapsed_ms"]:
         best = persistent
-    out = {"workload": f"c4_batch_{len(items)}_uneven", "precision": args.precision, "tol": TOL,
+    out = {"workload": f"c4_batch_{len(items)}_uneven", "precision": args.batch_precision,
+           "tol": TOL,
            "requests": len(items), "sum_q": int(sum(it["q"] for it in items)),
            "n_grid": list(synth.BATCH_N_GRID), "kernels": len(B.kerns), **untuned,
            "autotuned": tuned, "persistent": persistent,
@@ -473,11 +480,11 @@ def run_serve(args, pkg, ctx, dev, seed, big_kern, big_p):
     rng = np.random.default_rng(seed)
     out = []
     for it in pool.items[:8]:
-        submit_item(pkg, ctx, it, args.precision).wait()
+        submit_item(pkg, ctx, it, args.batch_precision).wait()
     if big is not None:  # the large shape once alone: its latency on an idle GPU
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        submit_item(pkg, ctx, big, args.precision).wait()
+        submit_item(pkg, ctx, big, args.batch_precision).wait()
         big_alone_ms = 1e3 * (time.perf_counter() - t0)
     for rate in rates:
         nreq = int(min(args.serve_requests, max(20, args.serve_seconds * rate)))
@@ -496,7 +503,7 @@ def run_serve(args, pkg, ctx, dev, seed, big_kern, big_p):
             while k < nreq and arrivals[k] <= now:
                 it = dict(which[k])
                 it["W"] = outs[k]
-                rq = submit_item(pkg, ctx, it, args.precision)
+                rq = submit_item(pkg, ctx, it, args.batch_precision)
                 tick[rq.ticket] = (k, rq)
                 k += 1
             _, _, done = ctx.poll(done_cap=256)
@@ -739,7 +746,7 @@ def main():
             prob.close()
             return st
         tol2 = {}
-        for prec in dict.fromkeys([args.precision, "mixed_tf32x3"]):
+        for prec in dict.fromkeys([args.precision, "mixed_fp32", "mixed_tf32x3"]):
             step2(prec)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -844,6 +851,7 @@ def main():
             "dtype": {"mixed_tf32": "tf32 products + f32 gather, f64 CG, df64 residuals",
                       "mixed_bf16": "bf16 products + f32 gather, f64 CG, df64 residuals",
                       "mixed_tf32x3": "3-term split-tf32 products + f32 gather, f64 CG, df64 residuals",
+                      "mixed_bf16x3": "bf16x3 products + f32 gather, f64 CG, df64 residuals",
                       "mixed_fp32": "f32 operator, f64 CG, df64 residuals",
                       "fp64_emulated": "df64 (fp32-pair) operator, f64 CG",
                       "fp64": "f64"}[args.precision],
@@ -867,7 +875,8 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None,
                          "traffic": (GDS32_TRAFFIC_PER_OBS_R40 * q
-                                     if r == 40 and args.precision == "mixed_fp32" else None),
+                                     if r == 40 and args.precision in ("mixed_fp32", "mixed_bf16x3")
+                                     else None),
                          "kernel": "gds_kernel<float> (gather-dot/scatter, Eqs. vl/yhat1)",
                          "peak_source": f"{peak_kind} hbm_gbs",
                          "bytes_per_launch": gds_bytes_per_launch,

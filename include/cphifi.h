@@ -74,6 +74,12 @@ enum { CPHIFI_MEM_HOST = 0, CPHIFI_MEM_DEVICE = 1 };
  *  MIXED_TF32X3  : as MIXED_TF32 with each operand split into two TF32 parts
  *                  (hi + lo) and the product accumulated as hi*hi + hi*lo +
  *                  lo*hi on the tensor cores: near-FP32 accuracy.
+ *  MIXED_BF16X3  : as MIXED_FP32 with the two n x n products on the tensor
+ *                  cores from the first 3 of the 8-bit BF16 slices that
+ *                  FP64_EMULATED uses (each operand row / column scaled to
+ *                  its largest entry; the slice products of index sum <= 2,
+ *                  summed exactly): 2^-24 of the scales, FP32-level accuracy.
+ *                  Needs the kernel's slices (else CPHIFI_E_UNSUPPORTED).
  *  FP64_EMULATED : every step FP64-accurate without the FP64 units: the
  *                  gather-dot/scatter in double-float arithmetic (pairs of
  *                  FP32 numbers, 48-bit significand, error-free TwoSum /
@@ -91,7 +97,8 @@ typedef enum cphifi_precision {
   CPHIFI_MIXED_TF32 = 2,
   CPHIFI_MIXED_BF16 = 3,
   CPHIFI_FP64_EMULATED = 4,
-  CPHIFI_MIXED_TF32X3 = 5
+  CPHIFI_MIXED_TF32X3 = 5,
+  CPHIFI_MIXED_BF16X3 = 6
 } cphifi_precision;
 
 /* Problem-creation flags. */

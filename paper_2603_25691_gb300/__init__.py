@@ -40,13 +40,14 @@ MIXED_TF32 = 2
 MIXED_BF16 = 3
 FP64_EMULATED = 4
 MIXED_TF32X3 = 5
+MIXED_BF16X3 = 6
 
 OBS_SORTED = 0x1
 NEED_LOWP = 0x4
 
 PRECISIONS = {"fp64": FP64, "mixed_fp32": MIXED_FP32, "mixed_tf32": MIXED_TF32,
               "mixed_bf16": MIXED_BF16, "fp64_emulated": FP64_EMULATED,
-              "mixed_tf32x3": MIXED_TF32X3}
+              "mixed_tf32x3": MIXED_TF32X3, "mixed_bf16x3": MIXED_BF16X3}
 NEED_FP64 = 0x2
 KEEP_OBS = 0x8
 VALS_F32 = 0x10

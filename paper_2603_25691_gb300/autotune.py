@@ -67,7 +67,8 @@ def tune(ctx, kernel, inst, precision="mixed_fp32", iters=6, reps=2) -> dict:
         times[w] = _time(ctx, kernel, inst, precision, {"gds_warps_per_sm": w}, iters, reps)[0]
     wbest = min(times, key=times.get)
     field = {"mixed_fp32": "split32", "mixed_tf32": "split_tc", "mixed_bf16": "split_tc",
-             "mixed_tf32x3": "split_tc", "fp64_emulated": "split_wide", "fp64": "split64"}
+             "mixed_tf32x3": "split_tc", "mixed_bf16x3": "split_wide",
+             "fp64_emulated": "split_wide", "fp64": "split64"}
     f = field[precision]
     ptimes = {}
     for s_ in [s for s in SPLITS if s <= max(1, (n + 31) // 32)]:

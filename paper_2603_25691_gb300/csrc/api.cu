@@ -1428,7 +1428,7 @@ namespace {
 
 bool is_lowp(int prec) {
   return prec == CPHIFI_MIXED_FP32 || prec == CPHIFI_MIXED_TF32 || prec == CPHIFI_MIXED_BF16 ||
-         prec == CPHIFI_MIXED_TF32X3;
+         prec == CPHIFI_MIXED_TF32X3 || prec == CPHIFI_MIXED_BF16X3;
 }
 bool is_tc(int prec) {
   return prec == CPHIFI_MIXED_TF32 || prec == CPHIFI_MIXED_BF16 || prec == CPHIFI_MIXED_TF32X3;
@@ -1502,6 +1502,22 @@ struct Launcher {
   // products of op(U_K) diag(scale) B over nsplitdf splits, from the BF16
   // slices on the tensor cores (oz_gemm.cu) when the kernel has them, else in
   // double-float arithmetic on the FP32 units.
+  // op(U_K) diag(scale) B from `slices` BF16 slices of each operand (the
+  // kernel's slices must exist), timed as an operator product.
+  cudaError_t gemm_oz(bool a_trans, const double* scale, const double* B, double* out_part,
+                      const DevScalars* skip, int slices) {
+    const cphifi_kernel* K = P->kern;
+    cudaError_t e = launch_oz_b(B, scale, P->n, P->r, P->n, P->ldt, P->ozb, P->ozce, skip, st);
+    ++launches;
+    if (e != cudaSuccess) return e;
+    cudaEvent_t b = tm ? tm->begin() : nullptr;
+    e = launch_oz_gemm(a_trans ? K->mOz1 : K->mOz2, a_trans ? K->oze : K->oze + P->n, P->mOzb,
+                       P->ozce, out_part, P->n, split_stride(), P->n, P->r, P->nsplitdf, skip,
+                       P->tc_err, st, slices);
+    if (tm) tm->end(b, tm->gemm);
+    ++launches;
+    return e;
+  }
   cudaError_t gemm_df(bool a_trans, const double* scale, const double* B, double* out_part,
                       const DevScalars* skip, int cat) {
     if (P->ozb) {  // tensor cores, from BF16 slices of both operands
@@ -1615,6 +1631,7 @@ struct Launcher {
   // D_K xin in the operand type; FP32 SIMT products, or tcgen05 TF32/BF16.
   cudaError_t op_lowp(int prec, const double* xin, double* out, DevScalars* s,
                       const DevScalars* skip) {
+    if (prec == CPHIFI_MIXED_BF16X3) return op_bf16x3(xin, out, s, skip);
     const bool x3 = prec == CPHIFI_MIXED_TF32X3;
     const bool tc = prec == CPHIFI_MIXED_TF32 || prec == CPHIFI_MIXED_BF16 || x3;
     const bool bf = prec == CPHIFI_MIXED_BF16;
@@ -1652,6 +1669,25 @@ struct Launcher {
     if (e != cudaSuccess) return e;
     return combine<float, double>(CM_APPLY, Cp, xin, nullptr, out, s, skip, ns);
   }
+  // Low-precision operator from 3 BF16 slices per operand on the tensor
+  // cores: Xhat = U_K (D_K xin) into FP64 partials, summed and rounded to
+  // FP32 for the FP32 gather-dot/scatter, then U_K' Yhat1 from Yhat1 widened
+  // to FP64 (its slices are cut from the FP64 values).
+  cudaError_t op_bf16x3(const double* xin, double* out, DevScalars* s, const DevScalars* skip) {
+    double* Cp = (double*)P->cpart;
+    const int ns = P->nsplitdf;
+    cudaError_t e;
+    if ((e = gemm_oz(true, P->kern->dK, xin, Cp, skip, 3)) != cudaSuccess) return e;
+    if ((e = combine<double, float>(CM_STORE, Cp, nullptr, nullptr, P->xh32, s, skip, ns)) != cudaSuccess) return e;
+    if ((e = (gram >= 1 && P->c32_ok) ? gram32(P->xh32, P->y132, skip, 1, P->n)
+                                      : gds32(P->xh32, P->y132, skip, 1, P->n)) != cudaSuccess)
+      return e;
+    ++launches;
+    if ((e = launch_convert<float, double>(P->y132, P->y164, (int64_t)P->n * P->r, st)) != cudaSuccess)
+      return e;
+    if ((e = gemm_oz(false, nullptr, P->y164, Cp, skip, 3)) != cudaSuccess) return e;
+    return combine<double, double>(CM_APPLY, Cp, xin, nullptr, out, s, skip, ns);
+  }
   // FP64-accurate operator of the given arithmetic (mode: CM_APPLY / CM_RESID).
   cudaError_t opwide(bool emulated, int mode, const double* xin, double* out, DevScalars* s,
                      const DevScalars* skip, int cat) {
@@ -1681,6 +1717,9 @@ struct Launcher {
   // The operand of the next low-precision product: pop = D_K p (+ BF16 copy).
   cudaError_t pupdate_lowp(int prec) {
     ++launches;
+    if (prec == CPHIFI_MIXED_BF16X3)  // the product slices p itself: no FP32 operand copy
+      return launch_pupdate<float>(P->n, P->r, P->z, P->p, nullptr, nullptr, P->n, nullptr, P->s,
+                                   st);
     return launch_pupdate<float>(P->n, P->r, P->z, P->p, P->pop32, P->kern->dK, P->ldt,
                                  prec == CPHIFI_MIXED_BF16 ? P->pop16 : nullptr, P->s, st);
   }
@@ -1757,7 +1796,7 @@ int check_params(cphifi_ctx* ctx, const cphifi_params* prm) {
   if (!(prm->tol > 0.0) || !std::isfinite(prm->tol))
     return fail(ctx, CPHIFI_E_INVALID_ARG, "tol must be finite and > 0");
   if (prm->max_iter < 0) return fail(ctx, CPHIFI_E_INVALID_ARG, "max_iter must be >= 0");
-  if (prm->precision < CPHIFI_FP64 || prm->precision > CPHIFI_MIXED_TF32X3)
+  if (prm->precision < CPHIFI_FP64 || prm->precision > CPHIFI_MIXED_BF16X3)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
   if (prm->gram < 0 || prm->gram > 2) return fail(ctx, CPHIFI_E_INVALID_ARG, "gram must be 0, 1 or 2");
   return CPHIFI_OK;
@@ -2304,6 +2343,8 @@ static int solve_prepare(cphifi_problem* P, const cphifi_params* prm, double* W_
   const int prec = prm->precision;
   if (is_tc(prec) && !P->kern->tc)
     return fail(ctx, CPHIFI_E_UNSUPPORTED, "tensor-core products unavailable for this kernel");
+  if (prec == CPHIFI_MIXED_BF16X3 && !P->ozb)
+    return fail(ctx, CPHIFI_E_UNSUPPORTED, "BF16 slices of U_K unavailable for this kernel");
   return prec != CPHIFI_FP64 ? ensure_lowp(P) : ensure_fp64(P);
 }
 
@@ -2977,10 +3018,12 @@ extern "C" int cphifi_problem_matvec(cphifi_problem* P, int precision, double la
   cphifi_ctx* ctx = P->ctx;
   const bool gram = (precision & CPHIFI_GRAM_FORM) != 0;
   precision &= ~CPHIFI_GRAM_FORM;
-  if (precision < CPHIFI_FP64 || precision > CPHIFI_MIXED_TF32X3)
+  if (precision < CPHIFI_FP64 || precision > CPHIFI_MIXED_BF16X3)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
   if (is_tc(precision) && !P->kern->tc)
     return fail(ctx, CPHIFI_E_UNSUPPORTED, "tensor-core products unavailable for this kernel");
+  if (precision == CPHIFI_MIXED_BF16X3 && !P->ozb)
+    return fail(ctx, CPHIFI_E_UNSUPPORTED, "BF16 slices of U_K unavailable for this kernel");
   Enter guard(ctx);
   int rc;
   if ((rc = precision == CPHIFI_FP64 ? ensure_fp64(P) : ensure_lowp(P)) != CPHIFI_OK) return rc;
@@ -3021,7 +3064,7 @@ extern "C" int cphifi_problem_gds(cphifi_problem* P, int precision, const double
   cphifi_ctx* ctx = P->ctx;
   const bool gram = (precision & CPHIFI_GRAM_FORM) != 0;
   precision &= ~CPHIFI_GRAM_FORM;
-  if (precision < CPHIFI_FP64 || precision > CPHIFI_MIXED_TF32X3)
+  if (precision < CPHIFI_FP64 || precision > CPHIFI_MIXED_BF16X3)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
   Enter guard(ctx);
   int rc;
@@ -3055,7 +3098,7 @@ extern "C" int cphifi_problem_gds(cphifi_problem* P, int precision, const double
 extern "C" int cphifi_problem_grams(cphifi_problem* P, int precision, double* C, int mem) {
   if (!P || !C) return CPHIFI_E_INVALID_ARG;
   cphifi_ctx* ctx = P->ctx;
-  if (precision < CPHIFI_FP64 || precision > CPHIFI_MIXED_TF32X3)
+  if (precision < CPHIFI_FP64 || precision > CPHIFI_MIXED_BF16X3)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "unknown precision");
   if (mem != CPHIFI_MEM_HOST && mem != CPHIFI_MEM_DEVICE)
     return fail(ctx, CPHIFI_E_INVALID_ARG, "mem must be HOST or DEVICE");

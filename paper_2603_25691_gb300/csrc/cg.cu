@@ -395,6 +395,10 @@ template cudaError_t launch_combine<float, float>(int, const float*, int64_t, in
                                                   const double*, const double*, const double*,
                                                   float*, DevScalars*, RedScratch, const DevScalars*,
                                                   cudaStream_t);
+template cudaError_t launch_combine<double, float>(int, const double*, int64_t, int, int, int,
+                                                   const double*, const double*, const double*,
+                                                   float*, DevScalars*, RedScratch, const DevScalars*,
+                                                   cudaStream_t);
 template cudaError_t launch_combine<float, double>(int, const float*, int64_t, int, int, int,
                                                    const double*, const double*, const double*,
                                                    double*, DevScalars*, RedScratch, const DevScalars*,

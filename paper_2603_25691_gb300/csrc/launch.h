@@ -161,7 +161,10 @@ cudaError_t launch_tc_gemm(bool bf16, const CUtensorMap& ma, const CUtensorMap& 
 // the row exponents e[0..n) (a1) and e[n..2n) (a2).  B slices: BF16
 // [7][64][ldt] (r <= 64 rows used, the rest zero) with column exponents
 // cexp[0..r).  C_split gets
-// FP64 partial products over nsplit ranges of k (oz_pick_split).
+// FP64 partial products over nsplit ranges of k (oz_pick_split).  slices = 3
+// uses the first 3 slices of each operand only (the products of slice index
+// sum <= 2): 2^-24 of the row and column scales, the low-precision operator
+// of CPHIFI_MIXED_BF16X3.
 int64_t oz_mpad(int n);
 size_t oz_uk_bytes(int n, int64_t ldt);
 size_t oz_b_bytes(int r, int64_t ldt);
@@ -178,7 +181,7 @@ int oz_pick_split(int n, int num_sms);
 cudaError_t launch_oz_gemm(const CUtensorMap& ma, const int* rexp, const CUtensorMap& mb,
                            const int* cexp, double* C, int64_t ldc, int64_t split_stride, int n,
                            int ncols, int nsplit, const DevScalars* skip, int* err,
-                           cudaStream_t st);
+                           cudaStream_t st, int slices = 7);
 
 // TF32 hi/lo split (hi = x with 13 low bits cleared, lo = x - hi).
 cudaError_t launch_tf32_split(const float* src, float* hi, float* lo, int64_t total,

@@ -102,14 +102,20 @@ __device__ __forceinline__ void oz_drain(uint32_t tbase, df (&acc)[NH], uint64_t
 
 }  // namespace
 
-template <int NP>
+// S: slices of each operand that take part (7: FP64-accurate; 3: products
+// t + u <= 2 of 8-bit slices, FP32-level accuracy, 2^-24 of the row and
+// column scales, for the low-precision operator).  The layouts are those of
+// the 7 slices; only the first S of each operand are loaded.
+template <int NP, int S>
 __global__ void __launch_bounds__(kOzThreads, 1)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                int mpad, const int* __restrict__ rexp, const int* __restrict__ cexp,
                double* __restrict__ C, int64_t ldc, int64_t split_stride, int n, int ncols,
                int kchunk, const DevScalars* skip, int* err) {
   if (dev_skip(skip)) return;
+  static_assert(S >= 1 && S <= kOzS, "slice count");
   constexpr int NH = NP / 2;  // columns per drain thread
+  constexpr int GX = S < 4 ? S : 4;  // groups read after every chunk (exact sums)
   extern __shared__ uint8_t smem_raw[];
   // ex_lo: the drain has read the group regions 0..3 of a chunk
   __shared__ uint64_t a_full[kOzAStages], a_empty[kOzAStages], b_full[2], b_empty[2], ex_full,
@@ -158,12 +164,12 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int k0 = kbeg + c * 64;
         const int bs = c & 1;
         if (c >= 2 && !mbar_wait(&b_empty[bs], (uint32_t)((c >> 1) & 1) ^ 1u, err, 1)) break;
-        mbar_expect_tx(&b_full[bs], kOzBBytes);
-        for (int u = 0; u < kOzS; ++u)
+        mbar_expect_tx(&b_full[bs], S * kOzBRows * 128);
+        for (int u = 0; u < S; ++u)
           tma_load_2d(bring + bs * kOzBBytes + u * kOzBRows * 128, &tmB, k0, u * kOzBRows,
                       &b_full[bs]);
-        for (int t = 0; t < kOzS; ++t) {
-          const int idx = c * kOzS + t, s = idx % kOzAStages;
+        for (int t = 0; t < S; ++t) {
+          const int idx = c * S + t, s = idx % kOzAStages;
           if (idx >= kOzAStages &&
               !mbar_wait(&a_empty[s], (uint32_t)((idx / kOzAStages) & 1) ^ 1u, err, 1)) {
             ok = false;
@@ -189,8 +195,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         if (!ok || !mbar_wait(&b_full[bs], (uint32_t)((c >> 1) & 1), err, 2)) break;
         const uint64_t dbs = db0 + (uint64_t)((bs * kOzBBytes) >> 4);
 #pragma unroll
-        for (int t = 0; t < kOzS; ++t) {
-          const int idx = c * kOzS + t, s = idx % kOzAStages;
+        for (int t = 0; t < S; ++t) {
+          const int idx = c * S + t, s = idx % kOzAStages;
           if (!mbar_wait(&a_full[s], (uint32_t)((idx / kOzAStages) & 1), err, 2)) {
             ok = false;
             break;
@@ -199,8 +205,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           const uint64_t das = da0 + (uint64_t)((s * kOzABytes) >> 4);
           // B_u0 .. B_{u0+m-1} in one MMA of N = 64 m into regions t+u0 ..
 #pragma unroll
-          for (int u0 = 0; u0 < kOzS - t; u0 += 4) {
-            const int m = min(4, kOzS - t - u0);
+          for (int u0 = 0; u0 < S - t; u0 += 4) {
+            const int m = min(4, S - t - u0);
             const uint32_t id = idesc<__nv_bfloat16>(64 * m);
             const uint32_t d = tmem + 64u * (uint32_t)(t + u0);
             const uint64_t db = dbs + (uint64_t)((u0 * kOzBRows * 128) >> 4);
@@ -234,14 +240,16 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     for (int ch = 0; ch < nch; ++ch) {
       ok = ok && mbar_wait(&ex_full, (uint32_t)(ch & 1), err, 4);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if constexpr (NH <= 24) {
-        oz_drain<NH, 0, 4>(tbase, acc, &ex_lo, true);
+      if constexpr (NH <= 24 || GX <= 2) {
+        oz_drain<NH, 0, GX>(tbase, acc, &ex_lo, true);
       } else {  // fewer registers in flight
         oz_drain<NH, 0, 2>(tbase, acc, &ex_lo, false);
-        oz_drain<NH, 2, 4>(tbase, acc, &ex_lo, true);
+        oz_drain<NH, 2, GX>(tbase, acc, &ex_lo, true);
       }
     }
-    if (nch > 0) oz_drain<NH, 4, 7>(tbase, acc, &ex_lo, false);
+    if constexpr (S > 4) {
+      if (nch > 0) oz_drain<NH, 4, S>(tbase, acc, &ex_lo, false);
+    }
     if (row < n && (ok || nslab == 0)) {
       const int ei = rexp[row];
       double* Cs = C + (int64_t)blockIdx.y * split_stride;
@@ -495,14 +503,14 @@ int oz_pick_split(int n, int num_sms) {
   return s < 1 ? 1 : s;
 }
 
-template <int NP>
+template <int NP, int S>
 static cudaError_t oz_launch(const CUtensorMap& ma, int mpad, const int* rexp, const CUtensorMap& mb,
                              const int* cexp, double* C, int64_t ldc, int64_t split_stride, int n,
                              int ncols, int nsplit, const DevScalars* skip, int* err,
                              cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel<NP>,
+    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel<NP, S>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
     if (e != cudaSuccess) return e;
     attr = true;
@@ -510,22 +518,36 @@ static cudaError_t oz_launch(const CUtensorMap& ma, int mpad, const int* rexp, c
   int kchunk = (n + nsplit - 1) / nsplit;
   kchunk = (kchunk + 255) / 256 * 256;  // whole exact chunks per split
   const dim3 grid((n + 127) / 128, nsplit);
-  oz_gemm_kernel<NP><<<grid, kOzThreads, kOzSmem, st>>>(ma, mb, mpad, rexp, cexp, C, ldc,
-                                                        split_stride, n, ncols, kchunk, skip, err);
+  oz_gemm_kernel<NP, S><<<grid, kOzThreads, kOzSmem, st>>>(ma, mb, mpad, rexp, cexp, C, ldc,
+                                                           split_stride, n, ncols, kchunk, skip,
+                                                           err);
   return cudaGetLastError();
+}
+
+template <int S>
+static cudaError_t oz_by_cols(const CUtensorMap& ma, int mpad, const int* rexp,
+                              const CUtensorMap& mb, const int* cexp, double* C, int64_t ldc,
+                              int64_t split_stride, int n, int ncols, int nsplit,
+                              const DevScalars* skip, int* err, cudaStream_t st) {
+  switch (tc_pad_cols(ncols)) {
+    case 16: return oz_launch<16, S>(ma, mpad, rexp, mb, cexp, C, ldc, split_stride, n, ncols, nsplit, skip, err, st);
+    case 32: return oz_launch<32, S>(ma, mpad, rexp, mb, cexp, C, ldc, split_stride, n, ncols, nsplit, skip, err, st);
+    case 48: return oz_launch<48, S>(ma, mpad, rexp, mb, cexp, C, ldc, split_stride, n, ncols, nsplit, skip, err, st);
+    default: return oz_launch<64, S>(ma, mpad, rexp, mb, cexp, C, ldc, split_stride, n, ncols, nsplit, skip, err, st);
+  }
 }
 
 cudaError_t launch_oz_gemm(const CUtensorMap& ma, const int* rexp, const CUtensorMap& mb,
                            const int* cexp, double* C, int64_t ldc, int64_t split_stride, int n,
                            int ncols, int nsplit, const DevScalars* skip, int* err,
-                           cudaStream_t st) {
+                           cudaStream_t st, int slices) {
   const int mpad = (int)oz_mpad(n);
-  switch (tc_pad_cols(ncols)) {
-    case 16: return oz_launch<16>(ma, mpad, rexp, mb, cexp, C, ldc, split_stride, n, ncols, nsplit, skip, err, st);
-    case 32: return oz_launch<32>(ma, mpad, rexp, mb, cexp, C, ldc, split_stride, n, ncols, nsplit, skip, err, st);
-    case 48: return oz_launch<48>(ma, mpad, rexp, mb, cexp, C, ldc, split_stride, n, ncols, nsplit, skip, err, st);
-    default: return oz_launch<64>(ma, mpad, rexp, mb, cexp, C, ldc, split_stride, n, ncols, nsplit, skip, err, st);
-  }
+  if (slices == 3)
+    return oz_by_cols<3>(ma, mpad, rexp, mb, cexp, C, ldc, split_stride, n, ncols, nsplit, skip,
+                         err, st);
+  if (slices != kOzS) return cudaErrorInvalidValue;
+  return oz_by_cols<kOzS>(ma, mpad, rexp, mb, cexp, C, ldc, split_stride, n, ncols, nsplit, skip,
+                          err, st);
 }
 
 }  // namespace cphifi

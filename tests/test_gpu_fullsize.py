@@ -85,7 +85,8 @@ def test_full_size_gather_dot_scatter_every_row(full):
 
 @pytest.mark.parametrize("precision,tol", [("mixed_fp32", 1e-6), ("mixed_fp32", 1e-8),
                                            ("mixed_tf32", 1e-6), ("mixed_bf16", 1e-6),
-                                           ("mixed_tf32x3", 1e-6)])
+                                           ("mixed_tf32x3", 1e-6), ("mixed_bf16x3", 1e-6),
+                                           ("mixed_bf16x3", 1e-8)])
 def test_full_size_solve(full, precision, tol):
     p, prob, C, b, Ws = full["p"], full["prob"], full["C"], full["b"], full["Ws"]
     W, st = prob.solve(p.lam, p.rho, tol, 500, precision=precision)

@@ -94,7 +94,8 @@ def _gate(p, W, tol, Wd):
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp64_emulated", 1e-10),
                                            ("mixed_fp32", 1e-6), ("mixed_fp32", 1e-10),
-                                           ("mixed_tf32", 1e-8), ("mixed_tf32x3", 1e-8)])
+                                           ("mixed_tf32", 1e-8), ("mixed_tf32x3", 1e-8),
+                                           ("mixed_bf16x3", 1e-8)])
 @pytest.mark.parametrize("gram", [1, 2])
 def test_gram_solves_c1_workload(ctx, pkg, precision, tol, gram):
     p = synth.workload("c1_fp64_n100_q6e3_r5", seed=0)

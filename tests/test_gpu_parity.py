@@ -125,7 +125,8 @@ def test_gather_dot_scatter(case):
 
 # Element-wise bounds of the operator (§4.4.1 product) per arithmetic.
 MATVEC_TOL = {"fp64": 1e-11, "fp64_emulated": 1e-11, "mixed_fp32": 5e-5,
-              "mixed_tf32": 1e-2, "mixed_bf16": 8e-2, "mixed_tf32x3": 5e-5}
+              "mixed_tf32": 1e-2, "mixed_bf16": 8e-2, "mixed_tf32x3": 5e-5,
+              "mixed_bf16x3": 1e-4}
 
 
 def test_matvec(case):
@@ -196,7 +197,8 @@ def _gate(p, W, tol, Wd=None):
                                            ("mixed_fp32", 1e-10), ("mixed_tf32", 1e-6),
                                            ("mixed_tf32", 1e-8), ("mixed_bf16", 1e-6),
                                            ("mixed_bf16", 1e-8), ("mixed_tf32x3", 1e-6),
-                                           ("mixed_tf32x3", 1e-10)])
+                                           ("mixed_tf32x3", 1e-10), ("mixed_bf16x3", 1e-6),
+                                           ("mixed_bf16x3", 1e-10)])
 def test_solve_c1_workload(ctx, pkg, precision, tol):
     """n=100, 20x30, q=6000, r=5, lambda=1e-4, rho=1e-6 (planted, 1% noise)."""
     p = synth.workload("c1_fp64_n100_q6e3_r5", seed=0)
@@ -315,7 +317,7 @@ def test_deterministic(ctx, pkg):
     p = synth.planted_problem(9, 70, (15, 16), 8000, 12, bandwidth=0.1, lam=1e-4, rho=1e-6)
     kern, prob = make(ctx, pkg, p)
     for prec in ("fp64", "mixed_fp32", "fp64_emulated", "mixed_tf32", "mixed_bf16",
-                 "mixed_tf32x3"):
+                 "mixed_tf32x3", "mixed_bf16x3"):
         W1, s1 = prob.solve(p.lam, p.rho, 1e-9, 500, precision=prec)
         W2, s2 = prob.solve(p.lam, p.rho, 1e-9, 500, precision=prec)
         np.testing.assert_array_equal(W1, W2)
@@ -429,7 +431,7 @@ HARD = {
 
 
 @pytest.mark.parametrize("name", list(HARD))
-@pytest.mark.parametrize("prec", ["mixed_fp32", "mixed_tf32x3", "fp64_emulated"])
+@pytest.mark.parametrize("prec", ["mixed_fp32", "mixed_tf32x3", "mixed_bf16x3", "fp64_emulated"])
 def test_slow_instances_reach_tolerance(ctx, pkg, name, prec):
     p = synth.batch_problem(HARD[name])
     dK, UK = np.linalg.eigh(p.K)
