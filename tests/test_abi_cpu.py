@@ -84,3 +84,21 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_constants_match_the_header():
+    # Every enum value and flag the binding mirrors has the header's value, and
+    # every operator arithmetic of the header has a name in the binding.
+    import paper_2603_25691_gb300 as pkg
+    text = open(HEADER).read()
+    values = {m.group(1): int(m.group(2))
+              for m in re.finditer(r"\bCPHIFI_([A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    values.update({m.group(1): int(m.group(2), 16)
+                   for m in re.finditer(r"#define\s+CPHIFI_([A-Z0-9_]+)\s+(0x[0-9a-fA-F]+)u?", text)})
+    mirrored = [k for k in values if hasattr(pkg, k)]
+    assert len(mirrored) >= 15, mirrored
+    for k in mirrored:
+        assert getattr(pkg, k) == values[k], k
+    enum = re.search(r"typedef enum cphifi_precision \{(.*?)\}", text, re.S).group(1)
+    precisions = {int(v) for v in re.findall(r"=\s*(\d+)", enum)}
+    assert precisions == set(pkg.PRECISIONS.values())
