@@ -93,8 +93,8 @@ def test_constants_match_the_header():
     text = open(HEADER).read()
     values = {m.group(1): int(m.group(2))
               for m in re.finditer(r"\bCPHIFI_([A-Z0-9_]+)\s*=\s*(\d+)", text)}
-    values.update({m.group(1): int(m.group(2), 16)
-                   for m in re.finditer(r"#define\s+CPHIFI_([A-Z0-9_]+)\s+(0x[0-9a-fA-F]+)u?", text)})
+    flag = r"#define\s+CPHIFI_([A-Z0-9_]+)\s+(0x[0-9a-fA-F]+)u?"
+    values.update({m.group(1): int(m.group(2), 16) for m in re.finditer(flag, text)})
     mirrored = [k for k in values if hasattr(pkg, k)]
     assert len(mirrored) >= 15, mirrored
     for k in mirrored:
