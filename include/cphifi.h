@@ -78,7 +78,8 @@ enum { CPHIFI_MEM_HOST = 0, CPHIFI_MEM_DEVICE = 1 };
  *                  cores from the first 3 of the 8-bit BF16 slices that
  *                  FP64_EMULATED uses (each operand row / column scaled to
  *                  its largest entry; the slice products of index sum <= 2,
- *                  summed exactly): 2^-24 of the scales, FP32-level accuracy.
+ *                  summed exactly): per term a few 2^-24 of the scales,
+ *                  FP32-level accuracy.
  *                  Needs the kernel's slices (else CPHIFI_E_UNSUPPORTED).
  *  FP64_EMULATED : every step FP64-accurate without the FP64 units: the
  *                  gather-dot/scatter in double-float arithmetic (pairs of

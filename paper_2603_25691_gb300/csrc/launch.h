@@ -163,8 +163,8 @@ cudaError_t launch_tc_gemm(bool bf16, const CUtensorMap& ma, const CUtensorMap& 
 // cexp[0..r).  C_split gets
 // FP64 partial products over nsplit ranges of k (oz_pick_split).  slices = 3
 // uses the first 3 slices of each operand only (the products of slice index
-// sum <= 2): 2^-24 of the row and column scales, the low-precision operator
-// of CPHIFI_MIXED_BF16X3.
+// sum <= 2): per term a few 2^-24 of the row and column scales, the
+// low-precision operator of CPHIFI_MIXED_BF16X3.
 int64_t oz_mpad(int n);
 size_t oz_uk_bytes(int n, int64_t ldt);
 size_t oz_b_bytes(int r, int64_t ldt);

@@ -103,9 +103,11 @@ __device__ __forceinline__ void oz_drain(uint32_t tbase, df (&acc)[NH], uint64_t
 }  // namespace
 
 // S: slices of each operand that take part (7: FP64-accurate; 3: products
-// t + u <= 2 of 8-bit slices, FP32-level accuracy, 2^-24 of the row and
-// column scales, for the low-precision operator).  The layouts are those of
-// the 7 slices; only the first S of each operand are loaded.
+// t + u <= 2 of 8-bit slices, FP32-level accuracy: per term the truncated
+// slices, 2^-24 (|a| + |b|), and the dropped products of index sum 3 and 4,
+// at most 2 2^-24 + 2^-32, of the row and column scales; for the
+// low-precision operator).  The layouts are those of the 7 slices; only the
+// first S of each operand are loaded.
 template <int NP, int S>
 __global__ void __launch_bounds__(kOzThreads, 1)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
