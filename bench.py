@@ -5,6 +5,9 @@ Gaussian-RBF points on [0, 1] (bandwidth 0.1), finite modes 400 x 500,
 q = 5e7 observations (uniform without replacement, sorted by kernel index),
 planted smooth rank-40 model + 1% noise, r = 40, lambda = 1e-4, rho = 1e-6,
 tolerance 1e-6 on the FP64 true relative residual.  Synthetic data (seeded).
+Operator arithmetic (--precision): mixed_bf16x3, the two n x n products on
+the tensor cores from 3 BF16 slices per operand, the gather-dot/scatter in
+FP32, FP64 CG scalars and FP64-accurate true residuals.
 
 A step is one subproblem through every step of the path: problem creation
 from device-resident inputs (validation, Zhat, row pointer, pieces, Gram,
