@@ -29,6 +29,10 @@ from . import CphifiError, Problem, size_bucket
 
 GDS_WARPS_PER_SM = (4, 8, 16, 24, 32)
 SPLITS = (1, 2, 4, 8, 12, 16, 24, 32)
+# the tuning field of the products each operator arithmetic runs
+PRODUCT_SPLIT_FIELD = {"mixed_fp32": "split32", "mixed_tf32": "split_tc", "mixed_bf16": "split_tc",
+                       "mixed_tf32x3": "split_tc", "mixed_bf16x3": "split_wide",
+                       "fp64_emulated": "split_wide", "fp64": "split64"}
 
 
 def _key(precision: str, bucket) -> str:
@@ -66,10 +70,7 @@ def tune(ctx, kernel, inst, precision="mixed_fp32", iters=6, reps=2) -> dict:
     for w in GDS_WARPS_PER_SM:
         times[w] = _time(ctx, kernel, inst, precision, {"gds_warps_per_sm": w}, iters, reps)[0]
     wbest = min(times, key=times.get)
-    field = {"mixed_fp32": "split32", "mixed_tf32": "split_tc", "mixed_bf16": "split_tc",
-             "mixed_tf32x3": "split_tc", "mixed_bf16x3": "split_wide",
-             "fp64_emulated": "split_wide", "fp64": "split64"}
-    f = field[precision]
+    f = PRODUCT_SPLIT_FIELD[precision]
     ptimes = {}
     for s_ in [s for s in SPLITS if s <= max(1, (n + 31) // 32)]:
         ptimes[s_] = _time(ctx, kernel, inst, precision, {"gds_warps_per_sm": wbest, f: s_},
